@@ -1,0 +1,405 @@
+"""Benchmark of the world-cache / screen-probe hot path on the 1080p workload.
+
+One step = one frame of the whole path on one batch of synthetic input:
+probe spawn, cache update (key, insert, fixed-point accumulation), resolve
+(blend + decay), query + probe irradiance, per-pixel interpolation.  The
+headline metric is hit records per second over the update + resolve + query
+window, with the full frame time reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+--impl reference times the CPU oracle (float64 numpy) on a bounded sample
+of each frame, on the host cores.  With N > 1 (torchrun) every rank runs an
+independent replica on its own frames (the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIG = 2
+METRIC = "M hit records/s and ms/frame (update+resolve+query), % HBM roofline"
+UNIT = "M records/s"
+N_FRAMES_DEFAULT = 16
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM traffic per launch of the dominant kernel from an ncu capture (profiles/),
+# keyed to the source it was taken on; null when the source has changed since.
+NCU_TRAFFIC = {}
+
+
+def _source_sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workload
+def make_frames(n_frames: int, rank: int):
+    import workload as wl
+    scene = wl.make_scene(CONFIG)
+    start = (rank * n_frames) % wl.CONFIGS[CONFIG]["frames"]
+    return [wl.make_frame(CONFIG, (start + k) % wl.CONFIGS[CONFIG]["frames"], scene) for k in range(n_frames)]
+
+
+def distinct_cells(frames, log2_slots):
+    """Cells touched per frame (U), counted by the library between update and resolve."""
+    import torch
+    import paper_2310_19855_gb300 as gi
+    from paper_2310_19855_gb300.pipeline import view_of
+    h = gi.gi_cache_create(log2_slots)
+    R = frames[0].n_records
+    slots = torch.empty(R, dtype=torch.int32, device="cuda")
+    out = []
+    try:
+        for i, fr in enumerate(frames):
+            rec = torch.from_numpy(fr.records).cuda()
+            gi.gi_cache_update(h, gi.hits_from_planes(rec, R), view_of(fr.camera, fr.frame), slots)
+            out.append(gi.gi_cache_stats(h)["touched"])
+            gi.gi_cache_resolve(h, i)
+    finally:
+        gi.gi_cache_destroy(h)
+    return out
+
+
+# ------------------------------------------------------------------ reference arm (CPU oracle)
+def oracle_window(frames, steps, warmup, sample_frac):
+    """Times the oracle's update + resolve + query + probe integration on the first
+    `sample_frac` of each frame's probes (whole probes, records in order)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle.cache import OracleCache
+    from oracle import probes as OP
+    from oracle.frame import ray_radiance
+    import workload as wl
+    cfg = wl.CONFIGS[CONFIG]
+    oc = OracleCache(cfg["log2_slots"])
+    fr0 = frames[0]
+    P = fr0.tiles_x * fr0.tiles_y
+    Ps = max(1, int(P * sample_frac))
+    rpp = fr0.rays_per_probe
+    Rs = Ps * rpp
+    times = []
+    for i in range(warmup + steps):
+        fr = frames[i % len(frames)]
+        cam = fr.camera
+        sp = OP.spawn(fr.gbuffer, cam, fr.frame)
+        rec = np.ascontiguousarray(fr.records[:, :Rs])
+        t0 = time.perf_counter()
+        ident = oc.update(rec, i, cam.pos, cam.fov_y, cam.width, cam.height)
+        oc.resolve(i)
+        rad, has = ray_radiance(oc, rec, ident)
+        OP.integrate(sp["valid"][:Ps], sp["nrm"][:Ps], rad.reshape(Ps, rpp, 3), has.reshape(Ps, rpp))
+        t1 = time.perf_counter()
+        if i >= warmup:
+            times.append(t1 - t0)
+    return Rs, times
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    frames = make_frames(min(args.frames, args.steps + args.warmup), 0)
+    Rs, times = oracle_window(frames, args.steps, args.warmup, args.sample)
+    total = sum(times)
+    value = Rs * len(times) / total / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config_dict(frames[0], "oracle sample"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {args.sample:.3f} of the probes of each 1080p frame ({Rs} records): "
+                                   "update + resolve + query + probe irradiance, numpy float64, one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config_dict(fr, note):
+    import workload as wl
+    cfg = wl.CONFIGS[CONFIG]
+    return {"workload": f"{cfg['name']}: {cfg['width']}x{cfg['height']} G-buffer, {fr.tiles_x * fr.tiles_y} probes x "
+                        f"{fr.rays_per_probe} rays = {fr.n_records} hit records/frame, {cfg['n_boxes']} boxes, "
+                        f"2^{cfg['log2_slots']} slots, 4 LODs, alpha 0.1, evict 8",
+            "records_per_step": fr.n_records, "pixels_per_step": cfg["width"] * cfg["height"],
+            "l2": "flushed between timed steps (256 MB write outside the events)", "note": note}
+
+
+# ------------------------------------------------------------------ native arm
+def run_native(args, rank, world, local_rank):
+    import torch
+    import paper_2310_19855_gb300 as gi
+    from paper_2310_19855_gb300.build import build
+    from paper_2310_19855_gb300.pipeline import Pipeline, view_of
+    import workload as wl
+    import workload.scene as wscene
+
+    build()
+    wscene.build_tracer()
+    torch.cuda.set_device(local_rank)
+    cfg = wl.CONFIGS[CONFIG]
+    n_frames = min(args.frames, args.steps + args.warmup)
+    frames = make_frames(n_frames, rank)
+    fr0 = frames[0]
+    W, H, R = fr0.camera.width, fr0.camera.height, fr0.n_records
+    U = distinct_cells(frames, cfg["log2_slots"])
+
+    pl = Pipeline(W, H, fr0.rays_per_probe, cfg["log2_slots"])
+    dev_rec = [torch.from_numpy(np.ascontiguousarray(f.records[:10])).cuda() for f in frames]
+    dev_gb = [torch.from_numpy(f.gbuffer).cuda() for f in frames]
+    views = [view_of(f.camera, f.frame) for f in frames]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    names = ["spawn", "update", "resolve", "integrate", "interpolate"]
+
+    def step(i, ev=None):
+        k = i % n_frames
+        gb, rec, v = dev_gb[k], dev_rec[k], views[k]
+        if ev is not None:
+            ev[0].record(stream)
+        pl.spawn(gb, v, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        gi.gi_cache_update(pl.cache, gi.hits_from_planes(rec, R), v, pl.slot_ids, stream)
+        if ev is not None:
+            ev[2].record(stream)
+        pl.resolve(i, stream)
+        if ev is not None:
+            ev[3].record(stream)
+        pl.integrate((0.0, 0.0, 0.0), stream)
+        if ev is not None:
+            ev[4].record(stream)
+        pl.interpolate(gb, v, stream)
+        if ev is not None:
+            ev[5].record(stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    rebuilds0 = gi.gi_cache_stats(pl.cache)["rebuilds"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = time.perf_counter()
+    for j in range(args.steps):
+        flush.zero_()
+        step(args.warmup + j, evs[j])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_start
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    st = gi.gi_cache_stats(pl.cache)
+    rebuilds = st["rebuilds"] - rebuilds0
+    per = np.array([[evs[j][k].elapsed_time(evs[j][k + 1]) for k in range(5)] for j in range(args.steps)])
+    frame_ms = per.sum(axis=1)
+    window_ms = per[:, 1:4].sum(axis=1)
+
+    # ---- end to end through host buffers: pinned host input -> device, frame, irradiance -> host
+    h_rec = [torch.from_numpy(np.ascontiguousarray(f.records[:10])).pin_memory() for f in frames[:2]]
+    h_gb = [torch.from_numpy(f.gbuffer).pin_memory() for f in frames[:2]]
+    h_out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+    d_rec = torch.empty_like(dev_rec[0])
+    d_gb = torch.empty_like(dev_gb[0])
+    e_steps = max(3, min(args.steps, 10))
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e_steps)]
+    base = args.warmup + args.steps
+    for j in range(e_steps):
+        k = j % 2
+        flush.zero_()
+        e_ev[j][0].record(stream)
+        d_rec.copy_(h_rec[k], non_blocking=True)
+        d_gb.copy_(h_gb[k], non_blocking=True)
+        v = views[k]
+        pl.spawn(d_gb, v, stream)
+        gi.gi_cache_update(pl.cache, gi.hits_from_planes(d_rec, R), v, pl.slot_ids, stream)
+        pl.resolve(base + j, stream)
+        pl.integrate((0.0, 0.0, 0.0), stream)
+        pl.interpolate(d_gb, v, stream)
+        h_out.copy_(pl.irr, non_blocking=True)
+        e_ev[j][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = np.array([a.elapsed_time(b) for a, b in e_ev])
+    h2d = h_rec[0].numel() * 4 + h_gb[0].numel() * 4
+    d2h = h_out.numel() * 4
+
+    # ---- max over ranks
+    tot = np.array([window_ms.sum(), frame_ms.sum(), t_wall, e2e_ms.sum()], np.float64)
+    if world > 1:
+        t = torch.tensor(tot, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot = t.cpu().numpy()
+    if rank != 0:
+        return
+    win_s = tot[0] / 1e3
+    value = world * R * args.steps / win_s / 1e6
+    frame_rate = world * R * args.steps / (tot[1] / 1e3) / 1e6
+    e2e_value = world * R * e_steps / (tot[3] / 1e3) / 1e6
+
+    # ---- roofline of the dominant kernel (algorithmic bytes / event-timed duration)
+    peak, peak_src = _peaks()
+    pass_ms = per.mean(axis=0)
+    dominant = names[int(np.argmax(pass_ms))]
+    U_mean = float(np.mean(U))
+    P = fr0.tiles_x * fr0.tiles_y
+    X = W * H
+    alg = {
+        # records 40 B in + slot id 4 B out; per touched cell a 32 B tag sector read, the 32 B
+        # accumulator read and written, and a 4 B touch-list entry
+        "update": R * 44 + U_mean * (32 + 64 + 4),
+        # per touched cell: touch entry 4, accumulator 32 read + 32 written, resolved 16 read + 16 written
+        "resolve": U_mean * (4 + 64 + 32),
+        # per ray a 4 B slot id and a 16 B resolved gather; per probe the normal 16 B and 112 B of SH out
+        "integrate": R * 20 + P * (16 + 112),
+        # per pixel 16 B G-buffer in, 16 B out; per probe 16 + 16 + 112 B read
+        "interpolate": X * 32 + P * 144,
+        # per probe 16 B G-buffer read, mask 4 B + pos 16 B + nrm 16 B written
+        "spawn": P * 52,
+    }
+    d_ms = pass_ms[names.index(dominant)]
+    achieved = alg[dominant] / (d_ms * 1e-3) / 1e9
+    src = os.path.join(ROOT, "paper_2310_19855_gb300", "csrc",
+                       "gi_cache.cu" if dominant in ("update", "resolve") else "gi_probes.cu")
+    tr = NCU_TRAFFIC.get(dominant)
+    traffic = tr["bytes_per_launch"] if tr and tr["source_sha"] == _source_sha(src) else None
+
+    # ---- oracle on the host cores, bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        Rs, ct = oracle_window(frames, steps=3, warmup=0, sample_frac=args.sample)
+        cpu = {"value": Rs * len(ct) / sum(ct) / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"3 frames x first {args.sample:.3f} of the probes ({Rs} records each): update + resolve "
+                         "+ query + probe irradiance, numpy float64, one thread"}
+
+    launches_per_step = 6  # k_spawn, k_mip_tail, k_update, k_resolve, k_integrate, k_interpolate
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(tot[1] / args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config_dict(fr0, "value over update+resolve+query(+probe irradiance); ms_per_step is the "
+                                    "whole frame (spawn ... interpolation)"),
+        "window_ms_per_step": float(tot[0] / args.steps),
+        "full_frame_records_per_s": frame_rate,
+        "pass_ms": {n: float(m) for n, m in zip(names, pass_ms)},
+        "touched_cells_per_frame": U_mean,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": dominant,
+                     "algorithmic_bytes_per_launch": alg[dominant], "peak_source": peak_src},
+        "roofline_window": {"achieved": sum(alg[n] for n in ("update", "resolve", "integrate")) /
+                                        (pass_ms[1:4].sum() * 1e-3) / 1e9, "peak": peak, "unit": "GB/s"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": float(tot[3] / e_steps)},
+        "gpu_launches": int(args.steps * launches_per_step + rebuilds),
+        "rebuilds_in_timed_region": int(rebuilds),
+        "clocks": clk,
+        "wall_s_timed": float(tot[2]),
+    }
+    print(json.dumps(line), flush=True)
+    pl.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--frames", type=int, default=N_FRAMES_DEFAULT, help="distinct pre-generated frames to cycle")
+    ap.add_argument("--sample", type=float, default=0.125, help="fraction of probes in the oracle's sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_native(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,321 @@
+/*
+ * gi.h -- C ABI of the world-space radiance cache and the screen-probe stage
+ * of GI-1.0 (two-level radiance caching), GPU implementation for sm_103a.
+ *
+ * Scope: the world cache of Section 2.2 (a spatial hash of cells keyed by a
+ * descriptor of the secondary vertex: quantised position, quantised
+ * direction, distance LOD and the light-leak bit of Section 2.2.2; bucket
+ * hash + fingerprint with linear probing; per-frame radiance accumulation;
+ * resolve with an exponential moving average (Section 2.2.3) and decay of
+ * untouched cells (Section 2.2.1); lookups for the screen-probe rays), and the
+ * screen probes it feeds (spawn per 8x8 tile with a Halton jitter, Section
+ * 2.1.1; probe mask + MIP chain and Algorithm 3, Section 2.1.5; probe
+ * irradiance through 3-band spherical harmonics, Section 2.4.2; per-pixel
+ * interpolation, Section 2.4.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named *device* point to CUDA device memory owned by the caller;
+ *    the library reads/writes them asynchronously on the given stream.  The
+ *    caller keeps them alive until the stream has passed the call.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; 0 = the legacy
+ *    default stream) and does not synchronise, except gi_cache_stats and
+ *    gi_cache_export, which synchronise `stream`.
+ *  - Arguments are validated on the host before anything is launched; a
+ *    failed validation returns GI_ERR_INVALID_ARG and launches nothing.
+ *    gi_last_error() then holds a message (per host thread).
+ *  - Nothing on the device traps.  Device-side anomalies (dropped hits,
+ *    bounded waits that ran out) are counted in device counters and surface
+ *    at the next gi_cache_stats.
+ *  - The library fails loudly: there is no CPU fallback.  Without a usable
+ *    CUDA device every launching call returns GI_ERR_CUDA.
+ */
+#ifndef GI_H
+#define GI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gi_status {
+    GI_OK = 0,
+    GI_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or configuration */
+    GI_ERR_OOM = 2,           /* device or pinned-host allocation failed */
+    GI_ERR_CUDA = 3,          /* a CUDA runtime call failed (no device, launch error, ...) */
+    GI_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out */
+    GI_ERR_DEVICE_FAULT = 5,  /* the device error word is set */
+    GI_ERR_CAPACITY = 6,      /* an export buffer is too small */
+    GI_WARN_DROPPED = 100     /* stats: some hits found no slot within max_probe (table too full) */
+} gi_status;
+
+/* Slot-id codes written by gi_cache_update for records that do not name a cell. */
+#define GI_SLOT_MISS 0xFFFFFFFEu  /* the ray left the scene: its radiance is the environment */
+#define GI_SLOT_NONE 0xFFFFFFFFu  /* no sample: invalid record, or a hit dropped for lack of a slot */
+
+/* Probe-mask sentinel of a tile without probe (Section 2.1.5). */
+#define GI_PROBE_NONE 0xFFFFFFFFu
+
+/* Per-pixel flags written in the alpha channel by gi_probes_interpolate (Section 2.4.1). */
+#define GI_INTERP_OK 0       /* edge-aware weighted average */
+#define GI_INTERP_RELAXED 1  /* every weight was zero: equal weights over the neighbours found */
+#define GI_INTERP_NONE 2     /* no neighbour probe found: irradiance 0 */
+#define GI_INTERP_SKY 3      /* the pixel sees no surface: irradiance 0 */
+
+enum { GI_KEY_DIR_NORMAL = 0, GI_KEY_DIR_RAY = 1 };
+enum { GI_RESOLVED_F32 = 0, GI_RESOLVED_F16 = 1 };
+
+typedef struct gi_cache_s *gi_cache_t;
+typedef void *gi_stream_t; /* cudaStream_t */
+
+/*
+ * Cache configuration.
+ *   log2_slots      table size N = 2^log2_slots slots, 10..28
+ *   cell_size       s0: side of a LOD-0 cell in world units (> 0)
+ *   num_lods        distance LODs 1..4; LOD l has side s0 * 2^l and is used
+ *                   where the screen-space cell size of Algorithm 6 is in
+ *                   [s0 2^l, s0 2^(l+1)) (the last LOD takes everything above)
+ *   alpha           blend weight of a new frame mean, (0, 1]
+ *   evict_frames    E >= 1: a cell untouched at E consecutive resolves is evicted
+ *   max_probe       longest linear-probing run, 1..255
+ *   key_dir         GI_KEY_DIR_NORMAL: direction term from the surface normal;
+ *                   GI_KEY_DIR_RAY: from the outgoing direction (minus the ray)
+ *   resolved_format GI_RESOLVED_F32 (16 B per slot) or GI_RESOLVED_F16 (8 B)
+ *   rebuild_load    fraction of slots occupied (live + stale cells) above which the
+ *                   next update first compacts the table, in [0.25, 0.95]
+ */
+typedef struct gi_cache_config {
+    uint32_t log2_slots;
+    float cell_size;
+    uint32_t num_lods;
+    float alpha;
+    uint32_t evict_frames;
+    uint32_t max_probe;
+    uint32_t key_dir;
+    uint32_t resolved_format;
+    float rebuild_load;
+} gi_cache_config;
+
+/*
+ * View of a frame: pinhole camera at cam_pos looking along cam_fwd with unit
+ * cam_right / cam_up; the ray through pixel (x, y) (row 0 on top) has
+ * direction normalize(fwd + sx right + sy up), sx = (2(x+0.5)/W - 1) tan(fov_y/2) W/H,
+ * sy = (1 - 2(y+0.5)/H) tan(fov_y/2).  fov_y and the size also give the
+ * screen-space cell size of Algorithm 6.  frame is the frame index (monotone).
+ */
+typedef struct gi_view {
+    uint32_t frame;
+    uint32_t width, height;
+    float cam_pos[3];
+    float cam_fwd[3];
+    float cam_right[3];
+    float cam_up[3];
+    double fov_y; /* radians */
+} gi_view;
+
+/*
+ * Hit records, structure of arrays, n records; each pointer is a device array
+ * of n float32 (any 4-byte alignment).  Record i is a hit when ray_len[i] is
+ * finite and >= 0 and pos is finite; ray_len = +inf marks a ray that left the
+ * scene; anything else (negative, NaN) marks no sample.  ray_dir is the unit
+ * probe-ray direction and is read only with GI_KEY_DIR_RAY (else may be NULL).
+ */
+typedef struct gi_hits {
+    const float *pos[3];
+    const float *nrm[3];
+    const float *rad[3];
+    const float *ray_len;
+    const float *ray_dir[3];
+    uint64_t n;
+} gi_hits;
+
+/* G-buffer: device float4 per pixel (nx, ny, nz, distance along the pixel ray;
+ * +inf = sky), row-major height x width, 16-byte aligned. */
+typedef struct gi_gbuffer {
+    const float *nd;
+    uint32_t width, height;
+} gi_gbuffer;
+
+#define GI_MAX_MIPS 16
+#define GI_SH_STRIDE 28 /* floats per probe: 9 coefficients x RGB (k*3 + c), 1 pad */
+
+/* Layout of the probe buffers of a width x height view (filled by gi_probes_layout). */
+typedef struct gi_probe_layout {
+    uint32_t tiles_x, tiles_y, num_probes, mip_count;
+    uint32_t mip_w[GI_MAX_MIPS], mip_h[GI_MAX_MIPS], mip_offset[GI_MAX_MIPS];
+    uint32_t mask_words; /* total u32 words of all mask levels */
+} gi_probe_layout;
+
+/*
+ * Probe buffers (device, caller-owned, sized by gi_probe_layout):
+ *   mask  u32[mask_words]: level k at mip_offset[k], mip_w[k] x mip_h[k] row-major;
+ *         a probe is packed as y << 16 | x (its pixel), GI_PROBE_NONE if absent
+ *   pos   float4[num_probes]: world position, distance along the pixel ray
+ *   nrm   float4[num_probes]: unit normal, w = 1 for a probe, 0 for none
+ *   sh    float[num_probes * GI_SH_STRIDE]: SH coefficients of the probe radiance
+ * Probe p is the probe of tile (p mod tiles_x, p / tiles_x).
+ */
+typedef struct gi_probes {
+    gi_probe_layout layout;
+    uint32_t *mask;
+    float *pos;
+    float *nrm;
+    float *sh;
+} gi_probes;
+
+/* Cumulative counters and table state (gi_cache_stats). */
+typedef struct gi_cache_stats_t {
+    uint64_t slots;           /* N */
+    uint64_t occupied;        /* slots holding a cell, live or stale */
+    uint64_t live;            /* cells not evicted as of the last resolve, plus cells touched since */
+    uint64_t touched;         /* cells touched since the last resolve */
+    uint64_t dropped;         /* hits that found no slot within max_probe (cumulative) */
+    uint64_t clamped;         /* hit records whose radiance was clamped to [0, 32768] or was NaN */
+    uint64_t rebuilds;        /* table compactions so far */
+    uint64_t updates, resolves;
+    uint32_t max_probe_seen;  /* longest probing run so far */
+    uint32_t error_word;      /* device error word (0 = none) */
+    int64_t last_resolved;    /* frame of the last resolve, -1 before the first */
+} gi_cache_stats_t;
+
+/* One live cell, as exported by gi_cache_export (host memory). */
+typedef struct gi_cell {
+    uint64_t identity;  /* home slot << 24 | 24-bit fingerprint */
+    uint64_t sum[3];    /* fixed-point sums accumulated since the last resolve (2^-24 units) */
+    uint32_t count;     /* samples accumulated since the last resolve */
+    uint32_t stamp;     /* 1 + last frame this cell was resolved with samples; 0 = never */
+    float value[3];     /* resolved radiance */
+    uint32_t slot;      /* current slot index (changes when the table is compacted) */
+} gi_cell;
+
+/* ---------------------------------------------------------------- errors */
+/* Message of the last failed call on this host thread ("" if none). */
+const char *gi_last_error(void);
+/* Name of a status code. */
+const char *gi_status_string(gi_status s);
+/* Library version, major * 10000 + minor * 100 + patch. */
+uint32_t gi_version(void);
+
+/* ---------------------------------------------------------------- world cache */
+/*
+ * Create a cache (Section 2.2.1): allocates the slot table (fingerprints,
+ * 32-byte fixed-point accumulators, resolved radiance), a spare table for
+ * compaction, the touch list and counters, on the current CUDA device.  The
+ * library owns this memory until gi_cache_destroy.  Synchronous.
+ * Errors: GI_ERR_INVALID_ARG (cfg out of range), GI_ERR_OOM, GI_ERR_CUDA.
+ */
+gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out);
+
+/* Free every resource of the cache (synchronises the device first). NULL is a no-op. */
+gi_status gi_cache_destroy(gi_cache_t cache);
+
+/*
+ * Accumulate one batch of hit records into the cache (Sections 2.2.1-2.2.3):
+ * per hit, the cell descriptor (quantised position, dominant-axis direction,
+ * distance LOD from Algorithm 6's cell size, light-leak bit), bucket hash +
+ * fingerprint, linear probing with atomicCAS on the fingerprint to find or
+ * insert the cell, then 64-bit fixed-point sums round(r * 2^24) per channel
+ * and a sample count.  Same-cell hits of a warp are merged before the global
+ * atomics.  slot_ids (device, n u32, caller-owned) receives each record's
+ * slot, GI_SLOT_MISS or GI_SLOT_NONE: the cached index of Section 2.2.1, valid
+ * until the next gi_cache_update.  Several updates may precede one resolve.
+ * If the previous resolve left the table fuller than rebuild_load, this call
+ * first compacts it (live cells only; slot indices change).
+ * Errors: GI_ERR_INVALID_ARG (NULL record plane, NULL slot_ids with n > 0,
+ * view size 0, non-positive fov), GI_ERR_CUDA.
+ */
+gi_status gi_cache_update(gi_cache_t cache, const gi_hits *hits, const gi_view *view, uint32_t *slot_ids,
+                          gi_stream_t stream);
+
+/*
+ * Resolve the frame (Section 2.2.3 and the decay rule of Section 2.2.1): for
+ * every cell touched since the last resolve, mean m = sum / (count 2^24);
+ * a cell without history (new, or evicted earlier) takes v = m, others
+ * v <- v + alpha (m - v); accumulators are cleared and the cell's stamp set to
+ * this frame.  Cells whose last touch is E or more frames before `frame` are
+ * evicted (they stay in the table until the next compaction but no longer
+ * answer queries, and restart without history if hit again).
+ * Errors: GI_ERR_INVALID_ARG (frame earlier than the previous resolve), GI_ERR_CUDA.
+ */
+gi_status gi_cache_resolve(gi_cache_t cache, uint32_t frame, gi_stream_t stream);
+
+/*
+ * Query the cache (Section 2.1.3: the radiance returned to a probe ray).
+ * By slot: slot_ids (device, n) as written by gi_cache_update; out (device float4[n])
+ * = (r, g, b, 1) for a slot, (env, 1) for GI_SLOT_MISS, (0, 0, 0, 0) for GI_SLOT_NONE.
+ * By point: hits (device, n records) + view; descriptor lookup without insertion;
+ * out = (r, g, b, 1) for a live cell, (0, 0, 0, 0) otherwise (a miss of the cache).
+ */
+typedef struct gi_query {
+    const uint32_t *slot_ids; /* by slot when non-NULL */
+    const gi_hits *points;    /* by point when slot_ids is NULL */
+    const gi_view *view;      /* by point: camera and view size for the descriptor */
+    uint64_t n;
+    float env[3];
+} gi_query;
+gi_status gi_cache_query(gi_cache_t cache, const gi_query *q, float *out, gi_stream_t stream);
+
+/*
+ * Counters and table state.  Synchronises `stream`, then scans the table.
+ * Returns GI_WARN_DROPPED when hits were dropped, GI_ERR_DEVICE_FAULT when the
+ * device error word is set (stats are filled in both cases).
+ */
+gi_status gi_cache_stats(gi_cache_t cache, gi_cache_stats_t *out, gi_stream_t stream);
+
+/*
+ * Copy every live cell (see gi_cache_stats_t.live) to host memory, sorted by
+ * identity.  Synchronises `stream`.  *count receives the number of live cells;
+ * if it exceeds capacity nothing is written and GI_ERR_CAPACITY is returned.
+ * out may be NULL with capacity 0 to ask for the count.
+ */
+gi_status gi_cache_export(gi_cache_t cache, gi_cell *out, uint64_t capacity, uint64_t *count, gi_stream_t stream);
+
+/* ---------------------------------------------------------------- screen probes */
+/* Probe buffer sizes of a width x height view (host only, no device access). */
+gi_status gi_probes_layout(uint32_t width, uint32_t height, gi_probe_layout *out);
+
+/*
+ * Spawn one probe per 8x8 tile (Section 2.1.1, upscale 1x1): the pixel
+ * 8 * tile + j, j = (floor(8 H_2(f+1)), floor(8 H_3(f+1))) the Halton point of
+ * frame f shared by every tile, clamped to the image; no probe on a sky pixel.
+ * Writes mask level 0 and its MIP chain (Section 2.1.5: first valid probe of
+ * each 2x2 block in the order (0,0), (1,0), (0,1), (1,1)), positions rebuilt
+ * from the G-buffer distance and the camera, normals from the G-buffer.
+ * `probes` must have been laid out for the view size.
+ */
+gi_status gi_probes_spawn(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *probes, gi_stream_t stream);
+
+/*
+ * Probe irradiance (Sections 2.1.4, 2.4.2): ray k of probe p is record
+ * p * rays_per_probe + k and samples hemi-octahedral cell k mod 64
+ * (cell 8j + i covers u in [-1 + i/4, -1 + (i+1)/4], v likewise with j, in
+ * the probe frame (t, b, n) of Duff et al. 2017; direction from (u, v):
+ * x = (u+v)/2, y = (u-v)/2, z = 1 - |x| - |y|, normalised).  Each ray's
+ * radiance is the cache's resolved value at its slot (the environment `env`
+ * for GI_SLOT_MISS; no sample for GI_SLOT_NONE); per-cell means, with the
+ * mean of populated cells copied into cells without sample; projection to 3
+ * SH bands through exact per-cell direction moments.  Writes probes->sh.
+ * rays_per_probe must be a positive multiple of 64.  Call after gi_cache_resolve.
+ */
+gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *probes, const uint32_t *slot_ids,
+                              uint32_t rays_per_probe, const float env[3], gi_stream_t stream);
+
+/*
+ * Per-pixel interpolation (Section 2.4.1): the four neighbours found by
+ * Algorithm 3 at offsets (0,0), (1,0), (0,1), (1,1) from tile floor((pixel - 4) / 8);
+ * weight = bilinear * max(0, n_p . n_q)^8 * max(0, 1 - plane_dist / cell_size(d_p));
+ * irradiance E = sum w E_q(n_p) / sum w with E_q(n) = sum_lm A_l L_lm Y_lm(n),
+ * A = (pi, 2pi/3, pi/4).  out: device float4 per pixel (E rgb, flag GI_INTERP_*).
+ */
+gi_status gi_probes_interpolate(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *probes, float *out,
+                                gi_stream_t stream);
+
+/* Per-cell direction moments used by gi_probes_integrate (host memory, 64 x 10
+ * doubles: solid angle, first moment xyz, second moment xx yy zz xy xz yz; local
+ * frame), computed in closed form for the spherical quadrilateral of each cell. */
+gi_status gi_cell_moments(double *out640);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GI_H */

@@ -126,6 +126,8 @@ class OracleCache:
         """Resolved radiance (n, 3) of each identity; zeros and found=False where absent."""
         row = self.find(ident)
         found = row >= 0
+        # a cell answers queries once it has been resolved
+        found[found] = self.has_hist[row[found]]
         out = np.zeros((row.size, 3))
         out[found] = self.value[row[found]]
         return out, found

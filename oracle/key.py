@@ -45,7 +45,7 @@ KEY_DIR_RAY = 1
 
 def distance_scale(fov_y: float, width: int, height: int) -> float:
     """Algorithm 6: cell_size(d) = distance_scale * d."""
-    return math.tan(fov_y * PROJ_SIZE * max(1.0 / height, height / float(width) ** 2))
+    return math.tan(fov_y * PROJ_SIZE * max(1.0 / height, height / (float(width) * float(width))))
 
 
 @dataclass
@@ -60,7 +60,7 @@ def lod_params(cell_size: float, num_lods: int, fov_y: float, width: int, height
     s0 = float(F32(cell_size))
     ds = distance_scale(fov_y, width, height)
     d0 = s0 / ds
-    thr = np.array([(d0 * 2.0 ** (k + 1)) ** 2 for k in range(3)], np.float64).astype(F32)
+    thr = np.array([(d0 * 2.0 ** (k + 1)) * (d0 * 2.0 ** (k + 1)) for k in range(3)], np.float64).astype(F32)
     side = np.array([s0 * 2.0 ** k for k in range(4)], np.float64).astype(F32)
     inv0 = F32(1.0 / s0)
     inv = np.array([float(inv0) * 2.0 ** (-k) for k in range(4)], np.float64).astype(F32)

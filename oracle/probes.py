@@ -174,6 +174,7 @@ def interpolate(gbuf, cam, sp, coeffs):
     esum = np.zeros((H, W, 3))
     nfound = np.zeros((H, W), np.int64)
     erel = np.zeros((H, W, 3))
+    emag = np.zeros((H, W))
     margin = np.full((H, W), np.inf)
     for (ox, oy) in NEIGHBOUR_OFFSETS:
         q = find_closest_probe(mips, tx, ty, ox, oy)
@@ -192,6 +193,9 @@ def interpolate(gbuf, cam, sp, coeffs):
         w = np.where(ok, bil * ndot ** NORMAL_POWER * wd, 0.0)
         Eq = sh.irradiance(coeffs[pi], n_p)
         Eq = np.where(ok[..., None], Eq, 0.0)
+        # size of the terms summed into Eq (diagnostic for rounding bounds, not part of the result)
+        terms = np.abs(sh.basis(n_p) * np.array([sh.A_HAT[b] for b in sh.BAND]))[..., :, None] * np.abs(coeffs[pi])
+        emag = np.maximum(emag, np.where(ok, terms.sum(axis=(-2, -1)), 0.0))
         wsum += w
         esum += w[..., None] * Eq
         erel += Eq
@@ -207,4 +211,4 @@ def interpolate(gbuf, cam, sp, coeffs):
     flag[nfound == 0] = FLAG_NONE
     irr[sky] = 0.0
     flag[sky] = FLAG_SKY
-    return irr, flag, dict(wsum=wsum, margin=margin, nfound=nfound)
+    return irr, flag, dict(wsum=wsum, margin=margin, nfound=nfound, emag=emag)

@@ -1,0 +1,280 @@
+"""Python binding of libgi.so: the world-space radiance cache and screen-probe
+stage of GI-1.0 on sm_103a.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  The functions keep the C names (gi_cache_create, gi_cache_update,
+...); device buffers are passed as integers (device pointers) or as objects
+with a data_ptr() method (torch tensors), streams as integers (cudaStream_t)
+or objects with a cuda_stream attribute.  If the library is not built this
+module raises on first use; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH, build  # noqa: F401
+
+# ---------------------------------------------------------------- constants (gi.h)
+GI_OK, GI_ERR_INVALID_ARG, GI_ERR_OOM, GI_ERR_CUDA, GI_ERR_TIMEOUT, GI_ERR_DEVICE_FAULT, GI_ERR_CAPACITY = range(7)
+GI_WARN_DROPPED = 100
+GI_SLOT_MISS = 0xFFFFFFFE
+GI_SLOT_NONE = 0xFFFFFFFF
+GI_PROBE_NONE = 0xFFFFFFFF
+GI_INTERP_OK, GI_INTERP_RELAXED, GI_INTERP_NONE, GI_INTERP_SKY = 0, 1, 2, 3
+GI_KEY_DIR_NORMAL, GI_KEY_DIR_RAY = 0, 1
+GI_RESOLVED_F32, GI_RESOLVED_F16 = 0, 1
+GI_MAX_MIPS = 16
+GI_SH_STRIDE = 28
+
+c_u32, c_u64, c_f32, c_f64, c_vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
+
+
+class gi_cache_config(ctypes.Structure):
+    _fields_ = [("log2_slots", c_u32), ("cell_size", c_f32), ("num_lods", c_u32), ("alpha", c_f32),
+                ("evict_frames", c_u32), ("max_probe", c_u32), ("key_dir", c_u32), ("resolved_format", c_u32),
+                ("rebuild_load", c_f32)]
+
+
+class gi_view(ctypes.Structure):
+    _fields_ = [("frame", c_u32), ("width", c_u32), ("height", c_u32), ("cam_pos", c_f32 * 3),
+                ("cam_fwd", c_f32 * 3), ("cam_right", c_f32 * 3), ("cam_up", c_f32 * 3), ("fov_y", c_f64)]
+
+
+class gi_hits(ctypes.Structure):
+    _fields_ = [("pos", c_vp * 3), ("nrm", c_vp * 3), ("rad", c_vp * 3), ("ray_len", c_vp), ("ray_dir", c_vp * 3),
+                ("n", c_u64)]
+
+
+class gi_gbuffer(ctypes.Structure):
+    _fields_ = [("nd", c_vp), ("width", c_u32), ("height", c_u32)]
+
+
+class gi_probe_layout(ctypes.Structure):
+    _fields_ = [("tiles_x", c_u32), ("tiles_y", c_u32), ("num_probes", c_u32), ("mip_count", c_u32),
+                ("mip_w", c_u32 * GI_MAX_MIPS), ("mip_h", c_u32 * GI_MAX_MIPS), ("mip_offset", c_u32 * GI_MAX_MIPS),
+                ("mask_words", c_u32)]
+
+
+class gi_probes(ctypes.Structure):
+    _fields_ = [("layout", gi_probe_layout), ("mask", c_vp), ("pos", c_vp), ("nrm", c_vp), ("sh", c_vp)]
+
+
+class gi_cache_stats_t(ctypes.Structure):
+    _fields_ = [("slots", c_u64), ("occupied", c_u64), ("live", c_u64), ("touched", c_u64), ("dropped", c_u64),
+                ("clamped", c_u64), ("rebuilds", c_u64), ("updates", c_u64), ("resolves", c_u64),
+                ("max_probe_seen", c_u32), ("error_word", c_u32), ("last_resolved", ctypes.c_int64)]
+
+
+class gi_cell(ctypes.Structure):
+    _fields_ = [("identity", c_u64), ("sum", c_u64 * 3), ("count", c_u32), ("stamp", c_u32), ("value", c_f32 * 3),
+                ("slot", c_u32)]
+
+
+class gi_query(ctypes.Structure):
+    _fields_ = [("slot_ids", c_vp), ("points", ctypes.POINTER(gi_hits)), ("view", ctypes.POINTER(gi_view)),
+                ("n", c_u64), ("env", c_f32 * 3)]
+
+
+CELL_DTYPE = np.dtype([("identity", "<u8"), ("sum", "<u8", (3,)), ("count", "<u4"), ("stamp", "<u4"),
+                       ("value", "<f4", (3,)), ("slot", "<u4")])
+assert CELL_DTYPE.itemsize == ctypes.sizeof(gi_cell)
+
+# ---------------------------------------------------------------- library
+_LIB = None
+
+
+class GiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libgi.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgi.so is not built ({LIB_PATH}); run paper_2310_19855_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "gi_last_error": (ctypes.c_char_p, []),
+            "gi_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "gi_version": (c_u32, []),
+            "gi_cache_create": (ctypes.c_int, [ctypes.POINTER(gi_cache_config), ctypes.POINTER(c_vp)]),
+            "gi_cache_destroy": (ctypes.c_int, [c_vp]),
+            "gi_cache_update": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_hits), ctypes.POINTER(gi_view), c_vp, c_vp]),
+            "gi_cache_resolve": (ctypes.c_int, [c_vp, c_u32, c_vp]),
+            "gi_cache_query": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_query), c_vp, c_vp]),
+            "gi_cache_stats": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_cache_stats_t), c_vp]),
+            "gi_cache_export": (ctypes.c_int, [c_vp, c_vp, c_u64, ctypes.POINTER(c_u64), c_vp]),
+            "gi_probes_layout": (ctypes.c_int, [c_u32, c_u32, ctypes.POINTER(gi_probe_layout)]),
+            "gi_probes_spawn": (ctypes.c_int, [ctypes.POINTER(gi_gbuffer), ctypes.POINTER(gi_view),
+                                               ctypes.POINTER(gi_probes), c_vp]),
+            "gi_probes_integrate": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_probes), c_vp, c_u32,
+                                                   ctypes.POINTER(c_f32), c_vp]),
+            "gi_probes_interpolate": (ctypes.c_int, [ctypes.POINTER(gi_gbuffer), ctypes.POINTER(gi_view),
+                                                     ctypes.POINTER(gi_probes), c_vp, c_vp]),
+            "gi_cell_moments": (ctypes.c_int, [ctypes.POINTER(c_f64)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"expected a device pointer or a tensor, got {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None or s == 0:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def check(status: int, what: str, allow=(GI_OK,)) -> int:
+    if status in allow:
+        return status
+    L = lib()
+    raise GiError(status, f"{what}: {L.gi_status_string(status).decode()}: {L.gi_last_error().decode()}")
+
+
+# ---------------------------------------------------------------- marshalling helpers
+def make_view(frame: int, width: int, height: int, cam_pos, cam_fwd, cam_right, cam_up, fov_y: float) -> gi_view:
+    v = gi_view()
+    v.frame, v.width, v.height = int(frame), int(width), int(height)
+    for name, val in (("cam_pos", cam_pos), ("cam_fwd", cam_fwd), ("cam_right", cam_right), ("cam_up", cam_up)):
+        arr = getattr(v, name)
+        for k in range(3):
+            arr[k] = float(np.float32(val[k]))
+    v.fov_y = float(fov_y)
+    return v
+
+
+def hits_from_planes(planes, n: int) -> gi_hits:
+    """gi_hits from a device float32 array of 13 contiguous planes of n records
+    (pos xyz, nrm xyz, rad rgb, ray_len, ray_dir xyz) or from 13 plane pointers."""
+    h = gi_hits()
+    if isinstance(planes, (list, tuple)):
+        ptrs = [_ptr(p) for p in planes]
+    else:
+        base = _ptr(planes)
+        ptrs = [base + 4 * k * n for k in range(13)]
+    for k in range(3):
+        h.pos[k], h.nrm[k], h.rad[k] = ptrs[k], ptrs[3 + k], ptrs[6 + k]
+        h.ray_dir[k] = ptrs[10 + k]
+    h.ray_len = ptrs[9]
+    h.n = int(n)
+    return h
+
+
+def gi_probes_layout(width: int, height: int) -> gi_probe_layout:
+    out = gi_probe_layout()
+    check(lib().gi_probes_layout(int(width), int(height), ctypes.byref(out)), "gi_probes_layout")
+    return out
+
+
+def make_probes(layout: gi_probe_layout, mask, pos, nrm, sh) -> gi_probes:
+    p = gi_probes()
+    p.layout = layout
+    p.mask, p.pos, p.nrm, p.sh = _ptr(mask), _ptr(pos), _ptr(nrm), _ptr(sh)
+    return p
+
+
+def gi_cell_moments() -> np.ndarray:
+    out = (c_f64 * 640)()
+    check(lib().gi_cell_moments(out), "gi_cell_moments")
+    return np.frombuffer(out, np.float64).reshape(64, 10).copy()
+
+
+# ---------------------------------------------------------------- entry points (same names as the C ABI)
+def gi_cache_create(log2_slots: int, cell_size: float = 0.05, num_lods: int = 4, alpha: float = 0.1,
+                    evict_frames: int = 8, max_probe: int = 128, key_dir: int = GI_KEY_DIR_NORMAL,
+                    resolved_format: int = GI_RESOLVED_F32, rebuild_load: float = 0.8) -> int:
+    cfg = gi_cache_config(log2_slots, cell_size, num_lods, alpha, evict_frames, max_probe, key_dir,
+                          resolved_format, rebuild_load)
+    h = c_vp()
+    check(lib().gi_cache_create(ctypes.byref(cfg), ctypes.byref(h)), "gi_cache_create")
+    return h.value
+
+
+def gi_cache_destroy(cache: int) -> None:
+    check(lib().gi_cache_destroy(cache), "gi_cache_destroy")
+
+
+def gi_cache_update(cache: int, hits: gi_hits, view: gi_view, slot_ids, stream=None) -> None:
+    check(lib().gi_cache_update(cache, ctypes.byref(hits), ctypes.byref(view), _ptr(slot_ids), _stream(stream)),
+          "gi_cache_update")
+
+
+def gi_cache_resolve(cache: int, frame: int, stream=None) -> None:
+    check(lib().gi_cache_resolve(cache, int(frame), _stream(stream)), "gi_cache_resolve")
+
+
+def gi_cache_query(cache: int, out, n: int, slot_ids=None, points: gi_hits | None = None,
+                   view: gi_view | None = None, env=(0.0, 0.0, 0.0), stream=None) -> None:
+    q = gi_query()
+    q.slot_ids = _ptr(slot_ids)
+    if points is not None:
+        q.points = ctypes.pointer(points)
+    if view is not None:
+        q.view = ctypes.pointer(view)
+    q.n = int(n)
+    for k in range(3):
+        q.env[k] = float(env[k])
+    check(lib().gi_cache_query(cache, ctypes.byref(q), _ptr(out), _stream(stream)), "gi_cache_query")
+
+
+def gi_cache_stats(cache: int, stream=None) -> dict:
+    st = gi_cache_stats_t()
+    status = check(lib().gi_cache_stats(cache, ctypes.byref(st), _stream(stream)), "gi_cache_stats",
+                   allow=(GI_OK, GI_WARN_DROPPED))
+    d = {name: getattr(st, name) for name, _ in gi_cache_stats_t._fields_}
+    d["status"] = status
+    return d
+
+
+def gi_cache_export(cache: int, stream=None) -> np.ndarray:
+    cnt = c_u64(0)
+    check(lib().gi_cache_export(cache, None, 0, ctypes.byref(cnt), _stream(stream)), "gi_cache_export")
+    out = np.zeros(cnt.value, CELL_DTYPE)
+    if cnt.value:
+        check(lib().gi_cache_export(cache, out.ctypes.data, cnt.value, ctypes.byref(cnt), _stream(stream)),
+              "gi_cache_export")
+    return out
+
+
+def gi_probes_spawn(gbuf: gi_gbuffer, view: gi_view, probes: gi_probes, stream=None) -> None:
+    check(lib().gi_probes_spawn(ctypes.byref(gbuf), ctypes.byref(view), ctypes.byref(probes), _stream(stream)),
+          "gi_probes_spawn")
+
+
+def gi_probes_integrate(cache: int, probes: gi_probes, slot_ids, rays_per_probe: int, env=(0.0, 0.0, 0.0),
+                        stream=None) -> None:
+    e = (c_f32 * 3)(*[float(x) for x in env])
+    check(lib().gi_probes_integrate(cache, ctypes.byref(probes), _ptr(slot_ids), int(rays_per_probe), e,
+                                    _stream(stream)), "gi_probes_integrate")
+
+
+def gi_probes_interpolate(gbuf: gi_gbuffer, view: gi_view, probes: gi_probes, out, stream=None) -> None:
+    check(lib().gi_probes_interpolate(ctypes.byref(gbuf), ctypes.byref(view), ctypes.byref(probes), _ptr(out),
+                                      _stream(stream)), "gi_probes_interpolate")
+
+
+def make_gbuffer(nd, width: int, height: int) -> gi_gbuffer:
+    g = gi_gbuffer()
+    g.nd, g.width, g.height = _ptr(nd), int(width), int(height)
+    return g

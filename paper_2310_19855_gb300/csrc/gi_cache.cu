@@ -1,0 +1,864 @@
+// World-space radiance cache (Section 2.2): descriptor, bucket hash +
+// fingerprint with linear probing, fixed-point accumulation, resolve with an
+// exponential moving average and decay-based eviction, lookups.
+//
+// Table layout (N = 2^log2_slots slots, structure of arrays):
+//   tags     u32[N]     fingerprint << 8 | (home mod 256); 0 = empty
+//   accum    Accum[N]   {u64 sum r,g,b; u32 count; u32 stamp}, one 32-byte sector
+//   resolved float4[N]  (r, g, b, 0) or half4 (r, g, b, 0)
+// plus a spare table of the same shape for compaction, the touch list
+// (u32[N], slots first touched since the last resolve) and a counter line.
+//
+// A cell is the pair (home, fingerprint): probing runs are shorter than 256
+// slots, so a tag, which carries home mod 256, can only match within the run
+// of its own home.  The set of cells and their sums are therefore independent
+// of the order in which warps insert them.
+#include <cuda_fp16.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "gi_internal.cuh"
+
+namespace gi {
+
+// ---------------------------------------------------------------- hashing
+// PCG hash (Jarzynski & Olano 2020): one LCG step, then PCG's RXS-M-XS output.
+__device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
+    uint32_t state = v * 747796405u + 2891336453u;
+    uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+
+// xxHash32 of a single 4-byte word with a seed (xxHash specification).
+__device__ __forceinline__ uint32_t xxh32_word(uint32_t w, uint32_t seed) {
+    uint32_t h = seed + 0x165667B1u + 4u;
+    h += w * 0xC2B2AE3Du;
+    h = __funnelshift_l(h, h, 17) * 0x27D4EB2Fu;
+    h ^= h >> 15;
+    h *= 0x85EBCA77u;
+    h ^= h >> 13;
+    h *= 0xC2B2AE3Du;
+    h ^= h >> 16;
+    return h;
+}
+
+// Bucket ("home" slot) from the first hash, 24-bit fingerprint from the second.
+__device__ __forceinline__ void cell_of_key(unsigned long long key, uint32_t mask, uint32_t &home,
+                                            uint32_t &tag) {
+    uint32_t lo = (uint32_t)key, hi = (uint32_t)(key >> 32);
+    home = pcg_hash(lo ^ pcg_hash(hi)) & mask;
+    uint32_t fp = xxh32_word(lo, xxh32_word(hi, 0u)) >> 8;
+    fp = fp ? fp : 1u;
+    tag = (fp << 8) | (home & 0xFFu);
+}
+
+__device__ __forceinline__ float pick4(const float (&a)[4], int i) {
+    return i == 0 ? a[0] : (i == 1 ? a[1] : (i == 2 ? a[2] : a[3]));
+}
+
+// Cell descriptor (Sections 2.2.1-2.2.2): LOD from the float32 squared camera
+// distance against the Algorithm-6 thresholds, position quantised with
+// floor(p * (1/s_l)) wrapped to 19 bits, dominant-axis direction code (ties
+// x > y > z, sign bit decides), leak bit ray_len < s_l.  Every float op is an
+// explicit round-to-nearest intrinsic so that no contraction changes a bit.
+// `flip` = 1 when the direction source is the probe ray (outgoing = -ray).
+__device__ __forceinline__ unsigned long long cell_key(const KeyParams &k, float px, float py, float pz, float sx,
+                                                       float sy, float sz, float len, uint32_t flip) {
+    float dx = __fsub_rn(px, k.cam[0]);
+    float dy = __fsub_rn(py, k.cam[1]);
+    float dz = __fsub_rn(pz, k.cam[2]);
+    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    int lod = 0;
+    if (k.num_lods > 1 && d2 >= k.thr[0]) lod = 1;
+    if (k.num_lods > 2 && d2 >= k.thr[1]) lod = 2;
+    if (k.num_lods > 3 && d2 >= k.thr[2]) lod = 3;
+    float inv = pick4(k.inv_side, lod);
+    float side = pick4(k.side, lod);
+    uint32_t qx = (uint32_t)__float2int_rd(__fmul_rn(px, inv)) & kQMask;
+    uint32_t qy = (uint32_t)__float2int_rd(__fmul_rn(py, inv)) & kQMask;
+    uint32_t qz = (uint32_t)__float2int_rd(__fmul_rn(pz, inv)) & kQMask;
+    unsigned long long leak = (len < side) ? 1ull : 0ull;
+    float ax = fabsf(sx), ay = fabsf(sy), az = fabsf(sz);
+    int axis = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    float comp = axis == 0 ? sx : (axis == 1 ? sy : sz);
+    uint32_t sgn = (__float_as_uint(comp) >> 31) ^ flip;
+    unsigned long long code = (unsigned long long)(2 * axis + (int)sgn);
+    return ((unsigned long long)lod << 61) | (leak << 60) | (code << 57) | ((unsigned long long)qx << 38) |
+           ((unsigned long long)qy << 19) | (unsigned long long)qz;
+}
+
+__device__ __forceinline__ bool isfinite3(float a, float b, float c) {
+    return isfinite(a) && isfinite(b) && isfinite(c);
+}
+
+// Fixed point of one channel: round-half-even(clamp(r, 0, 32768) * 2^24); NaN -> 0.
+__device__ __forceinline__ unsigned long long quantize(float r, uint32_t &bad) {
+    bad |= (r >= 0.0f && r <= kRadMax) ? 0u : 1u;
+    float c = fminf(fmaxf(r, 0.0f), kRadMax);
+    return __float2ull_rn(__fmul_rn(c, 16777216.0f));
+}
+
+// ---------------------------------------------------------------- update
+constexpr int kUpdThreads = 256;
+constexpr int kTouchBuf = 2048;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct UpdateArgs {
+    const float *p[3];
+    const float *nrm[3];
+    const float *rad[3];
+    const float *len;
+    const float *dir[3];
+    uint32_t *slot_ids;
+    unsigned long long n;
+    uint32_t *tags;
+    Accum *accum;
+    uint32_t *touch;
+    Counters *ctr;
+    uint32_t mask;
+    uint32_t max_probe;
+    KeyParams kp;
+};
+
+__device__ __forceinline__ void flush_touch(uint32_t *s_touch, uint32_t &s_n, uint32_t &s_base, uint32_t *touch,
+                                            Counters *ctr) {
+    // precondition: called by the whole block right after a __syncthreads()
+    if (threadIdx.x == 0) s_base = s_n ? atomicAdd(&ctr->touch_count, s_n) : 0u;
+    __syncthreads();
+    uint32_t n = s_n, base = s_base;
+    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) touch[base + j] = s_touch[j];
+    __syncthreads();
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+}
+
+template <int KEY_DIR>
+__global__ void __launch_bounds__(kUpdThreads) k_update(UpdateArgs a) {
+    __shared__ uint32_t s_touch[kTouchBuf];
+    __shared__ uint32_t s_n, s_base, s_clamped, s_maxp;
+    if (threadIdx.x == 0) {
+        s_n = 0;
+        s_clamped = 0;
+        s_maxp = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kUpdThreads;
+    uint32_t my_clamped = 0, my_maxp = 0;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * kUpdThreads; base < a.n; base += stride) {
+        const unsigned long long i = base + threadIdx.x;
+        const bool inr = i < a.n;
+        float len = inr ? __ldcs(a.len + i) : -1.0f;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        if (inr) {
+            px = __ldcs(a.p[0] + i);
+            py = __ldcs(a.p[1] + i);
+            pz = __ldcs(a.p[2] + i);
+        }
+        const bool hit = inr && isfinite(len) && len >= 0.0f && isfinite3(px, py, pz);
+        const bool miss = inr && len == INFINITY;
+        unsigned long long q0 = 0, q1 = 0, q2 = 0;
+        uint32_t home = 0, tag = 0;
+        if (hit) {
+            float sx, sy, sz;
+            if (KEY_DIR == GI_KEY_DIR_NORMAL) {
+                sx = __ldcs(a.nrm[0] + i);
+                sy = __ldcs(a.nrm[1] + i);
+                sz = __ldcs(a.nrm[2] + i);
+            } else {
+                sx = __ldcs(a.dir[0] + i);
+                sy = __ldcs(a.dir[1] + i);
+                sz = __ldcs(a.dir[2] + i);
+            }
+            uint32_t bad = 0;
+            q0 = quantize(__ldcs(a.rad[0] + i), bad);
+            q1 = quantize(__ldcs(a.rad[1] + i), bad);
+            q2 = quantize(__ldcs(a.rad[2] + i), bad);
+            my_clamped += bad;
+            unsigned long long key =
+                cell_key(a.kp, px, py, pz, sx, sy, sz, len, KEY_DIR == GI_KEY_DIR_NORMAL ? 0u : 1u);
+            cell_of_key(key, a.mask, home, tag);
+        }
+        // Merge the hits of this warp that name the same cell: one leader per cell
+        // adds the group's integer sums (order-independent, so still bit-exact).
+        const unsigned hm = __ballot_sync(kFull, hit);
+        unsigned peers = 0;
+        if (hit) peers = __match_any_sync(hm, ((unsigned long long)home << 32) | tag);
+        const unsigned above = peers & (0xFFFFFFFEu << lane);
+        int nxt = above ? (__ffs(above) - 1) : -1;
+        uint32_t cnt = hit ? 1u : 0u;
+        // pointer-jumping suffix sums along each group's lane list
+        while (__any_sync(kFull, nxt >= 0)) {
+            const int src = nxt >= 0 ? nxt : lane;
+            const unsigned long long o0 = __shfl_sync(kFull, q0, src);
+            const unsigned long long o1 = __shfl_sync(kFull, q1, src);
+            const unsigned long long o2 = __shfl_sync(kFull, q2, src);
+            const uint32_t oc = __shfl_sync(kFull, cnt, src);
+            const int on = __shfl_sync(kFull, nxt, src);
+            if (nxt >= 0) {
+                q0 += o0;
+                q1 += o1;
+                q2 += o2;
+                cnt += oc;
+                nxt = on;
+            }
+        }
+        const bool leader = hit && (peers & ((1u << lane) - 1u)) == 0u;
+        uint32_t slot = GI_SLOT_NONE;
+        if (leader) {
+            uint32_t s = home, k = 0;
+            for (; k < a.max_probe; ++k) {
+                uint32_t t = __ldcg(a.tags + s);
+                if (t == tag) {
+                    slot = s;
+                    break;
+                }
+                if (t == kEmpty) {
+                    uint32_t old = atomicCAS(a.tags + s, kEmpty, tag);
+                    if (old == kEmpty || old == tag) {
+                        slot = s;
+                        break;
+                    }
+                }
+                s = (s + 1u) & a.mask;
+            }
+            my_maxp = max(my_maxp, k + 1u);
+            if (slot != GI_SLOT_NONE) {
+                Accum *ac = a.accum + slot;
+                atomicAdd(&ac->sum[0], q0);
+                atomicAdd(&ac->sum[1], q1);
+                atomicAdd(&ac->sum[2], q2);
+                if (atomicAdd(&ac->count, cnt) == 0u) {
+                    uint32_t k2 = atomicAdd(&s_n, 1u);
+                    s_touch[k2] = slot;
+                }
+            } else {
+                atomicAdd(&a.ctr->dropped, (unsigned long long)cnt);
+            }
+        }
+        const int lead = hit ? (__ffs(peers) - 1) : lane;
+        const uint32_t my_slot = __shfl_sync(kFull, slot, lead);
+        if (inr) a.slot_ids[i] = hit ? my_slot : (miss ? GI_SLOT_MISS : GI_SLOT_NONE);
+        __syncthreads();
+        if (s_n > (uint32_t)(kTouchBuf - kUpdThreads)) flush_touch(s_touch, s_n, s_base, a.touch, a.ctr);
+    }
+    __syncthreads();
+    flush_touch(s_touch, s_n, s_base, a.touch, a.ctr);
+    // block totals of the statistics, one global atomic each
+    my_clamped = __reduce_add_sync(kFull, my_clamped);
+    my_maxp = __reduce_max_sync(kFull, my_maxp);
+    if (lane == 0) {
+        if (my_clamped) atomicAdd(&s_clamped, my_clamped);
+        atomicMax(&s_maxp, my_maxp);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_clamped) atomicAdd(&a.ctr->clamped, (unsigned long long)s_clamped);
+        if (s_maxp) atomicMax(&a.ctr->max_probe, s_maxp);
+    }
+}
+
+// ---------------------------------------------------------------- resolve
+constexpr int kResThreads = 256;
+
+struct ResolveArgs {
+    const uint32_t *touch;
+    Accum *accum;
+    void *resolved;
+    Counters *ctr;
+    float alpha;
+    uint32_t stamp_now;   // frame + 1
+    uint32_t has_lr;      // a resolve happened before
+    uint32_t lr;          // frame of that resolve
+    uint32_t evict;       // E
+    int f16;
+};
+
+__device__ __forceinline__ float3 load_resolved(const void *r, int f16, uint32_t s) {
+    if (f16) {
+        const ushort4 h = reinterpret_cast<const ushort4 *>(r)[s];
+        return make_float3(__half2float(__ushort_as_half(h.x)), __half2float(__ushort_as_half(h.y)),
+                           __half2float(__ushort_as_half(h.z)));
+    }
+    const float4 v = reinterpret_cast<const float4 *>(r)[s];
+    return make_float3(v.x, v.y, v.z);
+}
+
+__device__ __forceinline__ void store_resolved(void *r, int f16, uint32_t s, float3 v) {
+    if (f16) {
+        ushort4 h;
+        h.x = __half_as_ushort(__float2half_rn(v.x));
+        h.y = __half_as_ushort(__float2half_rn(v.y));
+        h.z = __half_as_ushort(__float2half_rn(v.z));
+        h.w = 0;
+        reinterpret_cast<ushort4 *>(r)[s] = h;
+    } else {
+        reinterpret_cast<float4 *>(r)[s] = make_float4(v.x, v.y, v.z, 0.0f);
+    }
+}
+
+__global__ void __launch_bounds__(kResThreads) k_resolve(ResolveArgs a) {
+    __shared__ uint32_t s_new;
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) s_new = 0;
+    __syncthreads();
+    const uint32_t n = __ldcg(&a.ctr->touch_count);
+    uint32_t fresh_new = 0;
+    for (uint32_t i = blockIdx.x * kResThreads + threadIdx.x; i < n; i += gridDim.x * kResThreads) {
+        const uint32_t s = __ldcs(a.touch + i);
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.accum + s);
+        const uint4 lo = src[0], hi = src[1];
+        const unsigned long long s0 = ((unsigned long long)lo.y << 32) | lo.x;
+        const unsigned long long s1 = ((unsigned long long)lo.w << 32) | lo.z;
+        const unsigned long long s2 = ((unsigned long long)hi.y << 32) | hi.x;
+        const uint32_t count = hi.z, stamp = hi.w;
+        const float fc = (float)count;
+        // mean = sum / (count 2^24)
+        float3 m = make_float3(__fdiv_rn(__ull2float_rn(s0), fc) * 5.9604644775390625e-8f,
+                               __fdiv_rn(__ull2float_rn(s1), fc) * 5.9604644775390625e-8f,
+                               __fdiv_rn(__ull2float_rn(s2), fc) * 5.9604644775390625e-8f);
+        // no history: never resolved, or evicted by an earlier resolve (untouched E frames)
+        const bool fresh = stamp == 0u || (a.has_lr && (a.lr - (stamp - 1u)) >= a.evict);
+        fresh_new += stamp == 0u ? 1u : 0u;
+        float3 v = m;
+        if (!fresh) {
+            float3 o = load_resolved(a.resolved, a.f16, s);
+            v = make_float3(o.x + a.alpha * (m.x - o.x), o.y + a.alpha * (m.y - o.y), o.z + a.alpha * (m.z - o.z));
+        }
+        store_resolved(a.resolved, a.f16, s, v);
+        uint4 *dst = reinterpret_cast<uint4 *>(a.accum + s);
+        dst[0] = make_uint4(0u, 0u, 0u, 0u);
+        dst[1] = make_uint4(0u, 0u, 0u, a.stamp_now);
+    }
+    fresh_new = __reduce_add_sync(kFull, fresh_new);
+    if ((threadIdx.x & 31) == 0 && fresh_new) atomicAdd(&s_new, fresh_new);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_new) atomicAdd(&a.ctr->occupied, s_new);
+        __threadfence();
+        const uint32_t t = atomicAdd(&a.ctr->ticket, 1u);
+        s_last = (t == gridDim.x - 1u);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        // every block has read the touch count: reset it for the next frame
+        a.ctr->touch_count = 0u;
+        a.ctr->ticket = 0u;
+    }
+}
+
+// ---------------------------------------------------------------- queries
+struct LiveRule {
+    uint32_t has_lr, lr, evict;
+};
+
+// a cell answers queries once resolved, until it is evicted
+__device__ __forceinline__ bool answers(uint32_t stamp, const LiveRule &r) {
+    return stamp != 0u && (!r.has_lr || (r.lr - (stamp - 1u)) < r.evict);
+}
+
+__global__ void k_query_slots(const uint32_t *slot_ids, unsigned long long n, const void *resolved, int f16,
+                              uint32_t slots, float e0, float e1, float e2, float4 *out) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t s = __ldcs(slot_ids + i);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (s < slots) {
+            float3 v = load_resolved(resolved, f16, s);
+            o = make_float4(v.x, v.y, v.z, 1.0f);
+        } else if (s == GI_SLOT_MISS) {
+            o = make_float4(e0, e1, e2, 1.0f);
+        }
+        __stcs(out + i, o);
+    }
+}
+
+template <int KEY_DIR>
+__global__ void k_query_points(UpdateArgs a, const void *resolved, int f16, LiveRule rule, float4 *out) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < a.n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const float len = a.len[i];
+        const float px = a.p[0][i], py = a.p[1][i], pz = a.p[2][i];
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (isfinite(len) && len >= 0.0f && isfinite3(px, py, pz)) {
+            const float *src0 = KEY_DIR == GI_KEY_DIR_NORMAL ? a.nrm[0] : a.dir[0];
+            const float *src1 = KEY_DIR == GI_KEY_DIR_NORMAL ? a.nrm[1] : a.dir[1];
+            const float *src2 = KEY_DIR == GI_KEY_DIR_NORMAL ? a.nrm[2] : a.dir[2];
+            unsigned long long key = cell_key(a.kp, px, py, pz, src0[i], src1[i], src2[i], len,
+                                              KEY_DIR == GI_KEY_DIR_NORMAL ? 0u : 1u);
+            uint32_t home, tag;
+            cell_of_key(key, a.mask, home, tag);
+            uint32_t s = home;
+            for (uint32_t k = 0; k < a.max_probe; ++k) {
+                const uint32_t t = __ldg(a.tags + s);
+                if (t == kEmpty) break;
+                if (t == tag) {
+                    if (answers(__ldg(&a.accum[s].stamp), rule)) {
+                        float3 v = load_resolved(resolved, f16, s);
+                        o = make_float4(v.x, v.y, v.z, 1.0f);
+                    }
+                    break;
+                }
+                s = (s + 1u) & a.mask;
+            }
+        }
+        out[i] = o;
+    }
+}
+
+// ---------------------------------------------------------------- compaction
+// Re-insert every live cell of the current table into the clean spare table
+// (home recovered from the slot and the tag's low byte) and clear the current
+// table behind it, so that it is clean when it becomes the spare.
+__global__ void k_rebuild(uint32_t *old_tags, Accum *old_acc, const void *old_res, uint32_t *new_tags,
+                          Accum *new_acc, void *new_res, int f16, uint32_t mask, uint32_t max_probe, LiveRule rule,
+                          Counters *ctr) {
+    uint32_t live = 0, dropped = 0;
+    const uint32_t N = mask + 1u;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const uint32_t t = old_tags[s];
+        if (t == kEmpty) continue;
+        const uint32_t stamp = old_acc[s].stamp;
+        if (answers(stamp, rule)) {
+            const uint32_t home = (s - ((s - (t & 0xFFu)) & 0xFFu)) & mask;
+            uint32_t ns = home, k = 0;
+            for (; k < max_probe; ++k) {
+                if (atomicCAS(new_tags + ns, kEmpty, t) == kEmpty) break;
+                ns = (ns + 1u) & mask;
+            }
+            if (k < max_probe) {
+                new_acc[ns].stamp = stamp;
+                if (f16)
+                    reinterpret_cast<ushort4 *>(new_res)[ns] = reinterpret_cast<const ushort4 *>(old_res)[s];
+                else
+                    reinterpret_cast<float4 *>(new_res)[ns] = reinterpret_cast<const float4 *>(old_res)[s];
+                ++live;
+            } else {
+                ++dropped;
+            }
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(old_acc + s);
+        dst[0] = make_uint4(0u, 0u, 0u, 0u);
+        dst[1] = make_uint4(0u, 0u, 0u, 0u);
+        old_tags[s] = kEmpty;
+    }
+    live = __reduce_add_sync(kFull, live);
+    dropped = __reduce_add_sync(kFull, dropped);
+    if ((threadIdx.x & 31) == 0) {
+        if (live) atomicAdd(&ctr->occupied, live);
+        if (dropped) atomicAdd(&ctr->dropped, (unsigned long long)dropped);
+    }
+}
+
+// ---------------------------------------------------------------- table scan for stats
+__global__ void k_scan_stats(const uint32_t *tags, const Accum *acc, uint32_t N, LiveRule rule,
+                             unsigned long long *out /* occupied, live */) {
+    unsigned long long occ = 0, live = 0;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        if (tags[s] == kEmpty) continue;
+        ++occ;
+        if (acc[s].count > 0u || answers(acc[s].stamp, rule)) ++live;
+    }
+    for (int o = 16; o; o >>= 1) {
+        occ += __shfl_xor_sync(kFull, occ, o);
+        live += __shfl_xor_sync(kFull, live, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, occ);
+        atomicAdd(out + 1, live);
+    }
+}
+
+} // namespace gi
+
+// ==================================================================== host side
+struct gi_cache_s {
+    gi_cache_config cfg;
+    int device;
+    uint32_t N, mask;
+    int sms;
+    int upd_blocks, res_blocks;
+    uint32_t *tags[2];
+    gi::Accum *accum[2];
+    void *resolved[2];
+    int cur;
+    uint32_t *touch;
+    gi::Counters *ctr;
+    gi::Counters *ctr_host;     // pinned snapshot
+    unsigned long long *scan;   // device scratch for stats (2 x u64)
+    cudaEvent_t snap_event;
+    bool snap_pending;
+    int64_t last_resolved;
+    bool touched_since_resolve;
+    bool rebuild_checked;
+    uint64_t rebuilds, updates, resolves;
+};
+
+namespace gi {
+
+CacheView cache_view(gi_cache_t c) {
+    CacheView v;
+    v.resolved = c->resolved[c->cur];
+    v.resolved_f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
+    v.slots = c->N;
+    return v;
+}
+
+static LiveRule live_rule(const gi_cache_s *c) {
+    LiveRule r;
+    r.has_lr = c->last_resolved >= 0 ? 1u : 0u;
+    r.lr = c->last_resolved >= 0 ? (uint32_t)c->last_resolved : 0u;
+    r.evict = c->cfg.evict_frames;
+    return r;
+}
+
+static bool config_ok(const gi_cache_config *c) {
+    if (!c) return false;
+    if (c->log2_slots < 10 || c->log2_slots > 28) return false;
+    if (!(c->cell_size > 0.0f) || !isfinite(c->cell_size)) return false;
+    if (c->num_lods < 1 || c->num_lods > 4) return false;
+    if (!(c->alpha > 0.0f && c->alpha <= 1.0f)) return false;
+    if (c->evict_frames < 1) return false;
+    if (c->max_probe < 1 || c->max_probe > 255) return false;
+    if (c->key_dir != GI_KEY_DIR_NORMAL && c->key_dir != GI_KEY_DIR_RAY) return false;
+    if (c->resolved_format != GI_RESOLVED_F32 && c->resolved_format != GI_RESOLVED_F16) return false;
+    if (!(c->rebuild_load >= 0.25f && c->rebuild_load <= 0.95f)) return false;
+    return true;
+}
+
+static bool hits_ok(const gi_hits *h, uint32_t key_dir) {
+    if (!h) return false;
+    if (h->n == 0) return true;
+    for (int a = 0; a < 3; ++a)
+        if (!h->pos[a] || !h->nrm[a] || !h->rad[a]) return false;
+    if (!h->ray_len) return false;
+    if (key_dir == GI_KEY_DIR_RAY)
+        for (int a = 0; a < 3; ++a)
+            if (!h->ray_dir[a]) return false;
+    return true;
+}
+
+static UpdateArgs update_args(gi_cache_s *c, const gi_hits *h, const gi_view *v, uint32_t *slot_ids) {
+    UpdateArgs a;
+    for (int k = 0; k < 3; ++k) {
+        a.p[k] = h->pos[k];
+        a.nrm[k] = h->nrm[k];
+        a.rad[k] = h->rad[k];
+        a.dir[k] = h->ray_dir[k];
+    }
+    a.len = h->ray_len;
+    a.slot_ids = slot_ids;
+    a.n = h->n;
+    a.tags = c->tags[c->cur];
+    a.accum = c->accum[c->cur];
+    a.touch = c->touch;
+    a.ctr = c->ctr;
+    a.mask = c->mask;
+    a.max_probe = c->cfg.max_probe;
+    a.kp = key_params(c->cfg.cell_size, c->cfg.num_lods, v);
+    return a;
+}
+
+static gi_status maybe_rebuild(gi_cache_s *c, cudaStream_t st) {
+    // Only at the first update after a resolve (all accumulators are clear then),
+    // and only once the occupancy read back after that resolve has arrived.
+    if (c->touched_since_resolve || c->rebuild_checked || !c->snap_pending) return GI_OK;
+    cudaError_t q = cudaEventQuery(c->snap_event);
+    if (q == cudaErrorNotReady) return GI_OK;
+    if (q != cudaSuccess) return cuda_status(q, "cudaEventQuery");
+    c->rebuild_checked = true;
+    c->snap_pending = false;
+    const double occ = (double)c->ctr_host->occupied;
+    if (occ <= (double)c->cfg.rebuild_load * (double)c->N) return GI_OK;
+    const int nxt = c->cur ^ 1;
+    gi_status s = cuda_status(cudaMemsetAsync(&c->ctr->occupied, 0, sizeof(uint32_t), st), "rebuild memset");
+    if (s != GI_OK) return s;
+    k_rebuild<<<c->sms * 8, 256, 0, st>>>(c->tags[c->cur], c->accum[c->cur], c->resolved[c->cur], c->tags[nxt],
+                                           c->accum[nxt], c->resolved[nxt], c->cfg.resolved_format == GI_RESOLVED_F16,
+                                           c->mask, c->cfg.max_probe, live_rule(c), c->ctr);
+    s = cuda_status(cudaGetLastError(), "k_rebuild launch");
+    if (s != GI_OK) return s;
+    c->cur = nxt;
+    c->rebuilds++;
+    return GI_OK;
+}
+
+static void free_cache(gi_cache_s *c) {
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->tags[k]);
+        cudaFree(c->accum[k]);
+        cudaFree(c->resolved[k]);
+    }
+    cudaFree(c->touch);
+    cudaFree(c->ctr);
+    cudaFree(c->scan);
+    if (c->ctr_host) cudaFreeHost(c->ctr_host);
+    if (c->snap_event) cudaEventDestroy(c->snap_event);
+    delete c;
+}
+
+} // namespace gi
+
+using namespace gi;
+
+extern "C" {
+
+gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
+    if (!out) {
+        set_error("gi_cache_create: out is NULL");
+        return GI_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!config_ok(cfg)) {
+        set_error("gi_cache_create: configuration out of range");
+        return GI_ERR_INVALID_ARG;
+    }
+    gi_cache_s *c = new gi_cache_s();
+    memset(c, 0, sizeof *c);
+    c->cfg = *cfg;
+    c->N = 1u << cfg->log2_slots;
+    c->mask = c->N - 1u;
+    c->last_resolved = -1;
+    gi_status s = cuda_status(cudaGetDevice(&c->device), "cudaGetDevice");
+    if (s == GI_OK) s = cuda_status(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device), "sm count");
+    const size_t N = c->N;
+    const size_t res_bytes = cfg->resolved_format == GI_RESOLVED_F16 ? 8 : 16;
+    for (int k = 0; k < 2 && s == GI_OK; ++k) {
+        s = cuda_status(cudaMalloc(&c->tags[k], N * 4), "cudaMalloc tags");
+        if (s == GI_OK) s = cuda_status(cudaMalloc(&c->accum[k], N * sizeof(Accum)), "cudaMalloc accum");
+        if (s == GI_OK) s = cuda_status(cudaMalloc(&c->resolved[k], N * res_bytes), "cudaMalloc resolved");
+        if (s == GI_OK) s = cuda_status(cudaMemset(c->tags[k], 0, N * 4), "memset");
+        if (s == GI_OK) s = cuda_status(cudaMemset(c->accum[k], 0, N * sizeof(Accum)), "memset");
+        if (s == GI_OK) s = cuda_status(cudaMemset(c->resolved[k], 0, N * res_bytes), "memset");
+    }
+    if (s == GI_OK) s = cuda_status(cudaMalloc(&c->touch, N * 4), "cudaMalloc touch");
+    if (s == GI_OK) s = cuda_status(cudaMalloc(&c->ctr, sizeof(Counters)), "cudaMalloc counters");
+    if (s == GI_OK) s = cuda_status(cudaMemset(c->ctr, 0, sizeof(Counters)), "memset");
+    if (s == GI_OK) s = cuda_status(cudaMalloc(&c->scan, 2 * sizeof(unsigned long long)), "cudaMalloc scan");
+    if (s == GI_OK) s = cuda_status(cudaMallocHost(&c->ctr_host, sizeof(Counters)), "cudaMallocHost");
+    if (s == GI_OK) s = cuda_status(cudaEventCreateWithFlags(&c->snap_event, cudaEventDisableTiming), "event");
+    if (s == GI_OK) {
+        int per_sm = 0;
+        s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<0>, kUpdThreads, 0),
+                        "occupancy");
+        c->upd_blocks = c->sms * std::max(per_sm, 1);
+        c->res_blocks = c->sms * 4;
+    }
+    if (s == GI_OK) s = cuda_status(cudaDeviceSynchronize(), "create sync");
+    if (s != GI_OK) {
+        free_cache(c);
+        return s;
+    }
+    *out = c;
+    return GI_OK;
+}
+
+gi_status gi_cache_destroy(gi_cache_t c) {
+    if (!c) return GI_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_cache(c);
+    return cuda_status(e, "gi_cache_destroy");
+}
+
+gi_status gi_cache_update(gi_cache_t c, const gi_hits *hits, const gi_view *view, uint32_t *slot_ids,
+                          gi_stream_t stream) {
+    if (!c) {
+        set_error("gi_cache_update: cache is NULL");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (!hits_ok(hits, c->cfg.key_dir)) {
+        set_error("gi_cache_update: hits has a NULL plane");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (!view_ok(view)) {
+        set_error("gi_cache_update: bad view (size or fov)");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (hits->n > 0 && !slot_ids) {
+        set_error("gi_cache_update: slot_ids is NULL");
+        return GI_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    gi_status s = maybe_rebuild(c, st);
+    if (s != GI_OK) return s;
+    c->updates++;
+    if (hits->n == 0) return GI_OK;
+    UpdateArgs a = update_args(c, hits, view, slot_ids);
+    unsigned long long need = (hits->n + kUpdThreads - 1) / kUpdThreads;
+    int blocks = (int)std::min<unsigned long long>((unsigned long long)c->upd_blocks, need);
+    if (c->cfg.key_dir == GI_KEY_DIR_NORMAL)
+        k_update<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(a);
+    else
+        k_update<GI_KEY_DIR_RAY><<<blocks, kUpdThreads, 0, st>>>(a);
+    s = cuda_status(cudaGetLastError(), "k_update launch");
+    if (s == GI_OK) c->touched_since_resolve = true;
+    return s;
+}
+
+gi_status gi_cache_resolve(gi_cache_t c, uint32_t frame, gi_stream_t stream) {
+    if (!c) {
+        set_error("gi_cache_resolve: cache is NULL");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (c->last_resolved >= 0 && (int64_t)frame < c->last_resolved) {
+        set_error("gi_cache_resolve: frame %u precedes the last resolved frame %lld", frame,
+                  (long long)c->last_resolved);
+        return GI_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    ResolveArgs a;
+    a.touch = c->touch;
+    a.accum = c->accum[c->cur];
+    a.resolved = c->resolved[c->cur];
+    a.ctr = c->ctr;
+    a.alpha = c->cfg.alpha;
+    a.stamp_now = frame + 1u;
+    a.has_lr = c->last_resolved >= 0;
+    a.lr = c->last_resolved >= 0 ? (uint32_t)c->last_resolved : 0u;
+    a.evict = c->cfg.evict_frames;
+    a.f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
+    k_resolve<<<c->res_blocks, kResThreads, 0, st>>>(a);
+    gi_status s = cuda_status(cudaGetLastError(), "k_resolve launch");
+    if (s != GI_OK) return s;
+    // occupancy snapshot, read by the next update to decide on a compaction
+    s = cuda_status(cudaMemcpyAsync(c->ctr_host, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st), "snapshot");
+    if (s == GI_OK) s = cuda_status(cudaEventRecord(c->snap_event, st), "snapshot event");
+    if (s != GI_OK) return s;
+    c->snap_pending = true;
+    c->rebuild_checked = false;
+    c->last_resolved = frame;
+    c->touched_since_resolve = false;
+    c->resolves++;
+    return GI_OK;
+}
+
+gi_status gi_cache_query(gi_cache_t c, const gi_query *q, float *out, gi_stream_t stream) {
+    if (!c || !q) {
+        set_error("gi_cache_query: NULL cache or query");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (q->n == 0) return GI_OK;
+    if (!out) {
+        set_error("gi_cache_query: out is NULL");
+        return GI_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
+    int blocks = (int)std::min<unsigned long long>((unsigned long long)c->sms * 16, (q->n + 255) / 256);
+    if (q->slot_ids) {
+        k_query_slots<<<blocks, 256, 0, st>>>(q->slot_ids, q->n, c->resolved[c->cur], f16, c->N, q->env[0],
+                                              q->env[1], q->env[2], reinterpret_cast<float4 *>(out));
+    } else {
+        if (!q->points || !hits_ok(q->points, c->cfg.key_dir) || q->points->n < q->n || !view_ok(q->view)) {
+            set_error("gi_cache_query: by point needs points with n records and a valid view");
+            return GI_ERR_INVALID_ARG;
+        }
+        UpdateArgs a = update_args(c, q->points, q->view, nullptr);
+        a.n = q->n;
+        if (c->cfg.key_dir == GI_KEY_DIR_NORMAL)
+            k_query_points<GI_KEY_DIR_NORMAL><<<blocks, 256, 0, st>>>(a, c->resolved[c->cur], f16, live_rule(c),
+                                                                      reinterpret_cast<float4 *>(out));
+        else
+            k_query_points<GI_KEY_DIR_RAY><<<blocks, 256, 0, st>>>(a, c->resolved[c->cur], f16, live_rule(c),
+                                                                   reinterpret_cast<float4 *>(out));
+    }
+    return cuda_status(cudaGetLastError(), "k_query launch");
+}
+
+gi_status gi_cache_stats(gi_cache_t c, gi_cache_stats_t *out, gi_stream_t stream) {
+    if (!c || !out) {
+        set_error("gi_cache_stats: NULL argument");
+        return GI_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    gi_status s = cuda_status(cudaMemsetAsync(c->scan, 0, 2 * sizeof(unsigned long long), st), "stats memset");
+    if (s != GI_OK) return s;
+    k_scan_stats<<<c->sms * 4, 256, 0, st>>>(c->tags[c->cur], c->accum[c->cur], c->N, live_rule(c), c->scan);
+    s = cuda_status(cudaGetLastError(), "k_scan_stats launch");
+    if (s != GI_OK) return s;
+    Counters h;
+    unsigned long long sc[2];
+    s = cuda_status(cudaMemcpyAsync(&h, c->ctr, sizeof h, cudaMemcpyDeviceToHost, st), "stats copy");
+    if (s == GI_OK) s = cuda_status(cudaMemcpyAsync(sc, c->scan, sizeof sc, cudaMemcpyDeviceToHost, st), "stats copy");
+    if (s == GI_OK) s = cuda_status(cudaStreamSynchronize(st), "stats sync");
+    if (s != GI_OK) return s;
+    memset(out, 0, sizeof *out);
+    out->slots = c->N;
+    out->occupied = sc[0];
+    out->live = sc[1];
+    out->touched = h.touch_count;
+    out->dropped = h.dropped;
+    out->clamped = h.clamped;
+    out->rebuilds = c->rebuilds;
+    out->updates = c->updates;
+    out->resolves = c->resolves;
+    out->max_probe_seen = h.max_probe;
+    out->error_word = h.error_word;
+    out->last_resolved = c->last_resolved;
+    if (h.error_word) return GI_ERR_DEVICE_FAULT;
+    if (h.dropped) return GI_WARN_DROPPED;
+    return GI_OK;
+}
+
+gi_status gi_cache_export(gi_cache_t c, gi_cell *out, uint64_t capacity, uint64_t *count, gi_stream_t stream) {
+    if (!c || !count || (capacity > 0 && !out)) {
+        set_error("gi_cache_export: NULL argument");
+        return GI_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = c->N;
+    const int f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
+    std::vector<uint32_t> tags(N);
+    std::vector<Accum> acc(N);
+    std::vector<unsigned char> res(N * (f16 ? 8 : 16));
+    gi_status s = cuda_status(cudaStreamSynchronize(st), "export sync");
+    if (s == GI_OK) s = cuda_status(cudaMemcpy(tags.data(), c->tags[c->cur], N * 4, cudaMemcpyDeviceToHost), "export");
+    if (s == GI_OK)
+        s = cuda_status(cudaMemcpy(acc.data(), c->accum[c->cur], N * sizeof(Accum), cudaMemcpyDeviceToHost), "export");
+    if (s == GI_OK)
+        s = cuda_status(cudaMemcpy(res.data(), c->resolved[c->cur], res.size(), cudaMemcpyDeviceToHost), "export");
+    if (s != GI_OK) return s;
+    const LiveRule r = live_rule(c);
+    std::vector<gi_cell> cells;
+    for (uint32_t i = 0; i < c->N; ++i) {
+        const uint32_t t = tags[i];
+        if (t == kEmpty) continue;
+        const Accum &a = acc[i];
+        const bool live = a.count > 0 || (a.stamp != 0 && (!r.has_lr || (r.lr - (a.stamp - 1u)) < r.evict));
+        if (!live) continue;
+        gi_cell cell;
+        const uint32_t home = (i - ((i - (t & 0xFFu)) & 0xFFu)) & c->mask;
+        cell.identity = ((uint64_t)home << 24) | (uint64_t)(t >> 8);
+        for (int k = 0; k < 3; ++k) cell.sum[k] = a.sum[k];
+        cell.count = a.count;
+        cell.stamp = a.stamp;
+        if (f16) {
+            const __half *h = reinterpret_cast<const __half *>(res.data()) + 4 * (size_t)i;
+            for (int k = 0; k < 3; ++k) cell.value[k] = __half2float(h[k]);
+        } else {
+            const float *f = reinterpret_cast<const float *>(res.data()) + 4 * (size_t)i;
+            for (int k = 0; k < 3; ++k) cell.value[k] = f[k];
+        }
+        cell.slot = i;
+        cells.push_back(cell);
+    }
+    std::sort(cells.begin(), cells.end(), [](const gi_cell &x, const gi_cell &y) { return x.identity < y.identity; });
+    *count = cells.size();
+    if (cells.size() > capacity) {
+        if (capacity > 0) {
+            set_error("gi_cache_export: %zu live cells exceed capacity %llu", cells.size(),
+                      (unsigned long long)capacity);
+            return GI_ERR_CAPACITY;
+        }
+        return GI_OK;
+    }
+    if (!cells.empty()) memcpy(out, cells.data(), cells.size() * sizeof(gi_cell));
+    return GI_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,611 @@
+// Screen probes (Section 2.1): spawn per 8x8 tile with a Halton jitter
+// (2.1.1), probe mask + MIP chain and the directional search of Algorithm 3
+// (2.1.5), probe irradiance through 3-band spherical harmonics (2.1.4, 2.4.2)
+// and per-pixel interpolation (2.4.1).
+#include <cuda_fp16.h>
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "gi_internal.cuh"
+
+namespace gi {
+
+constexpr unsigned kFullMask = 0xFFFFFFFFu;
+
+struct MipInfo {
+    int count;
+    int w[GI_MAX_MIPS], h[GI_MAX_MIPS], off[GI_MAX_MIPS];
+};
+
+static MipInfo mip_info(const gi_probe_layout &l) {
+    MipInfo m;
+    memset(&m, 0, sizeof m);
+    m.count = (int)l.mip_count;
+    for (int k = 0; k < (int)l.mip_count; ++k) {
+        m.w[k] = (int)l.mip_w[k];
+        m.h[k] = (int)l.mip_h[k];
+        m.off[k] = (int)l.mip_offset[k];
+    }
+    return m;
+}
+
+// ---------------------------------------------------------------- cell moments
+// Per hemi-octahedral cell (local frame): solid angle, first moment, second
+// moment (xx yy zz xy xz yz).  Table layout [moment][cell] for coalesced reads.
+__device__ float g_moments[10][64];
+
+// Each cell is a spherical quadrilateral: the octahedral map sends the straight
+// sides of the (u, v) square to straight segments, i.e. great-circle arcs.
+// Closed forms on a spherical polygon with counter-clockwise vertices a_k:
+//   solid angle   -- sum of triangle-fan excesses (Van Oosterom & Strackee 1983)
+//   first moment  -- 1/2 sum_k theta_k n_k  (Arvo 1995), n_k = unit(a_k x a_k+1)
+//   second moment -- 1/3 (Omega I + sum_k e_k n_k^T), e_k = integral of the
+//                    direction along arc k = a sin(theta) + c (1 - cos(theta)),
+//                    c the in-plane unit vector orthogonal to a towards b
+//                    (Stokes' theorem on the sphere applied to w_i w).
+static void hemioct_dir(double u, double v, double out[3]) {
+    double x = 0.5 * (u + v), y = 0.5 * (u - v);
+    double z = 1.0 - fabs(x) - fabs(y);
+    double n = sqrt(x * x + y * y + z * z);
+    out[0] = x / n;
+    out[1] = y / n;
+    out[2] = z / n;
+}
+
+static void cross3(const double a[3], const double b[3], double o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void cell_moments_closed_form(int c, double out[10]) {
+    const double h = 0.25;
+    const double u0 = -1.0 + (c & 7) * h, v0 = -1.0 + (c >> 3) * h;
+    // (u, v) -> (x, y) has determinant -1/2: reverse the square's order to get
+    // counter-clockwise seen from outside the sphere.
+    double V[4][3];
+    hemioct_dir(u0, v0, V[0]);
+    hemioct_dir(u0, v0 + h, V[1]);
+    hemioct_dir(u0 + h, v0 + h, V[2]);
+    hemioct_dir(u0 + h, v0, V[3]);
+    double omega = 0.0;
+    for (int k = 1; k < 3; ++k) {
+        double bc[3];
+        cross3(V[k], V[k + 1], bc);
+        double num = dot3(V[0], bc);
+        double den = 1.0 + dot3(V[0], V[k]) + dot3(V[k], V[k + 1]) + dot3(V[k + 1], V[0]);
+        omega += 2.0 * atan2(num, den);
+    }
+    double m1[3] = {0, 0, 0};
+    double m2[3][3] = {{omega, 0, 0}, {0, omega, 0}, {0, 0, omega}};
+    for (int k = 0; k < 4; ++k) {
+        const double *a = V[k], *b = V[(k + 1) & 3];
+        double cr[3];
+        cross3(a, b, cr);
+        double sn = sqrt(dot3(cr, cr));
+        double cs = dot3(a, b);
+        double th = atan2(sn, cs);
+        double nk[3] = {cr[0] / sn, cr[1] / sn, cr[2] / sn};
+        double e[3];
+        for (int i = 0; i < 3; ++i) {
+            double cdir = (b[i] - a[i] * cs) / sn;
+            e[i] = a[i] * sn + cdir * (1.0 - cs);
+            m1[i] += 0.5 * th * nk[i];
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) m2[i][j] += e[i] * nk[j];
+    }
+    out[0] = omega;
+    for (int i = 0; i < 3; ++i) out[1 + i] = m1[i];
+    const double s = 1.0 / 3.0;
+    out[4] = s * m2[0][0];
+    out[5] = s * m2[1][1];
+    out[6] = s * m2[2][2];
+    out[7] = s * 0.5 * (m2[0][1] + m2[1][0]);
+    out[8] = s * 0.5 * (m2[0][2] + m2[2][0]);
+    out[9] = s * 0.5 * (m2[1][2] + m2[2][1]);
+}
+
+static std::mutex g_moments_mutex;
+static bool g_moments_ready[64];
+
+static gi_status ensure_moments() {
+    int dev = 0;
+    gi_status s = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s != GI_OK) return s;
+    std::lock_guard<std::mutex> lock(g_moments_mutex);
+    if (dev >= 0 && dev < 64 && g_moments_ready[dev]) return GI_OK;
+    float table[10][64];
+    for (int c = 0; c < 64; ++c) {
+        double m[10];
+        cell_moments_closed_form(c, m);
+        for (int k = 0; k < 10; ++k) table[k][c] = (float)m[k];
+    }
+    s = cuda_status(cudaMemcpyToSymbol(g_moments, table, sizeof table), "upload cell moments");
+    if (s == GI_OK && dev >= 0 && dev < 64) g_moments_ready[dev] = true;
+    return s;
+}
+
+// ---------------------------------------------------------------- spawn
+struct SpawnArgs {
+    const float4 *gbuf;
+    uint32_t width, height;
+    CamParams cam;
+    int jx, jy;
+    uint32_t *mask;
+    float4 *pos;
+    float4 *nrm;
+    uint32_t tiles_x, tiles_y;
+    MipInfo mi;
+};
+
+// Block of 16x16 tiles: level 0 plus levels 1..4 of its region, built in shared memory.
+__global__ void __launch_bounds__(256) k_spawn(SpawnArgs a) {
+    __shared__ uint32_t s_lvl[2][16][16];
+    const int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
+    const uint32_t tx = blockIdx.x * 16 + lx, ty = blockIdx.y * 16 + ly;
+    uint32_t m = GI_PROBE_NONE;
+    if (tx < a.tiles_x && ty < a.tiles_y) {
+        const uint32_t px = min(8u * tx + (uint32_t)a.jx, a.width - 1u);
+        const uint32_t py = min(8u * ty + (uint32_t)a.jy, a.height - 1u);
+        const float4 nd = __ldg(a.gbuf + (size_t)py * a.width + px);
+        const bool valid = isfinite(nd.w) && nd.w >= 0.0f;
+        const uint32_t p = ty * a.tiles_x + tx;
+        if (valid) {
+            m = (py << 16) | px;
+            const float3 d = cam_ray_dir(a.cam, (float)px, (float)py);
+            a.pos[p] = make_float4(a.cam.pos[0] + d.x * nd.w, a.cam.pos[1] + d.y * nd.w, a.cam.pos[2] + d.z * nd.w,
+                                   nd.w);
+            a.nrm[p] = make_float4(nd.x, nd.y, nd.z, 1.0f);
+        } else {
+            a.pos[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+            a.nrm[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        a.mask[ty * a.tiles_x + tx] = m;
+    }
+    s_lvl[0][ly][lx] = m;
+    __syncthreads();
+    // level L keeps the first valid probe of each 2x2 block in the order (0,0), (1,0), (0,1), (1,1)
+    for (int L = 1; L <= 4 && L < a.mi.count; ++L) {
+        const int n = 16 >> L;
+        const int src = (L - 1) & 1, dst = L & 1;
+        uint32_t v = GI_PROBE_NONE;
+        const int x = threadIdx.x % n, y = threadIdx.x / n;
+        if ((int)threadIdx.x < n * n) {
+            const uint32_t c0 = s_lvl[src][2 * y][2 * x], c1 = s_lvl[src][2 * y][2 * x + 1];
+            const uint32_t c2 = s_lvl[src][2 * y + 1][2 * x], c3 = s_lvl[src][2 * y + 1][2 * x + 1];
+            v = c0 != GI_PROBE_NONE ? c0 : (c1 != GI_PROBE_NONE ? c1 : (c2 != GI_PROBE_NONE ? c2 : c3));
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < n * n) {
+            s_lvl[dst][y][x] = v;
+            const int X = blockIdx.x * n + x, Y = blockIdx.y * n + y;
+            if (X < a.mi.w[L] && Y < a.mi.h[L]) a.mask[a.mi.off[L] + Y * a.mi.w[L] + X] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Levels 5 and up, from level 4, in one block.
+__global__ void __launch_bounds__(1024) k_mip_tail(uint32_t *mask, MipInfo mi) {
+    for (int L = 5; L < mi.count; ++L) {
+        const int w = mi.w[L], h = mi.h[L], pw = mi.w[L - 1], ph = mi.h[L - 1];
+        const uint32_t *src = mask + mi.off[L - 1];
+        for (int t = threadIdx.x; t < w * h; t += blockDim.x) {
+            const int x = t % w, y = t / w;
+            uint32_t v = GI_PROBE_NONE;
+            const int cx[4] = {2 * x, 2 * x + 1, 2 * x, 2 * x + 1}, cy[4] = {2 * y, 2 * y, 2 * y + 1, 2 * y + 1};
+            for (int k = 0; k < 4 && v == GI_PROBE_NONE; ++k)
+                if (cx[k] < pw && cy[k] < ph) v = __ldcg(src + cy[k] * pw + cx[k]);
+            mask[mi.off[L] + y * w + x] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- probe irradiance
+struct IntegrateArgs {
+    const uint32_t *slot_ids;
+    const void *resolved;
+    int f16;
+    uint32_t slots;
+    const float4 *nrm;
+    float *sh;
+    uint32_t probes;
+    uint32_t rpp;
+    float env[3];
+};
+
+__device__ __forceinline__ float3 fetch_resolved(const void *r, int f16, uint32_t s) {
+    if (f16) {
+        const ushort4 h = __ldg(reinterpret_cast<const ushort4 *>(r) + s);
+        return make_float3(__half2float(__ushort_as_half(h.x)), __half2float(__ushort_as_half(h.y)),
+                           __half2float(__ushort_as_half(h.z)));
+    }
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(r) + s);
+    return make_float3(v.x, v.y, v.z);
+}
+
+// One warp per probe; lane l owns cells l and l + 32.
+__global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) {
+    const uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= a.probes) return;
+    const float4 n4 = __ldg(a.nrm + p);
+    float *out = a.sh + (size_t)p * GI_SH_STRIDE;
+    if (n4.w == 0.0f) {
+        if (lane < GI_SH_STRIDE) out[lane] = 0.0f;
+        return;
+    }
+    float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float cnt[2] = {0.f, 0.f};
+    const uint32_t *ids = a.slot_ids + (size_t)p * a.rpp;
+    for (uint32_t k = lane; k < a.rpp; k += 32) {
+        const int hsel = (k >> 5) & 1;  // cell k mod 64 = lane + 32 hsel
+        const uint32_t s = __ldcs(ids + k);
+        float3 r;
+        bool has = true;
+        if (s < a.slots)
+            r = fetch_resolved(a.resolved, a.f16, s);
+        else if (s == GI_SLOT_MISS)
+            r = make_float3(a.env[0], a.env[1], a.env[2]);
+        else {
+            has = false;
+            r = make_float3(0.f, 0.f, 0.f);
+        }
+        if (has) {
+            if (hsel) {
+                acc[1][0] += r.x; acc[1][1] += r.y; acc[1][2] += r.z; cnt[1] += 1.0f;
+            } else {
+                acc[0][0] += r.x; acc[0][1] += r.y; acc[0][2] += r.z; cnt[0] += 1.0f;
+            }
+        }
+    }
+    // cell means, then the radiance backup: cells without sample take the mean of populated cells
+    float L[2][3], pop[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int h = 0; h < 2; ++h) {
+        const float inv = cnt[h] > 0.f ? 1.0f / cnt[h] : 0.0f;
+        for (int c = 0; c < 3; ++c) {
+            L[h][c] = acc[h][c] * inv;
+            pop[c] += L[h][c];
+        }
+        pop[3] += cnt[h] > 0.f ? 1.0f : 0.0f;
+    }
+    for (int o = 16; o; o >>= 1)
+        for (int c = 0; c < 4; ++c) pop[c] += __shfl_xor_sync(kFullMask, pop[c], o);
+    const float binv = pop[3] > 0.f ? 1.0f / pop[3] : 0.0f;
+    for (int h = 0; h < 2; ++h)
+        if (cnt[h] == 0.f)
+            for (int c = 0; c < 3; ++c) L[h][c] = pop[c] * binv;
+    // direction moments of the probe radiance (local frame): 10 moments x RGB
+    float S[10][3];
+    for (int m = 0; m < 10; ++m) {
+        const float w0 = g_moments[m][lane], w1 = g_moments[m][lane + 32];
+        for (int c = 0; c < 3; ++c) S[m][c] = w0 * L[0][c] + w1 * L[1][c];
+    }
+    for (int o = 16; o; o >>= 1)
+        for (int m = 0; m < 10; ++m)
+            for (int c = 0; c < 3; ++c) S[m][c] += __shfl_xor_sync(kFullMask, S[m][c], o);
+    // probe frame (Duff et al. 2017): columns t, b, n of R
+    const float nx = n4.x, ny = n4.y, nz = n4.z;
+    const float sgn = copysignf(1.0f, nz);
+    const float ia = -1.0f / (sgn + nz);
+    const float bb = nx * ny * ia;
+    const float R[3][3] = {{1.0f + sgn * nx * nx * ia, bb, nx},
+                           {sgn * bb, sgn + ny * ny * ia, ny},
+                           {-sgn * nx, -ny, nz}};
+    // this lane's output element k = coefficient * 3 + channel
+    if (lane >= 27) {
+        if (lane == 27) out[27] = 0.0f;
+        return;
+    }
+    const int coef = lane / 3, c = lane - 3 * (lane / 3);
+    float Sc[10];  // this lane's channel, selected without dynamic indexing
+#pragma unroll
+    for (int m = 0; m < 10; ++m) Sc[m] = c == 0 ? S[m][0] : (c == 1 ? S[m][1] : S[m][2]);
+    const float S0 = Sc[0];
+    float S1[3], S2[3][3];
+    for (int i = 0; i < 3; ++i) S1[i] = Sc[1 + i];
+    S2[0][0] = Sc[4]; S2[1][1] = Sc[5]; S2[2][2] = Sc[6];
+    S2[0][1] = S2[1][0] = Sc[7];
+    S2[0][2] = S2[2][0] = Sc[8];
+    S2[1][2] = S2[2][1] = Sc[9];
+    float W1[3], W2[3][3];
+    for (int i = 0; i < 3; ++i) W1[i] = R[i][0] * S1[0] + R[i][1] * S1[1] + R[i][2] * S1[2];
+    for (int i = 0; i < 3; ++i)
+        for (int j = i; j < 3; ++j) {
+            float acc2 = 0.f;
+            for (int p2 = 0; p2 < 3; ++p2)
+                for (int q2 = 0; q2 < 3; ++q2) acc2 += R[i][p2] * R[j][q2] * S2[p2][q2];
+            W2[i][j] = W2[j][i] = acc2;
+        }
+    // real SH basis, bands 0..2: c0; c1 y, c1 z, c1 x; c2 xy, c2 yz, c3 (3z^2-1), c2 xz, c4 (x^2-y^2)
+    const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f, C2 = 1.0925484305920792f,
+                C3 = 0.31539156525252005f, C4 = 0.5462742152960396f;
+    float v;
+    switch (coef) {
+    case 0: v = C0 * S0; break;
+    case 1: v = C1 * W1[1]; break;
+    case 2: v = C1 * W1[2]; break;
+    case 3: v = C1 * W1[0]; break;
+    case 4: v = C2 * W2[0][1]; break;
+    case 5: v = C2 * W2[1][2]; break;
+    case 6: v = C3 * (3.0f * W2[2][2] - S0); break;
+    case 7: v = C2 * W2[0][2]; break;
+    default: v = C4 * (W2[0][0] - W2[1][1]); break;
+    }
+    out[lane] = v;
+}
+
+// ---------------------------------------------------------------- interpolation
+struct InterpArgs {
+    const float4 *gbuf;
+    uint32_t width, height;
+    CamParams cam;
+    float dscale;
+    const uint32_t *mask;
+    MipInfo mi;
+    const float4 *ppos;
+    const float4 *pnrm;
+    const float *sh;
+    uint32_t tiles_x;
+    float4 *out;
+};
+
+// Algorithm 3: from probe-space position (tx, ty) plus the offset, climb the MIP
+// chain (halving the position, floor) until a probe is found or the position
+// leaves the level.
+__device__ __forceinline__ uint32_t find_closest_probe(const uint32_t *mask, const MipInfo &mi, int tx, int ty, int ox,
+                                                       int oy) {
+#pragma unroll
+    for (int m = 0; m < GI_MAX_MIPS; ++m) {
+        if (m >= mi.count) break;
+        const int x = tx + ox, y = ty + oy;
+        if (x < 0 || y < 0 || x >= mi.w[m] || y >= mi.h[m]) break;
+        const uint32_t p = __ldg(mask + mi.off[m] + y * mi.w[m] + x);
+        if (p != GI_PROBE_NONE) return p;
+        tx >>= 1;
+        ty >>= 1;
+    }
+    return GI_PROBE_NONE;
+}
+
+// Block = 16x16 pixels starting at (16 bx - 4, 16 by - 4); warp = 8x4 pixels that
+// share one base tile, so the four neighbour probes are read once per warp.
+__global__ void __launch_bounds__(256) k_interpolate(InterpArgs a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = (int)blockIdx.x * 16 - 4 + 8 * (warp & 1) + (lane & 7);
+    const int y = (int)blockIdx.y * 16 - 4 + 4 * (warp >> 1) + (lane >> 3);
+    if (x < 0 || y < 0 || x >= (int)a.width || y >= (int)a.height) return;
+    const size_t pix = (size_t)y * a.width + x;
+    const float4 nd = __ldcs(a.gbuf + pix);
+    if (!(isfinite(nd.w) && nd.w >= 0.0f)) {
+        __stcs(a.out + pix, make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
+        return;
+    }
+    // positions relative to the camera: plane distances are small differences of
+    // points that share the camera origin, which cancels exactly here
+    const float3 d = cam_ray_dir(a.cam, (float)x, (float)y);
+    const float Px = d.x * nd.w, Py = d.y * nd.w, Pz = d.z * nd.w;
+    const float nx = nd.x, ny = nd.y, nz = nd.z;
+    const float cs = a.dscale * nd.w;
+    const int tx = (x - 4) >> 3, ty = (y - 4) >> 3;
+    const float fx = ((float)((x - 4) - 8 * tx) + 0.5f) * 0.125f;
+    const float fy = ((float)((y - 4) - 8 * ty) + 0.5f) * 0.125f;
+    // A_l Y_lm(n_p)
+    const float PI = 3.14159265358979f;
+    const float A0 = PI, A1 = 2.0f * PI / 3.0f, A2 = 0.25f * PI;
+    const float Yb[9] = {A0 * 0.28209479177387814f,
+                         A1 * 0.4886025119029199f * ny,
+                         A1 * 0.4886025119029199f * nz,
+                         A1 * 0.4886025119029199f * nx,
+                         A2 * 1.0925484305920792f * nx * ny,
+                         A2 * 1.0925484305920792f * ny * nz,
+                         A2 * 0.31539156525252005f * (3.0f * nz * nz - 1.0f),
+                         A2 * 1.0925484305920792f * nx * nz,
+                         A2 * 0.5462742152960396f * (nx * nx - ny * ny)};
+    float wsum = 0.f, es[3] = {0.f, 0.f, 0.f}, er[3] = {0.f, 0.f, 0.f};
+    int nfound = 0;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const int ox = o & 1, oy = o >> 1;
+        const uint32_t q = find_closest_probe(a.mask, a.mi, tx, ty, ox, oy);
+        if (q == GI_PROBE_NONE) continue;
+        const uint32_t qx = q & 0xFFFFu, qy = q >> 16;
+        const uint32_t pi = (qy >> 3) * a.tiles_x + (qx >> 3);
+        const float tq = __ldg(a.ppos + pi).w;
+        const float3 dq = cam_ray_dir(a.cam, (float)qx, (float)qy);
+        const float4 nq = __ldg(a.pnrm + pi);
+        const float bil = (ox ? fx : 1.0f - fx) * (oy ? fy : 1.0f - fy);
+        const float nd1 = fmaxf(nx * nq.x + ny * nq.y + nz * nq.z, 0.0f);
+        const float n2 = nd1 * nd1, n4 = n2 * n2, n8 = n4 * n4;
+        const float pd = fabsf((dq.x * tq - Px) * nx + (dq.y * tq - Py) * ny + (dq.z * tq - Pz) * nz);
+        const float wd = fmaxf(1.0f - pd / cs, 0.0f);
+        const float w = bil * n8 * wd;
+        const float4 *c4 = reinterpret_cast<const float4 *>(a.sh + (size_t)pi * GI_SH_STRIDE);
+        float c[28];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            const float4 v = __ldg(c4 + k);
+            c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
+        }
+        float E[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) E[ch] += Yb[k] * c[3 * k + ch];
+        wsum += w;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            es[ch] += w * E[ch];
+            er[ch] += E[ch];
+        }
+        ++nfound;
+    }
+    float4 r;
+    if (nfound == 0) {
+        r = make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_NONE);
+    } else if (wsum > 0.0f) {
+        const float inv = 1.0f / wsum;
+        r = make_float4(es[0] * inv, es[1] * inv, es[2] * inv, (float)GI_INTERP_OK);
+    } else {
+        const float inv = 1.0f / (float)nfound;
+        r = make_float4(er[0] * inv, er[1] * inv, er[2] * inv, (float)GI_INTERP_RELAXED);
+    }
+    __stcs(a.out + pix, r);
+}
+
+static bool layout_matches(const gi_probe_layout &l, uint32_t w, uint32_t h) {
+    return l.tiles_x == (w + 7) / 8 && l.tiles_y == (h + 7) / 8 && l.num_probes == l.tiles_x * l.tiles_y &&
+           l.mip_count >= 1 && l.mip_count <= GI_MAX_MIPS;
+}
+
+static int halton_times8(uint32_t i, uint32_t base) {
+    // floor(8 * radical_inverse_base(i)) with exact integer arithmetic
+    uint64_t num = 0, den = 1;
+    while (i) {
+        num = num * base + i % base;
+        den *= base;
+        i /= base;
+    }
+    return (int)((8 * num) / den);
+}
+
+} // namespace gi
+
+using namespace gi;
+
+extern "C" {
+
+gi_status gi_cell_moments(double *out640) {
+    if (!out640) {
+        set_error("gi_cell_moments: out is NULL");
+        return GI_ERR_INVALID_ARG;
+    }
+    for (int c = 0; c < 64; ++c) cell_moments_closed_form(c, out640 + 10 * c);
+    return GI_OK;
+}
+
+gi_status gi_probes_layout(uint32_t width, uint32_t height, gi_probe_layout *out) {
+    if (!out || width == 0 || height == 0 || width > 65535 || height > 65535) {
+        set_error("gi_probes_layout: bad size or NULL output");
+        return GI_ERR_INVALID_ARG;
+    }
+    memset(out, 0, sizeof *out);
+    out->tiles_x = (width + 7) / 8;
+    out->tiles_y = (height + 7) / 8;
+    out->num_probes = out->tiles_x * out->tiles_y;
+    uint32_t w = out->tiles_x, h = out->tiles_y, off = 0, k = 0;
+    for (;;) {
+        out->mip_w[k] = w;
+        out->mip_h[k] = h;
+        out->mip_offset[k] = off;
+        off += w * h;
+        ++k;
+        if (w == 1 && h == 1) break;
+        w = (w + 1) / 2;
+        h = (h + 1) / 2;
+    }
+    out->mip_count = k;
+    out->mask_words = off;
+    return GI_OK;
+}
+
+gi_status gi_probes_spawn(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr, gi_stream_t stream) {
+    if (!gbuf || !pr || !view_ok(view) || !gbuf->nd || !pr->mask || !pr->pos || !pr->nrm) {
+        set_error("gi_probes_spawn: NULL argument or bad view");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (gbuf->width != view->width || gbuf->height != view->height ||
+        !layout_matches(pr->layout, view->width, view->height) || ((uintptr_t)gbuf->nd & 15) ||
+        ((uintptr_t)pr->pos & 15) || ((uintptr_t)pr->nrm & 15)) {
+        set_error("gi_probes_spawn: G-buffer/probe layout does not match the view, or misaligned buffers");
+        return GI_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    SpawnArgs a;
+    a.gbuf = reinterpret_cast<const float4 *>(gbuf->nd);
+    a.width = view->width;
+    a.height = view->height;
+    a.cam = cam_params(view);
+    a.jx = halton_times8(view->frame + 1u, 2);
+    a.jy = halton_times8(view->frame + 1u, 3);
+    a.mask = pr->mask;
+    a.pos = reinterpret_cast<float4 *>(pr->pos);
+    a.nrm = reinterpret_cast<float4 *>(pr->nrm);
+    a.tiles_x = pr->layout.tiles_x;
+    a.tiles_y = pr->layout.tiles_y;
+    a.mi = mip_info(pr->layout);
+    dim3 grid((a.tiles_x + 15) / 16, (a.tiles_y + 15) / 16);
+    k_spawn<<<grid, 256, 0, st>>>(a);
+    gi_status s = cuda_status(cudaGetLastError(), "k_spawn launch");
+    if (s == GI_OK && a.mi.count > 5) {
+        k_mip_tail<<<1, 1024, 0, st>>>(pr->mask, a.mi);
+        s = cuda_status(cudaGetLastError(), "k_mip_tail launch");
+    }
+    return s;
+}
+
+gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *pr, const uint32_t *slot_ids,
+                              uint32_t rays_per_probe, const float env[3], gi_stream_t stream) {
+    if (!cache || !pr || !pr->nrm || !pr->sh || (!slot_ids && pr->layout.num_probes > 0)) {
+        set_error("gi_probes_integrate: NULL argument");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (rays_per_probe == 0 || rays_per_probe % 64 != 0 || ((uintptr_t)pr->nrm & 15)) {
+        set_error("gi_probes_integrate: rays_per_probe must be a positive multiple of 64; nrm 16-byte aligned");
+        return GI_ERR_INVALID_ARG;
+    }
+    gi_status s = ensure_moments();
+    if (s != GI_OK) return s;
+    const CacheView cv = cache_view(cache);
+    IntegrateArgs a;
+    a.slot_ids = slot_ids;
+    a.resolved = cv.resolved;
+    a.f16 = cv.resolved_f16;
+    a.slots = cv.slots;
+    a.nrm = reinterpret_cast<const float4 *>(pr->nrm);
+    a.sh = pr->sh;
+    a.probes = pr->layout.num_probes;
+    a.rpp = rays_per_probe;
+    for (int c = 0; c < 3; ++c) a.env[c] = env ? env[c] : 0.0f;
+    if (a.probes == 0) return GI_OK;
+    const unsigned blocks = (a.probes + 7) / 8;
+    k_integrate<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    return cuda_status(cudaGetLastError(), "k_integrate launch");
+}
+
+gi_status gi_probes_interpolate(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr, float *out,
+                                gi_stream_t stream) {
+    if (!gbuf || !pr || !out || !view_ok(view) || !gbuf->nd || !pr->mask || !pr->pos || !pr->nrm || !pr->sh) {
+        set_error("gi_probes_interpolate: NULL argument or bad view");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (gbuf->width != view->width || gbuf->height != view->height ||
+        !layout_matches(pr->layout, view->width, view->height) || ((uintptr_t)gbuf->nd & 15) ||
+        ((uintptr_t)out & 15) || ((uintptr_t)pr->sh & 15)) {
+        set_error("gi_probes_interpolate: layout does not match the view, or misaligned buffers");
+        return GI_ERR_INVALID_ARG;
+    }
+    InterpArgs a;
+    a.gbuf = reinterpret_cast<const float4 *>(gbuf->nd);
+    a.width = view->width;
+    a.height = view->height;
+    a.cam = cam_params(view);
+    a.dscale = (float)distance_scale(view->fov_y, view->width, view->height);
+    a.mask = pr->mask;
+    a.mi = mip_info(pr->layout);
+    a.ppos = reinterpret_cast<const float4 *>(pr->pos);
+    a.pnrm = reinterpret_cast<const float4 *>(pr->nrm);
+    a.sh = pr->sh;
+    a.tiles_x = pr->layout.tiles_x;
+    a.out = reinterpret_cast<float4 *>(out);
+    dim3 grid((view->width + 4 + 15) / 16, (view->height + 4 + 15) / 16);
+    k_interpolate<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    return cuda_status(cudaGetLastError(), "k_interpolate launch");
+}
+
+} // extern "C"

@@ -1,0 +1,87 @@
+"""Per-view frame chain on the GPU: spawn -> cache update -> resolve ->
+probe irradiance -> per-pixel interpolation (the paper's pass order,
+Sections 2.1.1, 2.2, 2.1.4, 2.4).  PyTorch only allocates device memory;
+every step is a call into libgi.so."""
+from __future__ import annotations
+
+import torch
+
+from . import (GI_RESOLVED_F32, GI_SH_STRIDE, gi_cache_create, gi_cache_destroy, gi_cache_resolve,
+               gi_cache_update, gi_probes_integrate, gi_probes_interpolate, gi_probes_layout, gi_probes_spawn,
+               hits_from_planes, make_gbuffer, make_probes, make_view)
+
+
+def view_of(camera, frame: int):
+    """gi_view from an object with pos, fwd, right, up, fov_y, width, height."""
+    return make_view(frame, camera.width, camera.height, camera.pos, camera.fwd, camera.right, camera.up,
+                     camera.fov_y)
+
+
+class ProbeBuffers:
+    """Device buffers of the screen probes of one view size."""
+
+    def __init__(self, width: int, height: int, device="cuda"):
+        self.layout = gi_probes_layout(width, height)
+        P = self.layout.num_probes
+        self.mask = torch.empty(self.layout.mask_words, dtype=torch.int32, device=device)
+        self.pos = torch.empty((P, 4), dtype=torch.float32, device=device)
+        self.nrm = torch.empty((P, 4), dtype=torch.float32, device=device)
+        self.sh = torch.empty((P, GI_SH_STRIDE), dtype=torch.float32, device=device)
+        self.struct = make_probes(self.layout, self.mask, self.pos, self.nrm, self.sh)
+
+    def mask_levels(self):
+        """Host copies of the MIP levels of the probe mask (uint32)."""
+        m = self.mask.cpu().numpy().view("uint32")
+        lv = []
+        for k in range(self.layout.mip_count):
+            w, h, off = self.layout.mip_w[k], self.layout.mip_h[k], self.layout.mip_offset[k]
+            lv.append(m[off:off + w * h].reshape(h, w))
+        return lv
+
+
+class Pipeline:
+    def __init__(self, width: int, height: int, rays_per_probe: int, log2_slots: int, cell_size=0.05,
+                 num_lods=4, alpha=0.1, evict_frames=8, max_probe=128, key_dir=0,
+                 resolved_format=GI_RESOLVED_F32, rebuild_load=0.8, device="cuda"):
+        self.width, self.height, self.rpp = width, height, rays_per_probe
+        self.probes = ProbeBuffers(width, height, device)
+        self.n_records = self.probes.layout.num_probes * rays_per_probe
+        self.slot_ids = torch.empty(self.n_records, dtype=torch.int32, device=device)
+        self.irr = torch.empty((height, width, 4), dtype=torch.float32, device=device)
+        self.cache = gi_cache_create(log2_slots, cell_size, num_lods, alpha, evict_frames, max_probe, key_dir,
+                                     resolved_format, rebuild_load)
+
+    def spawn(self, gbuf, view, stream=None):
+        gi_probes_spawn(make_gbuffer(gbuf, self.width, self.height), view, self.probes.struct, stream)
+
+    def update(self, records, view, stream=None):
+        gi_cache_update(self.cache, hits_from_planes(records, self.n_records), view, self.slot_ids, stream)
+
+    def resolve(self, frame: int, stream=None):
+        gi_cache_resolve(self.cache, frame, stream)
+
+    def integrate(self, env=(0.0, 0.0, 0.0), stream=None):
+        gi_probes_integrate(self.cache, self.probes.struct, self.slot_ids, self.rpp, env, stream)
+
+    def interpolate(self, gbuf, view, stream=None):
+        gi_probes_interpolate(make_gbuffer(gbuf, self.width, self.height), view, self.probes.struct, self.irr,
+                              stream)
+
+    def frame(self, gbuf, records, view, env=(0.0, 0.0, 0.0), stream=None):
+        """One frame of the whole path; gbuf (H, W, 4) and records (13, R) float32 on the device."""
+        self.spawn(gbuf, view, stream)
+        self.update(records, view, stream)
+        self.resolve(view.frame, stream)
+        self.integrate(env, stream)
+        self.interpolate(gbuf, view, stream)
+
+    def close(self):
+        if self.cache:
+            gi_cache_destroy(self.cache)
+            self.cache = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,90 @@
+"""libgi.so builds for sm_103a, loads without a GPU and exports every entry
+point that include/gi.h declares; host-only entry points behave as the header
+states (layout sizes, closed-form cell moments, argument validation before
+any launch)."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2310_19855_gb300 as gi
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gi.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gi.build()
+    return gi.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gi_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "gi_cache_update" in names and "gi_probes_interpolate" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_struct_sizes_match_header_layout():
+    assert ctypes.sizeof(gi.gi_view) == 72
+    assert ctypes.sizeof(gi.gi_hits) == 13 * 8 + 8
+    assert ctypes.sizeof(gi.gi_cell) == 56
+    assert ctypes.sizeof(gi.gi_cache_config) == 36
+
+
+def test_status_strings(lib):
+    assert lib.gi_status_string(gi.GI_ERR_INVALID_ARG) == b"GI_ERR_INVALID_ARG"
+    assert lib.gi_status_string(gi.GI_WARN_DROPPED) == b"GI_WARN_DROPPED"
+    assert lib.gi_version() >= 100
+
+
+def test_probe_layout(lib):
+    lay = gi.gi_probes_layout(1920, 1080)
+    assert (lay.tiles_x, lay.tiles_y, lay.num_probes) == (240, 135, 32400)
+    dims = [(lay.mip_w[k], lay.mip_h[k]) for k in range(lay.mip_count)]
+    assert dims == [(240, 135), (120, 68), (60, 34), (30, 17), (15, 9), (8, 5), (4, 3), (2, 2), (1, 1)]
+    assert lay.mask_words == sum(w * h for w, h in dims)
+    assert lay.mip_offset[3] == 240 * 135 + 120 * 68 + 60 * 34
+    lay = gi.gi_probes_layout(3, 5)
+    assert (lay.tiles_x, lay.tiles_y, lay.mip_count) == (1, 1, 1)
+
+
+def test_cell_moments_match_oracle_quadrature(lib):
+    from oracle import hemioct
+    om, m1, m2 = hemioct.moments()
+    m = gi.gi_cell_moments()
+    assert np.abs(m[:, 0] - om).max() < 1e-13
+    assert np.abs(m[:, 1:4] - m1).max() < 1e-13
+    for col, (i, j) in zip(range(4, 10), [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+        assert np.abs(m[:, col] - m2[:, i, j]).max() < 1e-13
+    assert abs(m[:, 0].sum() - 2 * math.pi) < 1e-12
+
+
+def test_invalid_arguments_are_rejected_on_the_host(lib):
+    h = ctypes.c_void_p()
+    bad = gi.gi_cache_config(40, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8)
+    assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    assert b"configuration" in lib.gi_last_error()
+    bad = gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 300, 0, 0, 0.8)  # probe runs must stay below 256
+    assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    bad = gi.gi_cache_config(16, -1.0, 4, 0.1, 8, 128, 0, 0, 0.8)
+    assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_cache_create(None, ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_cache_update(None, None, None, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_cache_resolve(None, 0, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_cache_stats(None, None, None) == gi.GI_ERR_INVALID_ARG
+    lay = gi.gi_probe_layout()
+    assert lib.gi_probes_layout(0, 10, ctypes.byref(lay)) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_probes_spawn(None, None, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_probes_interpolate(None, None, None, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_cell_moments(None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_cache_destroy(None) == gi.GI_OK

@@ -293,8 +293,8 @@ def render_gbuffer(scene: Scene, cam: Camera):
     gb = np.empty((cam.height, cam.width, 4), np.float32)
     gb[..., :3] = n
     gb[..., 3] = t
-    hit = (cam.pos[None, None, :] + d * t[..., None]).astype(np.float32)
-    hit[~np.isfinite(t)] = 0.0
+    tt = np.where(np.isfinite(t), t, np.float32(0.0))
+    hit = (cam.pos[None, None, :] + d * tt[..., None]).astype(np.float32)
     return gb, hit
 
 
