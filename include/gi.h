@@ -315,6 +315,38 @@ gi_status gi_probes_interpolate(const gi_gbuffer *gbuf, const gi_view *view, con
  * frame), computed in closed form for the spherical quadrilateral of each cell. */
 gi_status gi_cell_moments(double *out640);
 
+/* ---------------------------------------------------------------- allocation-free variant */
+/*
+ * Per-record cell means of one batch, without allocating device memory.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc -- a renderer plugin whose
+ * host engine owns the whole GPU memory budget, or a thread that must never block in the
+ * allocator -- and so cannot create a cache with gi_cache_create.
+ *
+ * Result: out (device float4[n], caller-owned) = (mean radiance of the record's cell, 1) for a
+ * hit, (env, 1) for a ray that left the scene (ray_len = +inf), (0, 0, 0, 0) for no sample.  It
+ * equals gi_cache_create(log2_slots = GI_NOALLOC_LOG2_SLOTS, cell_size, num_lods, key_dir,
+ * max_probe = 255) followed by gi_cache_update, gi_cache_resolve and gi_cache_query by slot on the
+ * same records: the cell descriptor, fixed-point sums and float32 mean are the same, with no
+ * temporal history (every call starts from an empty table).
+ *
+ * Scratch: one file-scope device array of GI_NOALLOC_SCRATCH_BYTES (about 10.5 MB) holds the
+ * table, touch list, counters and slot ids.  Every GPU that loads the library holds it until the
+ * process exits.  Each call clears the table and counters first, then overwrites the rest.  The
+ * first call on a device looks the array's address up (cudaGetSymbolAddress, with that device
+ * current) and caches it; make that first call before any stream capture.  Every call on a device
+ * shares the one array: calls that overlap on the GPU (other streams, other host threads) race
+ * and give wrong results -- serialise them.  Calls no cudaMalloc, cudaFree or allocating library.
+ *
+ * Errors: GI_ERR_INVALID_ARG for n > GI_NOALLOC_MAX_RECORDS, a NULL plane or output, a bad view,
+ * cell_size <= 0, num_lods outside 1..4 or an unknown key_dir; GI_ERR_CUDA if a launch fails.
+ */
+#define GI_NOALLOC_LOG2_SLOTS 18
+#define GI_NOALLOC_MAX_RECORDS 131072u
+#define GI_NOALLOC_SCRATCH_BYTES \
+    ((4u + 32u + 4u) * (1u << GI_NOALLOC_LOG2_SLOTS) + 4u * GI_NOALLOC_MAX_RECORDS + 128u)
+gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *view, float cell_size, uint32_t num_lods,
+                                uint32_t key_dir, const float env[3], float *out, gi_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

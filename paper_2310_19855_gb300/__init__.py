@@ -28,6 +28,8 @@ GI_KEY_DIR_NORMAL, GI_KEY_DIR_RAY = 0, 1
 GI_RESOLVED_F32, GI_RESOLVED_F16 = 0, 1
 GI_MAX_MIPS = 16
 GI_SH_STRIDE = 28
+GI_NOALLOC_LOG2_SLOTS = 18
+GI_NOALLOC_MAX_RECORDS = 131072
 
 c_u32, c_u64, c_f32, c_f64, c_vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
 
@@ -118,6 +120,8 @@ def lib() -> ctypes.CDLL:
             "gi_probes_interpolate": (ctypes.c_int, [ctypes.POINTER(gi_gbuffer), ctypes.POINTER(gi_view),
                                                      ctypes.POINTER(gi_probes), c_vp, c_vp]),
             "gi_cell_moments": (ctypes.c_int, [ctypes.POINTER(c_f64)]),
+            "gi_cell_means_noalloc": (ctypes.c_int, [ctypes.POINTER(gi_hits), ctypes.POINTER(gi_view), c_f32, c_u32,
+                                                     c_u32, ctypes.POINTER(c_f32), c_vp, c_vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -278,3 +282,12 @@ def make_gbuffer(nd, width: int, height: int) -> gi_gbuffer:
     g = gi_gbuffer()
     g.nd, g.width, g.height = _ptr(nd), int(width), int(height)
     return g
+
+
+def gi_cell_means_noalloc(hits: gi_hits, view: gi_view, out, cell_size: float = 0.05, num_lods: int = 4,
+                          key_dir: int = GI_KEY_DIR_NORMAL, env=(0.0, 0.0, 0.0), stream=None) -> None:
+    """Per-record cell means of one batch without any device allocation (see gi.h): for callers
+    that cannot call cudaMalloc.  out: device float4[n]."""
+    e = (c_f32 * 3)(*[float(x) for x in env])
+    check(lib().gi_cell_means_noalloc(ctypes.byref(hits), ctypes.byref(view), float(cell_size), int(num_lods),
+                                      int(key_dir), e, _ptr(out), _stream(stream)), "gi_cell_means_noalloc")

@@ -862,3 +862,147 @@ gi_status gi_cache_export(gi_cache_t c, gi_cell *out, uint64_t capacity, uint64_
 }
 
 } // extern "C"
+
+// ==================================================================== allocation-free cell means
+// One-shot variant of the update pass for callers that cannot allocate device memory: the
+// hash table, touch list, counters and per-record slot ids live in one file-scope device array
+// (zero at module load, cleared again at the start of every call), so nothing here calls
+// cudaMalloc / cudaFree.  Every GPU that loads the library holds this array until exit.
+namespace gi {
+
+constexpr uint32_t kNoAllocSlots = 1u << GI_NOALLOC_LOG2_SLOTS;
+constexpr size_t kNoAllocTagBytes = (size_t)kNoAllocSlots * sizeof(uint32_t);
+constexpr size_t kNoAllocAccumBytes = (size_t)kNoAllocSlots * sizeof(Accum);
+constexpr size_t kNoAllocTouchBytes = (size_t)kNoAllocSlots * sizeof(uint32_t);
+constexpr size_t kNoAllocSlotIdBytes = (size_t)GI_NOALLOC_MAX_RECORDS * sizeof(uint32_t);
+constexpr size_t kNoAllocBytes =
+    kNoAllocTagBytes + kNoAllocAccumBytes + kNoAllocTouchBytes + kNoAllocSlotIdBytes + sizeof(Counters);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Host-side addresses of g_noalloc_scratch, one per device (the symbol's name is only a host
+// stand-in; the device address must come from cudaGetSymbolAddress with that device current).
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_ptr[64];
+static int g_noalloc_blocks[64];
+
+static gi_status noalloc_setup(int dev, unsigned char **base, int *blocks) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (dev < 0 || dev >= 64) {
+        set_error("gi_cell_means_noalloc: device ordinal %d out of range", dev);
+        return GI_ERR_INVALID_ARG;
+    }
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        gi_status s = cuda_status(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+        if (s != GI_OK) return s;
+        int sms = 0, per_sm = 0;
+        s = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
+        if (s == GI_OK)
+            s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<0>, kUpdThreads, 0),
+                            "occupancy");
+        if (s != GI_OK) return s;
+        g_noalloc_blocks[dev] = sms * std::max(per_sm, 1);
+        g_noalloc_ptr[dev] = p;
+    }
+    *base = static_cast<unsigned char *>(g_noalloc_ptr[dev]);
+    *blocks = g_noalloc_blocks[dev];
+    return GI_OK;
+}
+
+__global__ void k_noalloc_clear(uint4 *p, size_t n16) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// out[i] = (mean of the cell of record i, 1); (env, 1) for a ray that left the scene; 0 otherwise.
+// The mean is computed with the same float32 operations as the resolve of a cell without history.
+__global__ void k_noalloc_means(const uint32_t *slot_ids, unsigned long long n, const Accum *accum, float e0,
+                                float e1, float e2, float4 *out) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t s = slot_ids[i];
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (s < kNoAllocSlots) {
+            const Accum a = accum[s];
+            const float fc = (float)a.count;
+            o = make_float4(__fdiv_rn(__ull2float_rn(a.sum[0]), fc) * 5.9604644775390625e-8f,
+                            __fdiv_rn(__ull2float_rn(a.sum[1]), fc) * 5.9604644775390625e-8f,
+                            __fdiv_rn(__ull2float_rn(a.sum[2]), fc) * 5.9604644775390625e-8f, 1.0f);
+        } else if (s == GI_SLOT_MISS) {
+            o = make_float4(e0, e1, e2, 1.0f);
+        }
+        out[i] = o;
+    }
+}
+
+} // namespace gi
+
+extern "C" gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *view, float cell_size,
+                                           uint32_t num_lods, uint32_t key_dir, const float env[3], float *out,
+                                           gi_stream_t stream) {
+    using namespace gi;
+    if (!hits_ok(hits, key_dir) || !view_ok(view) || (hits && hits->n > 0 && !out)) {
+        set_error("gi_cell_means_noalloc: NULL record plane or output, or bad view");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (!(cell_size > 0.0f) || !isfinite(cell_size) || num_lods < 1 || num_lods > 4 ||
+        (key_dir != GI_KEY_DIR_NORMAL && key_dir != GI_KEY_DIR_RAY)) {
+        set_error("gi_cell_means_noalloc: cell_size, num_lods or key_dir out of range");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (hits->n > GI_NOALLOC_MAX_RECORDS) {
+        set_error("gi_cell_means_noalloc: %llu records exceed the maximum of %u per call",
+                  (unsigned long long)hits->n, (unsigned)GI_NOALLOC_MAX_RECORDS);
+        return GI_ERR_INVALID_ARG;
+    }
+    if (hits->n == 0) return GI_OK;
+    int dev = 0;
+    gi_status s = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+    unsigned char *base = nullptr;
+    int blocks = 0;
+    if (s == GI_OK) s = noalloc_setup(dev, &base, &blocks);
+    if (s != GI_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *tags = reinterpret_cast<uint32_t *>(base);
+    Accum *accum = reinterpret_cast<Accum *>(base + kNoAllocTagBytes);
+    uint32_t *touch = reinterpret_cast<uint32_t *>(base + kNoAllocTagBytes + kNoAllocAccumBytes);
+    uint32_t *slot_ids = reinterpret_cast<uint32_t *>(base + kNoAllocTagBytes + kNoAllocAccumBytes + kNoAllocTouchBytes);
+    Counters *ctr = reinterpret_cast<Counters *>(base + kNoAllocTagBytes + kNoAllocAccumBytes + kNoAllocTouchBytes +
+                                                 kNoAllocSlotIdBytes);
+    // the table and the counters must start at zero; the touch list and slot ids are overwritten
+    k_noalloc_clear<<<blocks, 256, 0, st>>>(reinterpret_cast<uint4 *>(base),
+                                            (kNoAllocTagBytes + kNoAllocAccumBytes) / 16);
+    s = cuda_status(cudaGetLastError(), "k_noalloc_clear launch");
+    if (s != GI_OK) return s;
+    k_noalloc_clear<<<1, 32, 0, st>>>(reinterpret_cast<uint4 *>(ctr), sizeof(Counters) / 16);
+    s = cuda_status(cudaGetLastError(), "k_noalloc_clear launch");
+    if (s != GI_OK) return s;
+    UpdateArgs a;
+    for (int k = 0; k < 3; ++k) {
+        a.p[k] = hits->pos[k];
+        a.nrm[k] = hits->nrm[k];
+        a.rad[k] = hits->rad[k];
+        a.dir[k] = hits->ray_dir[k];
+    }
+    a.len = hits->ray_len;
+    a.slot_ids = slot_ids;
+    a.n = hits->n;
+    a.tags = tags;
+    a.accum = accum;
+    a.touch = touch;
+    a.ctr = ctr;
+    a.mask = kNoAllocSlots - 1u;
+    a.max_probe = 255;
+    a.kp = key_params(cell_size, num_lods, view);
+    const int ub = (int)std::min<unsigned long long>((unsigned long long)blocks, (hits->n + kUpdThreads - 1) / kUpdThreads);
+    if (key_dir == GI_KEY_DIR_NORMAL)
+        k_update<GI_KEY_DIR_NORMAL><<<ub, kUpdThreads, 0, st>>>(a);
+    else
+        k_update<GI_KEY_DIR_RAY><<<ub, kUpdThreads, 0, st>>>(a);
+    s = cuda_status(cudaGetLastError(), "k_update launch");
+    if (s != GI_OK) return s;
+    const float e0 = env ? env[0] : 0.0f, e1 = env ? env[1] : 0.0f, e2 = env ? env[2] : 0.0f;
+    k_noalloc_means<<<ub, 256, 0, st>>>(slot_ids, hits->n, accum, e0, e1, e2, reinterpret_cast<float4 *>(out));
+    return cuda_status(cudaGetLastError(), "k_noalloc_means launch");
+}
