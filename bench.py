@@ -35,6 +35,7 @@ METRIC = "M hit records/s and ms/frame (update+resolve+query), % HBM roofline"
 UNIT = "M records/s"
 N_FRAMES_DEFAULT = 16
 L2_FLUSH_BYTES = 256 << 20
+REFERENCE_BUDGET_S = 90.0
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture (profiles/),
 # keyed to the source it was taken on; null when the source has changed since.
@@ -55,7 +56,7 @@ def _peaks():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -76,9 +77,9 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -88,8 +89,11 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
+        for (tr, ln) in self.lines:
+            # keep the samples that arrived while the timed region ran (200 ms cadence)
+            if t0 is not None and not (t0 <= tr <= t1 + 0.25):
+                continue
+            f = [x.strip() for x in ln.split(",")[1:]]
             if len(f) < 9:
                 continue
             try:
@@ -169,7 +173,13 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     frames = make_frames(min(args.frames, args.steps + args.warmup), 0)
-    Rs, times = oracle_window(frames, args.steps, args.warmup, args.sample)
+    # keep the whole run within about REFERENCE_BUDGET_S: shrink the per-step sample if needed
+    _, t_cal = oracle_window(frames, 1, 0, args.sample)
+    per_step = REFERENCE_BUDGET_S / (args.steps + args.warmup)
+    sample = min(args.sample, args.sample * per_step / max(t_cal[0], 1e-6))
+    sample = max(sample, 64.0 / (frames[0].tiles_x * frames[0].tiles_y))
+    args.sample = sample
+    Rs, times = oracle_window(frames, args.steps, args.warmup, sample)
     total = sum(times)
     value = Rs * len(times) / total / 1e6
     line = {
@@ -178,7 +188,7 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config_dict(frames[0], "oracle sample"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"first {args.sample:.3f} of the probes of each 1080p frame ({Rs} records): "
+                         "sample": f"first {args.sample:.4f} of the probes of each 1080p frame ({Rs} records): "
                                    "update + resolve + query + probe irradiance, numpy float64, one thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -209,6 +219,7 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     cfg = wl.CONFIGS[CONFIG]
     n_frames = min(args.frames, args.steps + args.warmup)
+    # (frames are cycled: frame k of the path is replayed every n_frames steps)
     frames = make_frames(n_frames, rank)
     fr0 = frames[0]
     W, H, R = fr0.camera.width, fr0.camera.height, fr0.n_records
@@ -254,13 +265,16 @@ def run_native(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    time.sleep(0.5)  # let nvidia-smi start sampling before the timed region
+    torch.cuda.synchronize()
     t_start = time.perf_counter()
+    t_start_wall = time.time()
     for j in range(args.steps):
         flush.zero_()
         step(args.warmup + j, evs[j])
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_start
-    clk = clocks.stop()
+    clk = clocks.stop(t_start_wall, time.time())
     if world > 1:
         torch.distributed.barrier()
     st = gi.gi_cache_stats(pl.cache)
@@ -376,8 +390,8 @@ def run_native(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--frames", type=int, default=N_FRAMES_DEFAULT, help="distinct pre-generated frames to cycle")
     ap.add_argument("--sample", type=float, default=0.125, help="fraction of probes in the oracle's sample")

@@ -5,7 +5,7 @@
 // Table layout (N = 2^log2_slots slots, structure of arrays):
 //   tags     u32[N]     fingerprint << 8 | (home mod 256); 0 = empty
 //   accum    Accum[N]   {u64 sum r,g,b; u32 count; u32 stamp}, one 32-byte sector
-//   resolved float4[N]  (r, g, b, 0) or half4 (r, g, b, 0)
+//   resolved float4[N]  (r, g, b, 0), or half4 (r, g, b, 0) with GI_RESOLVED_F16
 // plus a spare table of the same shape for compaction, the touch list
 // (u32[N], slots first touched since the last resolve) and a counter line.
 //
@@ -104,9 +104,15 @@ __device__ __forceinline__ unsigned long long quantize(float r, uint32_t &bad) {
 }
 
 // ---------------------------------------------------------------- update
+// A block takes at most kUpdBlockRecords records (one grid-strided chunk per iteration), so its
+// shared-memory list of first touches can never overflow and is flushed once, at the end, with
+// one global atomic: warps never wait for one another inside the loop.
 constexpr int kUpdThreads = 256;
-constexpr int kTouchBuf = 2048;
+constexpr int kUpdBlockRecords = 2048;
 constexpr unsigned kFull = 0xFFFFFFFFu;
+
+typedef uint32_t SlotWord;  // tag = fingerprint << 8 | (home mod 256); 0 = empty
+__device__ __forceinline__ uint32_t word_tag(SlotWord w) { return w; }
 
 struct UpdateArgs {
     const float *p[3];
@@ -116,8 +122,9 @@ struct UpdateArgs {
     const float *dir[3];
     uint32_t *slot_ids;
     unsigned long long n;
-    uint32_t *tags;
+    SlotWord *tags;
     Accum *accum;
+    uint32_t acc_stride;  // Accum units between consecutive slots
     uint32_t *touch;
     Counters *ctr;
     uint32_t mask;
@@ -125,21 +132,9 @@ struct UpdateArgs {
     KeyParams kp;
 };
 
-__device__ __forceinline__ void flush_touch(uint32_t *s_touch, uint32_t &s_n, uint32_t &s_base, uint32_t *touch,
-                                            Counters *ctr) {
-    // precondition: called by the whole block right after a __syncthreads()
-    if (threadIdx.x == 0) s_base = s_n ? atomicAdd(&ctr->touch_count, s_n) : 0u;
-    __syncthreads();
-    uint32_t n = s_n, base = s_base;
-    for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) touch[base + j] = s_touch[j];
-    __syncthreads();
-    if (threadIdx.x == 0) s_n = 0;
-    __syncthreads();
-}
-
 template <int KEY_DIR>
-__global__ void __launch_bounds__(kUpdThreads) k_update(UpdateArgs a) {
-    __shared__ uint32_t s_touch[kTouchBuf];
+__global__ void __launch_bounds__(kUpdThreads, 8) k_update(UpdateArgs a) {
+    __shared__ uint32_t s_touch[kUpdBlockRecords];
     __shared__ uint32_t s_n, s_base, s_clamped, s_maxp;
     if (threadIdx.x == 0) {
         s_n = 0;
@@ -213,13 +208,13 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(UpdateArgs a) {
         if (leader) {
             uint32_t s = home, k = 0;
             for (; k < a.max_probe; ++k) {
-                uint32_t t = __ldcg(a.tags + s);
+                const uint32_t t = __ldcg(a.tags + s);
                 if (t == tag) {
                     slot = s;
                     break;
                 }
                 if (t == kEmpty) {
-                    uint32_t old = atomicCAS(a.tags + s, kEmpty, tag);
+                    const uint32_t old = atomicCAS(a.tags + s, kEmpty, tag);
                     if (old == kEmpty || old == tag) {
                         slot = s;
                         break;
@@ -229,26 +224,20 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(UpdateArgs a) {
             }
             my_maxp = max(my_maxp, k + 1u);
             if (slot != GI_SLOT_NONE) {
-                Accum *ac = a.accum + slot;
+                Accum *ac = a.accum + (size_t)slot * a.acc_stride;
                 atomicAdd(&ac->sum[0], q0);
                 atomicAdd(&ac->sum[1], q1);
                 atomicAdd(&ac->sum[2], q2);
-                if (atomicAdd(&ac->count, cnt) == 0u) {
-                    uint32_t k2 = atomicAdd(&s_n, 1u);
-                    s_touch[k2] = slot;
-                }
+                // the count was cleared by the last resolve: the first adder this frame appends the slot
+                if (atomicAdd(&ac->count, cnt) == 0u) s_touch[atomicAdd(&s_n, 1u)] = slot;
             } else {
                 atomicAdd(&a.ctr->dropped, (unsigned long long)cnt);
             }
         }
         const int lead = hit ? (__ffs(peers) - 1) : lane;
         const uint32_t my_slot = __shfl_sync(kFull, slot, lead);
-        if (inr) a.slot_ids[i] = hit ? my_slot : (miss ? GI_SLOT_MISS : GI_SLOT_NONE);
-        __syncthreads();
-        if (s_n > (uint32_t)(kTouchBuf - kUpdThreads)) flush_touch(s_touch, s_n, s_base, a.touch, a.ctr);
+        if (inr) __stcs(a.slot_ids + i, hit ? my_slot : (miss ? GI_SLOT_MISS : GI_SLOT_NONE));
     }
-    __syncthreads();
-    flush_touch(s_touch, s_n, s_base, a.touch, a.ctr);
     // block totals of the statistics, one global atomic each
     my_clamped = __reduce_add_sync(kFull, my_clamped);
     my_maxp = __reduce_max_sync(kFull, my_maxp);
@@ -258,9 +247,17 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(UpdateArgs a) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        s_base = s_n ? atomicAdd(&a.ctr->touch_count, s_n) : 0u;
         if (s_clamped) atomicAdd(&a.ctr->clamped, (unsigned long long)s_clamped);
         if (s_maxp) atomicMax(&a.ctr->max_probe, s_maxp);
     }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < s_n; j += kUpdThreads) a.touch[s_base + j] = s_touch[j];
+}
+
+// Grid of k_update: enough blocks that none takes more than kUpdBlockRecords records.
+static inline int update_blocks(unsigned long long n) {
+    return (int)((n + kUpdBlockRecords - 1) / kUpdBlockRecords);
 }
 
 // ---------------------------------------------------------------- resolve
@@ -269,7 +266,9 @@ constexpr int kResThreads = 256;
 struct ResolveArgs {
     const uint32_t *touch;
     Accum *accum;
+    uint32_t acc_stride;
     void *resolved;
+    uint32_t res_stride;  // bytes between consecutive resolved values
     Counters *ctr;
     float alpha;
     uint32_t stamp_now;   // frame + 1
@@ -279,61 +278,90 @@ struct ResolveArgs {
     int f16;
 };
 
-__device__ __forceinline__ float3 load_resolved(const void *r, int f16, uint32_t s) {
+__device__ __forceinline__ float3 load_resolved(const void *r, uint32_t stride, int f16, uint32_t s) {
+    r = static_cast<const char *>(r) + (size_t)s * stride;
     if (f16) {
-        const ushort4 h = reinterpret_cast<const ushort4 *>(r)[s];
+        const ushort4 h = *reinterpret_cast<const ushort4 *>(r);
         return make_float3(__half2float(__ushort_as_half(h.x)), __half2float(__ushort_as_half(h.y)),
                            __half2float(__ushort_as_half(h.z)));
     }
-    const float4 v = reinterpret_cast<const float4 *>(r)[s];
+    const float4 v = *reinterpret_cast<const float4 *>(r);
     return make_float3(v.x, v.y, v.z);
 }
 
-__device__ __forceinline__ void store_resolved(void *r, int f16, uint32_t s, float3 v) {
+__device__ __forceinline__ void store_resolved(void *r, uint32_t stride, int f16, uint32_t s, float3 v) {
+    r = static_cast<char *>(r) + (size_t)s * stride;
     if (f16) {
         ushort4 h;
         h.x = __half_as_ushort(__float2half_rn(v.x));
         h.y = __half_as_ushort(__float2half_rn(v.y));
         h.z = __half_as_ushort(__float2half_rn(v.z));
         h.w = 0;
-        reinterpret_cast<ushort4 *>(r)[s] = h;
+        *reinterpret_cast<ushort4 *>(r) = h;
     } else {
-        reinterpret_cast<float4 *>(r)[s] = make_float4(v.x, v.y, v.z, 0.0f);
+        *reinterpret_cast<float4 *>(r) = make_float4(v.x, v.y, v.z, 0.0f);
     }
 }
 
-__global__ void __launch_bounds__(kResThreads) k_resolve(ResolveArgs a) {
+constexpr int kResUnroll = 4;
+
+__global__ void __launch_bounds__(kResThreads, 3) k_resolve(ResolveArgs a) {
     __shared__ uint32_t s_new;
     __shared__ bool s_last;
     if (threadIdx.x == 0) s_new = 0;
     __syncthreads();
     const uint32_t n = __ldcg(&a.ctr->touch_count);
+    const uint32_t stride = gridDim.x * kResThreads;
     uint32_t fresh_new = 0;
-    for (uint32_t i = blockIdx.x * kResThreads + threadIdx.x; i < n; i += gridDim.x * kResThreads) {
-        const uint32_t s = __ldcs(a.touch + i);
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.accum + s);
-        const uint4 lo = src[0], hi = src[1];
-        const unsigned long long s0 = ((unsigned long long)lo.y << 32) | lo.x;
-        const unsigned long long s1 = ((unsigned long long)lo.w << 32) | lo.z;
-        const unsigned long long s2 = ((unsigned long long)hi.y << 32) | hi.x;
-        const uint32_t count = hi.z, stamp = hi.w;
-        const float fc = (float)count;
-        // mean = sum / (count 2^24)
-        float3 m = make_float3(__fdiv_rn(__ull2float_rn(s0), fc) * 5.9604644775390625e-8f,
-                               __fdiv_rn(__ull2float_rn(s1), fc) * 5.9604644775390625e-8f,
-                               __fdiv_rn(__ull2float_rn(s2), fc) * 5.9604644775390625e-8f);
-        // no history: never resolved, or evicted by an earlier resolve (untouched E frames)
-        const bool fresh = stamp == 0u || (a.has_lr && (a.lr - (stamp - 1u)) >= a.evict);
-        fresh_new += stamp == 0u ? 1u : 0u;
-        float3 v = m;
-        if (!fresh) {
-            float3 o = load_resolved(a.resolved, a.f16, s);
-            v = make_float3(o.x + a.alpha * (m.x - o.x), o.y + a.alpha * (m.y - o.y), o.z + a.alpha * (m.z - o.z));
+    // kResUnroll touched cells per thread and iteration, their loads issued together
+    for (uint32_t i0 = blockIdx.x * kResThreads + threadIdx.x; i0 < n; i0 += kResUnroll * stride) {
+        uint32_t s[kResUnroll];
+        uint4 lo[kResUnroll], hi[kResUnroll];
+#pragma unroll
+        for (int u = 0; u < kResUnroll; ++u) {
+            const uint32_t i = i0 + u * stride;
+            s[u] = i < n ? __ldcs(a.touch + i) : 0xFFFFFFFFu;
         }
-        store_resolved(a.resolved, a.f16, s, v);
-        uint4 *dst = reinterpret_cast<uint4 *>(a.accum + s);
-        dst[0] = make_uint4(0u, 0u, 0u, 0u);
-        dst[1] = make_uint4(0u, 0u, 0u, a.stamp_now);
+#pragma unroll
+        for (int u = 0; u < kResUnroll; ++u) {
+            if (s[u] != 0xFFFFFFFFu) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
+                lo[u] = __ldcg(src);
+                hi[u] = __ldcg(src + 1);
+            }
+        }
+        bool fresh[kResUnroll];
+        float3 old[kResUnroll];
+#pragma unroll
+        for (int u = 0; u < kResUnroll; ++u) {
+            const uint32_t stamp = hi[u].w;
+            // no history: never resolved, or evicted by an earlier resolve (untouched E frames)
+            fresh[u] = stamp == 0u || (a.has_lr && (a.lr - (stamp - 1u)) >= a.evict);
+            if (s[u] != 0xFFFFFFFFu && !fresh[u]) old[u] = load_resolved(a.resolved, a.res_stride, a.f16, s[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kResUnroll; ++u) {
+            if (s[u] == 0xFFFFFFFFu) continue;
+            const unsigned long long s0 = ((unsigned long long)lo[u].y << 32) | lo[u].x;
+            const unsigned long long s1 = ((unsigned long long)lo[u].w << 32) | lo[u].z;
+            const unsigned long long s2 = ((unsigned long long)hi[u].y << 32) | hi[u].x;
+            const float fc = (float)hi[u].z;
+            // mean = sum / (count 2^24)
+            const float3 m = make_float3(__fdiv_rn(__ull2float_rn(s0), fc) * 5.9604644775390625e-8f,
+                                         __fdiv_rn(__ull2float_rn(s1), fc) * 5.9604644775390625e-8f,
+                                         __fdiv_rn(__ull2float_rn(s2), fc) * 5.9604644775390625e-8f);
+            fresh_new += hi[u].w == 0u ? 1u : 0u;
+            float3 v = m;
+            if (!fresh[u]) {
+                const float3 o = old[u];
+                v = make_float3(o.x + a.alpha * (m.x - o.x), o.y + a.alpha * (m.y - o.y),
+                                o.z + a.alpha * (m.z - o.z));
+            }
+            store_resolved(a.resolved, a.res_stride, a.f16, s[u], v);
+            uint4 *dst = reinterpret_cast<uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
+            dst[0] = make_uint4(0u, 0u, 0u, 0u);
+            dst[1] = make_uint4(0u, 0u, 0u, a.stamp_now);
+        }
     }
     fresh_new = __reduce_add_sync(kFull, fresh_new);
     if ((threadIdx.x & 31) == 0 && fresh_new) atomicAdd(&s_new, fresh_new);
@@ -362,14 +390,14 @@ __device__ __forceinline__ bool answers(uint32_t stamp, const LiveRule &r) {
     return stamp != 0u && (!r.has_lr || (r.lr - (stamp - 1u)) < r.evict);
 }
 
-__global__ void k_query_slots(const uint32_t *slot_ids, unsigned long long n, const void *resolved, int f16,
+__global__ void k_query_slots(const uint32_t *slot_ids, unsigned long long n, const void *resolved, uint32_t res_stride, int f16,
                               uint32_t slots, float e0, float e1, float e2, float4 *out) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t s = __ldcs(slot_ids + i);
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (s < slots) {
-            float3 v = load_resolved(resolved, f16, s);
+            float3 v = load_resolved(resolved, res_stride, f16, s);
             o = make_float4(v.x, v.y, v.z, 1.0f);
         } else if (s == GI_SLOT_MISS) {
             o = make_float4(e0, e1, e2, 1.0f);
@@ -379,7 +407,8 @@ __global__ void k_query_slots(const uint32_t *slot_ids, unsigned long long n, co
 }
 
 template <int KEY_DIR>
-__global__ void k_query_points(UpdateArgs a, const void *resolved, int f16, LiveRule rule, float4 *out) {
+__global__ void k_query_points(UpdateArgs a, const void *resolved, uint32_t res_stride, int f16, LiveRule rule,
+                               float4 *out) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < a.n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const float len = a.len[i];
@@ -395,11 +424,11 @@ __global__ void k_query_points(UpdateArgs a, const void *resolved, int f16, Live
             cell_of_key(key, a.mask, home, tag);
             uint32_t s = home;
             for (uint32_t k = 0; k < a.max_probe; ++k) {
-                const uint32_t t = __ldg(a.tags + s);
+                const uint32_t t = word_tag(__ldg(a.tags + s));
                 if (t == kEmpty) break;
                 if (t == tag) {
-                    if (answers(__ldg(&a.accum[s].stamp), rule)) {
-                        float3 v = load_resolved(resolved, f16, s);
+                    if (answers(__ldg(&a.accum[(size_t)s * a.acc_stride].stamp), rule)) {
+                        float3 v = load_resolved(resolved, res_stride, f16, s);
                         o = make_float4(v.x, v.y, v.z, 1.0f);
                     }
                     break;
@@ -415,13 +444,13 @@ __global__ void k_query_points(UpdateArgs a, const void *resolved, int f16, Live
 // Re-insert every live cell of the current table into the clean spare table
 // (home recovered from the slot and the tag's low byte) and clear the current
 // table behind it, so that it is clean when it becomes the spare.
-__global__ void k_rebuild(uint32_t *old_tags, Accum *old_acc, const void *old_res, uint32_t *new_tags,
-                          Accum *new_acc, void *new_res, int f16, uint32_t mask, uint32_t max_probe, LiveRule rule,
+__global__ void k_rebuild(SlotWord *old_tags, Accum *old_acc, const void *old_res, SlotWord *new_tags, Accum *new_acc,
+                          void *new_res, uint32_t res_bytes, uint32_t mask, uint32_t max_probe, LiveRule rule,
                           Counters *ctr) {
     uint32_t live = 0, dropped = 0;
     const uint32_t N = mask + 1u;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
-        const uint32_t t = old_tags[s];
+        const uint32_t t = word_tag(old_tags[s]);
         if (t == kEmpty) continue;
         const uint32_t stamp = old_acc[s].stamp;
         if (answers(stamp, rule)) {
@@ -433,10 +462,10 @@ __global__ void k_rebuild(uint32_t *old_tags, Accum *old_acc, const void *old_re
             }
             if (k < max_probe) {
                 new_acc[ns].stamp = stamp;
-                if (f16)
-                    reinterpret_cast<ushort4 *>(new_res)[ns] = reinterpret_cast<const ushort4 *>(old_res)[s];
+                if (res_bytes == 8)
+                    reinterpret_cast<uint2 *>(new_res)[ns] = reinterpret_cast<const uint2 *>(old_res)[s];
                 else
-                    reinterpret_cast<float4 *>(new_res)[ns] = reinterpret_cast<const float4 *>(old_res)[s];
+                    reinterpret_cast<uint4 *>(new_res)[ns] = reinterpret_cast<const uint4 *>(old_res)[s];
                 ++live;
             } else {
                 ++dropped;
@@ -456,11 +485,11 @@ __global__ void k_rebuild(uint32_t *old_tags, Accum *old_acc, const void *old_re
 }
 
 // ---------------------------------------------------------------- table scan for stats
-__global__ void k_scan_stats(const uint32_t *tags, const Accum *acc, uint32_t N, LiveRule rule,
+__global__ void k_scan_stats(const SlotWord *tags, const Accum *acc, uint32_t N, LiveRule rule,
                              unsigned long long *out /* occupied, live */) {
     unsigned long long occ = 0, live = 0;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
-        if (tags[s] == kEmpty) continue;
+        if (word_tag(tags[s]) == kEmpty) continue;
         ++occ;
         if (acc[s].count > 0u || answers(acc[s].stamp, rule)) ++live;
     }
@@ -483,9 +512,10 @@ struct gi_cache_s {
     uint32_t N, mask;
     int sms;
     int upd_blocks, res_blocks;
-    uint32_t *tags[2];
+    gi::SlotWord *tags[2];
     gi::Accum *accum[2];
     void *resolved[2];
+    uint32_t res_bytes;  // 16 (float4) or 8 (half4)
     int cur;
     uint32_t *touch;
     gi::Counters *ctr;
@@ -504,6 +534,7 @@ namespace gi {
 CacheView cache_view(gi_cache_t c) {
     CacheView v;
     v.resolved = c->resolved[c->cur];
+    v.resolved_stride = c->res_bytes;
     v.resolved_f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
     v.slots = c->N;
     return v;
@@ -556,6 +587,7 @@ static UpdateArgs update_args(gi_cache_s *c, const gi_hits *h, const gi_view *v,
     a.n = h->n;
     a.tags = c->tags[c->cur];
     a.accum = c->accum[c->cur];
+    a.acc_stride = 1;
     a.touch = c->touch;
     a.ctr = c->ctr;
     a.mask = c->mask;
@@ -579,8 +611,8 @@ static gi_status maybe_rebuild(gi_cache_s *c, cudaStream_t st) {
     gi_status s = cuda_status(cudaMemsetAsync(&c->ctr->occupied, 0, sizeof(uint32_t), st), "rebuild memset");
     if (s != GI_OK) return s;
     k_rebuild<<<c->sms * 8, 256, 0, st>>>(c->tags[c->cur], c->accum[c->cur], c->resolved[c->cur], c->tags[nxt],
-                                           c->accum[nxt], c->resolved[nxt], c->cfg.resolved_format == GI_RESOLVED_F16,
-                                           c->mask, c->cfg.max_probe, live_rule(c), c->ctr);
+                                           c->accum[nxt], c->resolved[nxt], c->res_bytes, c->mask, c->cfg.max_probe,
+                                           live_rule(c), c->ctr);
     s = cuda_status(cudaGetLastError(), "k_rebuild launch");
     if (s != GI_OK) return s;
     c->cur = nxt;
@@ -624,17 +656,17 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
     c->N = 1u << cfg->log2_slots;
     c->mask = c->N - 1u;
     c->last_resolved = -1;
+    c->res_bytes = cfg->resolved_format == GI_RESOLVED_F16 ? 8u : 16u;
     gi_status s = cuda_status(cudaGetDevice(&c->device), "cudaGetDevice");
     if (s == GI_OK) s = cuda_status(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device), "sm count");
     const size_t N = c->N;
-    const size_t res_bytes = cfg->resolved_format == GI_RESOLVED_F16 ? 8 : 16;
     for (int k = 0; k < 2 && s == GI_OK; ++k) {
-        s = cuda_status(cudaMalloc(&c->tags[k], N * 4), "cudaMalloc tags");
+        s = cuda_status(cudaMalloc(&c->tags[k], N * sizeof(SlotWord)), "cudaMalloc tags");
         if (s == GI_OK) s = cuda_status(cudaMalloc(&c->accum[k], N * sizeof(Accum)), "cudaMalloc accum");
-        if (s == GI_OK) s = cuda_status(cudaMalloc(&c->resolved[k], N * res_bytes), "cudaMalloc resolved");
-        if (s == GI_OK) s = cuda_status(cudaMemset(c->tags[k], 0, N * 4), "memset");
+        if (s == GI_OK) s = cuda_status(cudaMalloc(&c->resolved[k], N * c->res_bytes), "cudaMalloc resolved");
+        if (s == GI_OK) s = cuda_status(cudaMemset(c->tags[k], 0, N * sizeof(SlotWord)), "memset");
         if (s == GI_OK) s = cuda_status(cudaMemset(c->accum[k], 0, N * sizeof(Accum)), "memset");
-        if (s == GI_OK) s = cuda_status(cudaMemset(c->resolved[k], 0, N * res_bytes), "memset");
+        if (s == GI_OK) s = cuda_status(cudaMemset(c->resolved[k], 0, N * c->res_bytes), "memset");
     }
     if (s == GI_OK) s = cuda_status(cudaMalloc(&c->touch, N * 4), "cudaMalloc touch");
     if (s == GI_OK) s = cuda_status(cudaMalloc(&c->ctr, sizeof(Counters)), "cudaMalloc counters");
@@ -647,7 +679,7 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
         s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<0>, kUpdThreads, 0),
                         "occupancy");
         c->upd_blocks = c->sms * std::max(per_sm, 1);
-        c->res_blocks = c->sms * 4;
+        c->res_blocks = c->sms * 3;
     }
     if (s == GI_OK) s = cuda_status(cudaDeviceSynchronize(), "create sync");
     if (s != GI_OK) {
@@ -689,8 +721,7 @@ gi_status gi_cache_update(gi_cache_t c, const gi_hits *hits, const gi_view *view
     c->updates++;
     if (hits->n == 0) return GI_OK;
     UpdateArgs a = update_args(c, hits, view, slot_ids);
-    unsigned long long need = (hits->n + kUpdThreads - 1) / kUpdThreads;
-    int blocks = (int)std::min<unsigned long long>((unsigned long long)c->upd_blocks, need);
+    const int blocks = update_blocks(hits->n);
     if (c->cfg.key_dir == GI_KEY_DIR_NORMAL)
         k_update<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(a);
     else
@@ -714,7 +745,9 @@ gi_status gi_cache_resolve(gi_cache_t c, uint32_t frame, gi_stream_t stream) {
     ResolveArgs a;
     a.touch = c->touch;
     a.accum = c->accum[c->cur];
+    a.acc_stride = 1;
     a.resolved = c->resolved[c->cur];
+    a.res_stride = c->res_bytes;
     a.ctr = c->ctr;
     a.alpha = c->cfg.alpha;
     a.stamp_now = frame + 1u;
@@ -751,7 +784,7 @@ gi_status gi_cache_query(gi_cache_t c, const gi_query *q, float *out, gi_stream_
     const int f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
     int blocks = (int)std::min<unsigned long long>((unsigned long long)c->sms * 16, (q->n + 255) / 256);
     if (q->slot_ids) {
-        k_query_slots<<<blocks, 256, 0, st>>>(q->slot_ids, q->n, c->resolved[c->cur], f16, c->N, q->env[0],
+        k_query_slots<<<blocks, 256, 0, st>>>(q->slot_ids, q->n, c->resolved[c->cur], c->res_bytes, f16, c->N, q->env[0],
                                               q->env[1], q->env[2], reinterpret_cast<float4 *>(out));
     } else {
         if (!q->points || !hits_ok(q->points, c->cfg.key_dir) || q->points->n < q->n || !view_ok(q->view)) {
@@ -761,10 +794,10 @@ gi_status gi_cache_query(gi_cache_t c, const gi_query *q, float *out, gi_stream_
         UpdateArgs a = update_args(c, q->points, q->view, nullptr);
         a.n = q->n;
         if (c->cfg.key_dir == GI_KEY_DIR_NORMAL)
-            k_query_points<GI_KEY_DIR_NORMAL><<<blocks, 256, 0, st>>>(a, c->resolved[c->cur], f16, live_rule(c),
+            k_query_points<GI_KEY_DIR_NORMAL><<<blocks, 256, 0, st>>>(a, c->resolved[c->cur], c->res_bytes, f16, live_rule(c),
                                                                       reinterpret_cast<float4 *>(out));
         else
-            k_query_points<GI_KEY_DIR_RAY><<<blocks, 256, 0, st>>>(a, c->resolved[c->cur], f16, live_rule(c),
+            k_query_points<GI_KEY_DIR_RAY><<<blocks, 256, 0, st>>>(a, c->resolved[c->cur], c->res_bytes, f16, live_rule(c),
                                                                    reinterpret_cast<float4 *>(out));
     }
     return cuda_status(cudaGetLastError(), "k_query launch");
@@ -813,11 +846,11 @@ gi_status gi_cache_export(gi_cache_t c, gi_cell *out, uint64_t capacity, uint64_
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = c->N;
     const int f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
-    std::vector<uint32_t> tags(N);
+    std::vector<SlotWord> tags(N);
     std::vector<Accum> acc(N);
-    std::vector<unsigned char> res(N * (f16 ? 8 : 16));
+    std::vector<unsigned char> res(N * c->res_bytes);
     gi_status s = cuda_status(cudaStreamSynchronize(st), "export sync");
-    if (s == GI_OK) s = cuda_status(cudaMemcpy(tags.data(), c->tags[c->cur], N * 4, cudaMemcpyDeviceToHost), "export");
+    if (s == GI_OK) s = cuda_status(cudaMemcpy(tags.data(), c->tags[c->cur], N * sizeof(SlotWord), cudaMemcpyDeviceToHost), "export");
     if (s == GI_OK)
         s = cuda_status(cudaMemcpy(acc.data(), c->accum[c->cur], N * sizeof(Accum), cudaMemcpyDeviceToHost), "export");
     if (s == GI_OK)
@@ -838,10 +871,10 @@ gi_status gi_cache_export(gi_cache_t c, gi_cell *out, uint64_t capacity, uint64_
         cell.count = a.count;
         cell.stamp = a.stamp;
         if (f16) {
-            const __half *h = reinterpret_cast<const __half *>(res.data()) + 4 * (size_t)i;
+            const __half *h = reinterpret_cast<const __half *>(res.data() + (size_t)i * c->res_bytes);
             for (int k = 0; k < 3; ++k) cell.value[k] = __half2float(h[k]);
         } else {
-            const float *f = reinterpret_cast<const float *>(res.data()) + 4 * (size_t)i;
+            const float *f = reinterpret_cast<const float *>(res.data() + (size_t)i * c->res_bytes);
             for (int k = 0; k < 3; ++k) cell.value[k] = f[k];
         }
         cell.slot = i;
@@ -871,7 +904,7 @@ gi_status gi_cache_export(gi_cache_t c, gi_cell *out, uint64_t capacity, uint64_
 namespace gi {
 
 constexpr uint32_t kNoAllocSlots = 1u << GI_NOALLOC_LOG2_SLOTS;
-constexpr size_t kNoAllocTagBytes = (size_t)kNoAllocSlots * sizeof(uint32_t);
+constexpr size_t kNoAllocTagBytes = (size_t)kNoAllocSlots * sizeof(SlotWord);
 constexpr size_t kNoAllocAccumBytes = (size_t)kNoAllocSlots * sizeof(Accum);
 constexpr size_t kNoAllocTouchBytes = (size_t)kNoAllocSlots * sizeof(uint32_t);
 constexpr size_t kNoAllocSlotIdBytes = (size_t)GI_NOALLOC_MAX_RECORDS * sizeof(uint32_t);
@@ -964,7 +997,7 @@ extern "C" gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *v
     if (s == GI_OK) s = noalloc_setup(dev, &base, &blocks);
     if (s != GI_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    uint32_t *tags = reinterpret_cast<uint32_t *>(base);
+    SlotWord *tags = reinterpret_cast<SlotWord *>(base);
     Accum *accum = reinterpret_cast<Accum *>(base + kNoAllocTagBytes);
     uint32_t *touch = reinterpret_cast<uint32_t *>(base + kNoAllocTagBytes + kNoAllocAccumBytes);
     uint32_t *slot_ids = reinterpret_cast<uint32_t *>(base + kNoAllocTagBytes + kNoAllocAccumBytes + kNoAllocTouchBytes);
@@ -990,12 +1023,13 @@ extern "C" gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *v
     a.n = hits->n;
     a.tags = tags;
     a.accum = accum;
+    a.acc_stride = 1;
     a.touch = touch;
     a.ctr = ctr;
     a.mask = kNoAllocSlots - 1u;
     a.max_probe = 255;
     a.kp = key_params(cell_size, num_lods, view);
-    const int ub = (int)std::min<unsigned long long>((unsigned long long)blocks, (hits->n + kUpdThreads - 1) / kUpdThreads);
+    const int ub = update_blocks(hits->n);
     if (key_dir == GI_KEY_DIR_NORMAL)
         k_update<GI_KEY_DIR_NORMAL><<<ub, kUpdThreads, 0, st>>>(a);
     else

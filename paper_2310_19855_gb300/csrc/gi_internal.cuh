@@ -62,7 +62,8 @@ CamParams cam_params(const gi_view *v);
 
 // Cache internals needed by the probe kernels.
 struct CacheView {
-    const void *resolved;  // float4[N] or ushort4 (half) [N]
+    const void *resolved;      // resolved radiance of slot 0: float4, or half4 (ushort4)
+    uint32_t resolved_stride;  // bytes between the resolved values of consecutive slots
     int resolved_f16;
     uint32_t slots;
 };

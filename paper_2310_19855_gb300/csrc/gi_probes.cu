@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(1024) k_mip_tail(uint32_t *mask, MipInfo mi) {
 struct IntegrateArgs {
     const uint32_t *slot_ids;
     const void *resolved;
+    uint32_t res_stride;
     int f16;
     uint32_t slots;
     const float4 *nrm;
@@ -219,14 +220,40 @@ struct IntegrateArgs {
     float env[3];
 };
 
-__device__ __forceinline__ float3 fetch_resolved(const void *r, int f16, uint32_t s) {
+__device__ __forceinline__ float3 fetch_resolved(const void *r, uint32_t stride, int f16, uint32_t s) {
+    r = static_cast<const char *>(r) + (size_t)s * stride;
     if (f16) {
-        const ushort4 h = __ldg(reinterpret_cast<const ushort4 *>(r) + s);
+        const ushort4 h = __ldg(reinterpret_cast<const ushort4 *>(r));
         return make_float3(__half2float(__ushort_as_half(h.x)), __half2float(__ushort_as_half(h.y)),
                            __half2float(__ushort_as_half(h.z)));
     }
-    const float4 v = __ldg(reinterpret_cast<const float4 *>(r) + s);
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(r));
     return make_float3(v.x, v.y, v.z);
+}
+
+__device__ __forceinline__ bool ray_sample(const IntegrateArgs &a, uint32_t s, float3 &r) {
+    if (s < a.slots) {
+        r = fetch_resolved(a.resolved, a.res_stride, a.f16, s);
+        return true;
+    }
+    r = make_float3(a.env[0], a.env[1], a.env[2]);
+    return s == GI_SLOT_MISS;
+}
+
+// Reduce-scatter across the warp: on return lane l holds the warp-wide sum of v[l]
+// (31 shuffles: each halving step sends the half of the values this lane gives up).
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const bool upper = (lane & d) != 0;
+#pragma unroll
+        for (int j = 0; j < d; ++j) {
+            const float send = upper ? v[j] : v[j + d];
+            const float keep = upper ? v[j + d] : v[j];
+            v[j] = keep + __shfl_xor_sync(kFullMask, send, d);
+        }
+    }
+    return v[0];
 }
 
 // One warp per probe; lane l owns cells l and l + 32.
@@ -243,25 +270,16 @@ __global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) {
     float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     float cnt[2] = {0.f, 0.f};
     const uint32_t *ids = a.slot_ids + (size_t)p * a.rpp;
-    for (uint32_t k = lane; k < a.rpp; k += 32) {
-        const int hsel = (k >> 5) & 1;  // cell k mod 64 = lane + 32 hsel
-        const uint32_t s = __ldcs(ids + k);
-        float3 r;
-        bool has = true;
-        if (s < a.slots)
-            r = fetch_resolved(a.resolved, a.f16, s);
-        else if (s == GI_SLOT_MISS)
-            r = make_float3(a.env[0], a.env[1], a.env[2]);
-        else {
-            has = false;
-            r = make_float3(0.f, 0.f, 0.f);
+    for (uint32_t k = lane; k < a.rpp; k += 64) {
+        // rays k and k + 32 sample cells lane and lane + 32; both gathers in flight together
+        const uint32_t s0 = __ldcs(ids + k), s1 = __ldcs(ids + k + 32);
+        float3 r0, r1;
+        const bool h0 = ray_sample(a, s0, r0), h1 = ray_sample(a, s1, r1);
+        if (h0) {
+            acc[0][0] += r0.x; acc[0][1] += r0.y; acc[0][2] += r0.z; cnt[0] += 1.0f;
         }
-        if (has) {
-            if (hsel) {
-                acc[1][0] += r.x; acc[1][1] += r.y; acc[1][2] += r.z; cnt[1] += 1.0f;
-            } else {
-                acc[0][0] += r.x; acc[0][1] += r.y; acc[0][2] += r.z; cnt[0] += 1.0f;
-            }
+        if (h1) {
+            acc[1][0] += r1.x; acc[1][1] += r1.y; acc[1][2] += r1.z; cnt[1] += 1.0f;
         }
     }
     // cell means, then the radiance backup: cells without sample take the mean of populated cells
@@ -280,15 +298,26 @@ __global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) {
     for (int h = 0; h < 2; ++h)
         if (cnt[h] == 0.f)
             for (int c = 0; c < 3; ++c) L[h][c] = pop[c] * binv;
-    // direction moments of the probe radiance (local frame): 10 moments x RGB
-    float S[10][3];
+    // direction moments of the probe radiance (local frame): value 3 m + c = moment m, channel c
+    float v[32];
+#pragma unroll
     for (int m = 0; m < 10; ++m) {
         const float w0 = g_moments[m][lane], w1 = g_moments[m][lane + 32];
-        for (int c = 0; c < 3; ++c) S[m][c] = w0 * L[0][c] + w1 * L[1][c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[3 * m + c] = w0 * L[0][c] + w1 * L[1][c];
     }
-    for (int o = 16; o; o >>= 1)
-        for (int m = 0; m < 10; ++m)
-            for (int c = 0; c < 3; ++c) S[m][c] += __shfl_xor_sync(kFullMask, S[m][c], o);
+    v[30] = 0.f;
+    v[31] = 0.f;
+    const float mine = warp_reduce_scatter32(v, lane);
+    // lane k < 27 writes coefficient k / 3 of channel k % 3: gather that channel's 10 moments
+    const int coef = lane / 3, c = lane - 3 * (lane / 3);
+    float Sc[10];
+#pragma unroll
+    for (int m = 0; m < 10; ++m) Sc[m] = __shfl_sync(kFullMask, mine, min(3 * m + c, 31));
+    if (lane >= 27) {
+        if (lane == 27) out[27] = 0.0f;
+        return;
+    }
     // probe frame (Duff et al. 2017): columns t, b, n of R
     const float nx = n4.x, ny = n4.y, nz = n4.z;
     const float sgn = copysignf(1.0f, nz);
@@ -297,15 +326,6 @@ __global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) {
     const float R[3][3] = {{1.0f + sgn * nx * nx * ia, bb, nx},
                            {sgn * bb, sgn + ny * ny * ia, ny},
                            {-sgn * nx, -ny, nz}};
-    // this lane's output element k = coefficient * 3 + channel
-    if (lane >= 27) {
-        if (lane == 27) out[27] = 0.0f;
-        return;
-    }
-    const int coef = lane / 3, c = lane - 3 * (lane / 3);
-    float Sc[10];  // this lane's channel, selected without dynamic indexing
-#pragma unroll
-    for (int m = 0; m < 10; ++m) Sc[m] = c == 0 ? S[m][0] : (c == 1 ? S[m][1] : S[m][2]);
     const float S0 = Sc[0];
     float S1[3], S2[3][3];
     for (int i = 0; i < 3; ++i) S1[i] = Sc[1 + i];
@@ -315,29 +335,32 @@ __global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) {
     S2[1][2] = S2[2][1] = Sc[9];
     float W1[3], W2[3][3];
     for (int i = 0; i < 3; ++i) W1[i] = R[i][0] * S1[0] + R[i][1] * S1[1] + R[i][2] * S1[2];
+    // W2 = R S2 R^T through T = R S2
+    float T[3][3];
+#pragma unroll
     for (int i = 0; i < 3; ++i)
-        for (int j = i; j < 3; ++j) {
-            float acc2 = 0.f;
-            for (int p2 = 0; p2 < 3; ++p2)
-                for (int q2 = 0; q2 < 3; ++q2) acc2 += R[i][p2] * R[j][q2] * S2[p2][q2];
-            W2[i][j] = W2[j][i] = acc2;
-        }
+#pragma unroll
+        for (int q2 = 0; q2 < 3; ++q2) T[i][q2] = R[i][0] * S2[0][q2] + R[i][1] * S2[1][q2] + R[i][2] * S2[2][q2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) W2[i][j] = W2[j][i] = T[i][0] * R[j][0] + T[i][1] * R[j][1] + T[i][2] * R[j][2];
     // real SH basis, bands 0..2: c0; c1 y, c1 z, c1 x; c2 xy, c2 yz, c3 (3z^2-1), c2 xz, c4 (x^2-y^2)
     const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f, C2 = 1.0925484305920792f,
                 C3 = 0.31539156525252005f, C4 = 0.5462742152960396f;
-    float v;
+    float val;
     switch (coef) {
-    case 0: v = C0 * S0; break;
-    case 1: v = C1 * W1[1]; break;
-    case 2: v = C1 * W1[2]; break;
-    case 3: v = C1 * W1[0]; break;
-    case 4: v = C2 * W2[0][1]; break;
-    case 5: v = C2 * W2[1][2]; break;
-    case 6: v = C3 * (3.0f * W2[2][2] - S0); break;
-    case 7: v = C2 * W2[0][2]; break;
-    default: v = C4 * (W2[0][0] - W2[1][1]); break;
+    case 0: val = C0 * S0; break;
+    case 1: val = C1 * W1[1]; break;
+    case 2: val = C1 * W1[2]; break;
+    case 3: val = C1 * W1[0]; break;
+    case 4: val = C2 * W2[0][1]; break;
+    case 5: val = C2 * W2[1][2]; break;
+    case 6: val = C3 * (3.0f * W2[2][2] - S0); break;
+    case 7: val = C2 * W2[0][2]; break;
+    default: val = C4 * (W2[0][0] - W2[1][1]); break;
     }
-    out[lane] = v;
+    out[lane] = val;
 }
 
 // ---------------------------------------------------------------- interpolation
@@ -355,13 +378,14 @@ struct InterpArgs {
     float4 *out;
 };
 
-// Algorithm 3: from probe-space position (tx, ty) plus the offset, climb the MIP
-// chain (halving the position, floor) until a probe is found or the position
+// Algorithm 3 from MIP level m0 on: probe-space position (tx, ty) at that level plus the
+// offset; climb the chain (halving the position, floor) until a probe is found or the position
 // leaves the level.
 __device__ __forceinline__ uint32_t find_closest_probe(const uint32_t *mask, const MipInfo &mi, int tx, int ty, int ox,
-                                                       int oy) {
+                                                       int oy, int m0) {
 #pragma unroll
-    for (int m = 0; m < GI_MAX_MIPS; ++m) {
+    for (int m = 1; m < GI_MAX_MIPS; ++m) {
+        if (m < m0) continue;
         if (m >= mi.count) break;
         const int x = tx + ox, y = ty + oy;
         if (x < 0 || y < 0 || x >= mi.w[m] || y >= mi.h[m]) break;
@@ -373,28 +397,49 @@ __device__ __forceinline__ uint32_t find_closest_probe(const uint32_t *mask, con
     return GI_PROBE_NONE;
 }
 
+__device__ __forceinline__ uint32_t pick_u4(const uint32_t (&v)[4], int i) {
+    return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
+}
+
 // Block = 16x16 pixels starting at (16 bx - 4, 16 by - 4); warp = 8x4 pixels that
-// share one base tile, so the four neighbour probes are read once per warp.
-__global__ void __launch_bounds__(256) k_interpolate(InterpArgs a) {
+// share one base tile, so the four neighbour probes are warp-uniform loads.
+__global__ void __launch_bounds__(256, 4) k_interpolate(InterpArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x = (int)blockIdx.x * 16 - 4 + 8 * (warp & 1) + (lane & 7);
     const int y = (int)blockIdx.y * 16 - 4 + 4 * (warp >> 1) + (lane >> 3);
-    if (x < 0 || y < 0 || x >= (int)a.width || y >= (int)a.height) return;
-    const size_t pix = (size_t)y * a.width + x;
-    const float4 nd = __ldcs(a.gbuf + pix);
-    if (!(isfinite(nd.w) && nd.w >= 0.0f)) {
-        __stcs(a.out + pix, make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
+    const bool inb = x >= 0 && y >= 0 && x < (int)a.width && y < (int)a.height;
+    const size_t pix = inb ? (size_t)y * a.width + x : 0;
+    const int tx = (x - 4) >> 3, ty = (y - 4) >> 3;
+    // the G-buffer texel and the four level-0 mask entries are independent: issue them together
+    const float4 nd = inb ? __ldcs(a.gbuf + pix) : make_float4(0.f, 0.f, 0.f, -1.0f);
+    uint32_t q[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const int qx = tx + (o & 1), qy = ty + (o >> 1);
+        const bool in0 = inb && qx >= 0 && qy >= 0 && qx < a.mi.w[0] && qy < a.mi.h[0];
+        q[o] = in0 ? __ldg(a.mask + qy * a.mi.w[0] + qx) : GI_PROBE_NONE;
+        // Algorithm 3 continues above level 0 only where level 0 holds no probe
+        if (in0 && q[o] == GI_PROBE_NONE) q[o] = find_closest_probe(a.mask, a.mi, tx >> 1, ty >> 1, o & 1, o >> 1, 1);
+    }
+    const bool sky = inb && !(isfinite(nd.w) && nd.w >= 0.0f);
+    const bool act = inb && !sky;
+    const unsigned am = __ballot_sync(kFullMask, act);
+    if (am == 0u) {  // the whole warp is sky or outside the image
+        if (inb) __stcs(a.out + pix, make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
         return;
     }
-    // positions relative to the camera: plane distances are small differences of
-    // points that share the camera origin, which cancels exactly here
-    const float3 d = cam_ray_dir(a.cam, (float)x, (float)y);
-    const float Px = d.x * nd.w, Py = d.y * nd.w, Pz = d.z * nd.w;
-    const float nx = nd.x, ny = nd.y, nz = nd.z;
-    const float cs = a.dscale * nd.w;
-    const int tx = (x - 4) >> 3, ty = (y - 4) >> 3;
-    const float fx = ((float)((x - 4) - 8 * tx) + 0.5f) * 0.125f;
-    const float fy = ((float)((y - 4) - 8 * ty) + 0.5f) * 0.125f;
+    // the pixel's normal, or the first active lane's for inactive lanes (they only help the warp)
+    const int src = __ffs(am) - 1;
+    const float sx_ = __shfl_sync(kFullMask, nd.x, src), sy_ = __shfl_sync(kFullMask, nd.y, src),
+                sz_ = __shfl_sync(kFullMask, nd.z, src);
+    const float nx = act ? nd.x : sx_, ny = act ? nd.y : sy_, nz = act ? nd.z : sz_;
+    uint32_t qs[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) qs[o] = __shfl_sync(kFullMask, q[o], src);
+    const bool same = !act || (__float_as_uint(nd.x) == __float_as_uint(sx_) && __float_as_uint(nd.y) == __float_as_uint(sy_) &&
+                               __float_as_uint(nd.z) == __float_as_uint(sz_) && q[0] == qs[0] && q[1] == qs[1] &&
+                               q[2] == qs[2] && q[3] == qs[3]);
+    const bool uniform = __all_sync(kFullMask, same);
     // A_l Y_lm(n_p)
     const float PI = 3.14159265358979f;
     const float A0 = PI, A1 = 2.0f * PI / 3.0f, A2 = 0.25f * PI;
@@ -407,41 +452,88 @@ __global__ void __launch_bounds__(256) k_interpolate(InterpArgs a) {
                          A2 * 0.31539156525252005f * (3.0f * nz * nz - 1.0f),
                          A2 * 1.0925484305920792f * nx * nz,
                          A2 * 0.5462742152960396f * (nx * nx - ny * ny)};
+    // E_q(n) = sum_k A_l Y_k(n) c_qk for the four neighbours
+    float Eo[4][3];
+    if (uniform) {
+        // lane 3 o + ch evaluates neighbour o, channel ch for the whole warp
+        const int o = lane / 3, ch = lane - 3 * (lane / 3);
+        float e = 0.f;
+        const uint32_t qo = pick_u4(qs, o < 4 ? o : 0);
+        if (lane < 12 && qo != GI_PROBE_NONE) {
+            const float *c = a.sh + (size_t)((qo >> 19) * a.tiles_x + ((qo & 0xFFFFu) >> 3)) * GI_SH_STRIDE + ch;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) e += Yb[k] * __ldg(c + 3 * k);
+        }
+#pragma unroll
+        for (int oo = 0; oo < 4; ++oo)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) Eo[oo][cc] = __shfl_sync(kFullMask, e, 3 * oo + cc);
+    } else {
+#pragma unroll
+        for (int oo = 0; oo < 4; ++oo) {
+            // keep each neighbour's 28 SH loads inside its own iteration (register pressure)
+            asm volatile("" ::: "memory");
+            Eo[oo][0] = Eo[oo][1] = Eo[oo][2] = 0.f;
+            if (q[oo] == GI_PROBE_NONE) continue;
+            const uint32_t pidx = (q[oo] >> 19) * a.tiles_x + ((q[oo] & 0xFFFFu) >> 3);
+            const float4 *c4 = reinterpret_cast<const float4 *>(a.sh + (size_t)pidx * GI_SH_STRIDE);
+            float c[28];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                const float4 v = __ldg(c4 + k);
+                c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) Eo[oo][cc] += Yb[k] * c[3 * k + cc];
+        }
+    }
+    if (!act) {
+        if (inb) __stcs(a.out + pix, make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
+        return;
+    }
+    // Plane distance of neighbour q from the pixel's plane, relative to the camera (the camera
+    // origin cancels): (P_q - P_p) . n_p = t_q (d_q . n_p) - t_p (d_p . n_p), with
+    // d = v / |v|, v = fwd + sx right + sy up.  Only the projections of fwd, right and up on n_p
+    // are needed per neighbour.
+    const float fn = a.cam.fwd[0] * nx + a.cam.fwd[1] * ny + a.cam.fwd[2] * nz;
+    const float rn = a.cam.right[0] * nx + a.cam.right[1] * ny + a.cam.right[2] * nz;
+    const float un = a.cam.up[0] * nx + a.cam.up[1] * ny + a.cam.up[2] * nz;
+    const float inv_cs = 1.0f / (a.dscale * nd.w);
+    float pn;  // t_p (d_p . n_p)
+    {
+        const float3 d = cam_ray_dir(a.cam, (float)x, (float)y);
+        pn = nd.w * (d.x * nx + d.y * ny + d.z * nz);
+    }
+    const float fx = ((float)((x - 4) - 8 * tx) + 0.5f) * 0.125f;
+    const float fy = ((float)((y - 4) - 8 * ty) + 0.5f) * 0.125f;
     float wsum = 0.f, es[3] = {0.f, 0.f, 0.f}, er[3] = {0.f, 0.f, 0.f};
     int nfound = 0;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
+        if (q[o] == GI_PROBE_NONE) continue;
+        const uint32_t pidx = (q[o] >> 19) * a.tiles_x + ((q[o] & 0xFFFFu) >> 3);
+        const float tq = __ldg(a.ppos + pidx).w;
+        const float4 nq = __ldg(a.pnrm + pidx);
         const int ox = o & 1, oy = o >> 1;
-        const uint32_t q = find_closest_probe(a.mask, a.mi, tx, ty, ox, oy);
-        if (q == GI_PROBE_NONE) continue;
-        const uint32_t qx = q & 0xFFFFu, qy = q >> 16;
-        const uint32_t pi = (qy >> 3) * a.tiles_x + (qx >> 3);
-        const float tq = __ldg(a.ppos + pi).w;
-        const float3 dq = cam_ray_dir(a.cam, (float)qx, (float)qy);
-        const float4 nq = __ldg(a.pnrm + pi);
+        const float qpx = (float)(q[o] & 0xFFFFu), qpy = (float)(q[o] >> 16);
+        const float sxq = (2.0f * (qpx + 0.5f) * a.cam.inv_w - 1.0f) * a.cam.sx_scale;
+        const float syq = (1.0f - 2.0f * (qpy + 0.5f) * a.cam.inv_h) * a.cam.sy_scale;
+        const float vx = a.cam.fwd[0] + sxq * a.cam.right[0] + syq * a.cam.up[0];
+        const float vy = a.cam.fwd[1] + sxq * a.cam.right[1] + syq * a.cam.up[1];
+        const float vz = a.cam.fwd[2] + sxq * a.cam.right[2] + syq * a.cam.up[2];
+        const float qn = tq * (fn + sxq * rn + syq * un) * rsqrtf(vx * vx + vy * vy + vz * vz);
         const float bil = (ox ? fx : 1.0f - fx) * (oy ? fy : 1.0f - fy);
         const float nd1 = fmaxf(nx * nq.x + ny * nq.y + nz * nq.z, 0.0f);
         const float n2 = nd1 * nd1, n4 = n2 * n2, n8 = n4 * n4;
-        const float pd = fabsf((dq.x * tq - Px) * nx + (dq.y * tq - Py) * ny + (dq.z * tq - Pz) * nz);
-        const float wd = fmaxf(1.0f - pd / cs, 0.0f);
+        const float wd = fmaxf(1.0f - fabsf(qn - pn) * inv_cs, 0.0f);
         const float w = bil * n8 * wd;
-        const float4 *c4 = reinterpret_cast<const float4 *>(a.sh + (size_t)pi * GI_SH_STRIDE);
-        float c[28];
-#pragma unroll
-        for (int k = 0; k < 7; ++k) {
-            const float4 v = __ldg(c4 + k);
-            c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
-        }
-        float E[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < 9; ++k)
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) E[ch] += Yb[k] * c[3 * k + ch];
         wsum += w;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            es[ch] += w * E[ch];
-            er[ch] += E[ch];
+            es[ch] += w * Eo[o][ch];
+            er[ch] += Eo[o][ch];
         }
         ++nfound;
     }
@@ -565,6 +657,7 @@ gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *pr, const uint3
     IntegrateArgs a;
     a.slot_ids = slot_ids;
     a.resolved = cv.resolved;
+    a.res_stride = cv.resolved_stride;
     a.f16 = cv.resolved_f16;
     a.slots = cv.slots;
     a.nrm = reinterpret_cast<const float4 *>(pr->nrm);
