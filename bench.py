@@ -30,7 +30,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-CONFIG = 2
+CONFIG = 2  # the 1080p workload; --config 5 selects the 4K stress workload
 METRIC = "M hit records/s and ms/frame (update+resolve+query), % HBM roofline"
 UNIT = "M records/s"
 N_FRAMES_DEFAULT = 16
@@ -111,17 +111,17 @@ class ClockSampler:
 # ------------------------------------------------------------------ workload
 def make_frames(n_frames: int, rank: int):
     import workload as wl
+    from paper_2310_19855_gb300.replicas import frame_indices
     scene = wl.make_scene(CONFIG)
-    start = (rank * n_frames) % wl.CONFIGS[CONFIG]["frames"]
-    return [wl.make_frame(CONFIG, (start + k) % wl.CONFIGS[CONFIG]["frames"], scene) for k in range(n_frames)]
+    return [wl.make_frame(CONFIG, f, scene) for f in frame_indices(rank, n_frames, wl.CONFIGS[CONFIG]["frames"])]
 
 
-def distinct_cells(frames, log2_slots):
+def distinct_cells(frames, log2_slots, resolved_format=0):
     """Cells touched per frame (U), counted by the library between update and resolve."""
     import torch
     import paper_2310_19855_gb300 as gi
     from paper_2310_19855_gb300.pipeline import view_of
-    h = gi.gi_cache_create(log2_slots)
+    h = gi.gi_cache_create(log2_slots, resolved_format=resolved_format)
     R = frames[0].n_records
     slots = torch.empty(R, dtype=torch.int32, device="cuda")
     out = []
@@ -211,6 +211,7 @@ def run_native(args, rank, world, local_rank):
     import paper_2310_19855_gb300 as gi
     from paper_2310_19855_gb300.build import build
     from paper_2310_19855_gb300.pipeline import Pipeline, view_of
+    from paper_2310_19855_gb300.replicas import aggregate_rate, barrier, max_over_ranks
     import workload as wl
     import workload.scene as wscene
 
@@ -223,9 +224,9 @@ def run_native(args, rank, world, local_rank):
     frames = make_frames(n_frames, rank)
     fr0 = frames[0]
     W, H, R = fr0.camera.width, fr0.camera.height, fr0.n_records
-    U = distinct_cells(frames, cfg["log2_slots"])
+    U = distinct_cells(frames, cfg["log2_slots"], cfg["resolved_format"])
 
-    pl = Pipeline(W, H, fr0.rays_per_probe, cfg["log2_slots"])
+    pl = Pipeline(W, H, fr0.rays_per_probe, cfg["log2_slots"], resolved_format=cfg["resolved_format"])
     dev_rec = [torch.from_numpy(np.ascontiguousarray(f.records[:10])).cuda() for f in frames]
     dev_gb = [torch.from_numpy(f.gbuffer).cuda() for f in frames]
     views = [view_of(f.camera, f.frame) for f in frames]
@@ -261,8 +262,7 @@ def run_native(args, rank, world, local_rank):
     rebuilds0 = gi.gi_cache_stats(pl.cache)["rebuilds"]
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.5)  # let nvidia-smi start sampling before the timed region
@@ -275,8 +275,7 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_start
     clk = clocks.stop(t_start_wall, time.time())
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     st = gi.gi_cache_stats(pl.cache)
     rebuilds = st["rebuilds"] - rebuilds0
     per = np.array([[evs[j][k].elapsed_time(evs[j][k + 1]) for k in range(5)] for j in range(args.steps)])
@@ -312,33 +311,29 @@ def run_native(args, rank, world, local_rank):
     d2h = h_out.numel() * 4
 
     # ---- max over ranks
-    tot = np.array([window_ms.sum(), frame_ms.sum(), t_wall, e2e_ms.sum()], np.float64)
-    if world > 1:
-        t = torch.tensor(tot, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot = t.cpu().numpy()
+    tot = np.array(max_over_ranks([window_ms.sum(), frame_ms.sum(), t_wall, e2e_ms.sum()], world, "cuda"))
     if rank != 0:
         return
-    win_s = tot[0] / 1e3
-    value = world * R * args.steps / win_s / 1e6
-    frame_rate = world * R * args.steps / (tot[1] / 1e3) / 1e6
-    e2e_value = world * R * e_steps / (tot[3] / 1e3) / 1e6
+    value = aggregate_rate(R, world, args.steps, tot[0] / 1e3) / 1e6
+    frame_rate = aggregate_rate(R, world, args.steps, tot[1] / 1e3) / 1e6
+    e2e_value = aggregate_rate(R, world, e_steps, tot[3] / 1e3) / 1e6
 
     # ---- roofline of the dominant kernel (algorithmic bytes / event-timed duration)
     peak, peak_src = _peaks()
     pass_ms = per.mean(axis=0)
     dominant = names[int(np.argmax(pass_ms))]
     U_mean = float(np.mean(U))
+    res_b = 8 if cfg["resolved_format"] == 1 else 16
     P = fr0.tiles_x * fr0.tiles_y
     X = W * H
     alg = {
         # records 40 B in + slot id 4 B out; per touched cell a 32 B tag sector read, the 32 B
         # accumulator read and written, and a 4 B touch-list entry
         "update": R * 44 + U_mean * (32 + 64 + 4),
-        # per touched cell: touch entry 4, accumulator 32 read + 32 written, resolved 16 read + 16 written
-        "resolve": U_mean * (4 + 64 + 32),
-        # per ray a 4 B slot id and a 16 B resolved gather; per probe the normal 16 B and 112 B of SH out
-        "integrate": R * 20 + P * (16 + 112),
+        # per touched cell: touch entry 4, accumulator 32 read + 32 written, resolved read + written
+        "resolve": U_mean * (4 + 64 + 2 * res_b),
+        # per ray a 4 B slot id and a resolved gather; per probe the normal 16 B and 112 B of SH out
+        "integrate": R * (4 + res_b) + P * (16 + 112),
         # per pixel 16 B G-buffer in, 16 B out; per probe 16 + 16 + 112 B read
         "interpolate": X * 32 + P * 144,
         # per probe 16 B G-buffer read, mask 4 B + pos 16 B + nrm 16 B written
@@ -379,6 +374,9 @@ def run_native(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": float(tot[3] / e_steps)},
         "gpu_launches": int(args.steps * launches_per_step + rebuilds),
+        "dropped_hits": int(st["dropped"]),
+        "table": {"slots": int(st["slots"]), "occupied": int(st["occupied"]), "live": int(st["live"]),
+                  "max_probe_seen": int(st["max_probe_seen"]), "rebuilds_total": int(st["rebuilds"])},
         "rebuilds_in_timed_region": int(rebuilds),
         "clocks": clk,
         "wall_s_timed": float(tot[2]),
@@ -396,7 +394,11 @@ def main():
     ap.add_argument("--frames", type=int, default=N_FRAMES_DEFAULT, help="distinct pre-generated frames to cycle")
     ap.add_argument("--sample", type=float, default=0.125, help="fraction of probes in the oracle's sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 5],
+                    help="2: boxes at 1080p (default); 5: boxes at 4K, 2^24 slots, FP16 resolved radiance")
     args = ap.parse_args()
+    global CONFIG
+    CONFIG = args.config
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -6,6 +6,11 @@ import numpy as np
 import torch
 
 import paper_2310_19855_gb300 as gi
+import workload as wl
+from oracle import probes as OP
+from oracle import sh as OSH
+from oracle.cache import OracleCache
+from oracle.frame import run_frame
 from paper_2310_19855_gb300.pipeline import Pipeline, view_of
 
 # float32 path vs float64 oracle (tolerances)
@@ -66,5 +71,75 @@ def check_slot_ids(slots: np.ndarray, ex: np.ndarray, rec: np.ndarray, oracle_id
     assert np.array_equal(slot_identities(ex, slots, n_slots)[hit], oracle_ident[hit])
 
 
-__all__ = ["Pipeline", "view_of", "require_gpu", "dev", "u32", "close", "check_export_matches", "slot_identities",
+def sh_gpu(pl):
+    return pl.probes.sh.cpu().numpy()[:, :27].reshape(-1, 9, 3).astype(np.float64)
+
+
+def compare_frame(pl, fr, out, allow_sensitive_frac, rel=1e-4):
+    P = pl.probes.layout.num_probes
+    # spawn: mask levels bit-exact, probe positions to float32 rounding
+    mips_o = OP.build_mips(out["spawn"]["mask"])
+    mips_g = pl.probes.mask_levels()
+    assert len(mips_o) == len(mips_g)
+    for a, b in zip(mips_o, mips_g):
+        assert np.array_equal(a, b)
+    pos_g = pl.probes.pos.cpu().numpy()
+    nrm_g = pl.probes.nrm.cpu().numpy()
+    v = out["spawn"]["valid"]
+    assert np.array_equal(nrm_g[:, 3] == 1.0, v)
+    scale = 1.0 + np.abs(fr.camera.pos).max() + np.abs(out["spawn"]["dist"]).max()
+    assert np.abs(pos_g[v, :3] - out["spawn"]["pos"][v]).max() < 4e-7 * scale
+    assert np.array_equal(nrm_g[v, :3], out["spawn"]["nrm"][v])
+    # probe SH: relative to the probe's band-0 magnitude (individual coefficients can cancel)
+    sg, so = sh_gpu(pl), out["sh"]
+    mag = np.abs(so[:, 0:1, :]).max(axis=2, keepdims=True) + 1e-6
+    err = np.abs(sg - so) / mag
+    assert err.max() < rel, err.max()
+    # irradiance at each probe normal
+    Eg = OSH.irradiance(sg[v], out["spawn"]["nrm"][v])
+    Eo = OSH.irradiance(so[v], out["spawn"]["nrm"][v])
+    assert close(Eg, Eo, rel=rel, atol=1e-6).all()
+    # interpolation
+    irr = pl.irr.cpu().numpy()
+    flag_g = irr[..., 3].astype(np.int64)
+    flag_o = out["flag"]
+    wsum, margin = out["diag"]["wsum"], out["diag"]["margin"]
+    # decision-sensitive pixels: a neighbour's plane test within 1e-3 of its cut, or a weight
+    # sum so small that float32 weight rounding moves the weighted mean by more than 1e-4
+    sensitive = (margin < 1e-3) | ((wsum > 0) & (wsum < 1e-2))
+    agree = ~sensitive
+    assert np.array_equal(flag_g[agree], flag_o[agree]), np.count_nonzero(flag_g[agree] != flag_o[agree])
+    # float32 evaluation of sum_k A_l Y_k(n) c_k cancels in dark pixels: bound the absolute error by the
+    # magnitude of the summed terms (emag) as well as 1e-4 of the value
+    emag = out["diag"]["emag"][..., None]
+    ok = (np.abs(irr[..., :3] - out["irr"]) <= rel * np.abs(out["irr"]) + 1e-5 * emag + 1e-7).all(axis=-1)
+    bad = agree & ~ok
+    assert np.count_nonzero(bad) == 0, (np.count_nonzero(bad), np.abs(irr[..., :3] - out["irr"])[bad].max())
+    X = flag_o.size
+    assert np.count_nonzero(sensitive) <= allow_sensitive_frac * X, np.count_nonzero(sensitive) / X
+    return np.count_nonzero(sensitive), np.count_nonzero(flag_g != flag_o)
+
+
+def run_frames(config, frames, allow_sensitive_frac=0.02, rel=1e-4, resolved_format=0):
+    cfg = wl.CONFIGS[config]
+    fr0 = frames[0]
+    pl = Pipeline(fr0.camera.width, fr0.camera.height, fr0.rays_per_probe, cfg["log2_slots"],
+                  resolved_format=resolved_format)
+    oc = OracleCache(cfg["log2_slots"])
+    stats = []
+    try:
+        for fr in frames:
+            view = view_of(fr.camera, fr.frame)
+            gb = dev(fr.gbuffer)
+            rec = dev(fr.records)
+            pl.frame(gb, rec, view)
+            torch.cuda.synchronize()
+            out = run_frame(oc, fr)
+            stats.append(compare_frame(pl, fr, out, allow_sensitive_frac, rel))
+    finally:
+        pl.close()
+    return stats
+
+
+__all__ = ["compare_frame", "run_frames", "sh_gpu", "Pipeline", "view_of", "require_gpu", "dev", "u32", "close", "check_export_matches", "slot_identities",
            "check_slot_ids", "REL", "ABS"]

@@ -43,15 +43,15 @@ REC_PLANES = ("px", "py", "pz", "nx", "ny", "nz", "r", "g", "b", "len", "dx", "d
 CONFIGS = {
     1: dict(name="cornell-64x64", scene="cornell", width=64, height=64, fov_deg=60.0,
             rays_per_probe=256, log2_slots=16, cell_size=0.05, num_lods=4, alpha=0.1,
-            evict_frames=8, frames=4, moving_camera=False),
+            evict_frames=8, frames=4, moving_camera=False, resolved_format=0),
     2: dict(name="boxes-1080p", scene="boxes", width=1920, height=1080, fov_deg=60.0,
             rays_per_probe=64, log2_slots=22, cell_size=0.05, num_lods=4, alpha=0.1,
             evict_frames=8, frames=64, moving_camera=True, n_boxes=4096,
-            room=(64.0, 16.0, 64.0), moving_emitters=0),
+            room=(64.0, 16.0, 64.0), moving_emitters=0, resolved_format=0),
     5: dict(name="boxes-4k", scene="boxes", width=3840, height=2160, fov_deg=60.0,
             rays_per_probe=64, log2_slots=24, cell_size=0.05, num_lods=4, alpha=0.1,
             evict_frames=8, frames=64, moving_camera=True, n_boxes=16384,
-            room=(96.0, 20.0, 96.0), moving_emitters=3),
+            room=(96.0, 20.0, 96.0), moving_emitters=3, resolved_format=1),
 }
 
 
