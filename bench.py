@@ -385,6 +385,136 @@ def run_native(args, rank, world, local_rank):
     pl.close()
 
 
+# ------------------------------------------------------------------ batched arm (many views)
+def run_batched(args, rank, world, local_rank):
+    """16 views of uneven resolution per frame: batched passes replayed from a CUDA graph (launch
+    shapes from the autotuner), against the same views run one after another through the
+    single-view calls."""
+    import torch
+    import paper_2310_19855_gb300 as gi
+    from paper_2310_19855_gb300 import autotune
+    from paper_2310_19855_gb300.build import build
+    from paper_2310_19855_gb300.pipeline import BatchPipeline, Pipeline, view_of
+    from paper_2310_19855_gb300.replicas import aggregate_rate, barrier, frame_indices, max_over_ranks
+    import workload as wl
+    import workload.scene as wscene
+
+    build()
+    wscene.build_tracer()
+    torch.cuda.set_device(local_rank)
+    specs = wl.batched_views(wl.CONFIGS[3]["n_views"])
+    F = max(1, min(args.frames, 2))
+    frames = []
+    for cfg, seed in specs:
+        scene = wl.make_scene(cfg, seed)
+        frames.append([wl.make_frame(cfg, g, scene, seed_base=seed) for g in frame_indices(rank, F, cfg["frames"])])
+    V = len(specs)
+    recs = [[torch.from_numpy(np.ascontiguousarray(frames[v][k].records[:10])).cuda() for v in range(V)]
+            for k in range(F)]
+    gbufs = [[torch.from_numpy(frames[v][k].gbuffer).cuda() for v in range(V)] for k in range(F)]
+    gviews = [[view_of(frames[v][k].camera, frames[v][k].frame) for v in range(V)] for k in range(F)]
+    R_total = sum(frames[v][0].n_records for v in range(V))
+    X_total = sum(cfg["width"] * cfg["height"] for cfg, _ in specs)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    bp = BatchPipeline([(cfg["width"], cfg["height"], cfg["log2_slots"]) for cfg, _ in specs], 64)
+    counter = [0]
+
+    def batched_frame(use_graph=True):
+        k = counter[0]
+        bp.frame(gbufs[k % F], recs[k % F], gviews[k % F], use_graph=use_graph, stream=stream, resolve_frame=k)
+        counter[0] += 1
+
+    tuning, timings = autotune.tune(bp, batched_frame, frames=3)
+
+    def timed(fn, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for j in range(steps):
+            flush.zero_()
+            evs[j][0].record(stream)
+            fn()
+            evs[j][1].record(stream)
+        torch.cuda.synchronize()
+        return np.array([a.elapsed_time(b) for a, b in evs])
+
+    for _ in range(args.warmup):
+        batched_frame(True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    barrier(world)
+    clocks.start()
+    time.sleep(0.5)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ms_graph = timed(lambda: batched_frame(True), args.steps)
+    clk = clocks.stop(t0, time.time())
+    barrier(world)
+    ms_nograph = timed(lambda: batched_frame(False), max(3, min(args.steps, 50)))
+
+    # the same views one after another through the single-view calls (own caches)
+    singles = [Pipeline(cfg["width"], cfg["height"], 64, cfg["log2_slots"]) for cfg, _ in specs]
+    scount = [0]
+
+    def sequential_frame():
+        k = scount[0]
+        for v in range(V):
+            sp = singles[v]
+            sp.spawn(gbufs[k % F][v], gviews[k % F][v], stream)
+            gi.gi_cache_update(sp.cache, gi.hits_from_planes(recs[k % F][v], sp.n_records), gviews[k % F][v],
+                               sp.slot_ids, stream)
+            sp.resolve(k, stream)
+            sp.integrate((0.0, 0.0, 0.0), stream)
+            sp.interpolate(gbufs[k % F][v], gviews[k % F][v], stream)
+        scount[0] += 1
+
+    for _ in range(args.warmup):
+        sequential_frame()
+    ms_seq = timed(sequential_frame, max(3, min(args.steps, 50)))
+    tot = np.array(max_over_ranks([ms_graph.sum(), ms_nograph.mean(), ms_seq.mean()], world, "cuda"))
+    for sp in singles:
+        sp.close()
+    bp.close()
+    if rank != 0:
+        return
+    value = aggregate_rate(R_total, world, args.steps, tot[0] / 1e3) / 1e6
+    frame_ms = tot[0] / args.steps
+    peak, peak_src = _peaks()
+    # whole-frame algorithmic bytes (same per-unit figures as the single-view bench, U not measured
+    # here: 0.4 touched cells per record, the 1080p workload's ratio)
+    U = 0.4 * R_total
+    P = R_total / 64
+    alg = (R_total * 44 + U * 100) + U * 100 + (R_total * 20 + P * 128) + (X_total * 32 + P * 144) + P * 52
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(frame_ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: {V} views ("
+                               + ", ".join(f"{c['width']}x{c['height']}" for c, _ in specs)
+                               + f"), {R_total} records and {X_total} pixels per frame, one launch per pass "
+                                 "over all views, CUDA-graph replay",
+                   "records_per_step": R_total, "pixels_per_step": X_total,
+                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "tuning": {"update_records_per_block": tuning.update_records_per_block,
+                              "resolve_blocks_per_sm": tuning.resolve_blocks_per_sm,
+                              "integrate_threads": tuning.integrate_threads},
+                   "note": "value and ms_per_step over the whole frame of all views (spawn ... interpolation)"},
+        "frames_per_s": {"batched_graph": 1e3 / frame_ms, "batched_no_graph": 1e3 / tot[1],
+                         "sequential_single_view_calls": 1e3 / tot[2]},
+        "ms_per_frame": {"batched_graph": float(frame_ms), "batched_no_graph": float(tot[1]),
+                         "sequential_single_view_calls": float(tot[2])},
+        "autotune_ms": timings,
+        "roofline": {"bound": "hbm", "achieved": alg / (frame_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg / (frame_ms * 1e-3) / 1e9 / peak, "traffic": None,
+                     "kernel": "whole batched frame (six launches)", "algorithmic_bytes_per_launch": alg,
+                     "peak_source": peak_src},
+        "cpu_baseline": None,
+        "gpu_launches": int(args.steps * 7),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,8 +524,9 @@ def main():
     ap.add_argument("--frames", type=int, default=N_FRAMES_DEFAULT, help="distinct pre-generated frames to cycle")
     ap.add_argument("--sample", type=float, default=0.125, help="fraction of probes in the oracle's sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 5],
-                    help="2: boxes at 1080p (default); 5: boxes at 4K, 2^24 slots, FP16 resolved radiance")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 5],
+                    help="2: boxes at 1080p (default); 3: 16 batched views; 5: boxes at 4K, 2^24 slots, FP16 "
+                         "resolved radiance")
     args = ap.parse_args()
     global CONFIG
     CONFIG = args.config
@@ -410,7 +541,10 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        run_native(args, rank, world, local_rank)
+        if CONFIG == 3:
+            run_batched(args, rank, world, local_rank)
+        else:
+            run_native(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch

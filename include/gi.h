@@ -315,6 +315,49 @@ gi_status gi_probes_interpolate(const gi_gbuffer *gbuf, const gi_view *view, con
  * frame), computed in closed form for the spherical quadrilateral of each cell. */
 gi_status gi_cell_moments(double *out640);
 
+/* ---------------------------------------------------------------- many views per frame */
+/*
+ * The same pass chain for many independent views (each with its own cache, camera, G-buffer and
+ * records) with one kernel launch per pass over all views: per frame, gi_batch_frame runs spawn,
+ * update, resolve, probe irradiance and interpolation for every view, exactly as the single-view
+ * calls gi_probes_spawn, gi_cache_update, gi_cache_resolve(resolve_frame), gi_probes_integrate and
+ * gi_probes_interpolate would, with the same results.  With use_graph != 0 the launches are
+ * captured into a CUDA graph the first time (and again whenever a view's size changes) on a
+ * stream of the batch's own, then replayed on `stream`.
+ */
+#define GI_BATCH_MAX_VIEWS 256
+
+typedef struct gi_batch_s *gi_batch_t;
+
+/* Launch shapes, chosen by an autotuner (defaults: 2048, 3, 256). */
+typedef struct gi_batch_tuning {
+    uint32_t update_records_per_block; /* records per update block, multiple of 256 in [256, 2048] */
+    uint32_t resolve_blocks_per_sm;    /* resolve blocks per SM over all views, 1..3 */
+    uint32_t integrate_threads;        /* threads per integrate block (one warp per probe), 64..256 */
+} gi_batch_tuning;
+
+/* One view of a frame.  All pointers are device pointers owned by the caller; hits.n must equal
+ * probes.layout.num_probes * rays_per_probe; every cache of a batch uses the same key_dir. */
+typedef struct gi_batch_view {
+    gi_cache_t cache;
+    gi_view view;            /* view.frame drives the spawn jitter */
+    uint32_t resolve_frame;  /* frame at which this view's cache is resolved (never decreasing) */
+    gi_hits hits;
+    gi_gbuffer gbuf;
+    gi_probes probes;
+    uint32_t *slot_ids;
+    float *irradiance; /* float4 per pixel */
+    float env[3];
+} gi_batch_view;
+
+/* Create a batch of n_views views (1..GI_BATCH_MAX_VIEWS); tuning may be NULL (defaults). */
+gi_status gi_batch_create(uint32_t n_views, uint32_t rays_per_probe, const gi_batch_tuning *tuning, gi_batch_t *out);
+/* Change the launch shapes (synchronises the device; captured graphs are dropped). */
+gi_status gi_batch_set_tuning(gi_batch_t b, const gi_batch_tuning *tuning);
+/* Run one frame of every view (views: n_views entries).  Asynchronous on stream. */
+gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_graph, gi_stream_t stream);
+gi_status gi_batch_destroy(gi_batch_t b);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 /*
  * Per-record cell means of one batch, without allocating device memory.  The paper has no

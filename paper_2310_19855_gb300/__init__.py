@@ -80,6 +80,16 @@ class gi_query(ctypes.Structure):
                 ("n", c_u64), ("env", c_f32 * 3)]
 
 
+class gi_batch_tuning(ctypes.Structure):
+    _fields_ = [("update_records_per_block", c_u32), ("resolve_blocks_per_sm", c_u32), ("integrate_threads", c_u32)]
+
+
+class gi_batch_view(ctypes.Structure):
+    _fields_ = [("cache", c_vp), ("view", gi_view), ("resolve_frame", c_u32), ("hits", gi_hits), ("gbuf", gi_gbuffer),
+                ("probes", gi_probes),
+                ("slot_ids", c_vp), ("irradiance", c_vp), ("env", c_f32 * 3)]
+
+
 CELL_DTYPE = np.dtype([("identity", "<u8"), ("sum", "<u8", (3,)), ("count", "<u4"), ("stamp", "<u4"),
                        ("value", "<f4", (3,)), ("slot", "<u4")])
 assert CELL_DTYPE.itemsize == ctypes.sizeof(gi_cell)
@@ -120,6 +130,10 @@ def lib() -> ctypes.CDLL:
             "gi_probes_interpolate": (ctypes.c_int, [ctypes.POINTER(gi_gbuffer), ctypes.POINTER(gi_view),
                                                      ctypes.POINTER(gi_probes), c_vp, c_vp]),
             "gi_cell_moments": (ctypes.c_int, [ctypes.POINTER(c_f64)]),
+            "gi_batch_create": (ctypes.c_int, [c_u32, c_u32, ctypes.POINTER(gi_batch_tuning), ctypes.POINTER(c_vp)]),
+            "gi_batch_set_tuning": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_batch_tuning)]),
+            "gi_batch_frame": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_batch_view), c_u32, c_vp]),
+            "gi_batch_destroy": (ctypes.c_int, [c_vp]),
             "gi_cell_means_noalloc": (ctypes.c_int, [ctypes.POINTER(gi_hits), ctypes.POINTER(gi_view), c_f32, c_u32,
                                                      c_u32, ctypes.POINTER(c_f32), c_vp, c_vp]),
         }
@@ -291,3 +305,23 @@ def gi_cell_means_noalloc(hits: gi_hits, view: gi_view, out, cell_size: float = 
     e = (c_f32 * 3)(*[float(x) for x in env])
     check(lib().gi_cell_means_noalloc(ctypes.byref(hits), ctypes.byref(view), float(cell_size), int(num_lods),
                                       int(key_dir), e, _ptr(out), _stream(stream)), "gi_cell_means_noalloc")
+
+
+def gi_batch_create(n_views: int, rays_per_probe: int, tuning: gi_batch_tuning | None = None) -> int:
+    h = c_vp()
+    check(lib().gi_batch_create(int(n_views), int(rays_per_probe), ctypes.byref(tuning) if tuning else None,
+                                ctypes.byref(h)), "gi_batch_create")
+    return h.value
+
+
+def gi_batch_set_tuning(batch: int, tuning: gi_batch_tuning) -> None:
+    check(lib().gi_batch_set_tuning(batch, ctypes.byref(tuning)), "gi_batch_set_tuning")
+
+
+def gi_batch_frame(batch: int, views, use_graph: bool = False, stream=None) -> None:
+    """views: a ctypes array of gi_batch_view (one entry per view of the batch)."""
+    check(lib().gi_batch_frame(batch, views, 1 if use_graph else 0, _stream(stream)), "gi_batch_frame")
+
+
+def gi_batch_destroy(batch: int) -> None:
+    check(lib().gi_batch_destroy(batch), "gi_batch_destroy")

@@ -111,29 +111,10 @@ constexpr int kUpdThreads = 256;
 constexpr int kUpdBlockRecords = 2048;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-typedef uint32_t SlotWord;  // tag = fingerprint << 8 | (home mod 256); 0 = empty
-__device__ __forceinline__ uint32_t word_tag(SlotWord w) { return w; }
 
-struct UpdateArgs {
-    const float *p[3];
-    const float *nrm[3];
-    const float *rad[3];
-    const float *len;
-    const float *dir[3];
-    uint32_t *slot_ids;
-    unsigned long long n;
-    SlotWord *tags;
-    Accum *accum;
-    uint32_t acc_stride;  // Accum units between consecutive slots
-    uint32_t *touch;
-    Counters *ctr;
-    uint32_t mask;
-    uint32_t max_probe;
-    KeyParams kp;
-};
 
 template <int KEY_DIR>
-__global__ void __launch_bounds__(kUpdThreads, 8) k_update(UpdateArgs a) {
+__device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, uint32_t nblk) {
     __shared__ uint32_t s_touch[kUpdBlockRecords];
     __shared__ uint32_t s_n, s_base, s_clamped, s_maxp;
     if (threadIdx.x == 0) {
@@ -143,9 +124,9 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_update(UpdateArgs a) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const unsigned long long stride = (unsigned long long)gridDim.x * kUpdThreads;
+    const unsigned long long stride = (unsigned long long)nblk * kUpdThreads;
     uint32_t my_clamped = 0, my_maxp = 0;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * kUpdThreads; base < a.n; base += stride) {
+    for (unsigned long long base = (unsigned long long)blk * kUpdThreads; base < a.n; base += stride) {
         const unsigned long long i = base + threadIdx.x;
         const bool inr = i < a.n;
         float len = inr ? __ldcs(a.len + i) : -1.0f;
@@ -255,6 +236,11 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_update(UpdateArgs a) {
     for (uint32_t j = threadIdx.x; j < s_n; j += kUpdThreads) a.touch[s_base + j] = s_touch[j];
 }
 
+template <int KEY_DIR>
+__global__ void __launch_bounds__(kUpdThreads, 8) k_update(UpdateArgs a) {
+    update_body<KEY_DIR>(a, blockIdx.x, gridDim.x);
+}
+
 // Grid of k_update: enough blocks that none takes more than kUpdBlockRecords records.
 static inline int update_blocks(unsigned long long n) {
     return (int)((n + kUpdBlockRecords - 1) / kUpdBlockRecords);
@@ -263,20 +249,6 @@ static inline int update_blocks(unsigned long long n) {
 // ---------------------------------------------------------------- resolve
 constexpr int kResThreads = 256;
 
-struct ResolveArgs {
-    const uint32_t *touch;
-    Accum *accum;
-    uint32_t acc_stride;
-    void *resolved;
-    uint32_t res_stride;  // bytes between consecutive resolved values
-    Counters *ctr;
-    float alpha;
-    uint32_t stamp_now;   // frame + 1
-    uint32_t has_lr;      // a resolve happened before
-    uint32_t lr;          // frame of that resolve
-    uint32_t evict;       // E
-    int f16;
-};
 
 __device__ __forceinline__ float3 load_resolved(const void *r, uint32_t stride, int f16, uint32_t s) {
     r = static_cast<const char *>(r) + (size_t)s * stride;
@@ -305,16 +277,16 @@ __device__ __forceinline__ void store_resolved(void *r, uint32_t stride, int f16
 
 constexpr int kResUnroll = 4;
 
-__global__ void __launch_bounds__(kResThreads, 3) k_resolve(ResolveArgs a) {
+__device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
     __shared__ uint32_t s_new;
     __shared__ bool s_last;
     if (threadIdx.x == 0) s_new = 0;
     __syncthreads();
     const uint32_t n = __ldcg(&a.ctr->touch_count);
-    const uint32_t stride = gridDim.x * kResThreads;
+    const uint32_t stride = nblk * kResThreads;
     uint32_t fresh_new = 0;
     // kResUnroll touched cells per thread and iteration, their loads issued together
-    for (uint32_t i0 = blockIdx.x * kResThreads + threadIdx.x; i0 < n; i0 += kResUnroll * stride) {
+    for (uint32_t i0 = blk * kResThreads + threadIdx.x; i0 < n; i0 += kResUnroll * stride) {
         uint32_t s[kResUnroll];
         uint4 lo[kResUnroll], hi[kResUnroll];
 #pragma unroll
@@ -370,20 +342,25 @@ __global__ void __launch_bounds__(kResThreads, 3) k_resolve(ResolveArgs a) {
         if (s_new) atomicAdd(&a.ctr->occupied, s_new);
         __threadfence();
         const uint32_t t = atomicAdd(&a.ctr->ticket, 1u);
-        s_last = (t == gridDim.x - 1u);
+        s_last = (t == nblk - 1u);
     }
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
         // every block has read the touch count: reset it for the next frame
         a.ctr->touch_count = 0u;
         a.ctr->ticket = 0u;
+        // occupancy for the host's compaction decision, then the frame it belongs to
+        if (a.occ_out) {
+            reinterpret_cast<volatile uint32_t *>(a.occ_out)[0] = atomicAdd(&a.ctr->occupied, 0u);
+            __threadfence_system();
+            reinterpret_cast<volatile uint32_t *>(a.occ_out)[1] = a.stamp_now;
+        }
     }
 }
 
+__global__ void __launch_bounds__(kResThreads, 3) k_resolve(ResolveArgs a) { resolve_body(a, blockIdx.x, gridDim.x); }
+
 // ---------------------------------------------------------------- queries
-struct LiveRule {
-    uint32_t has_lr, lr, evict;
-};
 
 // a cell answers queries once resolved, until it is evicted
 __device__ __forceinline__ bool answers(uint32_t stamp, const LiveRule &r) {
@@ -503,6 +480,50 @@ __global__ void k_scan_stats(const SlotWord *tags, const Accum *acc, uint32_t N,
     }
 }
 
+
+// ---------------------------------------------------------------- batched passes (many views)
+template <int KEY_DIR>
+__global__ void __launch_bounds__(kUpdThreads, 8) k_update_batched(const UpdateArgs *args, const uint32_t *prefix,
+                                                                   uint32_t nviews) {
+    __shared__ UpdateArgs sa;
+    const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
+    load_view_args(sa, args + v);
+    __syncthreads();
+    const uint32_t p0 = __ldg(prefix + v), p1 = __ldg(prefix + v + 1);
+    update_body<KEY_DIR>(sa, blockIdx.x - p0, p1 - p0);
+}
+
+__global__ void __launch_bounds__(kResThreads, 3) k_resolve_batched(const ResolveArgs *args, const uint32_t *prefix,
+                                                                    uint32_t nviews) {
+    __shared__ ResolveArgs sa;
+    const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
+    load_view_args(sa, args + v);
+    __syncthreads();
+    const uint32_t p0 = __ldg(prefix + v), p1 = __ldg(prefix + v + 1);
+    resolve_body(sa, blockIdx.x - p0, p1 - p0);
+}
+
+uint32_t update_blocks_for(unsigned long long n, uint32_t records_per_block) {
+    return (uint32_t)((n + records_per_block - 1) / records_per_block);
+}
+
+gi_status launch_update_batched(const UpdateArgs *args, const uint32_t *prefix, uint32_t nviews, uint32_t blocks,
+                                int key_dir, cudaStream_t st) {
+    if (blocks == 0) return GI_OK;
+    if (key_dir == GI_KEY_DIR_NORMAL)
+        k_update_batched<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(args, prefix, nviews);
+    else
+        k_update_batched<GI_KEY_DIR_RAY><<<blocks, kUpdThreads, 0, st>>>(args, prefix, nviews);
+    return cuda_status(cudaGetLastError(), "k_update_batched launch");
+}
+
+gi_status launch_resolve_batched(const ResolveArgs *args, const uint32_t *prefix, uint32_t nviews, uint32_t blocks,
+                                 cudaStream_t st) {
+    if (blocks == 0) return GI_OK;
+    k_resolve_batched<<<blocks, kResThreads, 0, st>>>(args, prefix, nviews);
+    return cuda_status(cudaGetLastError(), "k_resolve_batched launch");
+}
+
 } // namespace gi
 
 // ==================================================================== host side
@@ -519,10 +540,9 @@ struct gi_cache_s {
     int cur;
     uint32_t *touch;
     gi::Counters *ctr;
-    gi::Counters *ctr_host;     // pinned snapshot
+    volatile uint32_t *occ_host; // mapped pinned {occupied, stamp of the resolve that wrote it}
+    uint32_t *occ_dev;           // its device address
     unsigned long long *scan;   // device scratch for stats (2 x u64)
-    cudaEvent_t snap_event;
-    bool snap_pending;
     int64_t last_resolved;
     bool touched_since_resolve;
     bool rebuild_checked;
@@ -562,7 +582,7 @@ static bool config_ok(const gi_cache_config *c) {
     return true;
 }
 
-static bool hits_ok(const gi_hits *h, uint32_t key_dir) {
+bool hits_ok(const gi_hits *h, uint32_t key_dir) {
     if (!h) return false;
     if (h->n == 0) return true;
     for (int a = 0; a < 3; ++a)
@@ -574,7 +594,7 @@ static bool hits_ok(const gi_hits *h, uint32_t key_dir) {
     return true;
 }
 
-static UpdateArgs update_args(gi_cache_s *c, const gi_hits *h, const gi_view *v, uint32_t *slot_ids) {
+UpdateArgs cache_update_args(gi_cache_s *c, const gi_hits *h, const gi_view *v, uint32_t *slot_ids) {
     UpdateArgs a;
     for (int k = 0; k < 3; ++k) {
         a.p[k] = h->pos[k];
@@ -597,15 +617,12 @@ static UpdateArgs update_args(gi_cache_s *c, const gi_hits *h, const gi_view *v,
 }
 
 static gi_status maybe_rebuild(gi_cache_s *c, cudaStream_t st) {
-    // Only at the first update after a resolve (all accumulators are clear then),
-    // and only once the occupancy read back after that resolve has arrived.
-    if (c->touched_since_resolve || c->rebuild_checked || !c->snap_pending) return GI_OK;
-    cudaError_t q = cudaEventQuery(c->snap_event);
-    if (q == cudaErrorNotReady) return GI_OK;
-    if (q != cudaSuccess) return cuda_status(q, "cudaEventQuery");
+    // Only at the first update after a resolve (all accumulators are clear then), from the
+    // occupancy that resolve wrote to mapped host memory (skipped while it has not arrived).
+    if (c->touched_since_resolve || c->rebuild_checked || c->last_resolved < 0) return GI_OK;
+    if (c->occ_host[1] != (uint32_t)c->last_resolved + 1u) return GI_OK;
     c->rebuild_checked = true;
-    c->snap_pending = false;
-    const double occ = (double)c->ctr_host->occupied;
+    const double occ = (double)c->occ_host[0];
     if (occ <= (double)c->cfg.rebuild_load * (double)c->N) return GI_OK;
     const int nxt = c->cur ^ 1;
     gi_status s = cuda_status(cudaMemsetAsync(&c->ctr->occupied, 0, sizeof(uint32_t), st), "rebuild memset");
@@ -620,6 +637,42 @@ static gi_status maybe_rebuild(gi_cache_s *c, cudaStream_t st) {
     return GI_OK;
 }
 
+ResolveArgs cache_resolve_args(gi_cache_s *c, uint32_t frame) {
+    ResolveArgs a;
+    a.touch = c->touch;
+    a.accum = c->accum[c->cur];
+    a.acc_stride = 1;
+    a.resolved = c->resolved[c->cur];
+    a.res_stride = c->res_bytes;
+    a.ctr = c->ctr;
+    a.alpha = c->cfg.alpha;
+    a.stamp_now = frame + 1u;
+    a.has_lr = c->last_resolved >= 0;
+    a.lr = c->last_resolved >= 0 ? (uint32_t)c->last_resolved : 0u;
+    a.evict = c->cfg.evict_frames;
+    a.f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
+    a.occ_out = c->occ_dev;
+    return a;
+}
+
+void cache_after_resolve(gi_cache_s *c, uint32_t frame) {
+    c->rebuild_checked = false;
+    c->last_resolved = frame;
+    c->touched_since_resolve = false;
+    c->resolves++;
+}
+
+gi_status cache_before_update(gi_cache_s *c, cudaStream_t st) {
+    gi_status s = maybe_rebuild(c, st);
+    if (s == GI_OK) c->updates++;
+    return s;
+}
+
+void cache_after_update(gi_cache_s *c) { c->touched_since_resolve = true; }
+int cache_key_dir(const gi_cache_s *c) { return (int)c->cfg.key_dir; }
+int cache_device(const gi_cache_s *c) { return c->device; }
+int64_t cache_last_resolved(const gi_cache_s *c) { return c->last_resolved; }
+
 static void free_cache(gi_cache_s *c) {
     for (int k = 0; k < 2; ++k) {
         cudaFree(c->tags[k]);
@@ -629,8 +682,7 @@ static void free_cache(gi_cache_s *c) {
     cudaFree(c->touch);
     cudaFree(c->ctr);
     cudaFree(c->scan);
-    if (c->ctr_host) cudaFreeHost(c->ctr_host);
-    if (c->snap_event) cudaEventDestroy(c->snap_event);
+    if (c->occ_host) cudaFreeHost((void *)c->occ_host);
     delete c;
 }
 
@@ -672,8 +724,16 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
     if (s == GI_OK) s = cuda_status(cudaMalloc(&c->ctr, sizeof(Counters)), "cudaMalloc counters");
     if (s == GI_OK) s = cuda_status(cudaMemset(c->ctr, 0, sizeof(Counters)), "memset");
     if (s == GI_OK) s = cuda_status(cudaMalloc(&c->scan, 2 * sizeof(unsigned long long)), "cudaMalloc scan");
-    if (s == GI_OK) s = cuda_status(cudaMallocHost(&c->ctr_host, sizeof(Counters)), "cudaMallocHost");
-    if (s == GI_OK) s = cuda_status(cudaEventCreateWithFlags(&c->snap_event, cudaEventDisableTiming), "event");
+    if (s == GI_OK) {
+        void *hp = nullptr;
+        s = cuda_status(cudaHostAlloc(&hp, 2 * sizeof(uint32_t), cudaHostAllocMapped), "cudaHostAlloc");
+        if (s == GI_OK) {
+            c->occ_host = static_cast<volatile uint32_t *>(hp);
+            c->occ_host[0] = 0u;
+            c->occ_host[1] = 0u;
+            s = cuda_status(cudaHostGetDevicePointer((void **)&c->occ_dev, hp, 0), "cudaHostGetDevicePointer");
+        }
+    }
     if (s == GI_OK) {
         int per_sm = 0;
         s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<0>, kUpdThreads, 0),
@@ -720,7 +780,7 @@ gi_status gi_cache_update(gi_cache_t c, const gi_hits *hits, const gi_view *view
     if (s != GI_OK) return s;
     c->updates++;
     if (hits->n == 0) return GI_OK;
-    UpdateArgs a = update_args(c, hits, view, slot_ids);
+    UpdateArgs a = cache_update_args(c, hits, view, slot_ids);
     const int blocks = update_blocks(hits->n);
     if (c->cfg.key_dir == GI_KEY_DIR_NORMAL)
         k_update<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(a);
@@ -742,31 +802,11 @@ gi_status gi_cache_resolve(gi_cache_t c, uint32_t frame, gi_stream_t stream) {
         return GI_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    ResolveArgs a;
-    a.touch = c->touch;
-    a.accum = c->accum[c->cur];
-    a.acc_stride = 1;
-    a.resolved = c->resolved[c->cur];
-    a.res_stride = c->res_bytes;
-    a.ctr = c->ctr;
-    a.alpha = c->cfg.alpha;
-    a.stamp_now = frame + 1u;
-    a.has_lr = c->last_resolved >= 0;
-    a.lr = c->last_resolved >= 0 ? (uint32_t)c->last_resolved : 0u;
-    a.evict = c->cfg.evict_frames;
-    a.f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
+    const ResolveArgs a = cache_resolve_args(c, frame);
     k_resolve<<<c->res_blocks, kResThreads, 0, st>>>(a);
     gi_status s = cuda_status(cudaGetLastError(), "k_resolve launch");
     if (s != GI_OK) return s;
-    // occupancy snapshot, read by the next update to decide on a compaction
-    s = cuda_status(cudaMemcpyAsync(c->ctr_host, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st), "snapshot");
-    if (s == GI_OK) s = cuda_status(cudaEventRecord(c->snap_event, st), "snapshot event");
-    if (s != GI_OK) return s;
-    c->snap_pending = true;
-    c->rebuild_checked = false;
-    c->last_resolved = frame;
-    c->touched_since_resolve = false;
-    c->resolves++;
+    cache_after_resolve(c, frame);
     return GI_OK;
 }
 
@@ -791,7 +831,7 @@ gi_status gi_cache_query(gi_cache_t c, const gi_query *q, float *out, gi_stream_
             set_error("gi_cache_query: by point needs points with n records and a valid view");
             return GI_ERR_INVALID_ARG;
         }
-        UpdateArgs a = update_args(c, q->points, q->view, nullptr);
+        UpdateArgs a = cache_update_args(c, q->points, q->view, nullptr);
         a.n = q->n;
         if (c->cfg.key_dir == GI_KEY_DIR_NORMAL)
             k_query_points<GI_KEY_DIR_NORMAL><<<blocks, 256, 0, st>>>(a, c->resolved[c->cur], c->res_bytes, f16, live_rule(c),

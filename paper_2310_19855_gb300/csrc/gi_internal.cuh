@@ -60,6 +60,93 @@ struct CamParams {
 };
 CamParams cam_params(const gi_view *v);
 
+
+// ---------------------------------------------------------------- per-pass arguments
+typedef uint32_t SlotWord;  // tag = fingerprint << 8 | (home mod 256); 0 = empty
+__device__ __forceinline__ uint32_t word_tag(SlotWord w) { return w; }
+
+struct UpdateArgs {
+    const float *p[3];
+    const float *nrm[3];
+    const float *rad[3];
+    const float *len;
+    const float *dir[3];
+    uint32_t *slot_ids;
+    unsigned long long n;
+    SlotWord *tags;
+    Accum *accum;
+    uint32_t acc_stride;  // Accum units between consecutive slots
+    uint32_t *touch;
+    Counters *ctr;
+    uint32_t mask;
+    uint32_t max_probe;
+    KeyParams kp;
+};
+
+struct ResolveArgs {
+    const uint32_t *touch;
+    Accum *accum;
+    uint32_t acc_stride;
+    void *resolved;
+    uint32_t res_stride;  // bytes between consecutive resolved values
+    Counters *ctr;
+    float alpha;
+    uint32_t stamp_now;   // frame + 1
+    uint32_t has_lr;      // a resolve happened before
+    uint32_t lr;          // frame of that resolve
+    uint32_t evict;       // E
+    int f16;
+    uint32_t *occ_out;    // host-mapped {occupied slots, stamp_now}, written by the last block
+};
+
+struct LiveRule {
+    uint32_t has_lr, lr, evict;
+};
+
+struct MipInfo {
+    int count;
+    int w[GI_MAX_MIPS], h[GI_MAX_MIPS], off[GI_MAX_MIPS];
+};
+
+struct SpawnArgs {
+    const float4 *gbuf;
+    uint32_t width, height;
+    CamParams cam;
+    int jx, jy;
+    uint32_t *mask;
+    float4 *pos;
+    float4 *nrm;
+    uint32_t tiles_x, tiles_y;
+    MipInfo mi;
+};
+
+struct IntegrateArgs {
+    const uint32_t *slot_ids;
+    const void *resolved;
+    uint32_t res_stride;
+    int f16;
+    uint32_t slots;
+    const float4 *nrm;
+    float *sh;
+    uint32_t probes;
+    uint32_t rpp;
+    float env[3];
+};
+
+struct InterpArgs {
+    const float4 *gbuf;
+    uint32_t width, height;
+    CamParams cam;
+    float dscale;
+    const uint32_t *mask;
+    MipInfo mi;
+    const float4 *ppos;
+    const float4 *pnrm;
+    const float *sh;
+    uint32_t tiles_x;
+    float4 *out;
+};
+
 // Cache internals needed by the probe kernels.
 struct CacheView {
     const void *resolved;      // resolved radiance of slot 0: float4, or half4 (ushort4)
@@ -69,10 +156,66 @@ struct CacheView {
 };
 CacheView cache_view(gi_cache_t c);
 
+// Host helpers of the cache used by the batched pass chain (gi_cache.cu).
+bool hits_ok(const gi_hits *h, uint32_t key_dir);
+UpdateArgs cache_update_args(gi_cache_t c, const gi_hits *h, const gi_view *v, uint32_t *slot_ids);
+gi_status cache_before_update(gi_cache_t c, cudaStream_t st);  // compaction check, counters
+void cache_after_update(gi_cache_t c);
+ResolveArgs cache_resolve_args(gi_cache_t c, uint32_t frame);
+void cache_after_resolve(gi_cache_t c, uint32_t frame);
+int cache_key_dir(const gi_cache_s *c);
+int cache_device(const gi_cache_s *c);
+int64_t cache_last_resolved(const gi_cache_s *c);
+
+// Launchers of the batched passes: one launch per pass over every view; args and prefix tables
+// (nviews + 1 block-count prefixes) live in device memory.
+uint32_t update_blocks_for(unsigned long long n, uint32_t records_per_block);
+gi_status launch_update_batched(const UpdateArgs *args, const uint32_t *prefix, uint32_t nviews, uint32_t blocks,
+                                int key_dir, cudaStream_t st);
+gi_status launch_resolve_batched(const ResolveArgs *args, const uint32_t *prefix, uint32_t nviews, uint32_t blocks,
+                                 cudaStream_t st);
+gi_status launch_spawn_batched(const SpawnArgs *args, const uint32_t *prefix, uint32_t nviews, uint32_t blocks,
+                               cudaStream_t st);
+gi_status launch_integrate_batched(const IntegrateArgs *args, const uint32_t *prefix, uint32_t nviews,
+                                   uint32_t blocks, uint32_t threads, cudaStream_t st);
+gi_status launch_interpolate_batched(const InterpArgs *args, const uint32_t *prefix, uint32_t nviews,
+                                     uint32_t blocks, cudaStream_t st);
+
+// Host helpers of the probe passes used by the batched pass chain (gi_probes.cu).
+gi_status ensure_moments();
+gi_status spawn_check(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr);
+SpawnArgs spawn_args(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr);
+gi_status integrate_check(gi_cache_t cache, const gi_probes *pr, const uint32_t *slot_ids, uint32_t rays_per_probe);
+IntegrateArgs integrate_args(gi_cache_t cache, const gi_probes *pr, const uint32_t *slot_ids, uint32_t rpp,
+                             const float env[3]);
+gi_status interp_check(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr, const float *out);
+InterpArgs interp_args(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr, float *out);
+
 } // namespace gi
 
 // ---------------------------------------------------------------- device helpers
 namespace gi {
+
+// View of a flat block index through the prefix table of per-view block counts (prefix[0] = 0,
+// prefix[nviews] = total): the v with prefix[v] <= blk < prefix[v + 1].
+__device__ __forceinline__ uint32_t view_of_block(const uint32_t *prefix, uint32_t nviews, uint32_t blk) {
+    uint32_t lo = 0, hi = nviews;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= blk) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Copy one view's pass arguments from global to shared memory (whole block; sync after).
+template <typename T>
+__device__ __forceinline__ void load_view_args(T &dst, const T *src) {
+    static_assert(sizeof(T) % 4 == 0, "argument structs are copied as 32-bit words");
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(&dst);
+    for (uint32_t i = threadIdx.x; i < sizeof(T) / 4; i += blockDim.x) d[i] = __ldg(s + i);
+}
 
 __device__ __forceinline__ float3 cam_ray_dir(const CamParams &c, float x, float y) {
     // sx = (2(x+0.5)/W - 1) tan(fov/2) W/H, sy = (1 - 2(y+0.5)/H) tan(fov/2)

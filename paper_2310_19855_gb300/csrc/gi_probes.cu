@@ -14,10 +14,6 @@ namespace gi {
 
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
 
-struct MipInfo {
-    int count;
-    int w[GI_MAX_MIPS], h[GI_MAX_MIPS], off[GI_MAX_MIPS];
-};
 
 static MipInfo mip_info(const gi_probe_layout &l) {
     MipInfo m;
@@ -112,7 +108,7 @@ static void cell_moments_closed_form(int c, double out[10]) {
 static std::mutex g_moments_mutex;
 static bool g_moments_ready[64];
 
-static gi_status ensure_moments() {
+gi_status ensure_moments() {
     int dev = 0;
     gi_status s = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
     if (s != GI_OK) return s;
@@ -130,23 +126,12 @@ static gi_status ensure_moments() {
 }
 
 // ---------------------------------------------------------------- spawn
-struct SpawnArgs {
-    const float4 *gbuf;
-    uint32_t width, height;
-    CamParams cam;
-    int jx, jy;
-    uint32_t *mask;
-    float4 *pos;
-    float4 *nrm;
-    uint32_t tiles_x, tiles_y;
-    MipInfo mi;
-};
 
 // Block of 16x16 tiles: level 0 plus levels 1..4 of its region, built in shared memory.
-__global__ void __launch_bounds__(256) k_spawn(SpawnArgs a) {
+__device__ __forceinline__ void spawn_body(const SpawnArgs &a, uint32_t bx, uint32_t by) {
     __shared__ uint32_t s_lvl[2][16][16];
     const int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
-    const uint32_t tx = blockIdx.x * 16 + lx, ty = blockIdx.y * 16 + ly;
+    const uint32_t tx = bx * 16 + lx, ty = by * 16 + ly;
     uint32_t m = GI_PROBE_NONE;
     if (tx < a.tiles_x && ty < a.tiles_y) {
         const uint32_t px = min(8u * tx + (uint32_t)a.jx, a.width - 1u);
@@ -182,15 +167,17 @@ __global__ void __launch_bounds__(256) k_spawn(SpawnArgs a) {
         __syncthreads();
         if ((int)threadIdx.x < n * n) {
             s_lvl[dst][y][x] = v;
-            const int X = blockIdx.x * n + x, Y = blockIdx.y * n + y;
+            const int X = bx * n + x, Y = by * n + y;
             if (X < a.mi.w[L] && Y < a.mi.h[L]) a.mask[a.mi.off[L] + Y * a.mi.w[L] + X] = v;
         }
         __syncthreads();
     }
 }
 
+__global__ void __launch_bounds__(256) k_spawn(SpawnArgs a) { spawn_body(a, blockIdx.x, blockIdx.y); }
+
 // Levels 5 and up, from level 4, in one block.
-__global__ void __launch_bounds__(1024) k_mip_tail(uint32_t *mask, MipInfo mi) {
+__device__ __forceinline__ void mip_tail_body(uint32_t *mask, const MipInfo &mi) {
     for (int L = 5; L < mi.count; ++L) {
         const int w = mi.w[L], h = mi.h[L], pw = mi.w[L - 1], ph = mi.h[L - 1];
         const uint32_t *src = mask + mi.off[L - 1];
@@ -206,19 +193,9 @@ __global__ void __launch_bounds__(1024) k_mip_tail(uint32_t *mask, MipInfo mi) {
     }
 }
 
+__global__ void __launch_bounds__(1024) k_mip_tail(uint32_t *mask, MipInfo mi) { mip_tail_body(mask, mi); }
+
 // ---------------------------------------------------------------- probe irradiance
-struct IntegrateArgs {
-    const uint32_t *slot_ids;
-    const void *resolved;
-    uint32_t res_stride;
-    int f16;
-    uint32_t slots;
-    const float4 *nrm;
-    float *sh;
-    uint32_t probes;
-    uint32_t rpp;
-    float env[3];
-};
 
 __device__ __forceinline__ float3 fetch_resolved(const void *r, uint32_t stride, int f16, uint32_t s) {
     r = static_cast<const char *>(r) + (size_t)s * stride;
@@ -257,8 +234,8 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
 }
 
 // One warp per probe; lane l owns cells l and l + 32.
-__global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) {
-    const uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t blk) {
+    const uint32_t p = (blk * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= a.probes) return;
     const float4 n4 = __ldg(a.nrm + p);
@@ -363,20 +340,9 @@ __global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) {
     out[lane] = val;
 }
 
+__global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) { integrate_body(a, blockIdx.x); }
+
 // ---------------------------------------------------------------- interpolation
-struct InterpArgs {
-    const float4 *gbuf;
-    uint32_t width, height;
-    CamParams cam;
-    float dscale;
-    const uint32_t *mask;
-    MipInfo mi;
-    const float4 *ppos;
-    const float4 *pnrm;
-    const float *sh;
-    uint32_t tiles_x;
-    float4 *out;
-};
 
 // Algorithm 3 from MIP level m0 on: probe-space position (tx, ty) at that level plus the
 // offset; climb the chain (halving the position, floor) until a probe is found or the position
@@ -403,10 +369,10 @@ __device__ __forceinline__ uint32_t pick_u4(const uint32_t (&v)[4], int i) {
 
 // Block = 16x16 pixels starting at (16 bx - 4, 16 by - 4); warp = 8x4 pixels that
 // share one base tile, so the four neighbour probes are warp-uniform loads.
-__global__ void __launch_bounds__(256, 4) k_interpolate(InterpArgs a) {
+__device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t bx, uint32_t by) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x = (int)blockIdx.x * 16 - 4 + 8 * (warp & 1) + (lane & 7);
-    const int y = (int)blockIdx.y * 16 - 4 + 4 * (warp >> 1) + (lane >> 3);
+    const int x = (int)bx * 16 - 4 + 8 * (warp & 1) + (lane & 7);
+    const int y = (int)by * 16 - 4 + 4 * (warp >> 1) + (lane >> 3);
     const bool inb = x >= 0 && y >= 0 && x < (int)a.width && y < (int)a.height;
     const size_t pix = inb ? (size_t)y * a.width + x : 0;
     const int tx = (x - 4) >> 3, ty = (y - 4) >> 3;
@@ -550,6 +516,8 @@ __global__ void __launch_bounds__(256, 4) k_interpolate(InterpArgs a) {
     __stcs(a.out + pix, r);
 }
 
+__global__ void __launch_bounds__(256, 4) k_interpolate(InterpArgs a) { interpolate_body(a, blockIdx.x, blockIdx.y); }
+
 static bool layout_matches(const gi_probe_layout &l, uint32_t w, uint32_t h) {
     return l.tiles_x == (w + 7) / 8 && l.tiles_y == (h + 7) / 8 && l.num_probes == l.tiles_x * l.tiles_y &&
            l.mip_count >= 1 && l.mip_count <= GI_MAX_MIPS;
@@ -564,6 +532,160 @@ static int halton_times8(uint32_t i, uint32_t base) {
         i /= base;
     }
     return (int)((8 * num) / den);
+}
+
+
+gi_status spawn_check(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr) {
+    if (!gbuf || !pr || !view_ok(view) || !gbuf->nd || !pr->mask || !pr->pos || !pr->nrm) {
+        set_error("gi_probes_spawn: NULL argument or bad view");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (gbuf->width != view->width || gbuf->height != view->height ||
+        !layout_matches(pr->layout, view->width, view->height) || ((uintptr_t)gbuf->nd & 15) ||
+        ((uintptr_t)pr->pos & 15) || ((uintptr_t)pr->nrm & 15)) {
+        set_error("gi_probes_spawn: G-buffer/probe layout does not match the view, or misaligned buffers");
+        return GI_ERR_INVALID_ARG;
+    }
+    return GI_OK;
+}
+
+SpawnArgs spawn_args(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr) {
+    SpawnArgs a;
+    a.gbuf = reinterpret_cast<const float4 *>(gbuf->nd);
+    a.width = view->width;
+    a.height = view->height;
+    a.cam = cam_params(view);
+    a.jx = halton_times8(view->frame + 1u, 2);
+    a.jy = halton_times8(view->frame + 1u, 3);
+    a.mask = pr->mask;
+    a.pos = reinterpret_cast<float4 *>(pr->pos);
+    a.nrm = reinterpret_cast<float4 *>(pr->nrm);
+    a.tiles_x = pr->layout.tiles_x;
+    a.tiles_y = pr->layout.tiles_y;
+    a.mi = mip_info(pr->layout);
+    return a;
+}
+
+gi_status integrate_check(gi_cache_t cache, const gi_probes *pr, const uint32_t *slot_ids, uint32_t rays_per_probe) {
+    if (!cache || !pr || !pr->nrm || !pr->sh || (!slot_ids && pr->layout.num_probes > 0)) {
+        set_error("gi_probes_integrate: NULL argument");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (rays_per_probe == 0 || rays_per_probe % 64 != 0 || ((uintptr_t)pr->nrm & 15)) {
+        set_error("gi_probes_integrate: rays_per_probe must be a positive multiple of 64; nrm 16-byte aligned");
+        return GI_ERR_INVALID_ARG;
+    }
+    return GI_OK;
+}
+
+IntegrateArgs integrate_args(gi_cache_t cache, const gi_probes *pr, const uint32_t *slot_ids, uint32_t rpp,
+                             const float env[3]) {
+    const CacheView cv = cache_view(cache);
+    IntegrateArgs a;
+    a.slot_ids = slot_ids;
+    a.resolved = cv.resolved;
+    a.res_stride = cv.resolved_stride;
+    a.f16 = cv.resolved_f16;
+    a.slots = cv.slots;
+    a.nrm = reinterpret_cast<const float4 *>(pr->nrm);
+    a.sh = pr->sh;
+    a.probes = pr->layout.num_probes;
+    a.rpp = rpp;
+    for (int c = 0; c < 3; ++c) a.env[c] = env ? env[c] : 0.0f;
+    return a;
+}
+
+gi_status interp_check(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr, const float *out) {
+    if (!gbuf || !pr || !out || !view_ok(view) || !gbuf->nd || !pr->mask || !pr->pos || !pr->nrm || !pr->sh) {
+        set_error("gi_probes_interpolate: NULL argument or bad view");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (gbuf->width != view->width || gbuf->height != view->height ||
+        !layout_matches(pr->layout, view->width, view->height) || ((uintptr_t)gbuf->nd & 15) ||
+        ((uintptr_t)out & 15) || ((uintptr_t)pr->sh & 15)) {
+        set_error("gi_probes_interpolate: layout does not match the view, or misaligned buffers");
+        return GI_ERR_INVALID_ARG;
+    }
+    return GI_OK;
+}
+
+InterpArgs interp_args(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr, float *out) {
+    InterpArgs a;
+    a.gbuf = reinterpret_cast<const float4 *>(gbuf->nd);
+    a.width = view->width;
+    a.height = view->height;
+    a.cam = cam_params(view);
+    a.dscale = (float)distance_scale(view->fov_y, view->width, view->height);
+    a.mask = pr->mask;
+    a.mi = mip_info(pr->layout);
+    a.ppos = reinterpret_cast<const float4 *>(pr->pos);
+    a.pnrm = reinterpret_cast<const float4 *>(pr->nrm);
+    a.sh = pr->sh;
+    a.tiles_x = pr->layout.tiles_x;
+    a.out = reinterpret_cast<float4 *>(out);
+    return a;
+}
+
+
+// ---------------------------------------------------------------- batched passes (many views)
+__global__ void __launch_bounds__(256) k_spawn_batched(const SpawnArgs *args, const uint32_t *prefix, uint32_t nviews) {
+    __shared__ SpawnArgs sa;
+    const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
+    load_view_args(sa, args + v);
+    __syncthreads();
+    const uint32_t b = blockIdx.x - __ldg(prefix + v), gx = (sa.tiles_x + 15) / 16;
+    spawn_body(sa, b % gx, b / gx);
+}
+
+// MIP levels 5 and up of every view: one block per view.
+__global__ void __launch_bounds__(1024) k_mip_tail_batched(const SpawnArgs *args) {
+    __shared__ SpawnArgs sa;
+    load_view_args(sa, args + blockIdx.x);
+    __syncthreads();
+    if (sa.mi.count > 5) mip_tail_body(sa.mask, sa.mi);
+}
+
+__global__ void __launch_bounds__(256) k_integrate_batched(const IntegrateArgs *args, const uint32_t *prefix,
+                                                           uint32_t nviews) {
+    __shared__ IntegrateArgs sa;
+    const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
+    load_view_args(sa, args + v);
+    __syncthreads();
+    integrate_body(sa, blockIdx.x - __ldg(prefix + v));
+}
+
+__global__ void __launch_bounds__(256, 4) k_interpolate_batched(const InterpArgs *args, const uint32_t *prefix,
+                                                                uint32_t nviews) {
+    __shared__ InterpArgs sa;
+    const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
+    load_view_args(sa, args + v);
+    __syncthreads();
+    const uint32_t b = blockIdx.x - __ldg(prefix + v), gx = (sa.width + 4 + 15) / 16;
+    interpolate_body(sa, b % gx, b / gx);
+}
+
+gi_status launch_spawn_batched(const SpawnArgs *args, const uint32_t *prefix, uint32_t nviews, uint32_t blocks,
+                               cudaStream_t st) {
+    if (blocks == 0) return GI_OK;
+    k_spawn_batched<<<blocks, 256, 0, st>>>(args, prefix, nviews);
+    gi_status s = cuda_status(cudaGetLastError(), "k_spawn_batched launch");
+    if (s != GI_OK) return s;
+    k_mip_tail_batched<<<nviews, 1024, 0, st>>>(args);
+    return cuda_status(cudaGetLastError(), "k_mip_tail_batched launch");
+}
+
+gi_status launch_integrate_batched(const IntegrateArgs *args, const uint32_t *prefix, uint32_t nviews,
+                                   uint32_t blocks, uint32_t threads, cudaStream_t st) {
+    if (blocks == 0) return GI_OK;
+    k_integrate_batched<<<blocks, threads, 0, st>>>(args, prefix, nviews);
+    return cuda_status(cudaGetLastError(), "k_integrate_batched launch");
+}
+
+gi_status launch_interpolate_batched(const InterpArgs *args, const uint32_t *prefix, uint32_t nviews,
+                                     uint32_t blocks, cudaStream_t st) {
+    if (blocks == 0) return GI_OK;
+    k_interpolate_batched<<<blocks, 256, 0, st>>>(args, prefix, nviews);
+    return cuda_status(cudaGetLastError(), "k_interpolate_batched launch");
 }
 
 } // namespace gi
@@ -607,33 +729,13 @@ gi_status gi_probes_layout(uint32_t width, uint32_t height, gi_probe_layout *out
 }
 
 gi_status gi_probes_spawn(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr, gi_stream_t stream) {
-    if (!gbuf || !pr || !view_ok(view) || !gbuf->nd || !pr->mask || !pr->pos || !pr->nrm) {
-        set_error("gi_probes_spawn: NULL argument or bad view");
-        return GI_ERR_INVALID_ARG;
-    }
-    if (gbuf->width != view->width || gbuf->height != view->height ||
-        !layout_matches(pr->layout, view->width, view->height) || ((uintptr_t)gbuf->nd & 15) ||
-        ((uintptr_t)pr->pos & 15) || ((uintptr_t)pr->nrm & 15)) {
-        set_error("gi_probes_spawn: G-buffer/probe layout does not match the view, or misaligned buffers");
-        return GI_ERR_INVALID_ARG;
-    }
+    gi_status s = spawn_check(gbuf, view, pr);
+    if (s != GI_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    SpawnArgs a;
-    a.gbuf = reinterpret_cast<const float4 *>(gbuf->nd);
-    a.width = view->width;
-    a.height = view->height;
-    a.cam = cam_params(view);
-    a.jx = halton_times8(view->frame + 1u, 2);
-    a.jy = halton_times8(view->frame + 1u, 3);
-    a.mask = pr->mask;
-    a.pos = reinterpret_cast<float4 *>(pr->pos);
-    a.nrm = reinterpret_cast<float4 *>(pr->nrm);
-    a.tiles_x = pr->layout.tiles_x;
-    a.tiles_y = pr->layout.tiles_y;
-    a.mi = mip_info(pr->layout);
+    const SpawnArgs a = spawn_args(gbuf, view, pr);
     dim3 grid((a.tiles_x + 15) / 16, (a.tiles_y + 15) / 16);
     k_spawn<<<grid, 256, 0, st>>>(a);
-    gi_status s = cuda_status(cudaGetLastError(), "k_spawn launch");
+    s = cuda_status(cudaGetLastError(), "k_spawn launch");
     if (s == GI_OK && a.mi.count > 5) {
         k_mip_tail<<<1, 1024, 0, st>>>(pr->mask, a.mi);
         s = cuda_status(cudaGetLastError(), "k_mip_tail launch");
@@ -643,28 +745,11 @@ gi_status gi_probes_spawn(const gi_gbuffer *gbuf, const gi_view *view, const gi_
 
 gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *pr, const uint32_t *slot_ids,
                               uint32_t rays_per_probe, const float env[3], gi_stream_t stream) {
-    if (!cache || !pr || !pr->nrm || !pr->sh || (!slot_ids && pr->layout.num_probes > 0)) {
-        set_error("gi_probes_integrate: NULL argument");
-        return GI_ERR_INVALID_ARG;
-    }
-    if (rays_per_probe == 0 || rays_per_probe % 64 != 0 || ((uintptr_t)pr->nrm & 15)) {
-        set_error("gi_probes_integrate: rays_per_probe must be a positive multiple of 64; nrm 16-byte aligned");
-        return GI_ERR_INVALID_ARG;
-    }
-    gi_status s = ensure_moments();
+    gi_status s = integrate_check(cache, pr, slot_ids, rays_per_probe);
     if (s != GI_OK) return s;
-    const CacheView cv = cache_view(cache);
-    IntegrateArgs a;
-    a.slot_ids = slot_ids;
-    a.resolved = cv.resolved;
-    a.res_stride = cv.resolved_stride;
-    a.f16 = cv.resolved_f16;
-    a.slots = cv.slots;
-    a.nrm = reinterpret_cast<const float4 *>(pr->nrm);
-    a.sh = pr->sh;
-    a.probes = pr->layout.num_probes;
-    a.rpp = rays_per_probe;
-    for (int c = 0; c < 3; ++c) a.env[c] = env ? env[c] : 0.0f;
+    s = ensure_moments();
+    if (s != GI_OK) return s;
+    const IntegrateArgs a = integrate_args(cache, pr, slot_ids, rays_per_probe, env);
     if (a.probes == 0) return GI_OK;
     const unsigned blocks = (a.probes + 7) / 8;
     k_integrate<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
@@ -673,29 +758,9 @@ gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *pr, const uint3
 
 gi_status gi_probes_interpolate(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr, float *out,
                                 gi_stream_t stream) {
-    if (!gbuf || !pr || !out || !view_ok(view) || !gbuf->nd || !pr->mask || !pr->pos || !pr->nrm || !pr->sh) {
-        set_error("gi_probes_interpolate: NULL argument or bad view");
-        return GI_ERR_INVALID_ARG;
-    }
-    if (gbuf->width != view->width || gbuf->height != view->height ||
-        !layout_matches(pr->layout, view->width, view->height) || ((uintptr_t)gbuf->nd & 15) ||
-        ((uintptr_t)out & 15) || ((uintptr_t)pr->sh & 15)) {
-        set_error("gi_probes_interpolate: layout does not match the view, or misaligned buffers");
-        return GI_ERR_INVALID_ARG;
-    }
-    InterpArgs a;
-    a.gbuf = reinterpret_cast<const float4 *>(gbuf->nd);
-    a.width = view->width;
-    a.height = view->height;
-    a.cam = cam_params(view);
-    a.dscale = (float)distance_scale(view->fov_y, view->width, view->height);
-    a.mask = pr->mask;
-    a.mi = mip_info(pr->layout);
-    a.ppos = reinterpret_cast<const float4 *>(pr->pos);
-    a.pnrm = reinterpret_cast<const float4 *>(pr->nrm);
-    a.sh = pr->sh;
-    a.tiles_x = pr->layout.tiles_x;
-    a.out = reinterpret_cast<float4 *>(out);
+    gi_status s = interp_check(gbuf, view, pr, out);
+    if (s != GI_OK) return s;
+    const InterpArgs a = interp_args(gbuf, view, pr, out);
     dim3 grid((view->width + 4 + 15) / 16, (view->height + 4 + 15) / 16);
     k_interpolate<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
     return cuda_status(cudaGetLastError(), "k_interpolate launch");

@@ -6,9 +6,10 @@ from __future__ import annotations
 
 import torch
 
-from . import (GI_RESOLVED_F32, GI_SH_STRIDE, gi_cache_create, gi_cache_destroy, gi_cache_resolve,
-               gi_cache_update, gi_probes_integrate, gi_probes_interpolate, gi_probes_layout, gi_probes_spawn,
-               hits_from_planes, make_gbuffer, make_probes, make_view)
+from . import (GI_RESOLVED_F32, GI_SH_STRIDE, gi_batch_create, gi_batch_destroy, gi_batch_frame, gi_batch_view,
+               gi_cache_create, gi_cache_destroy, gi_cache_resolve, gi_cache_update, gi_probes_integrate,
+               gi_probes_interpolate, gi_probes_layout, gi_probes_spawn, hits_from_planes, make_gbuffer, make_probes,
+               make_view)
 
 
 def view_of(camera, frame: int):
@@ -79,6 +80,62 @@ class Pipeline:
         if self.cache:
             gi_cache_destroy(self.cache)
             self.cache = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchPipeline:
+    """Many views per frame through one batch (one launch per pass over all views).
+
+    views: list of (width, height, log2_slots) per view; every view uses rays_per_probe rays per
+    probe.  Each view owns a cache and its probe / slot-id / irradiance buffers."""
+
+    def __init__(self, views, rays_per_probe: int = 64, tuning=None, cache_kw=None, device="cuda"):
+        cache_kw = cache_kw or {}
+        self.rpp = rays_per_probe
+        self.views = []
+        for (w, h, log2_slots) in views:
+            pb = ProbeBuffers(w, h, device)
+            n = pb.layout.num_probes * rays_per_probe
+            self.views.append(dict(
+                width=w, height=h, probes=pb, n_records=n,
+                slot_ids=torch.empty(n, dtype=torch.int32, device=device),
+                irr=torch.empty((h, w, 4), dtype=torch.float32, device=device),
+                cache=gi_cache_create(log2_slots, **cache_kw)))
+        self.batch = gi_batch_create(len(self.views), rays_per_probe, tuning)
+        self._desc = (gi_batch_view * len(self.views))()
+
+    def frame(self, gbufs, records, gviews, env=(0.0, 0.0, 0.0), use_graph=False, stream=None,
+              resolve_frame: int | None = None):
+        """One frame of every view: gbufs[v] (H, W, 4), records[v] (planes, R) on the device, gviews[v]
+        the view (camera, size, frame index of the spawn jitter); the caches resolve at
+        resolve_frame (default: each view's frame index)."""
+        for v, st in enumerate(self.views):
+            d = self._desc[v]
+            d.cache = st["cache"]
+            d.view = gviews[v]
+            d.resolve_frame = gviews[v].frame if resolve_frame is None else int(resolve_frame)
+            d.hits = hits_from_planes(records[v], st["n_records"])
+            d.gbuf = make_gbuffer(gbufs[v], st["width"], st["height"])
+            d.probes = st["probes"].struct
+            d.slot_ids = st["slot_ids"].data_ptr()
+            d.irradiance = st["irr"].data_ptr()
+            for k in range(3):
+                d.env[k] = float(env[k])
+        gi_batch_frame(self.batch, self._desc, use_graph, stream)
+
+    def close(self):
+        if self.batch:
+            gi_batch_destroy(self.batch)
+            self.batch = None
+        for st in self.views:
+            if st.get("cache"):
+                gi_cache_destroy(st["cache"])
+                st["cache"] = None
 
     def __del__(self):
         try:

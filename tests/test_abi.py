@@ -6,6 +6,7 @@ import ctypes
 import math
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -34,11 +35,29 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
-def test_struct_sizes_match_header_layout():
-    assert ctypes.sizeof(gi.gi_view) == 72
-    assert ctypes.sizeof(gi.gi_hits) == 13 * 8 + 8
-    assert ctypes.sizeof(gi.gi_cell) == 56
-    assert ctypes.sizeof(gi.gi_cache_config) == 36
+STRUCTS = ["gi_cache_config", "gi_view", "gi_hits", "gi_gbuffer", "gi_probe_layout", "gi_probes",
+           "gi_cache_stats_t", "gi_cell", "gi_query", "gi_batch_tuning", "gi_batch_view"]
+
+
+def test_struct_layouts_match_the_c_header(tmp_path):
+    # sizeof and every field offset as the C compiler lays them out, against the ctypes mirror
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gi.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in getattr(gi, name)._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = dict(line.split(" ") for line in out if line)
+    for name in STRUCTS:
+        cls = getattr(gi, name)
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
 
 
 def test_status_strings(lib):

@@ -8,6 +8,7 @@ arithmetic; the oracle and the CUDA path both read its output unchanged.
 """
 from .scene import (  # noqa: F401
     CONFIGS,
+    batched_views,
     Camera,
     Frame,
     build_tracer,

@@ -55,6 +55,30 @@ CONFIGS = {
 }
 
 
+# Configuration 3: 16 independent views of uneven resolution, each its own seeded scene (Cornell
+# boxes and small box rooms alternating), 64 rays per probe (0.23 M to 3.7 M records per view).
+_VIEW_SIZES = ((640, 360), (1280, 720), (1920, 1080), (2560, 1440))
+
+
+def batched_views(n_views: int = 16, sizes=_VIEW_SIZES):
+    """Per-view configuration dicts of the batched workload (with their seed bases)."""
+    views = []
+    for v in range(n_views):
+        w, h = sizes[v % len(sizes)]
+        if v % 2 == 0:
+            cfg = dict(CONFIGS[1], width=w, height=h, rays_per_probe=64, frames=32, moving_camera=False,
+                       log2_slots=21 if w * h > 1_000_000 else 20)
+        else:
+            cfg = dict(CONFIGS[2], width=w, height=h, frames=32, n_boxes=512, room=(24.0, 8.0, 24.0),
+                       log2_slots=21 if w * h > 1_000_000 else 20)
+        cfg["name"] = f"view{v}-{cfg['scene']}-{w}x{h}"
+        views.append((cfg, SEED_BASE + 3000 + 100 * v))
+    return views
+
+
+CONFIGS[3] = dict(name="batched-16-views", scene="batched", n_views=16, frames=32)
+
+
 # --------------------------------------------------------------------------- tracer
 def build_tracer(force: bool = False) -> str:
     """Compile the C ray caster (gcc, OpenMP, no FP contraction)."""
@@ -217,9 +241,12 @@ def _boxes(rng: np.random.Generator, cfg: dict) -> Scene:
     return Scene(bmin, bmax, albedo, emission, moving, "boxes", (lx, ly, lz), path)
 
 
-def make_scene(config: int) -> Scene:
-    cfg = CONFIGS[config]
-    rng = np.random.default_rng(SEED_BASE + 1000 * config)
+def make_scene(config, seed: int | None = None) -> Scene:
+    """Scene of a configuration number (seeded by it) or of a configuration dict and seed."""
+    cfg = CONFIGS[config] if isinstance(config, int) else config
+    if seed is None:
+        seed = SEED_BASE + 1000 * config
+    rng = np.random.default_rng(seed)
     if cfg["scene"] == "cornell":
         return _cornell(rng)
     return _boxes(rng, cfg)
@@ -362,15 +389,20 @@ class Frame:
         return self.records.shape[1]
 
 
-def make_frame(config: int, f: int, scene: Scene | None = None, rays_per_probe: int | None = None) -> Frame:
-    cfg = CONFIGS[config]
+def make_frame(config, f: int, scene: Scene | None = None, rays_per_probe: int | None = None,
+               seed_base: int | None = None) -> Frame:
+    """Frame f of a configuration number or of a configuration dict (then seed_base is required;
+    the frame's random draws use seed_base + f)."""
+    cfg = CONFIGS[config] if isinstance(config, int) else config
+    if seed_base is None:
+        seed_base = SEED_BASE + 1000 * config
     if scene is None:
-        scene = make_scene(config)
+        scene = make_scene(config, seed_base)
     frames = cfg["frames"]
     sc = scene.at_frame(f, frames)
     cam = _camera(sc, cfg, f if cfg["moving_camera"] else 0)
     gb, hit = render_gbuffer(sc, cam)
-    rng = np.random.default_rng(SEED_BASE + 1000 * config + f)
+    rng = np.random.default_rng(seed_base + f)
     rpp = rays_per_probe or cfg["rays_per_probe"]
     W, H = cam.width, cam.height
     tx_n, ty_n = (W + 7) // 8, (H + 7) // 8
@@ -421,7 +453,8 @@ def make_frame(config: int, f: int, scene: Scene | None = None, rays_per_probe: 
     rec[6:9] = rad.T
     rec[9] = ln
     rec[10:13] = d.T
-    return Frame(config, f, cam, gb, np.ascontiguousarray(rec), rpp, tx_n, ty_n, (jx, jy), valid, lp, li)
+    return Frame(config if isinstance(config, int) else -1, f, cam, gb, np.ascontiguousarray(rec), rpp, tx_n, ty_n,
+                 (jx, jy), valid, lp, li)
 
 
 def make_frames(config: int, frames: int | None = None, start: int = 0, **kw):
