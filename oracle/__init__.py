@@ -24,6 +24,8 @@ Modules, by the part of the paper they follow:
                  Algorithm 3), probe irradiance (Section 2.4.2) and per-pixel
                  interpolation (Section 2.4.1)
   frame.py    -- one frame of the whole path, in the paper's pass order
+  surrogate.py -- the learned radiance surrogate (no paper section: multiresolution hash
+                 encoding, relative L2 loss and Adam from their own publications)
 
 Parity pins are in tests/test_oracle_*.py; every function here is pinned
 there against closed forms, brute force or library routines.
