@@ -358,6 +358,160 @@ gi_status gi_batch_set_tuning(gi_batch_t b, const gi_batch_tuning *tuning);
 gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_graph, gi_stream_t stream);
 gi_status gi_batch_destroy(gi_batch_t b);
 
+/* ---------------------------------------------------------------- learned radiance surrogate */
+/*
+ * An online-trained network that maps a hit (position, normal) to radiance.  The paper has no
+ * learned part: its world cache answers every query from hash cells.  The surrogate is trained
+ * on the cache's own resolved cells and answers the queries the cache serves worst: hits whose
+ * insertion was dropped (GI_SLOT_NONE), hits on cells resolved for the first time (no history
+ * yet), and hits at coarse LODs.  The cache stays the reference: the error of the network on its
+ * latest training batch, measured against the cache's values, decides whether it answers at all.
+ *
+ * Model (published methods, not the paper's):
+ *  - multiresolution hash encoding (Mueller et al. 2022): GI_NRC_LEVELS levels, level l a grid of
+ *    resolution[l] cells per axis over the box [aabb_lo, aabb_hi] (positions are clamped into it);
+ *    each level holds 2^log2_table entries of GI_NRC_FEATURES float16 features; the point's
+ *    features are the trilinear interpolation of the 8 vertices of its cell; a vertex is
+ *    addressed densely when 6 (resolution + 1)^3 <= 2^log2_table, else by the spatial hash
+ *    x * 1 ^ y * 2654435761 ^ z * 805459861 ^ d * 2246822519 (mod 2^log2_table), where
+ *    d in 0..5 is the normal's dominant axis and sign (the cell key's direction code);
+ *  - a network 32 -> 64 -> ReLU -> 64 -> ReLU -> 3 without bias terms, bfloat16 weights and
+ *    activations, float32 accumulation, on the tensor cores; radiance = max(output, 0);
+ *  - loss over a batch of B samples: (1/B) sum_s m_s sum_c (y - t)^2 / (y^2 + loss_eps), with no
+ *    gradient through the denominator (relative L2, Mueller et al. 2021); m_s = 0 skips a sample;
+ *  - Adam with bias correction on float32 master copies of every parameter; on the table it is
+ *    sparse: an entry no sample of the step touched (gradient exactly 0) keeps its value and its
+ *    moments, as in PyTorch's SparseAdam.
+ */
+#define GI_NRC_LEVELS 16
+#define GI_NRC_FEATURES 2
+#define GI_NRC_HIDDEN 64
+#define GI_NRC_OUTPUTS 3
+#define GI_NRC_MAX_BATCH (1u << 20)
+
+typedef struct gi_nrc_s *gi_nrc_t;
+
+/*
+ * Surrogate configuration.
+ *   log2_table   entries per level, 2^10 .. 2^24
+ *   resolution   cells per axis of each level, 1 .. 2^20
+ *   aabb_lo/hi   box the positions are normalised into (hi > lo on every axis)
+ *   lr, beta1, beta2, adam_eps   Adam (lr > 0, betas in [0, 1), eps >= 0)
+ *   loss_eps     relative-L2 denominator term (> 0)
+ *   batch        training samples per gi_nrc_train_frame, 128 .. GI_NRC_MAX_BATCH
+ *   train_steps  minibatches (and Adam steps) those samples are split into; batch must be a
+ *                multiple of train_steps with at least 128 samples per minibatch
+ *   max_records  largest record count of a view passed to gi_nrc_train_frame / gi_nrc_query_frame
+ *   max_queries  most records gi_nrc_query_frame answers per call (the rest keep the cache's value)
+ *   trust        the network answers only while its L1 error on the latest training batch,
+ *                relative to the targets' L1 norm, is at most trust (>= 0)
+ *   query_lod    hits whose cell LOD is >= query_lod are answered by the network (>= 4: none)
+ *   seed         parameter initialisation: table features uniform in [-1e-4, 1e-4], weights
+ *                uniform in +-sqrt(6 / (fan_in + fan_out)), from a splitmix64 stream
+ */
+typedef struct gi_nrc_config {
+    uint32_t log2_table;
+    uint32_t resolution[GI_NRC_LEVELS];
+    float aabb_lo[3], aabb_hi[3];
+    float lr, beta1, beta2, adam_eps;
+    float loss_eps;
+    uint32_t batch;
+    uint32_t train_steps;
+    uint32_t max_records;
+    uint32_t max_queries;
+    float trust;
+    uint32_t query_lod;
+    uint64_t seed;
+} gi_nrc_config;
+
+/* Sample points (device planes of n float32, any 4-byte alignment). */
+typedef struct gi_points {
+    const float *pos[3];
+    const float *nrm[3];
+    uint32_t n;
+} gi_points;
+
+/* Counters of a surrogate (gi_nrc_stats). */
+typedef struct gi_nrc_stats_t {
+    uint64_t steps;        /* Adam steps taken */
+    float loss;            /* loss of the latest gi_nrc_backward batch, or the mean over the
+                              minibatches of the latest gi_nrc_train_frame */
+    float judged_error;    /* sum m |y - t| / sum m |t| over those samples, each evaluated before
+                              its own Adam step */
+    uint32_t trusted;      /* judged_error <= trust and steps > 0 */
+    uint32_t queries;      /* records answered by the latest gi_nrc_query_frame */
+} gi_nrc_stats_t;
+
+/* Create (allocates every parameter, Adam state and scratch buffer; initialises from cfg->seed).
+ * Synchronous.  Errors: GI_ERR_INVALID_ARG, GI_ERR_OOM, GI_ERR_CUDA. */
+gi_status gi_nrc_create(const gi_nrc_config *cfg, gi_nrc_t *out);
+gi_status gi_nrc_destroy(gi_nrc_t nrc);
+
+/*
+ * Parameters as float32 host arrays: table [GI_NRC_LEVELS][2^log2_table][2], w1 [64][32] (output
+ * unit, encoded feature 2l + f), w2 [64][64], w3 [3][64].  set_params replaces the master copies
+ * and resets Adam (moments and step count) and the gradient accumulators; any pointer may be
+ * NULL to leave that part alone.  get_params copies the masters out.  Both synchronise the device.
+ */
+gi_status gi_nrc_set_params(gi_nrc_t nrc, const float *table, const float *w1, const float *w2, const float *w3);
+gi_status gi_nrc_get_params(gi_nrc_t nrc, float *table, float *w1, float *w2, float *w3);
+/* Gradient accumulators, same layouts (host arrays; NULL skips a part).  Synchronise the device. */
+gi_status gi_nrc_set_gradients(gi_nrc_t nrc, const float *table, const float *w1, const float *w2, const float *w3);
+gi_status gi_nrc_get_gradients(gi_nrc_t nrc, float *table, float *w1, float *w2, float *w3);
+
+/* Radiance of n points: out (device float4[n]) = (max(y, 0), 1).  n <= GI_NRC_MAX_BATCH. */
+gi_status gi_nrc_infer(gi_nrc_t nrc, const gi_points *pts, float *out, gi_stream_t stream);
+
+/*
+ * Loss gradients of one batch, added to the gradient accumulators (which an Adam step clears).
+ * target: device planes [3][n] float32; mask: device float[n] of 0/1, or NULL for all 1;
+ * batch_norm: B of the loss (0: B = n).  The loss and judged error go to gi_nrc_stats.
+ */
+gi_status gi_nrc_backward(gi_nrc_t nrc, const gi_points *pts, const float *const target[3], const float *mask,
+                          uint32_t batch_norm, gi_stream_t stream);
+
+/* One Adam step of every parameter from the gradient accumulators, which it then clears. */
+gi_status gi_nrc_adam(gi_nrc_t nrc, gi_stream_t stream);
+
+/*
+ * Training on a view's resolved cells (call after gi_cache_resolve of the frame): sample
+ * k < cfg.batch is record pcg(k ^ pcg(frame + 1)) mod hits->n (PCG hash: one LCG step with
+ * multiplier 747796405 and increment 2891336453, then the RXS-M-XS output permutation); its
+ * target is the cache's resolved radiance of the record's cell (slot_ids from gi_cache_update),
+ * masked out for records without a cell.  Minibatch j = samples [j b, (j + 1) b), b = batch /
+ * train_steps, each followed by its Adam step (loss normalised by b).
+ */
+gi_status gi_nrc_train_frame(gi_nrc_t nrc, gi_cache_t cache, const gi_hits *hits, const uint32_t *slot_ids,
+                             uint32_t frame, gi_stream_t stream);
+
+/*
+ * Pick the records of a view the network answers and evaluate it there (call after
+ * gi_cache_resolve and gi_nrc_train_frame): hits whose slot is GI_SLOT_NONE, hits on cells
+ * resolved this frame for the first time, and hits whose cell LOD (the view's Algorithm 6
+ * thresholds, as in the cell key) is >= cfg.query_lod -- only while the judged error of the
+ * latest training batch is <= cfg.trust, and at most cfg.max_queries records.  The answers stay
+ * in the surrogate for gi_probes_integrate_nrc.
+ */
+gi_status gi_nrc_query_frame(gi_nrc_t nrc, gi_cache_t cache, const gi_hits *hits, const uint32_t *slot_ids,
+                             const gi_view *view, gi_stream_t stream);
+
+/*
+ * The records answered by the latest gi_nrc_query_frame, in increasing record order: records
+ * (device u32[capacity]) and their radiance rad (device float4[capacity], (r, g, b, 1)); *count
+ * (host) receives the number answered.  Synchronises `stream`.  GI_ERR_CAPACITY (nothing copied)
+ * when count > capacity; NULL records and rad with capacity 0 ask for the count only.
+ */
+gi_status gi_nrc_answers(gi_nrc_t nrc, uint32_t *records, float *rad, uint32_t capacity, uint32_t *count,
+                         gi_stream_t stream);
+
+/* gi_probes_integrate with the radiance of the records picked by the latest gi_nrc_query_frame
+ * taken from the network instead of the cache. */
+gi_status gi_probes_integrate_nrc(gi_cache_t cache, gi_nrc_t nrc, const gi_probes *probes, const uint32_t *slot_ids,
+                                  uint32_t rays_per_probe, const float env[3], gi_stream_t stream);
+
+/* Counters (synchronises `stream`). */
+gi_status gi_nrc_stats(gi_nrc_t nrc, gi_nrc_stats_t *out, gi_stream_t stream);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 /*
  * Per-record cell means of one batch, without allocating device memory.  The paper has no

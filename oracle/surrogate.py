@@ -17,7 +17,10 @@ the published methods the surrogate is built from:
 * the relative L2 loss (Lehtinen et al. 2018, used for radiance by Mueller et al. 2021,
   "Real-time neural radiance caching"): (y - t)^2 / (sg(y)^2 + eps), sg = no gradient through
   the denominator;
-* Adam (Kingma and Ba 2015) with both bias corrections.
+* Adam (Kingma and Ba 2015) with both bias corrections; on the hash table in its sparse form
+  (PyTorch's SparseAdam): an entry whose gradient is exactly zero in a step -- no sample of the
+  step touched it -- keeps its value and both moments, the others step with the global step
+  count's bias correction.
 
 Readings taken for this surrogate:
 
@@ -241,21 +244,29 @@ def adam_init(prm: Params) -> AdamState:
                      Params(z(prm.table), z(prm.w1), z(prm.w2), z(prm.w3)), 0)
 
 
-def adam_step(spec: Spec, prm: Params, grads: Params, st: AdamState) -> Params:
-    """One Adam step on every parameter: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
-    p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).  Updates st in place."""
+def adam_step(spec: Spec, prm: Params, grads: Params, st: AdamState, sparse_table: bool = True) -> Params:
+    """One Adam step: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+    p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), t the global step count.  With
+    sparse_table, table entries whose gradient (both features) is exactly 0 are left as they are,
+    moments included.  Updates st in place."""
     st.step += 1
     t = st.step
     c1 = 1.0 - spec.beta1 ** t
     c2 = 1.0 - spec.beta2 ** t
     out = {}
     for name in ("table", "w1", "w2", "w3"):
-        g = getattr(grads, name)
-        m = spec.beta1 * getattr(st.m, name) + (1.0 - spec.beta1) * g
-        v = spec.beta2 * getattr(st.v, name) + (1.0 - spec.beta2) * g * g
+        g = np.asarray(getattr(grads, name), np.float64)
+        m0, v0 = getattr(st.m, name), getattr(st.v, name)
+        p0 = np.asarray(getattr(prm, name), np.float64)
+        m = spec.beta1 * m0 + (1.0 - spec.beta1) * g
+        v = spec.beta2 * v0 + (1.0 - spec.beta2) * g * g
+        p = p0 - spec.lr * (m / c1) / (np.sqrt(v / c2) + spec.adam_eps)
+        if name == "table" and sparse_table:
+            keep = np.all(g == 0.0, axis=-1, keepdims=True)
+            m, v, p = np.where(keep, m0, m), np.where(keep, v0, v), np.where(keep, p0, p)
         setattr(st.m, name, m)
         setattr(st.v, name, v)
-        out[name] = np.asarray(getattr(prm, name), np.float64) - spec.lr * (m / c1) / (np.sqrt(v / c2) + spec.adam_eps)
+        out[name] = p
     return Params(out["table"], out["w1"], out["w2"], out["w3"])
 
 

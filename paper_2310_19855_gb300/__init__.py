@@ -31,6 +31,12 @@ GI_SH_STRIDE = 28
 GI_NOALLOC_LOG2_SLOTS = 18
 GI_NOALLOC_MAX_RECORDS = 131072
 
+GI_NRC_LEVELS = 16
+GI_NRC_FEATURES = 2
+GI_NRC_HIDDEN = 64
+GI_NRC_OUTPUTS = 3
+GI_NRC_MAX_BATCH = 1 << 20
+
 c_u32, c_u64, c_f32, c_f64, c_vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
 
 
@@ -90,6 +96,22 @@ class gi_batch_view(ctypes.Structure):
                 ("slot_ids", c_vp), ("irradiance", c_vp), ("env", c_f32 * 3)]
 
 
+class gi_nrc_config(ctypes.Structure):
+    _fields_ = [("log2_table", c_u32), ("resolution", c_u32 * GI_NRC_LEVELS), ("aabb_lo", c_f32 * 3),
+                ("aabb_hi", c_f32 * 3), ("lr", c_f32), ("beta1", c_f32), ("beta2", c_f32), ("adam_eps", c_f32),
+                ("loss_eps", c_f32), ("batch", c_u32), ("train_steps", c_u32), ("max_records", c_u32),
+                ("max_queries", c_u32),
+                ("trust", c_f32), ("query_lod", c_u32), ("seed", c_u64)]
+
+
+class gi_points(ctypes.Structure):
+    _fields_ = [("pos", c_vp * 3), ("nrm", c_vp * 3), ("n", c_u32)]
+
+
+class gi_nrc_stats_t(ctypes.Structure):
+    _fields_ = [("steps", c_u64), ("loss", c_f32), ("judged_error", c_f32), ("trusted", c_u32), ("queries", c_u32)]
+
+
 CELL_DTYPE = np.dtype([("identity", "<u8"), ("sum", "<u8", (3,)), ("count", "<u4"), ("stamp", "<u4"),
                        ("value", "<f4", (3,)), ("slot", "<u4")])
 assert CELL_DTYPE.itemsize == ctypes.sizeof(gi_cell)
@@ -136,6 +158,23 @@ def lib() -> ctypes.CDLL:
             "gi_batch_destroy": (ctypes.c_int, [c_vp]),
             "gi_cell_means_noalloc": (ctypes.c_int, [ctypes.POINTER(gi_hits), ctypes.POINTER(gi_view), c_f32, c_u32,
                                                      c_u32, ctypes.POINTER(c_f32), c_vp, c_vp]),
+            "gi_nrc_create": (ctypes.c_int, [ctypes.POINTER(gi_nrc_config), ctypes.POINTER(c_vp)]),
+            "gi_nrc_destroy": (ctypes.c_int, [c_vp]),
+            "gi_nrc_set_params": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+            "gi_nrc_get_params": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+            "gi_nrc_set_gradients": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+            "gi_nrc_get_gradients": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+            "gi_nrc_infer": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_points), c_vp, c_vp]),
+            "gi_nrc_backward": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_points), ctypes.POINTER(c_vp), c_vp, c_u32,
+                                               c_vp]),
+            "gi_nrc_adam": (ctypes.c_int, [c_vp, c_vp]),
+            "gi_nrc_train_frame": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(gi_hits), c_vp, c_u32, c_vp]),
+            "gi_nrc_query_frame": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(gi_hits), c_vp,
+                                                  ctypes.POINTER(gi_view), c_vp]),
+            "gi_nrc_answers": (ctypes.c_int, [c_vp, c_vp, c_vp, c_u32, ctypes.POINTER(c_u32), c_vp]),
+            "gi_probes_integrate_nrc": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(gi_probes), c_vp, c_u32,
+                                                       ctypes.POINTER(c_f32), c_vp]),
+            "gi_nrc_stats": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_nrc_stats_t), c_vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -325,3 +364,134 @@ def gi_batch_frame(batch: int, views, use_graph: bool = False, stream=None) -> N
 
 def gi_batch_destroy(batch: int) -> None:
     check(lib().gi_batch_destroy(batch), "gi_batch_destroy")
+
+
+# ---------------------------------------------------------------- learned radiance surrogate
+def default_resolutions(n_min: int = 16, n_max: int = 2048, levels: int = GI_NRC_LEVELS) -> tuple:
+    """Geometric level resolutions floor(n_min b^l), b = (n_max / n_min)^(1 / (levels - 1)), the last one n_max."""
+    b = (n_max / n_min) ** (1.0 / (levels - 1))
+    res = [int(np.floor(n_min * b ** l + 1e-9)) for l in range(levels)]
+    res[-1] = int(n_max)
+    return tuple(res)
+
+
+def make_nrc_config(aabb_lo, aabb_hi, log2_table: int = 19, resolutions=None, lr: float = 1e-2, beta1: float = 0.9,
+                    beta2: float = 0.99, adam_eps: float = 1e-15, loss_eps: float = 0.01, batch: int = 65536,
+                    train_steps: int = 4, max_records: int = 1 << 22, max_queries: int = 1 << 20, trust: float = 0.05,
+                    query_lod: int = 2, seed: int = 1) -> gi_nrc_config:
+    c = gi_nrc_config()
+    c.log2_table = int(log2_table)
+    res = resolutions or default_resolutions()
+    for l in range(GI_NRC_LEVELS):
+        c.resolution[l] = int(res[l])
+    for a in range(3):
+        c.aabb_lo[a] = float(aabb_lo[a])
+        c.aabb_hi[a] = float(aabb_hi[a])
+    c.lr, c.beta1, c.beta2, c.adam_eps, c.loss_eps = float(lr), float(beta1), float(beta2), float(adam_eps), float(loss_eps)
+    c.batch, c.train_steps = int(batch), int(train_steps)
+    c.max_records, c.max_queries = int(max_records), int(max_queries)
+    c.trust, c.query_lod, c.seed = float(trust), int(query_lod), int(seed)
+    return c
+
+
+def gi_nrc_create(cfg: gi_nrc_config) -> int:
+    h = c_vp()
+    check(lib().gi_nrc_create(ctypes.byref(cfg), ctypes.byref(h)), "gi_nrc_create")
+    return h.value
+
+
+def gi_nrc_destroy(nrc: int) -> None:
+    check(lib().gi_nrc_destroy(nrc), "gi_nrc_destroy")
+
+
+def _host_f32(a):
+    if a is None:
+        return None
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    return arr
+
+
+def gi_nrc_set_params(nrc: int, table=None, w1=None, w2=None, w3=None) -> None:
+    """Host float32 arrays: table (16, 2^log2_table, 2), w1 (64, 32), w2 (64, 64), w3 (3, 64); None keeps a part."""
+    arrs = [_host_f32(x) for x in (table, w1, w2, w3)]
+    check(lib().gi_nrc_set_params(nrc, *[a.ctypes.data if a is not None else None for a in arrs]), "gi_nrc_set_params")
+
+
+def _get(fn, nrc: int, log2_table: int, what: str):
+    table = np.empty((GI_NRC_LEVELS, 1 << log2_table, 2), np.float32)
+    w1 = np.empty((GI_NRC_HIDDEN, 2 * GI_NRC_LEVELS), np.float32)
+    w2 = np.empty((GI_NRC_HIDDEN, GI_NRC_HIDDEN), np.float32)
+    w3 = np.empty((GI_NRC_OUTPUTS, GI_NRC_HIDDEN), np.float32)
+    check(fn(nrc, table.ctypes.data, w1.ctypes.data, w2.ctypes.data, w3.ctypes.data), what)
+    return table, w1, w2, w3
+
+
+def gi_nrc_get_params(nrc: int, log2_table: int):
+    """(table, w1, w2, w3) float32 master copies."""
+    return _get(lib().gi_nrc_get_params, nrc, log2_table, "gi_nrc_get_params")
+
+
+def gi_nrc_set_gradients(nrc: int, table=None, w1=None, w2=None, w3=None) -> None:
+    arrs = [_host_f32(x) for x in (table, w1, w2, w3)]
+    check(lib().gi_nrc_set_gradients(nrc, *[a.ctypes.data if a is not None else None for a in arrs]),
+          "gi_nrc_set_gradients")
+
+
+def gi_nrc_get_gradients(nrc: int, log2_table: int):
+    return _get(lib().gi_nrc_get_gradients, nrc, log2_table, "gi_nrc_get_gradients")
+
+
+def make_points(pos_planes, nrm_planes, n: int) -> gi_points:
+    """gi_points from device tensors pos (3, n) and nrm (3, n) float32 (contiguous rows)."""
+    p = gi_points()
+    for a in range(3):
+        p.pos[a] = _ptr(pos_planes[a])
+        p.nrm[a] = _ptr(nrm_planes[a])
+    p.n = int(n)
+    return p
+
+
+def gi_nrc_infer(nrc: int, pts: gi_points, out, stream=None) -> None:
+    check(lib().gi_nrc_infer(nrc, ctypes.byref(pts), _ptr(out), _stream(stream)), "gi_nrc_infer")
+
+
+def gi_nrc_backward(nrc: int, pts: gi_points, target_planes, mask=None, batch_norm: int = 0, stream=None) -> None:
+    tp = (c_vp * 3)(*[_ptr(target_planes[c]) for c in range(3)])
+    check(lib().gi_nrc_backward(nrc, ctypes.byref(pts), tp, _ptr(mask), int(batch_norm), _stream(stream)),
+          "gi_nrc_backward")
+
+
+def gi_nrc_adam(nrc: int, stream=None) -> None:
+    check(lib().gi_nrc_adam(nrc, _stream(stream)), "gi_nrc_adam")
+
+
+def gi_nrc_train_frame(nrc: int, cache: int, hits: gi_hits, slot_ids, frame: int, stream=None) -> None:
+    check(lib().gi_nrc_train_frame(nrc, cache, ctypes.byref(hits), _ptr(slot_ids), int(frame), _stream(stream)),
+          "gi_nrc_train_frame")
+
+
+def gi_nrc_query_frame(nrc: int, cache: int, hits: gi_hits, slot_ids, view: gi_view, stream=None) -> None:
+    check(lib().gi_nrc_query_frame(nrc, cache, ctypes.byref(hits), _ptr(slot_ids), ctypes.byref(view),
+                                   _stream(stream)), "gi_nrc_query_frame")
+
+
+def gi_nrc_answers(nrc: int, records=None, rad=None, capacity: int = 0, stream=None) -> int:
+    """Number of records answered by the latest query frame; with device buffers records (u32) and
+    rad (float4) of `capacity` entries, also copies them."""
+    c = c_u32()
+    check(lib().gi_nrc_answers(nrc, _ptr(records), _ptr(rad), int(capacity), ctypes.byref(c), _stream(stream)),
+          "gi_nrc_answers")
+    return c.value
+
+
+def gi_probes_integrate_nrc(cache: int, nrc: int, probes: gi_probes, slot_ids, rays_per_probe: int,
+                            env=(0.0, 0.0, 0.0), stream=None) -> None:
+    e = (c_f32 * 3)(*[float(x) for x in env])
+    check(lib().gi_probes_integrate_nrc(cache, nrc, ctypes.byref(probes), _ptr(slot_ids), int(rays_per_probe), e,
+                                        _stream(stream)), "gi_probes_integrate_nrc")
+
+
+def gi_nrc_stats(nrc: int, stream=None) -> dict:
+    st = gi_nrc_stats_t()
+    check(lib().gi_nrc_stats(nrc, ctypes.byref(st), _stream(stream)), "gi_nrc_stats")
+    return {k: getattr(st, k) for k, _ in gi_nrc_stats_t._fields_}

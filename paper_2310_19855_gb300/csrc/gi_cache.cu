@@ -27,13 +27,6 @@
 namespace gi {
 
 // ---------------------------------------------------------------- hashing
-// PCG hash (Jarzynski & Olano 2020): one LCG step, then PCG's RXS-M-XS output.
-__device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
-    uint32_t state = v * 747796405u + 2891336453u;
-    uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
-    return (word >> 22u) ^ word;
-}
-
 // xxHash32 of a single 4-byte word with a seed (xxHash specification).
 __device__ __forceinline__ uint32_t xxh32_word(uint32_t w, uint32_t seed) {
     uint32_t h = seed + 0x165667B1u + 4u;
@@ -69,14 +62,7 @@ __device__ __forceinline__ float pick4(const float (&a)[4], int i) {
 // `flip` = 1 when the direction source is the probe ray (outgoing = -ray).
 __device__ __forceinline__ unsigned long long cell_key(const KeyParams &k, float px, float py, float pz, float sx,
                                                        float sy, float sz, float len, uint32_t flip) {
-    float dx = __fsub_rn(px, k.cam[0]);
-    float dy = __fsub_rn(py, k.cam[1]);
-    float dz = __fsub_rn(pz, k.cam[2]);
-    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    int lod = 0;
-    if (k.num_lods > 1 && d2 >= k.thr[0]) lod = 1;
-    if (k.num_lods > 2 && d2 >= k.thr[1]) lod = 2;
-    if (k.num_lods > 3 && d2 >= k.thr[2]) lod = 3;
+    const int lod = key_lod(k, px, py, pz);
     float inv = pick4(k.inv_side, lod);
     float side = pick4(k.side, lod);
     uint32_t qx = (uint32_t)__float2int_rd(__fmul_rn(px, inv)) & kQMask;
@@ -261,17 +247,19 @@ __device__ __forceinline__ float3 load_resolved(const void *r, uint32_t stride, 
     return make_float3(v.x, v.y, v.z);
 }
 
-__device__ __forceinline__ void store_resolved(void *r, uint32_t stride, int f16, uint32_t s, float3 v) {
+// The 4th lane marks a cell resolved without history (its first resolve, or its first since an
+// eviction): 1 for such a cell, 0 otherwise.  The surrogate reads it to find cold cells.
+__device__ __forceinline__ void store_resolved(void *r, uint32_t stride, int f16, uint32_t s, float3 v, bool cold) {
     r = static_cast<char *>(r) + (size_t)s * stride;
     if (f16) {
         ushort4 h;
         h.x = __half_as_ushort(__float2half_rn(v.x));
         h.y = __half_as_ushort(__float2half_rn(v.y));
         h.z = __half_as_ushort(__float2half_rn(v.z));
-        h.w = 0;
+        h.w = cold ? (unsigned short)0x3C00u : (unsigned short)0u;
         *reinterpret_cast<ushort4 *>(r) = h;
     } else {
-        *reinterpret_cast<float4 *>(r) = make_float4(v.x, v.y, v.z, 0.0f);
+        *reinterpret_cast<float4 *>(r) = make_float4(v.x, v.y, v.z, cold ? 1.0f : 0.0f);
     }
 }
 
@@ -329,7 +317,7 @@ __device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk,
                 v = make_float3(o.x + a.alpha * (m.x - o.x), o.y + a.alpha * (m.y - o.y),
                                 o.z + a.alpha * (m.z - o.z));
             }
-            store_resolved(a.resolved, a.res_stride, a.f16, s[u], v);
+            store_resolved(a.resolved, a.res_stride, a.f16, s[u], v, fresh[u]);
             uint4 *dst = reinterpret_cast<uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
             dst[0] = make_uint4(0u, 0u, 0u, 0u);
             dst[1] = make_uint4(0u, 0u, 0u, a.stamp_now);

@@ -44,6 +44,29 @@ struct KeyParams {
     int num_lods;
 };
 
+#ifdef __CUDACC__
+// PCG hash (Jarzynski & Olano 2020): one LCG step, then PCG's RXS-M-XS output.
+__host__ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
+    uint32_t state = v * 747796405u + 2891336453u;
+    uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+
+// LOD of the cell descriptor: the float32 squared camera distance (fixed order, no contraction)
+// against the Algorithm-6 thresholds.
+__device__ __forceinline__ int key_lod(const KeyParams &k, float px, float py, float pz) {
+    const float dx = __fsub_rn(px, k.cam[0]);
+    const float dy = __fsub_rn(py, k.cam[1]);
+    const float dz = __fsub_rn(pz, k.cam[2]);
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    int lod = 0;
+    if (k.num_lods > 1 && d2 >= k.thr[0]) lod = 1;
+    if (k.num_lods > 2 && d2 >= k.thr[1]) lod = 2;
+    if (k.num_lods > 3 && d2 >= k.thr[2]) lod = 3;
+    return lod;
+}
+#endif
+
 // Host helpers (gi_common.cu)
 void set_error(const char *fmt, ...);
 gi_status cuda_status(cudaError_t e, const char *what);
@@ -131,6 +154,8 @@ struct IntegrateArgs {
     uint32_t probes;
     uint32_t rpp;
     float env[3];
+    const uint32_t *ovr_bits;  // surrogate answers: bit r set -> record r takes ovr[r] (or NULL)
+    const float4 *ovr;
 };
 
 struct InterpArgs {
@@ -155,6 +180,9 @@ struct CacheView {
     uint32_t slots;
 };
 CacheView cache_view(gi_cache_t c);
+
+// Answers of the latest gi_nrc_query_frame for a view of n records (gi_nrc.cu).
+gi_status nrc_override(gi_nrc_t nrc, uint64_t n, const uint32_t **bits, const float4 **ovr);
 
 // Host helpers of the cache used by the batched pass chain (gi_cache.cu).
 bool hits_ok(const gi_hits *h, uint32_t key_dir);

@@ -233,7 +233,9 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
     return v[0];
 }
 
-// One warp per probe; lane l owns cells l and l + 32.
+// One warp per probe; lane l owns cells l and l + 32.  With SURR, records whose bit is set in
+// a.ovr_bits take their radiance from a.ovr (the surrogate's answers) instead of the cache.
+template <bool SURR = false>
 __device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t blk) {
     const uint32_t p = (blk * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -251,7 +253,22 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t 
         // rays k and k + 32 sample cells lane and lane + 32; both gathers in flight together
         const uint32_t s0 = __ldcs(ids + k), s1 = __ldcs(ids + k + 32);
         float3 r0, r1;
-        const bool h0 = ray_sample(a, s0, r0), h1 = ray_sample(a, s1, r1);
+        bool h0 = ray_sample(a, s0, r0), h1 = ray_sample(a, s1, r1);
+        if (SURR) {
+            // rpp is a multiple of 64: rays k and k + 32 are bit `lane` of two consecutive words
+            const size_t rec = (size_t)p * a.rpp + k;
+            const uint32_t w0 = __ldg(a.ovr_bits + (rec >> 5)), w1 = __ldg(a.ovr_bits + (rec >> 5) + 1);
+            if ((w0 >> lane) & 1u) {
+                const float4 o = __ldg(a.ovr + rec);
+                r0 = make_float3(o.x, o.y, o.z);
+                h0 = true;
+            }
+            if ((w1 >> lane) & 1u) {
+                const float4 o = __ldg(a.ovr + rec + 32);
+                r1 = make_float3(o.x, o.y, o.z);
+                h1 = true;
+            }
+        }
         if (h0) {
             acc[0][0] += r0.x; acc[0][1] += r0.y; acc[0][2] += r0.z; cnt[0] += 1.0f;
         }
@@ -341,6 +358,7 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t 
 }
 
 __global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) { integrate_body(a, blockIdx.x); }
+__global__ void __launch_bounds__(256) k_integrate_surr(IntegrateArgs a) { integrate_body<true>(a, blockIdx.x); }
 
 // ---------------------------------------------------------------- interpolation
 
@@ -592,6 +610,8 @@ IntegrateArgs integrate_args(gi_cache_t cache, const gi_probes *pr, const uint32
     a.probes = pr->layout.num_probes;
     a.rpp = rpp;
     for (int c = 0; c < 3; ++c) a.env[c] = env ? env[c] : 0.0f;
+    a.ovr_bits = nullptr;
+    a.ovr = nullptr;
     return a;
 }
 
@@ -754,6 +774,26 @@ gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *pr, const uint3
     const unsigned blocks = (a.probes + 7) / 8;
     k_integrate<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
     return cuda_status(cudaGetLastError(), "k_integrate launch");
+}
+
+gi_status gi_probes_integrate_nrc(gi_cache_t cache, gi_nrc_t nrc, const gi_probes *pr, const uint32_t *slot_ids,
+                                  uint32_t rays_per_probe, const float env[3], gi_stream_t stream) {
+    gi_status s = integrate_check(cache, pr, slot_ids, rays_per_probe);
+    if (s != GI_OK) return s;
+    if (!nrc) {
+        set_error("gi_probes_integrate_nrc: NULL surrogate");
+        return GI_ERR_INVALID_ARG;
+    }
+    s = ensure_moments();
+    if (s != GI_OK) return s;
+    IntegrateArgs a = integrate_args(cache, pr, slot_ids, rays_per_probe, env);
+    if (a.probes == 0) return GI_OK;
+    const uint64_t n = (uint64_t)a.probes * rays_per_probe;
+    s = nrc_override(nrc, n, &a.ovr_bits, &a.ovr);
+    if (s != GI_OK) return s;
+    const unsigned blocks = (a.probes + 7) / 8;
+    k_integrate_surr<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    return cuda_status(cudaGetLastError(), "k_integrate_surr launch");
 }
 
 gi_status gi_probes_interpolate(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr, float *out,

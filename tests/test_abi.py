@@ -36,7 +36,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 STRUCTS = ["gi_cache_config", "gi_view", "gi_hits", "gi_gbuffer", "gi_probe_layout", "gi_probes",
-           "gi_cache_stats_t", "gi_cell", "gi_query", "gi_batch_tuning", "gi_batch_view"]
+           "gi_cache_stats_t", "gi_cell", "gi_query", "gi_batch_tuning", "gi_batch_view", "gi_nrc_config",
+           "gi_points", "gi_nrc_stats_t"]
 
 
 def test_struct_layouts_match_the_c_header(tmp_path):
@@ -107,3 +108,26 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.gi_probes_interpolate(None, None, None, None, None) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_cell_moments(None) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_cache_destroy(None) == gi.GI_OK
+
+
+def test_surrogate_arguments_are_rejected_on_the_host(lib):
+    h = ctypes.c_void_p()
+    good = gi.make_nrc_config((-1, 0, -1), (1, 2, 1))
+    for field, value in (("log2_table", 30), ("batch", 64), ("lr", 0.0), ("beta2", 1.0), ("loss_eps", 0.0)):
+        bad = gi.make_nrc_config((-1, 0, -1), (1, 2, 1))
+        setattr(bad, field, value)
+        assert lib.gi_nrc_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG, field
+    bad = gi.make_nrc_config((-1, 0, -1), (1, 0, 1))  # empty box
+    assert lib.gi_nrc_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    bad = gi.make_nrc_config((-1, 0, -1), (1, 2, 1), resolutions=(0,) + gi.default_resolutions()[1:])
+    assert lib.gi_nrc_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    assert good.resolution[15] == 2048 and good.resolution[0] == 16
+    assert lib.gi_nrc_create(None, ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_nrc_infer(None, None, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_nrc_backward(None, None, None, None, 0, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_nrc_adam(None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_nrc_train_frame(None, None, None, None, 0, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_nrc_query_frame(None, None, None, None, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_probes_integrate_nrc(None, None, None, None, 64, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_nrc_stats(None, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_nrc_destroy(None) == gi.GI_OK

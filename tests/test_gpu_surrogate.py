@@ -1,0 +1,310 @@
+"""GPU parity of the learned radiance surrogate against the oracle (oracle/surrogate.py), through
+the C ABI: network output, loss gradients of every parameter, the Adam step, the records a query
+frame picks, probe irradiance with the network's answers, and what training gains over the
+untrained network on the Cornell box's own cache.
+
+Tolerances: the GPU rounds exactly where the oracle's emulation does (float16 features, bfloat16
+weights / activations / output gradient) and sums in float32, so outputs and gradients differ
+from the emulated float64 oracle by float32 rounding plus the rare bfloat16 rounding that a
+float32-level difference flips (2^-8 of one operand); the bounds below are norm-relative."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2310_19855_gb300 as gi
+import workload as wl
+from oracle import key as OK
+from oracle import probes as OP
+from oracle import surrogate as S
+from oracle.cache import OracleCache
+from paper_2310_19855_gb300.pipeline import Pipeline, view_of
+
+from _gpu_util import dev, require_gpu, u32
+
+pytestmark = pytest.mark.gpu
+SI = wl.surrogate_inputs
+LOG2_T = 14
+
+
+def _spec(resolutions=SI.SMALL_RESOLUTIONS, log2_table=LOG2_T, aabb=SI.CORNELL_AABB, lr=1e-2):
+    return S.Spec(resolutions=tuple(resolutions), log2_table=log2_table, aabb_lo=aabb[0], aabb_hi=aabb[1], lr=lr)
+
+
+def _nrc(spec, **kw):
+    cfg = gi.make_nrc_config(spec.aabb_lo, spec.aabb_hi, log2_table=spec.log2_table, resolutions=spec.resolutions,
+                             lr=spec.lr, beta1=spec.beta1, beta2=spec.beta2, adam_eps=spec.adam_eps,
+                             loss_eps=spec.loss_eps, **kw)
+    return gi.gi_nrc_create(cfg)
+
+
+def _points(pos, nrm):
+    P, N = dev(pos), dev(nrm)
+    return gi.make_points(P, N, pos.shape[1]), (P, N)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def test_infer_matches_oracle():
+    spec = _spec()
+    prm = SI.params(1, LOG2_T)
+    nrc = _nrc(spec, batch=1024, max_records=4096, max_queries=4096)
+    try:
+        gi.gi_nrc_set_params(nrc, *prm)
+        for n in (1, 127, 1000, 4099):  # one tile, ragged tails, several CTAs' tiles
+            pos, nrm = SI.points(2 + n, n)
+            pts, keep = _points(pos, nrm)
+            out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+            gi.gi_nrc_infer(nrc, pts, out)
+            got = out.cpu().numpy()
+            ref = S.query(spec, S.Params(*prm), pos, nrm, emulate=True)
+            assert np.all(got[:, 3] == 1.0)
+            err = np.linalg.norm(got[:, :3] - ref) / max(np.linalg.norm(ref), 1e-12)
+            assert err < 2e-3, (n, err)
+            assert np.abs(got[:, :3] - ref).max() < 1e-2 * np.abs(ref).max() + 1e-6, n
+    finally:
+        gi.gi_nrc_destroy(nrc)
+
+
+def test_backward_gradients_match_oracle():
+    spec = _spec()
+    prm = SI.params(3, LOG2_T)
+    n, B = 1000, 1200
+    pos, nrm = SI.points(4, n)
+    tgt, msk = SI.targets(5, n)
+    nrc = _nrc(spec, batch=1024, max_records=4096, max_queries=4096)
+    try:
+        gi.gi_nrc_set_params(nrc, *prm)
+        pts, keep = _points(pos, nrm)
+        T, M = dev(tgt), dev(msk)
+        gi.gi_nrc_backward(nrc, pts, [T[0], T[1], T[2]], M, B)
+        st = gi.gi_nrc_stats(nrc)
+        gt, g1, g2, g3 = gi.gi_nrc_get_gradients(nrc, LOG2_T)
+    finally:
+        gi.gi_nrc_destroy(nrc)
+    L, judge, g = S.backward(spec, S.Params(*prm), pos, nrm, tgt.T, msk, B, emulate=True)
+    assert abs(st["loss"] - L) <= 1e-3 * L
+    assert abs(st["judged_error"] - judge[0] / judge[1]) <= 1e-3 * judge[0] / judge[1]
+    for name, got, ref in (("w1", g1, g.w1), ("w2", g2, g.w2), ("w3", g3, g.w3), ("table", gt, g.table)):
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < 2e-3, (name, err)
+    # the entries no sample touches get nothing
+    touched = np.zeros(gt.shape[:2], bool)
+    idx, _ = S.corners(spec, pos, nrm)
+    for l in range(spec.levels):
+        touched[l, idx[:, l, :].reshape(-1)] = True
+    assert np.all(gt[~touched] == 0.0)
+
+
+def test_adam_step_matches_oracle():
+    spec = _spec(lr=5e-3)
+    prm = SI.params(6, LOG2_T)
+    nrc = _nrc(spec, batch=1024, max_records=4096, max_queries=4096)
+    try:
+        gi.gi_nrc_set_params(nrc, *prm)
+        p = S.Params(*[a.astype(np.float64) for a in prm])
+        st = S.adam_init(p)
+        for step in range(3):
+            # a different half of the table touched at every step: the sparse rule matters
+            grads = list(SI.gradients(7 + step, LOG2_T))
+            gi.gi_nrc_set_gradients(nrc, *grads)
+            gi.gi_nrc_adam(nrc)
+            p = S.adam_step(spec, p, S.Params(*[a.astype(np.float64) for a in grads]), st)
+            got = gi.gi_nrc_get_params(nrc, LOG2_T)
+            for name, a, b in zip(("table", "w1", "w2", "w3"), got, (p.table, p.w1, p.w2, p.w3)):
+                err = np.abs(a - b).max()
+                assert err < 1e-5 * (np.abs(b).max() + spec.lr), (step, name, err)
+            # the gradient accumulators are cleared by the step
+            g = gi.gi_nrc_get_gradients(nrc, LOG2_T)
+            assert all(np.all(x == 0) for x in g)
+        assert gi.gi_nrc_stats(nrc)["steps"] == 3
+    finally:
+        gi.gi_nrc_destroy(nrc)
+
+
+def _cornell(width, height, rpp=64):
+    cfg = dict(wl.CONFIGS[1], width=width, height=height, rays_per_probe=rpp, frames=64)
+    seed = wl.scene.SEED_BASE + 4000
+    return cfg, wl.make_scene(cfg, seed), seed
+
+
+def _trust_as_is(nrc, spec):
+    """Take one Adam step with zero gradients (parameters unchanged) after a backward pass, so the
+    network counts as trained and its judged error is defined."""
+    pos, nrm = SI.points(99, 256, (spec.aabb_lo, spec.aabb_hi))
+    tgt, _ = SI.targets(98, 256)
+    pts, keep = _points(pos, nrm)
+    T = dev(tgt)
+    gi.gi_nrc_backward(nrc, pts, [T[0], T[1], T[2]])
+    z = [np.zeros((16, 1 << spec.log2_table, 2), np.float32), np.zeros((64, 32), np.float32),
+         np.zeros((64, 64), np.float32), np.zeros((3, 64), np.float32)]
+    gi.gi_nrc_set_gradients(nrc, *z)
+    gi.gi_nrc_adam(nrc)
+    torch.cuda.synchronize()
+
+
+def _hits(fr):
+    R = dev(fr.records)
+    return gi.hits_from_planes(R, fr.records.shape[1]), R
+
+
+def test_integrate_with_network_answers_matches_oracle():
+    """query_lod 0 and unlimited trust: every hit is answered by the network; probe irradiance
+    then equals the oracle's integration of the oracle network's radiance."""
+    cfg, scene, seed = _cornell(128, 128)
+    fr = wl.make_frame(cfg, 0, scene, seed_base=seed)
+    spec = _spec()
+    prm = SI.params(11, LOG2_T, table_scale=0.3)
+    nrc = _nrc(spec, batch=1024, max_records=fr.n_records, max_queries=fr.n_records, trust=1e30, query_lod=0)
+    pl = Pipeline(128, 128, 64, 16)
+    try:
+        gi.gi_nrc_set_params(nrc, *prm)
+        _trust_as_is(nrc, spec)
+        view = view_of(fr.camera, 0)
+        gb = dev(fr.gbuffer)
+        hits, R = _hits(fr)
+        pl.spawn(gb, view)
+        pl.update(R, view)
+        pl.resolve(0)
+        gi.gi_nrc_query_frame(nrc, pl.cache, hits, pl.slot_ids, view)
+        gi.gi_probes_integrate_nrc(pl.cache, nrc, pl.probes.struct, pl.slot_ids, 64)
+        sh = pl.probes.sh.cpu().numpy()[:, :27].reshape(-1, 9, 3)
+        n_ans = gi.gi_nrc_answers(nrc)
+    finally:
+        pl.close()
+        gi.gi_nrc_destroy(nrc)
+    rec = fr.records
+    hit = OK.record_is_hit(rec)
+    assert n_ans == int(hit.sum())
+    rad = np.zeros((rec.shape[1], 3))
+    rad[hit] = S.query(spec, S.Params(*prm), rec[0:3, hit], rec[3:6, hit], emulate=True)
+    has = hit | np.isposinf(rec[9])
+    sp = OP.spawn(fr.gbuffer, fr.camera, 0)
+    P = sp["valid"].size
+    ref = OP.integrate(sp["valid"], sp["nrm"], rad.reshape(P, 64, 3), has.reshape(P, 64))
+    err = np.linalg.norm(sh - ref) / np.linalg.norm(ref)
+    assert err < 2e-3, err
+
+
+def test_untrusted_network_leaves_integrate_unchanged():
+    cfg, scene, seed = _cornell(128, 128)
+    fr = wl.make_frame(cfg, 0, scene, seed_base=seed)
+    spec = _spec()
+    nrc = _nrc(spec, batch=1024, max_records=fr.n_records, max_queries=fr.n_records, trust=0.0, query_lod=0)
+    pl = Pipeline(128, 128, 64, 16)
+    try:
+        gi.gi_nrc_set_params(nrc, *SI.params(12, LOG2_T))
+        _trust_as_is(nrc, spec)
+        view = view_of(fr.camera, 0)
+        gb = dev(fr.gbuffer)
+        hits, R = _hits(fr)
+        pl.spawn(gb, view)
+        pl.update(R, view)
+        pl.resolve(0)
+        pl.integrate()
+        plain = pl.probes.sh.clone()
+        gi.gi_nrc_query_frame(nrc, pl.cache, hits, pl.slot_ids, view)
+        gi.gi_probes_integrate_nrc(pl.cache, nrc, pl.probes.struct, pl.slot_ids, 64)
+        assert gi.gi_nrc_stats(nrc)["trusted"] == 0
+        assert gi.gi_nrc_answers(nrc) == 0
+        assert torch.equal(plain, pl.probes.sh)
+    finally:
+        pl.close()
+        gi.gi_nrc_destroy(nrc)
+
+
+def test_query_selection_matches_the_rules():
+    """Answered records = hits on cells resolved for the first time, or at LOD >= query_lod,
+    decided from the oracle's cache history and its float32 LOD rule."""
+    cfg = dict(wl.CONFIGS[2], width=320, height=180, n_boxes=512, room=(24.0, 8.0, 24.0), frames=8)
+    seed = wl.scene.SEED_BASE + 4100
+    scene = wl.make_scene(cfg, seed)
+    spec = _spec(aabb=((-12.5, -0.5, -12.5), (12.5, 8.5, 12.5)))
+    frames = [wl.make_frame(cfg, f, scene, seed_base=seed) for f in range(3)]
+    n = frames[0].n_records
+    nrc = _nrc(spec, batch=1024, max_records=n, max_queries=n, trust=1e30, query_lod=2)
+    pl = Pipeline(320, 180, 64, 17)
+    oc = OracleCache(17)
+    try:
+        gi.gi_nrc_set_params(nrc, *SI.params(13, LOG2_T))
+        _trust_as_is(nrc, spec)
+        for fr in frames:
+            f = fr.frame
+            view = view_of(fr.camera, f)
+            hits, R = _hits(fr)
+            pl.update(R, view)
+            pl.resolve(f)
+            gi.gi_nrc_query_frame(nrc, pl.cache, hits, pl.slot_ids, view)
+            cnt = gi.gi_nrc_answers(nrc)
+            recs = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
+            rads = torch.empty((max(cnt, 1), 4), dtype=torch.float32, device="cuda")
+            assert gi.gi_nrc_answers(nrc, recs, rads, cnt) == cnt
+            got = np.sort(u32(recs)[:cnt])
+            # oracle: cold = touched this frame without history before it; LOD from the key rule
+            cam = fr.camera
+            ident = oc.update(fr.records, f, cam.pos, cam.fov_y, cam.width, cam.height)
+            row = oc.find(ident)
+            hit = OK.record_is_hit(fr.records)
+            cold = hit & ~oc.has_hist[np.maximum(row, 0)]
+            oc.resolve(f)
+            lp = OK.lod_params(0.05, 4, cam.fov_y, cam.width, cam.height)
+            _, lod = OK.cell_key(fr.records, cam.pos, lp)
+            want = np.flatnonzero(hit & (cold | (lod >= 2)))
+            assert np.array_equal(got, want), (f, got.size, want.size)
+            assert np.all(rads.cpu().numpy()[:cnt, 3] == 1.0)
+            if f > 0:
+                assert 0 < np.count_nonzero(cold) < np.count_nonzero(hit)
+    finally:
+        pl.close()
+        gi.gi_nrc_destroy(nrc)
+
+
+def test_training_on_the_cornell_cache_beats_the_untrained_network():
+    """Online training on the cache's own resolved cells (Cornell box, static camera, 64 frames):
+    the network's relative L1 error against the FP64 oracle cache at every hit of the last frame
+    falls far below the untrained network's (which answers about zero everywhere)."""
+    W = H = 256
+    cfg, scene, seed = _cornell(W, H)
+    spec = _spec(resolutions=(16, 22, 30, 42, 58, 80, 111, 153, 212, 294, 406, 561, 776, 1072, 1482, 2048),
+                 log2_table=18)
+    frames = 48
+    n = (W // 8) * (H // 8) * 64
+    kw = dict(batch=65536, train_steps=4, max_records=n, max_queries=n, trust=0.05, query_lod=2, seed=5)
+    trained = _nrc(spec, **kw)
+    untrained = _nrc(spec, **kw)
+    pl = Pipeline(W, H, 64, 18)
+    oc = OracleCache(18)
+    judged = []
+    try:
+        for f in range(frames):
+            fr = wl.make_frame(cfg, f, scene, seed_base=seed)
+            view = view_of(fr.camera, f)
+            hits, R = _hits(fr)
+            pl.update(R, view)
+            pl.resolve(f)
+            gi.gi_nrc_train_frame(trained, pl.cache, hits, pl.slot_ids, f)
+            judged.append(gi.gi_nrc_stats(trained)["judged_error"])
+            cam = fr.camera
+            oc.update(fr.records, f, cam.pos, cam.fov_y, cam.width, cam.height)
+            oc.resolve(f)
+        hit = OK.record_is_hit(fr.records)
+        ref, found = oc.query_records(fr.records, cam.pos, cam.fov_y, cam.width, cam.height)
+        sel = hit & found
+        pos, nrm = fr.records[0:3, sel], fr.records[3:6, sel]
+        pts, keep = _points(np.ascontiguousarray(pos), np.ascontiguousarray(nrm))
+        errs = {}
+        for name, net in (("trained", trained), ("untrained", untrained)):
+            out = torch.empty((pos.shape[1], 4), dtype=torch.float32, device="cuda")
+            gi.gi_nrc_infer(net, pts, out)
+            y = out.cpu().numpy()[:, :3]
+            errs[name] = np.abs(y - ref[sel]).sum() / np.abs(ref[sel]).sum()
+        print("relative L1 error vs the FP64 oracle cache:", errs, "judged:", judged[0], "->", judged[-1])
+        assert errs["untrained"] > 0.9
+        assert errs["trained"] < 0.25
+        assert judged[-1] < 0.5 * judged[1]
+    finally:
+        pl.close()
+        gi.gi_nrc_destroy(trained)
+        gi.gi_nrc_destroy(untrained)

@@ -325,3 +325,25 @@ def test_emulated_precision_stays_near_float64():
     for name in ("table", "w1", "w2", "w3"):
         a, b = getattr(g16, name), getattr(g64, name)
         assert np.linalg.norm(a - b) <= 0.1 * np.linalg.norm(b), name
+
+
+def test_sparse_table_adam_leaves_untouched_entries_alone():
+    """An entry with a zero gradient in a step keeps value and moments (so its later steps see the
+    moments of its last touch), while a dense step would keep moving it by momentum."""
+    spec = S.Spec(resolutions=(2,), log2_table=4, aabb_lo=(0, 0, 0), aabb_hi=(1, 1, 1), lr=0.01)
+    rng = np.random.default_rng(30)
+    prm = S.Params(rng.normal(size=(1, 16, 2)), rng.normal(size=(64, 2)), rng.normal(size=(64, 64)),
+                   rng.normal(size=(3, 64)))
+    g1 = S.Params(rng.normal(size=(1, 16, 2)), np.zeros((64, 2)), np.zeros((64, 64)), np.zeros((3, 64)))
+    g2 = S.Params(g1.table.copy(), np.zeros((64, 2)), np.zeros((64, 64)), np.zeros((3, 64)))
+    g2.table[0, :8] = 0.0   # entries 0..7 untouched in step 2
+    g2.table[0, 8, 0] = 0.0  # entry 8: one feature zero, still touched
+    st_s, st_d = S.adam_init(prm), S.adam_init(prm)
+    ps = S.adam_step(spec, S.adam_step(spec, prm, g1, st_s), g2, st_s)
+    pd = S.adam_step(spec, S.adam_step(spec, prm, g1, st_d, sparse_table=False), g2, st_d, sparse_table=False)
+    after1 = S.adam_step(spec, prm, g1, S.adam_init(prm))
+    np.testing.assert_array_equal(ps.table[0, :8], after1.table[0, :8])
+    # entry 8 and beyond step in both forms alike; untouched entries drift only in the dense form
+    np.testing.assert_allclose(ps.table[0, 8:], pd.table[0, 8:], rtol=0, atol=1e-15)
+    assert np.all(np.abs(pd.table[0, :8] - after1.table[0, :8]) > 1e-4)
+    np.testing.assert_array_equal(st_s.m.table[0, :8], (1 - spec.beta1) * g1.table[0, :8])

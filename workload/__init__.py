@@ -19,3 +19,4 @@ from .scene import (  # noqa: F401
     records_random,
     REC_PLANES,
 )
+from . import surrogate_inputs  # noqa: F401,E402

@@ -14,6 +14,8 @@ Recipe (all seeded; the seed of frame f of configuration c is
   per channel; 1920x1080 pixels, 64 rays per probe; the camera follows a
   closed Catmull-Rom spline through 8 seeded control points; one point light
   moves on a circle under the ceiling;
+* configuration 4 -- the Cornell box of configuration 1 at 1920x1080, 64
+  rays per probe, static camera, 128 frames (the learned-surrogate workload);
 * configuration 5 -- the same recipe at 3840x2160 with 16,384 boxes in a
   96 x 20 x 96 m room, three of the emissive boxes moving on circles.
 
@@ -77,6 +79,15 @@ def batched_views(n_views: int = 16, sizes=_VIEW_SIZES):
 
 
 CONFIGS[3] = dict(name="batched-16-views", scene="batched", n_views=16, frames=32)
+
+# Configuration 4: the Cornell box of configuration 1 seen at 1080p (static camera, 64 rays per
+# probe), plus the learned surrogate: 16-level hash encoding with 2^19 entries per level and
+# resolutions 16 .. 2048 over the box, trained on 65,536 resolved cells per frame (4 minibatches),
+# queried for cold cells, dropped inserts and LOD >= 2; 128 frames.
+CONFIGS[4] = dict(CONFIGS[1], name="cornell-1080p-surrogate", width=1920, height=1080, rays_per_probe=64,
+                  log2_slots=20, frames=128, nrc_log2_table=19, nrc_batch=65536, nrc_train_steps=4,
+                  nrc_query_lod=2, nrc_lr=1e-2, nrc_trust=0.05,
+                  nrc_resolutions=(16, 22, 30, 42, 58, 80, 111, 153, 212, 294, 406, 561, 776, 1072, 1482, 2048))
 
 
 # --------------------------------------------------------------------------- tracer
