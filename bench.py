@@ -37,9 +37,22 @@ N_FRAMES_DEFAULT = 16
 L2_FLUSH_BYTES = 256 << 20
 REFERENCE_BUDGET_S = 90.0
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture (profiles/),
-# keyed to the source it was taken on; null when the source has changed since.
-NCU_TRAFFIC = {}
+# DRAM traffic per launch of the dominant kernel from an ncu capture (profiles/), keyed by
+# "configuration:kernel" and by the source it was taken on; null when the source has changed since.
+NCU_TRAFFIC = {
+    # k_update, boxes-1080p (profiles/k_update_boxes-1080p.md): 159.6 MB read + 22.1 MB written
+    "2:update": {"bytes_per_launch": 181652736, "source": "gi_cache.cu", "source_sha": "d54abd387582618e"},
+    # k_nrc_adam_table, Cornell 1080p (profiles/nrc_training_cornell-1080p.md): 3.22 TB/s x 40.16 us
+    "4:adam_table": {"bytes_per_launch": 129501000, "source": "gi_nrc.cu", "source_sha": "94a0221974ed412e"},
+}
+
+
+def ncu_traffic(key):
+    tr = NCU_TRAFFIC.get(key)
+    if not tr:
+        return None
+    src = os.path.join(ROOT, "paper_2310_19855_gb300", "csrc", tr["source"])
+    return tr["bytes_per_launch"] if _source_sha(src) == tr["source_sha"] else None
 
 
 def _source_sha(path):
@@ -341,10 +354,7 @@ def run_native(args, rank, world, local_rank):
     }
     d_ms = pass_ms[names.index(dominant)]
     achieved = alg[dominant] / (d_ms * 1e-3) / 1e9
-    src = os.path.join(ROOT, "paper_2310_19855_gb300", "csrc",
-                       "gi_cache.cu" if dominant in ("update", "resolve") else "gi_probes.cu")
-    tr = NCU_TRAFFIC.get(dominant)
-    traffic = tr["bytes_per_launch"] if tr and tr["source_sha"] == _source_sha(src) else None
+    traffic = ncu_traffic(f"{CONFIG}:{dominant}")
 
     # ---- oracle on the host cores, bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -593,7 +603,7 @@ def run_surrogate(args, rank, world, local_rank):
         mark(5)
 
     # setup: the configuration's frames of online training (both caches see the same frames)
-    setup = cfg["frames"]
+    setup = cfg["frames"] if args.setup_frames is None else args.setup_frames
     judged = []
     for i in range(setup):
         surr_step(i)
@@ -714,7 +724,7 @@ def run_surrogate(args, rank, world, local_rank):
                       "note": "errors against the float32 cache, which matches the float64 oracle cache to 1e-4 "
                               "(parity tests); the float64-oracle comparison of the network is in the tests"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_nrc_adam_table (sparse Adam on the hash table)",
+                     "traffic": ncu_traffic("4:adam_table"), "kernel": "k_nrc_adam_table (sparse Adam on the hash table)",
                      "algorithmic_bytes_per_launch": adam_bytes, "touched_entries": n_touched,
                      "launch_ms": adam_ms, "peak_source": peak_src},
         "cpu_baseline": cpu,
@@ -736,6 +746,9 @@ def main():
     ap.add_argument("--frames", type=int, default=N_FRAMES_DEFAULT, help="distinct pre-generated frames to cycle")
     ap.add_argument("--sample", type=float, default=0.125, help="fraction of probes in the oracle's sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--setup-frames", type=int, default=None,
+                    help="configuration 4: frames of online training before the warm-up (default: the "
+                         "configuration's 128)")
     ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
                     help="2: boxes at 1080p (default); 3: 16 batched views; 4: Cornell box at 1080p with the "
                          "learned surrogate; 5: boxes at 4K, 2^24 slots, FP16 resolved radiance")

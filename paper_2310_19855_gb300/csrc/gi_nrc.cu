@@ -54,6 +54,8 @@ constexpr uint32_t kImgBytes = 28672;
 
 // float32 master weights: W1 | W2 | W3, row-major [out][in]
 constexpr int kW1 = 0, kW2 = kHid * kIn, kW3 = kW2 + kHid * kHid, kWCount = kW3 + kOut * kHid;
+// a CTA's partial: the weight gradients of its tiles, then its loss, sum m|y - t|, sum m|t|
+constexpr int kPartStride = kWCount + 4;
 
 // global input tile: [128 samples][32 features] bf16 core matrices; 8-sample group g = bytes 512 g ..
 constexpr uint32_t kXTile = kTile * kIn * 2;  // 8192
@@ -135,8 +137,8 @@ struct MlpArgs {
     float dy_scale;            // 2 / B
     float loss_eps;
     float *dX;                 // train: [n_pad][32] float32
-    float *wgrad;              // train: W1 | W2 | W3 gradient accumulators
-    float *stats;              // train: loss, sum m|y - t|, sum m|t|
+    float *wpart;              // train: per-CTA partial W1 | W2 | W3 gradients and loss sums,
+                               // rows of kPartStride floats (reduced by k_nrc_wgrad_reduce)
     float4 *out;               // infer: (max(y, 0), 1)
     const uint32_t *out_idx;   // infer: out[out_idx[s]] when given, else out[s]
     uint32_t *err;
@@ -562,29 +564,35 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
         if (abort_s) break;
     }
 
+    float *part = TRAIN ? a.wpart + (size_t)blockIdx.x * kPartStride : nullptr;
     if (abort_s) {
         if (t == 0) atomicOr(a.err, kErrTimeout);
+        if (TRAIN)
+            for (int i = t; i < kPartStride; i += kTile) part[i] = 0.0f;
     } else if (TRAIN && it > 0) {
         // weight gradients of this CTA's tiles: rows 0..63 of GA are dW2, rows 64..127 columns
-        // 64..95 are dW1; rows 0..63 of GC are dW3^T
+        // 64..95 are dW1; rows 0..63 of GC are dW3^T.  Plain stores into the CTA's partial row.
         tc::fence_after_sync();
         if (warp < 2) {
             float z[64];
             tmem_ld64(tmem, warp, kTmGA, z);
-            for (int j = 0; j < 64; ++j) atomicAdd(a.wgrad + kW2 + t * kHid + j, z[j]);
+            float4 *d2 = reinterpret_cast<float4 *>(part + kW2 + t * kHid);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) d2[j] = make_float4(z[4 * j], z[4 * j + 1], z[4 * j + 2], z[4 * j + 3]);
             float g[16];
             tc::tmem_ld16(tc::tmem_lane_addr(tmem, warp, kTmGC), g);
             tc::wait_ld();
-            for (int c = 0; c < kOut; ++c) atomicAdd(a.wgrad + kW3 + c * kHid + t, g[c]);
+            for (int c = 0; c < kOut; ++c) part[kW3 + c * kHid + t] = g[c];
         } else {
             float g0[16], g1[16];
             tc::tmem_ld16(tc::tmem_lane_addr(tmem, warp, kTmGA + 64), g0);
             tc::tmem_ld16(tc::tmem_lane_addr(tmem, warp, kTmGA + 80), g1);
             tc::wait_ld();
-            const uint32_t o = t - 64;
-            for (int j = 0; j < 16; ++j) {
-                atomicAdd(a.wgrad + kW1 + o * kIn + j, g0[j]);
-                atomicAdd(a.wgrad + kW1 + o * kIn + 16 + j, g1[j]);
+            float4 *d1 = reinterpret_cast<float4 *>(part + kW1 + (t - 64) * kIn);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                d1[j] = make_float4(g0[4 * j], g0[4 * j + 1], g0[4 * j + 2], g0[4 * j + 3]);
+                d1[4 + j] = make_float4(g1[4 * j], g1[4 * j + 1], g1[4 * j + 2], g1[4 * j + 3]);
             }
         }
         for (int d = 16; d; d >>= 1) {
@@ -592,11 +600,14 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
             jerr += __shfl_xor_sync(0xFFFFFFFFu, jerr, d);
             jtgt += __shfl_xor_sync(0xFFFFFFFFu, jtgt, d);
         }
+        __shared__ float red_s[4][3];
         if ((t & 31) == 0) {
-            atomicAdd(a.stats + 0, loss * 0.5f * a.dy_scale);
-            atomicAdd(a.stats + 1, jerr);
-            atomicAdd(a.stats + 2, jtgt);
+            red_s[warp][0] = loss;
+            red_s[warp][1] = jerr;
+            red_s[warp][2] = jtgt;
         }
+        __syncthreads();
+        if (t < 3) part[kWCount + t] = (red_s[0][t] + red_s[1][t] + red_s[2][t] + red_s[3][t]) * (t == 0 ? 0.5f * a.dy_scale : 1.0f);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -604,6 +615,29 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
 }
 
 // ---------------------------------------------------------------- gradient scatter and Adam
+
+// Sum the MLP kernel's per-CTA partials into the weight-gradient accumulators and the loss sums.
+// Block = 32 consecutive values x 8 warps; warp w sums parts w, w + 8, ...; then the 8 warp sums
+// in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) k_nrc_wgrad_reduce(const float *wpart, int parts, float *wg, float *stats) {
+    __shared__ float acc[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    float s = 0.0f;
+    if (i < kWCount + 3) {
+#pragma unroll 4
+        for (int p = w; p < parts; p += 8) s += __ldcg(wpart + (size_t)p * kPartStride + i);
+    }
+    acc[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && i < kWCount + 3) {
+        float t = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += acc[k][lane];
+        if (i < kWCount) wg[i] += t;
+        else stats[i - kWCount] += t;
+    }
+}
 
 __global__ void __launch_bounds__(kEncThreads) k_nrc_scatter(ScatterArgs a) {
     const uint32_t T = 1u << a.geo.log2_table;
@@ -793,6 +827,7 @@ struct gi_nrc_s {
     float *w = nullptr, *wm = nullptr, *wv = nullptr, *wg = nullptr;
     uint8_t *wimg = nullptr;
     float *stats = nullptr;      // loss, sum m|y - t|, sum m|t|, spare
+    float *wpart = nullptr;      // per-CTA partial weight gradients of the training network kernel
     uint32_t *err = nullptr;
     // per-batch scratch, capacity `cap` samples (a multiple of 128)
     uint32_t cap = 0;
@@ -827,7 +862,7 @@ gi_status nrc_alloc(void **p, size_t bytes) {
 }
 
 void nrc_free(gi_nrc_s *s) {
-    void *ptrs[] = {s->tab, s->grad, s->tab16, s->w, s->wm, s->wv, s->wg, s->wimg, s->stats, s->err,
+    void *ptrs[] = {s->tab, s->grad, s->tab16, s->w, s->wm, s->wv, s->wg, s->wimg, s->stats, s->err, s->wpart,
                     s->X, s->Tt, s->dX, s->idx, s->bits, s->ovr, s->qidx, s->qcount};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -889,8 +924,7 @@ gi_status launch_mlp(gi_nrc_s *s, bool train, uint32_t n, const uint32_t *count,
     m.dy_scale = dy_scale;
     m.loss_eps = s->cfg.loss_eps;
     m.dX = s->dX;
-    m.wgrad = s->wg;
-    m.stats = s->stats;
+    m.wpart = s->wpart;
     m.out = out;
     m.out_idx = out_idx;
     m.err = s->err;
@@ -899,6 +933,10 @@ gi_status launch_mlp(gi_nrc_s *s, bool train, uint32_t n, const uint32_t *count,
     if (train) {
         const unsigned grid = std::min<uint32_t>(tiles, (uint32_t)s->sms);
         k_nrc_mlp<true><<<grid, kTile, kSmTrain, st>>>(m);
+        gi_status r = cuda_status(cudaGetLastError(), "k_nrc_mlp launch");
+        if (r != GI_OK) return r;
+        k_nrc_wgrad_reduce<<<(kWCount + 3 + 31) / 32, 256, 0, st>>>(s->wpart, (int)grid, s->wg, s->stats);
+        return cuda_status(cudaGetLastError(), "k_nrc_wgrad_reduce launch");
     } else {
         const unsigned grid = std::min<uint32_t>(tiles, 2u * (uint32_t)s->sms);
         k_nrc_mlp<false><<<grid, kTile, kSmInfer, st>>>(m);
@@ -1038,6 +1076,7 @@ gi_status gi_nrc_create(const gi_nrc_config *cfg, gi_nrc_t *out) {
     if (st == GI_OK) st = nrc_alloc((void **)&s->wg, kWCount * 4);
     if (st == GI_OK) st = nrc_alloc((void **)&s->wimg, kImgBytes);
     if (st == GI_OK) st = nrc_alloc((void **)&s->stats, 16);
+    if (st == GI_OK) st = nrc_alloc((void **)&s->wpart, (size_t)s->sms * kPartStride * 4);
     if (st == GI_OK) st = nrc_alloc((void **)&s->err, 4);
     if (st == GI_OK) st = nrc_alloc((void **)&s->qcount, 4);
     const uint32_t maxr = std::max<uint32_t>(cfg->max_records, 32);

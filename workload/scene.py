@@ -86,7 +86,7 @@ CONFIGS[3] = dict(name="batched-16-views", scene="batched", n_views=16, frames=3
 # queried for cold cells, dropped inserts and LOD >= 2; 128 frames.
 CONFIGS[4] = dict(CONFIGS[1], name="cornell-1080p-surrogate", width=1920, height=1080, rays_per_probe=64,
                   log2_slots=20, frames=128, nrc_log2_table=19, nrc_batch=65536, nrc_train_steps=4,
-                  nrc_query_lod=2, nrc_lr=1e-2, nrc_trust=0.05,
+                  nrc_query_lod=2, nrc_lr=2e-2, nrc_trust=0.05,
                   nrc_resolutions=(16, 22, 30, 42, 58, 80, 111, 153, 212, 294, 406, 561, 776, 1072, 1482, 2048))
 
 
