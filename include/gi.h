@@ -64,6 +64,7 @@ typedef enum gi_status {
 
 enum { GI_KEY_DIR_NORMAL = 0, GI_KEY_DIR_RAY = 1 };
 enum { GI_RESOLVED_F32 = 0, GI_RESOLVED_F16 = 1 };
+enum { GI_FIRST_TOUCH_AUTO = 0, GI_FIRST_TOUCH_LIST = 1, GI_FIRST_TOUCH_BITMAP = 2 };
 
 typedef struct gi_cache_s *gi_cache_t;
 typedef void *gi_stream_t; /* cudaStream_t */
@@ -83,6 +84,12 @@ typedef void *gi_stream_t; /* cudaStream_t */
  *   resolved_format GI_RESOLVED_F32 (16 B per slot) or GI_RESOLVED_F16 (8 B)
  *   rebuild_load    fraction of slots occupied (live + stale cells) above which the
  *                   next update first compacts the table, in [0.25, 0.95]
+ *   first_touch     how the slots touched since the last resolve are recorded:
+ *                   GI_FIRST_TOUCH_LIST (a list, appended per block: cheapest update),
+ *                   GI_FIRST_TOUCH_BITMAP (one bit per slot, walked in slot order by the
+ *                   resolve: fewer DRAM bursts when the table exceeds the L2), or
+ *                   GI_FIRST_TOUCH_AUTO (the bitmap when the 32-byte accumulators of all
+ *                   slots exceed the device's L2, else the list).  Results are identical.
  */
 typedef struct gi_cache_config {
     uint32_t log2_slots;
@@ -94,6 +101,7 @@ typedef struct gi_cache_config {
     uint32_t key_dir;
     uint32_t resolved_format;
     float rebuild_load;
+    uint32_t first_touch;
 } gi_cache_config;
 
 /*

@@ -26,6 +26,7 @@ GI_PROBE_NONE = 0xFFFFFFFF
 GI_INTERP_OK, GI_INTERP_RELAXED, GI_INTERP_NONE, GI_INTERP_SKY = 0, 1, 2, 3
 GI_KEY_DIR_NORMAL, GI_KEY_DIR_RAY = 0, 1
 GI_RESOLVED_F32, GI_RESOLVED_F16 = 0, 1
+GI_FIRST_TOUCH_AUTO, GI_FIRST_TOUCH_LIST, GI_FIRST_TOUCH_BITMAP = 0, 1, 2
 GI_MAX_MIPS = 16
 GI_SH_STRIDE = 28
 GI_NOALLOC_LOG2_SLOTS = 18
@@ -43,7 +44,7 @@ c_u32, c_u64, c_f32, c_f64, c_vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_fl
 class gi_cache_config(ctypes.Structure):
     _fields_ = [("log2_slots", c_u32), ("cell_size", c_f32), ("num_lods", c_u32), ("alpha", c_f32),
                 ("evict_frames", c_u32), ("max_probe", c_u32), ("key_dir", c_u32), ("resolved_format", c_u32),
-                ("rebuild_load", c_f32)]
+                ("rebuild_load", c_f32), ("first_touch", c_u32)]
 
 
 class gi_view(ctypes.Structure):
@@ -260,9 +261,10 @@ def gi_cell_moments() -> np.ndarray:
 # ---------------------------------------------------------------- entry points (same names as the C ABI)
 def gi_cache_create(log2_slots: int, cell_size: float = 0.05, num_lods: int = 4, alpha: float = 0.1,
                     evict_frames: int = 8, max_probe: int = 128, key_dir: int = GI_KEY_DIR_NORMAL,
-                    resolved_format: int = GI_RESOLVED_F32, rebuild_load: float = 0.8) -> int:
+                    resolved_format: int = GI_RESOLVED_F32, rebuild_load: float = 0.8,
+                    first_touch: int = GI_FIRST_TOUCH_AUTO) -> int:
     cfg = gi_cache_config(log2_slots, cell_size, num_lods, alpha, evict_frames, max_probe, key_dir,
-                          resolved_format, rebuild_load)
+                          resolved_format, rebuild_load, first_touch)
     h = c_vp()
     check(lib().gi_cache_create(ctypes.byref(cfg), ctypes.byref(h)), "gi_cache_create")
     return h.value

@@ -5,9 +5,13 @@
 // Table layout (N = 2^log2_slots slots, structure of arrays):
 //   tags     u32[N]     fingerprint << 8 | (home mod 256); 0 = empty
 //   accum    Accum[N]   {u64 sum r,g,b; u32 count; u32 stamp}, one 32-byte sector
-//   resolved float4[N]  (r, g, b, 0), or half4 (r, g, b, 0) with GI_RESOLVED_F16
-// plus a spare table of the same shape for compaction, the touch list
-// (u32[N], slots first touched since the last resolve) and a counter line.
+//   resolved float4[N]  (r, g, b, cold), or half4 with GI_RESOLVED_F16
+// plus a spare table of the same shape for compaction, a record of the slots touched
+// since the last resolve and a counter line.  The first touch of a cell (its count's
+// returning add sees 0) either sets the slot's bit in a bitmap (u32[N/32]), which the
+// resolve walks and clears in slot order, or is staged per block in shared memory and
+// appended to a touch list (u32[N]).  A cache whose accumulators exceed the L2 takes
+// the bitmap (slot-ordered resolve traffic), a smaller one the list (cheaper updates).
 //
 // A cell is the pair (home, fingerprint): probing runs are shorter than 256
 // slots, so a tag, which carries home mod 256, can only match within the run
@@ -99,9 +103,13 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 
 
+// The count's returning add detects the first touch of a cell this frame.  With a.bitmap that
+// touch sets the slot's bit (a non-returning atomicOr); without, it goes to the block's
+// shared-memory list and then, once per block, to the touch list.
 template <int KEY_DIR>
 __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, uint32_t nblk) {
     __shared__ uint32_t s_touch[kUpdBlockRecords];
+    const bool bitmap = a.bitmap != nullptr;
     __shared__ uint32_t s_n, s_base, s_clamped, s_maxp;
     if (threadIdx.x == 0) {
         s_n = 0;
@@ -195,8 +203,11 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
                 atomicAdd(&ac->sum[0], q0);
                 atomicAdd(&ac->sum[1], q1);
                 atomicAdd(&ac->sum[2], q2);
-                // the count was cleared by the last resolve: the first adder this frame appends the slot
-                if (atomicAdd(&ac->count, cnt) == 0u) s_touch[atomicAdd(&s_n, 1u)] = slot;
+                // the count was cleared by the last resolve: the first adder this frame records the slot
+                if (atomicAdd(&ac->count, cnt) == 0u) {
+                    if (bitmap) atomicOr(a.bitmap + (slot >> 5), 1u << (slot & 31u));
+                    else s_touch[atomicAdd(&s_n, 1u)] = slot;
+                }
             } else {
                 atomicAdd(&a.ctr->dropped, (unsigned long long)cnt);
             }
@@ -214,12 +225,14 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        s_base = s_n ? atomicAdd(&a.ctr->touch_count, s_n) : 0u;
+        if (!bitmap) s_base = s_n ? atomicAdd(&a.ctr->touch_count, s_n) : 0u;
         if (s_clamped) atomicAdd(&a.ctr->clamped, (unsigned long long)s_clamped);
         if (s_maxp) atomicMax(&a.ctr->max_probe, s_maxp);
     }
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < s_n; j += kUpdThreads) a.touch[s_base + j] = s_touch[j];
+    if (!bitmap) {
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < s_n; j += kUpdThreads) a.touch[s_base + j] = s_touch[j];
+    }
 }
 
 template <int KEY_DIR>
@@ -265,64 +278,58 @@ __device__ __forceinline__ void store_resolved(void *r, uint32_t stride, int f16
 
 constexpr int kResUnroll = 4;
 
-__device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
+// Resolve up to kResUnroll touched slots (0xFFFFFFFF = none), their loads issued together:
+// mean = sum / (count 2^24); a cell without history (never resolved, or evicted by an earlier
+// resolve) takes the mean, the others blend; accumulator cleared, stamp = frame + 1.
+__device__ __forceinline__ void resolve_slots(const ResolveArgs &a, const uint32_t (&s)[kResUnroll], uint32_t &fresh_new) {
+    uint4 lo[kResUnroll], hi[kResUnroll];
+#pragma unroll
+    for (int u = 0; u < kResUnroll; ++u) {
+        if (s[u] != 0xFFFFFFFFu) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
+            lo[u] = __ldcg(src);
+            hi[u] = __ldcg(src + 1);
+        }
+    }
+    bool fresh[kResUnroll];
+    float3 old[kResUnroll];
+#pragma unroll
+    for (int u = 0; u < kResUnroll; ++u) {
+        const uint32_t stamp = hi[u].w;
+        // no history: never resolved, or evicted by an earlier resolve (untouched E frames)
+        fresh[u] = stamp == 0u || (a.has_lr && (a.lr - (stamp - 1u)) >= a.evict);
+        if (s[u] != 0xFFFFFFFFu && !fresh[u]) old[u] = load_resolved(a.resolved, a.res_stride, a.f16, s[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kResUnroll; ++u) {
+        if (s[u] == 0xFFFFFFFFu) continue;
+        const unsigned long long s0 = ((unsigned long long)lo[u].y << 32) | lo[u].x;
+        const unsigned long long s1 = ((unsigned long long)lo[u].w << 32) | lo[u].z;
+        const unsigned long long s2 = ((unsigned long long)hi[u].y << 32) | hi[u].x;
+        const float fc = (float)hi[u].z;
+        // mean = sum / (count 2^24)
+        const float3 m = make_float3(__fdiv_rn(__ull2float_rn(s0), fc) * 5.9604644775390625e-8f,
+                                     __fdiv_rn(__ull2float_rn(s1), fc) * 5.9604644775390625e-8f,
+                                     __fdiv_rn(__ull2float_rn(s2), fc) * 5.9604644775390625e-8f);
+        fresh_new += hi[u].w == 0u ? 1u : 0u;
+        float3 v = m;
+        if (!fresh[u]) {
+            const float3 o = old[u];
+            v = make_float3(o.x + a.alpha * (m.x - o.x), o.y + a.alpha * (m.y - o.y), o.z + a.alpha * (m.z - o.z));
+        }
+        store_resolved(a.resolved, a.res_stride, a.f16, s[u], v, fresh[u]);
+        uint4 *dst = reinterpret_cast<uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
+        dst[0] = make_uint4(0u, 0u, 0u, 0u);
+        dst[1] = make_uint4(0u, 0u, 0u, a.stamp_now);
+    }
+}
+
+// Block totals of newly occupied slots, then the last block (ticket) publishes the occupancy.
+__device__ __forceinline__ void resolve_finish(const ResolveArgs &a, uint32_t nblk, uint32_t fresh_new) {
     __shared__ uint32_t s_new;
     __shared__ bool s_last;
     if (threadIdx.x == 0) s_new = 0;
     __syncthreads();
-    const uint32_t n = __ldcg(&a.ctr->touch_count);
-    const uint32_t stride = nblk * kResThreads;
-    uint32_t fresh_new = 0;
-    // kResUnroll touched cells per thread and iteration, their loads issued together
-    for (uint32_t i0 = blk * kResThreads + threadIdx.x; i0 < n; i0 += kResUnroll * stride) {
-        uint32_t s[kResUnroll];
-        uint4 lo[kResUnroll], hi[kResUnroll];
-#pragma unroll
-        for (int u = 0; u < kResUnroll; ++u) {
-            const uint32_t i = i0 + u * stride;
-            s[u] = i < n ? __ldcs(a.touch + i) : 0xFFFFFFFFu;
-        }
-#pragma unroll
-        for (int u = 0; u < kResUnroll; ++u) {
-            if (s[u] != 0xFFFFFFFFu) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
-                lo[u] = __ldcg(src);
-                hi[u] = __ldcg(src + 1);
-            }
-        }
-        bool fresh[kResUnroll];
-        float3 old[kResUnroll];
-#pragma unroll
-        for (int u = 0; u < kResUnroll; ++u) {
-            const uint32_t stamp = hi[u].w;
-            // no history: never resolved, or evicted by an earlier resolve (untouched E frames)
-            fresh[u] = stamp == 0u || (a.has_lr && (a.lr - (stamp - 1u)) >= a.evict);
-            if (s[u] != 0xFFFFFFFFu && !fresh[u]) old[u] = load_resolved(a.resolved, a.res_stride, a.f16, s[u]);
-        }
-#pragma unroll
-        for (int u = 0; u < kResUnroll; ++u) {
-            if (s[u] == 0xFFFFFFFFu) continue;
-            const unsigned long long s0 = ((unsigned long long)lo[u].y << 32) | lo[u].x;
-            const unsigned long long s1 = ((unsigned long long)lo[u].w << 32) | lo[u].z;
-            const unsigned long long s2 = ((unsigned long long)hi[u].y << 32) | hi[u].x;
-            const float fc = (float)hi[u].z;
-            // mean = sum / (count 2^24)
-            const float3 m = make_float3(__fdiv_rn(__ull2float_rn(s0), fc) * 5.9604644775390625e-8f,
-                                         __fdiv_rn(__ull2float_rn(s1), fc) * 5.9604644775390625e-8f,
-                                         __fdiv_rn(__ull2float_rn(s2), fc) * 5.9604644775390625e-8f);
-            fresh_new += hi[u].w == 0u ? 1u : 0u;
-            float3 v = m;
-            if (!fresh[u]) {
-                const float3 o = old[u];
-                v = make_float3(o.x + a.alpha * (m.x - o.x), o.y + a.alpha * (m.y - o.y),
-                                o.z + a.alpha * (m.z - o.z));
-            }
-            store_resolved(a.resolved, a.res_stride, a.f16, s[u], v, fresh[u]);
-            uint4 *dst = reinterpret_cast<uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
-            dst[0] = make_uint4(0u, 0u, 0u, 0u);
-            dst[1] = make_uint4(0u, 0u, 0u, a.stamp_now);
-        }
-    }
     fresh_new = __reduce_add_sync(kFull, fresh_new);
     if ((threadIdx.x & 31) == 0 && fresh_new) atomicAdd(&s_new, fresh_new);
     __syncthreads();
@@ -344,6 +351,50 @@ __device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk,
             reinterpret_cast<volatile uint32_t *>(a.occ_out)[1] = a.stamp_now;
         }
     }
+}
+
+// touch-list form: kResUnroll list entries per thread and iteration
+__device__ __forceinline__ void resolve_list_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
+    const uint32_t n = __ldcg(&a.ctr->touch_count);
+    const uint32_t stride = nblk * kResThreads;
+    uint32_t fresh_new = 0;
+    for (uint32_t i0 = blk * kResThreads + threadIdx.x; i0 < n; i0 += kResUnroll * stride) {
+        uint32_t s[kResUnroll];
+#pragma unroll
+        for (int u = 0; u < kResUnroll; ++u) {
+            const uint32_t i = i0 + u * stride;
+            s[u] = i < n ? __ldcs(a.touch + i) : 0xFFFFFFFFu;
+        }
+        resolve_slots(a, s, fresh_new);
+    }
+    resolve_finish(a, nblk, fresh_new);
+}
+
+// bitmap form: a thread takes a word (32 consecutive slots), clears it and resolves its set bits
+// kResUnroll at a time, in slot order
+__device__ __forceinline__ void resolve_bm_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
+    const uint32_t stride = nblk * kResThreads;
+    uint32_t fresh_new = 0;
+    for (uint32_t w = blk * kResThreads + threadIdx.x; w < a.words; w += stride) {
+        uint32_t bits = __ldcg(a.bitmap + w);
+        if (!bits) continue;
+        a.bitmap[w] = 0u;
+        while (bits) {
+            uint32_t s[kResUnroll];
+#pragma unroll
+            for (int u = 0; u < kResUnroll; ++u) {
+                s[u] = bits ? w * 32u + (uint32_t)(__ffs(bits) - 1) : 0xFFFFFFFFu;
+                bits &= bits - 1u;
+            }
+            resolve_slots(a, s, fresh_new);
+        }
+    }
+    resolve_finish(a, nblk, fresh_new);
+}
+
+__device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
+    if (a.bitmap) resolve_bm_body(a, blk, nblk);
+    else resolve_list_body(a, blk, nblk);
 }
 
 __global__ void __launch_bounds__(kResThreads, 3) k_resolve(ResolveArgs a) { resolve_body(a, blockIdx.x, gridDim.x); }
@@ -450,10 +501,11 @@ __global__ void k_rebuild(SlotWord *old_tags, Accum *old_acc, const void *old_re
 }
 
 // ---------------------------------------------------------------- table scan for stats
-__global__ void k_scan_stats(const SlotWord *tags, const Accum *acc, uint32_t N, LiveRule rule,
-                             unsigned long long *out /* occupied, live */) {
-    unsigned long long occ = 0, live = 0;
+__global__ void k_scan_stats(const SlotWord *tags, const Accum *acc, const uint32_t *bitmap, uint32_t N, LiveRule rule,
+                             unsigned long long *out /* occupied, live, touched */) {
+    unsigned long long occ = 0, live = 0, touched = 0;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        if (bitmap && (s & 31u) == 0u) touched += __popc(bitmap[s >> 5]);
         if (word_tag(tags[s]) == kEmpty) continue;
         ++occ;
         if (acc[s].count > 0u || answers(acc[s].stamp, rule)) ++live;
@@ -461,10 +513,12 @@ __global__ void k_scan_stats(const SlotWord *tags, const Accum *acc, uint32_t N,
     for (int o = 16; o; o >>= 1) {
         occ += __shfl_xor_sync(kFull, occ, o);
         live += __shfl_xor_sync(kFull, live, o);
+        touched += __shfl_xor_sync(kFull, touched, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(out, occ);
         atomicAdd(out + 1, live);
+        atomicAdd(out + 2, touched);
     }
 }
 
@@ -527,6 +581,7 @@ struct gi_cache_s {
     uint32_t res_bytes;  // 16 (float4) or 8 (half4)
     int cur;
     uint32_t *touch;
+    uint32_t *bitmap;            // touched slots since the last resolve, one bit each
     gi::Counters *ctr;
     volatile uint32_t *occ_host; // mapped pinned {occupied, stamp of the resolve that wrote it}
     uint32_t *occ_dev;           // its device address
@@ -567,6 +622,7 @@ static bool config_ok(const gi_cache_config *c) {
     if (c->key_dir != GI_KEY_DIR_NORMAL && c->key_dir != GI_KEY_DIR_RAY) return false;
     if (c->resolved_format != GI_RESOLVED_F32 && c->resolved_format != GI_RESOLVED_F16) return false;
     if (!(c->rebuild_load >= 0.25f && c->rebuild_load <= 0.95f)) return false;
+    if (c->first_touch > GI_FIRST_TOUCH_BITMAP) return false;
     return true;
 }
 
@@ -597,6 +653,7 @@ UpdateArgs cache_update_args(gi_cache_s *c, const gi_hits *h, const gi_view *v, 
     a.accum = c->accum[c->cur];
     a.acc_stride = 1;
     a.touch = c->touch;
+    a.bitmap = c->bitmap;
     a.ctr = c->ctr;
     a.mask = c->mask;
     a.max_probe = c->cfg.max_probe;
@@ -628,6 +685,8 @@ static gi_status maybe_rebuild(gi_cache_s *c, cudaStream_t st) {
 ResolveArgs cache_resolve_args(gi_cache_s *c, uint32_t frame) {
     ResolveArgs a;
     a.touch = c->touch;
+    a.bitmap = c->bitmap;
+    a.words = c->N / 32u;
     a.accum = c->accum[c->cur];
     a.acc_stride = 1;
     a.resolved = c->resolved[c->cur];
@@ -668,6 +727,7 @@ static void free_cache(gi_cache_s *c) {
         cudaFree(c->resolved[k]);
     }
     cudaFree(c->touch);
+    cudaFree(c->bitmap);
     cudaFree(c->ctr);
     cudaFree(c->scan);
     if (c->occ_host) cudaFreeHost((void *)c->occ_host);
@@ -708,10 +768,21 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
         if (s == GI_OK) s = cuda_status(cudaMemset(c->accum[k], 0, N * sizeof(Accum)), "memset");
         if (s == GI_OK) s = cuda_status(cudaMemset(c->resolved[k], 0, N * c->res_bytes), "memset");
     }
-    if (s == GI_OK) s = cuda_status(cudaMalloc(&c->touch, N * 4), "cudaMalloc touch");
+    // First touches: a slot bitmap walked in slot order by the resolve when the accumulators
+    // exceed L2 (its ordered accesses then save DRAM traffic), else a touch list (cheaper updates).
+    int l2 = 0;
+    if (s == GI_OK) s = cuda_status(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device), "L2 size");
+    const bool use_bitmap = cfg->first_touch == GI_FIRST_TOUCH_BITMAP ||
+                            (cfg->first_touch == GI_FIRST_TOUCH_AUTO && N * sizeof(Accum) > (size_t)l2);
+    if (s == GI_OK && use_bitmap) {
+        s = cuda_status(cudaMalloc(&c->bitmap, N / 8), "cudaMalloc bitmap");
+        if (s == GI_OK) s = cuda_status(cudaMemset(c->bitmap, 0, N / 8), "memset");
+    } else if (s == GI_OK) {
+        s = cuda_status(cudaMalloc(&c->touch, N * 4), "cudaMalloc touch");
+    }
     if (s == GI_OK) s = cuda_status(cudaMalloc(&c->ctr, sizeof(Counters)), "cudaMalloc counters");
     if (s == GI_OK) s = cuda_status(cudaMemset(c->ctr, 0, sizeof(Counters)), "memset");
-    if (s == GI_OK) s = cuda_status(cudaMalloc(&c->scan, 2 * sizeof(unsigned long long)), "cudaMalloc scan");
+    if (s == GI_OK) s = cuda_status(cudaMalloc(&c->scan, 3 * sizeof(unsigned long long)), "cudaMalloc scan");
     if (s == GI_OK) {
         void *hp = nullptr;
         s = cuda_status(cudaHostAlloc(&hp, 2 * sizeof(uint32_t), cudaHostAllocMapped), "cudaHostAlloc");
@@ -837,13 +908,13 @@ gi_status gi_cache_stats(gi_cache_t c, gi_cache_stats_t *out, gi_stream_t stream
         return GI_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    gi_status s = cuda_status(cudaMemsetAsync(c->scan, 0, 2 * sizeof(unsigned long long), st), "stats memset");
+    gi_status s = cuda_status(cudaMemsetAsync(c->scan, 0, 3 * sizeof(unsigned long long), st), "stats memset");
     if (s != GI_OK) return s;
-    k_scan_stats<<<c->sms * 4, 256, 0, st>>>(c->tags[c->cur], c->accum[c->cur], c->N, live_rule(c), c->scan);
+    k_scan_stats<<<c->sms * 4, 256, 0, st>>>(c->tags[c->cur], c->accum[c->cur], c->bitmap, c->N, live_rule(c), c->scan);
     s = cuda_status(cudaGetLastError(), "k_scan_stats launch");
     if (s != GI_OK) return s;
     Counters h;
-    unsigned long long sc[2];
+    unsigned long long sc[3];
     s = cuda_status(cudaMemcpyAsync(&h, c->ctr, sizeof h, cudaMemcpyDeviceToHost, st), "stats copy");
     if (s == GI_OK) s = cuda_status(cudaMemcpyAsync(sc, c->scan, sizeof sc, cudaMemcpyDeviceToHost, st), "stats copy");
     if (s == GI_OK) s = cuda_status(cudaStreamSynchronize(st), "stats sync");
@@ -852,7 +923,7 @@ gi_status gi_cache_stats(gi_cache_t c, gi_cache_stats_t *out, gi_stream_t stream
     out->slots = c->N;
     out->occupied = sc[0];
     out->live = sc[1];
-    out->touched = h.touch_count;
+    out->touched = c->bitmap ? sc[2] : h.touch_count;
     out->dropped = h.dropped;
     out->clamped = h.clamped;
     out->rebuilds = c->rebuilds;
@@ -1053,6 +1124,7 @@ extern "C" gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *v
     a.accum = accum;
     a.acc_stride = 1;
     a.touch = touch;
+    a.bitmap = nullptr;
     a.ctr = ctr;
     a.mask = kNoAllocSlots - 1u;
     a.max_probe = 255;

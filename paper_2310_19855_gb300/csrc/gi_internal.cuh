@@ -100,6 +100,7 @@ struct UpdateArgs {
     Accum *accum;
     uint32_t acc_stride;  // Accum units between consecutive slots
     uint32_t *touch;
+    uint32_t *bitmap;     // touched slots, one bit each (NULL: first touches go to the touch list)
     Counters *ctr;
     uint32_t mask;
     uint32_t max_probe;
@@ -108,6 +109,8 @@ struct UpdateArgs {
 
 struct ResolveArgs {
     const uint32_t *touch;
+    uint32_t *bitmap;     // touched slots (walked and cleared by the resolve)
+    uint32_t words;       // bitmap words = slots / 32
     Accum *accum;
     uint32_t acc_stride;
     void *resolved;

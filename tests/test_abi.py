@@ -91,12 +91,14 @@ def test_cell_moments_match_oracle_quadrature(lib):
 
 def test_invalid_arguments_are_rejected_on_the_host(lib):
     h = ctypes.c_void_p()
-    bad = gi.gi_cache_config(40, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8)
+    bad = gi.gi_cache_config(40, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, 0)
     assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
     assert b"configuration" in lib.gi_last_error()
-    bad = gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 300, 0, 0, 0.8)  # probe runs must stay below 256
+    bad = gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 300, 0, 0, 0.8, 0)  # probe runs must stay below 256
     assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
-    bad = gi.gi_cache_config(16, -1.0, 4, 0.1, 8, 128, 0, 0, 0.8)
+    bad = gi.gi_cache_config(16, -1.0, 4, 0.1, 8, 128, 0, 0, 0.8, 0)
+    assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    bad = gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, 3)  # unknown first-touch record
     assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_cache_create(None, ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_cache_update(None, None, None, None, None) == gi.GI_ERR_INVALID_ARG

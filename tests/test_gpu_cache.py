@@ -42,11 +42,16 @@ def _run_update(h, rec_np, view, n_slots):
     return u32(slots)[:n]
 
 
-def _frames_parity(config, frames, key_dir=0, log2_slots=None, resolved_format=0, value_rel=1e-4):
+# both records of the slots touched since the last resolve (results must not depend on it)
+FIRST_TOUCH = pytest.mark.parametrize("first_touch", [gi.GI_FIRST_TOUCH_LIST, gi.GI_FIRST_TOUCH_BITMAP],
+                                      ids=["touch-list", "bitmap"])
+
+
+def _frames_parity(config, frames, key_dir=0, log2_slots=None, resolved_format=0, value_rel=1e-4, first_touch=0):
     cfg = wl.CONFIGS[config]
     ls = log2_slots or cfg["log2_slots"]
     oc = OracleCache(ls, key_dir=key_dir)
-    h = gi.gi_cache_create(ls, key_dir=key_dir, resolved_format=resolved_format)
+    h = gi.gi_cache_create(ls, key_dir=key_dir, resolved_format=resolved_format, first_touch=first_touch)
     try:
         for fr in frames:
             cam = fr.camera
@@ -56,6 +61,7 @@ def _frames_parity(config, frames, key_dir=0, log2_slots=None, resolved_format=0
             ex = gi.gi_cache_export(h)
             check_export_matches(ex, oc, resolved=False)
             check_slot_ids(slots, ex, fr.records, ident, 1 << ls)
+            assert gi.gi_cache_stats(h)["touched"] == int(np.count_nonzero(oc.count))
             gi.gi_cache_resolve(h, fr.frame)
             oc.resolve(fr.frame)
             check_export_matches(gi.gi_cache_export(h), oc, resolved=True, value_rel=value_rel)
@@ -67,8 +73,9 @@ def _frames_parity(config, frames, key_dir=0, log2_slots=None, resolved_format=0
         gi.gi_cache_destroy(h)
 
 
-def test_cornell_frames_bit_exact():
-    _frames_parity(1, wl.make_frames(1))
+@FIRST_TOUCH
+def test_cornell_frames_bit_exact(first_touch):
+    _frames_parity(1, wl.make_frames(1), first_touch=first_touch)
 
 
 def test_cornell_frames_ray_direction_descriptor():
@@ -84,18 +91,20 @@ def test_cornell_frames_fp16_resolved():
     _frames_parity(1, frames, resolved_format=gi.GI_RESOLVED_F16, value_rel=bound)
 
 
-def test_full_size_1080p_two_frames():
+@FIRST_TOUCH
+def test_full_size_1080p_two_frames(first_touch):
     # the 1080p workload at full size, in the launch configuration the bench uses
     scene = wl.make_scene(2)
-    _frames_parity(2, [wl.make_frame(2, f, scene) for f in (0, 1)])
+    _frames_parity(2, [wl.make_frame(2, f, scene) for f in (0, 1)], first_touch=first_touch)
 
 
+@FIRST_TOUCH
 @pytest.mark.parametrize("n", [0, 1, 31, 33, 257, 10007])
-def test_ragged_batches_and_split_updates(n):
+def test_ragged_batches_and_split_updates(n, first_touch):
     cam = _Cam((0.3, -0.2, 0.1))
     ls = 16
     oc = OracleCache(ls)
-    h = gi.gi_cache_create(ls)
+    h = gi.gi_cache_create(ls, first_touch=first_touch)
     try:
         for f in range(3):
             rec = wl.records_random(n, seed=100 + f, extent=1.5, cam=cam.pos)
@@ -115,7 +124,8 @@ def test_ragged_batches_and_split_updates(n):
         gi.gi_cache_destroy(h)
 
 
-def test_all_records_in_one_cell():
+@FIRST_TOUCH
+def test_all_records_in_one_cell(first_touch):
     # every lane of every warp names the same cell: the warp merge and the atomics must add up exactly
     n = 50000
     rec = np.zeros((13, n), np.float32)
@@ -126,7 +136,7 @@ def test_all_records_in_one_cell():
     rec[9] = 1.0
     cam = _Cam()
     oc = OracleCache(10)
-    h = gi.gi_cache_create(10)
+    h = gi.gi_cache_create(10, first_touch=first_touch)
     try:
         view = view_of(cam, 0)
         _run_update(h, rec, view, 1 << 10)
@@ -138,7 +148,8 @@ def test_all_records_in_one_cell():
         gi.gi_cache_destroy(h)
 
 
-def test_every_key_retrievable_in_a_crowded_table():
+@FIRST_TOUCH
+def test_every_key_retrievable_in_a_crowded_table(first_touch):
     # 2^10 slots at ~60 % load: long probing runs, no drop, no duplicate, every record finds its cell
     cam = _Cam(W=1920, H=1080)  # every cell at LOD 0 within 12 m
     rng = np.random.default_rng(9)
@@ -151,7 +162,7 @@ def test_every_key_retrievable_in_a_crowded_table():
     rec[9] = 1.0
     ls = 10
     oc = OracleCache(ls)
-    h = gi.gi_cache_create(ls, max_probe=255)
+    h = gi.gi_cache_create(ls, max_probe=255, first_touch=first_touch)
     try:
         view = view_of(cam, 0)
         slots = _run_update(h, rec, view, 1 << ls)
@@ -175,7 +186,8 @@ def test_every_key_retrievable_in_a_crowded_table():
         gi.gi_cache_destroy(h)
 
 
-def test_eviction_at_eighth_untouched_resolve_and_fresh_restart():
+@FIRST_TOUCH
+def test_eviction_at_eighth_untouched_resolve_and_fresh_restart(first_touch):
     cam = _Cam()
     a = np.zeros((13, 64), np.float32)
     a[0:3] = np.float32(0.11)
@@ -185,7 +197,7 @@ def test_eviction_at_eighth_untouched_resolve_and_fresh_restart():
     b = a.copy()
     b[0:3] = np.float32(0.61)
     oc = OracleCache(12)
-    h = gi.gi_cache_create(12)
+    h = gi.gi_cache_create(12, first_touch=first_touch)
     try:
         for f in range(0, 20):
             rec = np.concatenate([a, b], axis=1) if f == 0 else b
@@ -206,12 +218,13 @@ def test_eviction_at_eighth_untouched_resolve_and_fresh_restart():
         gi.gi_cache_destroy(h)
 
 
-def test_compaction_keeps_the_live_set():
+@FIRST_TOUCH
+def test_compaction_keeps_the_live_set(first_touch):
     # a small table that fills with stale cells and is compacted several times
     cam = _Cam()
     ls = 14
     oc = OracleCache(ls, evict_frames=2)
-    h = gi.gi_cache_create(ls, evict_frames=2, rebuild_load=0.3)
+    h = gi.gi_cache_create(ls, evict_frames=2, rebuild_load=0.3, first_touch=first_touch)
     try:
         for f in range(16):
             rec = wl.records_random(1500, seed=500 + f, extent=1.0)
