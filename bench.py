@@ -323,6 +323,28 @@ def run_native(args, rank, world, local_rank):
     h2d = h_rec[0].numel() * 4 + h_gb[0].numel() * 4
     d2h = h_out.numel() * 4
 
+    # ---- the filtered probe chain (Algorithm 5): gather, filter x, filter y, project, per pass
+    P = fr0.tiles_x * fr0.tiles_y
+    atlas = torch.empty((P, 64, 4), dtype=torch.float32, device="cuda")
+    atlas_tmp = torch.empty_like(atlas)
+    f_steps = max(3, min(args.steps, 50))
+    f_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(f_steps)]
+    for j in range(f_steps):
+        k = j % n_frames
+        flush.zero_()
+        f_ev[j][0].record(stream)
+        gi.gi_probes_gather(pl.cache, pl.probes.struct, pl.slot_ids, dev_rec[k][9], fr0.rays_per_probe, atlas,
+                            stream=stream)
+        f_ev[j][1].record(stream)
+        gi.gi_probes_filter(pl.probes.struct, views[k], atlas, atlas_tmp, 0, stream)
+        f_ev[j][2].record(stream)
+        gi.gi_probes_filter(pl.probes.struct, views[k], atlas_tmp, atlas, 1, stream)
+        f_ev[j][3].record(stream)
+        gi.gi_probes_project(pl.probes.struct, atlas, stream)
+        f_ev[j][4].record(stream)
+    torch.cuda.synchronize()
+    f_ms = np.array([[f_ev[j][i].elapsed_time(f_ev[j][i + 1]) for i in range(4)] for j in range(f_steps)]).mean(axis=0)
+
     # ---- max over ranks
     tot = np.array(max_over_ranks([window_ms.sum(), frame_ms.sum(), t_wall, e2e_ms.sum()], world, "cuda"))
     if rank != 0:
@@ -364,6 +386,17 @@ def run_native(args, rank, world, local_rank):
                "sample": f"3 frames x first {args.sample:.3f} of the probes ({Rs} records each): update + resolve "
                          "+ query + probe irradiance, numpy float64, one thread"}
 
+    # k_filter: each atlas entry (16 B) read once and written once per pass, plus the probe's and its
+    # neighbours' position and normal (32 B per probe); the neighbours' same cell are L2 re-reads
+    filt_bytes = P * 64 * 32 + P * 32
+    filt_ms = float(min(f_ms[1], f_ms[2]))
+    probe_filter = {"pass_ms": {"gather": float(f_ms[0]), "filter_x": float(f_ms[1]), "filter_y": float(f_ms[2]),
+                                "project": float(f_ms[3])},
+                    "note": "gi_probes_gather + 2 x gi_probes_filter + gi_probes_project in place of "
+                            "gi_probes_integrate (Algorithm 5), L2 flushed before each chain",
+                    "roofline": {"bound": "hbm", "kernel": "k_filter", "algorithmic_bytes_per_launch": filt_bytes,
+                                 "achieved": filt_bytes / (filt_ms * 1e-3) / 1e9, "peak": peak,
+                                 "frac": filt_bytes / (filt_ms * 1e-3) / 1e9 / peak, "unit": "GB/s"}}
     launches_per_step = 6  # k_spawn, k_mip_tail, k_update, k_resolve, k_integrate, k_interpolate
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -388,6 +421,7 @@ def run_native(args, rank, world, local_rank):
         "table": {"slots": int(st["slots"]), "occupied": int(st["occupied"]), "live": int(st["live"]),
                   "max_probe_seen": int(st["max_probe_seen"]), "rebuilds_total": int(st["rebuilds"])},
         "rebuilds_in_timed_region": int(rebuilds),
+        "probe_filter": probe_filter,
         "clocks": clk,
         "wall_s_timed": float(tot[2]),
     }

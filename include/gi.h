@@ -309,6 +309,34 @@ gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *probes, const u
                               uint32_t rays_per_probe, const float env[3], gi_stream_t stream);
 
 /*
+ * The same probe irradiance in three passes, with the probe filter of Section 2.3 (Algorithm 5)
+ * in between.  The probe atlas is a device float4 array of num_probes x 64 entries (16-byte
+ * aligned, caller-owned): entry p * 64 + c = (radiance rgb, hit distance) of cell c of probe p.
+ *
+ * gi_probes_gather: per cell the mean radiance of its rays as in gi_probes_integrate (radiance
+ * backup included) and the mean ray length of its rays that hit a surface (+inf when none did);
+ * ray_len = the records' ray lengths (device, num_probes * rays_per_probe floats).  Zeros for a
+ * tile without probe.
+ *
+ * gi_probes_filter: one pass of the separable 7x7 sparse blur along axis 0 (x) or 1 (y) of the
+ * probe grid: each cell is averaged with the same cell of the probes that Algorithm 3 finds at
+ * steps -1, +1, -2, +2, -3, +3, skipping a neighbour farther than cell_size(d_p) (Algorithm 6)
+ * from the probe's plane, a cell whose direction points behind the neighbour's normal, and a
+ * neighbour whose hit point (at the smaller of the two hit distances) lies more than pi/50 off the
+ * cell direction seen from the probe; weight 1 (the probe) and 1 / (1 + |d_p - d_q| / cell_size(d_p))
+ * per accepted neighbour; the running hit distance is the weighted mean.  atlas_out must not alias
+ * atlas_in.
+ *
+ * gi_probes_project: SH coefficients of every probe from its atlas into probes->sh, as
+ * gi_probes_integrate does from the rays (gather + project == integrate).
+ */
+gi_status gi_probes_gather(gi_cache_t cache, const gi_probes *probes, const uint32_t *slot_ids, const float *ray_len,
+                           uint32_t rays_per_probe, const float env[3], float *atlas, gi_stream_t stream);
+gi_status gi_probes_filter(const gi_probes *probes, const gi_view *view, const float *atlas_in, float *atlas_out,
+                           uint32_t axis, gi_stream_t stream);
+gi_status gi_probes_project(const gi_probes *probes, const float *atlas, gi_stream_t stream);
+
+/*
  * Per-pixel interpolation (Section 2.4.1): the four neighbours found by
  * Algorithm 3 at offsets (0,0), (1,0), (0,1), (1,1) from tile floor((pixel - 4) / 8);
  * weight = bilinear * max(0, n_p . n_q)^8 * max(0, 1 - plane_dist / cell_size(d_p));

@@ -15,6 +15,18 @@ irradiance and per-pixel interpolation.
   radiance; cells with no sample get the mean of the populated cells
   (radiance backup); projection to three SH bands through the cells'
   direction moments.
+* Probe filtering (Section 2.3, Algorithm 5): the probe's 8x8 cell radiance (and
+  the mean hit distance of each cell's rays, in the 4th channel) blurred with the
+  same cell of the probes found by Algorithm 3 at steps -1, +1, -2, +2, -3, +3
+  along one probe-grid axis per pass (x, then y: a separable 7x7 sparse blur);
+  a neighbour is skipped when it lies farther than cell_size from the probe's
+  plane, when the cell direction points behind its normal, or when the hit point
+  seen from it (at the smaller of the two hit distances) is more than pi/50 off
+  the cell direction from the probe.  Readings: the depth weight, which the paper
+  leaves unspecified, is 1 / (1 + |d_p - d_q| / cell_size(d_p)); a cell whose rays
+  all missed has hit distance +inf, and a hit point at infinity is exactly along
+  the cell direction (angle test passes); the cell direction is the world
+  direction of the cell's centre (u, v) in the probe frame.
 * Interpolation (Section 2.4.1): four neighbours found with Algorithm 3 at
   offsets (0,0), (1,0), (0,1), (1,1) from the tile below-left of the pixel
   (pixel - (4,4) in probe space); weight = bilinear * max(0, n_p.n_q)^8 *
@@ -152,6 +164,122 @@ def integrate(valid, nrm, ray_rad, ray_has, moments=None):
     S2w = np.einsum("pia,pjb,pabx->pijx", R, R, S2)
     coeffs = sh.project_moments(S0, S1w, S2w)
     return np.where(np.asarray(valid)[:, None, None], coeffs, 0.0)
+
+
+def gather(valid, ray_rad, ray_has, ray_len):
+    """Probe atlas (P, 64, 4): per hemi-octahedral cell the mean radiance of its rays that produced
+    a sample, the radiance backup (mean of the populated cells) where none did (Section 2.1.4), and
+    in the 4th channel the mean ray length of its rays that hit a surface (+inf when none did).
+    Probes that do not exist get zeros."""
+    ray_has = np.asarray(ray_has, bool)
+    P, rpp = ray_has.shape
+    cell = np.arange(rpp) & 63
+    onehot = (cell[:, None] == np.arange(64)[None, :]).astype(np.float64)  # (RPP, 64)
+    w = ray_has.astype(np.float64)
+    csum = np.einsum("pk,kc,pkx->pcx", w, onehot, np.asarray(ray_rad, np.float64))
+    cnt = np.einsum("pk,kc->pc", w, onehot)
+    pop = cnt > 0
+    L = np.where(pop[..., None], csum / np.maximum(cnt, 1.0)[..., None], 0.0)
+    npop = pop.sum(axis=1)
+    backup = np.where((npop > 0)[:, None], L.sum(axis=1) / np.maximum(npop, 1)[:, None], 0.0)
+    L = np.where(pop[..., None], L, backup[:, None, :])
+    ln = np.asarray(ray_len, np.float64).reshape(P, rpp)
+    hit = ray_has & np.isfinite(ln) & (ln >= 0)
+    hsum = np.einsum("pk,kc->pc", np.where(hit, ln, 0.0), onehot)
+    hcnt = np.einsum("pk,kc->pc", hit.astype(np.float64), onehot)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        hd = np.where(hcnt > 0, hsum / np.maximum(hcnt, 1.0), np.inf)
+    atlas = np.concatenate([L, hd[..., None]], axis=-1)
+    return np.where(np.asarray(valid)[:, None, None], atlas, 0.0)
+
+
+def project(valid, nrm, atlas, moments=None):
+    """SH coefficients (P, 9, 3) of the cell radiance atlas[..., :3] through the cells' direction
+    moments (Section 2.4.2), in the probe frame rotated to world space."""
+    if moments is None:
+        moments = hemioct.moments()
+    omega, m1, m2 = moments
+    L = np.asarray(atlas, np.float64)[..., :3]
+    S0 = np.einsum("c,pcx->px", omega, L)
+    S1 = np.einsum("ca,pcx->pax", m1, L)
+    S2 = np.einsum("cab,pcx->pabx", m2, L)
+    t, b = hemioct.onb(nrm)
+    R = np.stack([t, b, np.asarray(nrm, np.float64)], axis=-1)
+    S1w = np.einsum("pia,pax->pix", R, S1)
+    S2w = np.einsum("pia,pjb,pabx->pijx", R, R, S2)
+    coeffs = sh.project_moments(S0, S1w, S2w)
+    return np.where(np.asarray(valid)[:, None, None], coeffs, 0.0)
+
+
+def cell_dirs_world(nrm):
+    """World direction (P, 64, 3) of each cell centre: cell 8 j + i at u = -1 + (i + 0.5)/4,
+    v = -1 + (j + 0.5)/4 in the probe frame (t, b, n)."""
+    c = np.arange(64)
+    local = hemioct.uv_to_dir(-1.0 + ((c & 7) + 0.5) * 0.25, -1.0 + ((c >> 3) + 0.5) * 0.25)  # (64, 3)
+    n = np.asarray(nrm, np.float64)
+    t, b = hemioct.onb(n)
+    return (local[None, :, 0:1] * t[:, None, :] + local[None, :, 1:2] * b[:, None, :]
+            + local[None, :, 2:3] * n[:, None, :])
+
+
+FILTER_COS = math.cos(math.pi / 50.0)
+
+
+def filter_pass(atlas, sp, cam, axis: int):
+    """One pass of Algorithm 5 along probe-grid axis 0 (x) or 1 (y).  atlas (P, 64, 4) as from
+    gather; sp the spawn dict (mask, pos, nrm, dist, valid, tiles_x, tiles_y).  Returns the
+    filtered atlas and, per probe and cell, the smallest margin of its accept/reject decisions
+    (|plane - cs| / cs, |n_q . dir|, |angle - cos(pi/50)|), for comparisons in other precisions."""
+    atlas = np.asarray(atlas, np.float64)
+    P = atlas.shape[0]
+    mips = build_mips(sp["mask"])
+    txn = sp["tiles_x"]
+    pidx = np.arange(P)
+    tx, ty = pidx % txn, pidx // txn
+    valid = np.asarray(sp["valid"], bool)
+    pos, nrm, dist = sp["pos"], sp["nrm"], sp["dist"]
+    cs = distance_scale(cam.fov_y, cam.width, cam.height) * dist  # (P,)
+    dirs = cell_dirs_world(nrm)  # (P, 64, 3)
+    rad = atlas[..., :3].copy()
+    acc_a = atlas[..., 3].copy()
+    weight = np.ones((P, 64))
+    hd = atlas[..., 3].copy()
+    margin = np.full((P, 64), np.inf)
+    for i in range(6):
+        step = (((i & 1) << 1) - 1) * ((i >> 1) + 1)
+        ox, oy = (step, 0) if axis == 0 else (0, step)
+        q = find_closest_probe(mips, tx, ty, ox, oy)
+        found = (q != SENTINEL) & valid
+        qx = (q & 0xFFFF).astype(np.int64)
+        qy = (q >> 16).astype(np.int64)
+        qi = np.where(found, (qy >> 3) * txn + (qx >> 3), 0)
+        plane = np.abs(((pos[qi] - pos) * nrm).sum(axis=-1))  # (P,)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            pm = np.where(cs > 0, np.abs(plane - cs) / cs, np.inf)
+        ncheck = (dirs * nrm[qi][:, None, :]).sum(axis=-1)  # (P, 64)
+        hdc = np.minimum(atlas[qi, :, 3], hd)
+        fin = np.isfinite(hdc)
+        hp = pos[qi][:, None, :] + dirs * np.where(fin, hdc, 0.0)[..., None]
+        v = hp - pos[:, None, :]
+        vn = np.linalg.norm(v, axis=-1)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ang = np.where(fin, (dirs * v).sum(axis=-1) / vn, 1.0)
+        ang = np.where(fin & (vn == 0), 1.0, ang)
+        ok = found[:, None] & (plane <= cs)[:, None] & (ncheck >= 0.0) & (ang >= FILTER_COS)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            w = 1.0 / (1.0 + np.abs(dist - dist[qi]) / cs)
+        w = np.where(ok, w[:, None], 0.0)
+        rad += w[..., None] * atlas[qi, :, :3]
+        with np.errstate(invalid="ignore"):  # 0 * inf in rejected entries, discarded by the where
+            acc_a += np.where(ok, w * hdc, 0.0)
+        weight += w
+        with np.errstate(invalid="ignore"):
+            hd = np.where(ok, acc_a / weight, hd)
+        m = np.minimum(np.minimum(np.where(found, pm, np.inf)[:, None], np.abs(ncheck)),
+                       np.where(fin, np.abs(ang - FILTER_COS), np.inf))
+        margin = np.where(found[:, None], np.minimum(margin, m), margin)
+    out = np.concatenate([rad / weight[..., None], (acc_a / weight)[..., None]], axis=-1)
+    return np.where(valid[:, None, None], out, atlas), margin
 
 
 def interpolate(gbuf, cam, sp, coeffs):

@@ -153,6 +153,11 @@ def lib() -> ctypes.CDLL:
             "gi_probes_interpolate": (ctypes.c_int, [ctypes.POINTER(gi_gbuffer), ctypes.POINTER(gi_view),
                                                      ctypes.POINTER(gi_probes), c_vp, c_vp]),
             "gi_cell_moments": (ctypes.c_int, [ctypes.POINTER(c_f64)]),
+            "gi_probes_gather": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_probes), c_vp, c_vp, c_u32,
+                                                ctypes.POINTER(c_f32), c_vp, c_vp]),
+            "gi_probes_filter": (ctypes.c_int, [ctypes.POINTER(gi_probes), ctypes.POINTER(gi_view), c_vp, c_vp, c_u32,
+                                                c_vp]),
+            "gi_probes_project": (ctypes.c_int, [ctypes.POINTER(gi_probes), c_vp, c_vp]),
             "gi_batch_create": (ctypes.c_int, [c_u32, c_u32, ctypes.POINTER(gi_batch_tuning), ctypes.POINTER(c_vp)]),
             "gi_batch_set_tuning": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_batch_tuning)]),
             "gi_batch_frame": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_batch_view), c_u32, c_vp]),
@@ -331,6 +336,24 @@ def gi_probes_integrate(cache: int, probes: gi_probes, slot_ids, rays_per_probe:
 def gi_probes_interpolate(gbuf: gi_gbuffer, view: gi_view, probes: gi_probes, out, stream=None) -> None:
     check(lib().gi_probes_interpolate(ctypes.byref(gbuf), ctypes.byref(view), ctypes.byref(probes), _ptr(out),
                                       _stream(stream)), "gi_probes_interpolate")
+
+
+def gi_probes_gather(cache: int, probes: gi_probes, slot_ids, ray_len, rays_per_probe: int, atlas,
+                     env=(0.0, 0.0, 0.0), stream=None) -> None:
+    """Probe atlas (device float4 per probe and cell: radiance rgb, mean hit distance)."""
+    e = (c_f32 * 3)(*[float(x) for x in env])
+    check(lib().gi_probes_gather(cache, ctypes.byref(probes), _ptr(slot_ids), _ptr(ray_len), int(rays_per_probe), e,
+                                 _ptr(atlas), _stream(stream)), "gi_probes_gather")
+
+
+def gi_probes_filter(probes: gi_probes, view: gi_view, atlas_in, atlas_out, axis: int, stream=None) -> None:
+    """One pass of the probe filter (Algorithm 5) along axis 0 (x) or 1 (y)."""
+    check(lib().gi_probes_filter(ctypes.byref(probes), ctypes.byref(view), _ptr(atlas_in), _ptr(atlas_out), int(axis),
+                                 _stream(stream)), "gi_probes_filter")
+
+
+def gi_probes_project(probes: gi_probes, atlas, stream=None) -> None:
+    check(lib().gi_probes_project(ctypes.byref(probes), _ptr(atlas), _stream(stream)), "gi_probes_project")
 
 
 def make_gbuffer(nd, width: int, height: int) -> gi_gbuffer:

@@ -159,6 +159,7 @@ struct IntegrateArgs {
     float env[3];
     const uint32_t *ovr_bits;  // surrogate answers: bit r set -> record r takes ovr[r] (or NULL)
     const float4 *ovr;
+    const float *ray_len;      // ray lengths of the records (probe atlas: mean hit distance per cell)
 };
 
 struct InterpArgs {

@@ -105,6 +105,11 @@ static void cell_moments_closed_form(int c, double out[10]) {
     out[9] = s * 0.5 * (m2[1][2] + m2[2][1]);
 }
 
+// Local unit direction of each cell's centre (u, v) = (-1 + (i + 1/2)/4, -1 + (j + 1/2)/4), cell 8 j + i.
+__constant__ float c_cell_dir[64][3];
+// cos(pi / 50): the angle-error threshold of the probe filter (Algorithm 5)
+__constant__ float c_filter_cos;
+
 static std::mutex g_moments_mutex;
 static bool g_moments_ready[64];
 
@@ -121,6 +126,18 @@ gi_status ensure_moments() {
         for (int k = 0; k < 10; ++k) table[k][c] = (float)m[k];
     }
     s = cuda_status(cudaMemcpyToSymbol(g_moments, table, sizeof table), "upload cell moments");
+    float dirs[64][3];
+    for (int c = 0; c < 64; ++c) {
+        const double u = -1.0 + ((c & 7) + 0.5) * 0.25, v = -1.0 + ((c >> 3) + 0.5) * 0.25;
+        const double x = 0.5 * (u + v), y = 0.5 * (u - v), z = 1.0 - fabs(x) - fabs(y);
+        const double n = sqrt(x * x + y * y + z * z);
+        dirs[c][0] = (float)(x / n);
+        dirs[c][1] = (float)(y / n);
+        dirs[c][2] = (float)(z / n);
+    }
+    const float fc = (float)cos(3.14159265358979323846 / 50.0);
+    if (s == GI_OK) s = cuda_status(cudaMemcpyToSymbol(c_cell_dir, dirs, sizeof dirs), "upload cell directions");
+    if (s == GI_OK) s = cuda_status(cudaMemcpyToSymbol(c_filter_cos, &fc, sizeof fc), "upload filter threshold");
     if (s == GI_OK && dev >= 0 && dev < 64) g_moments_ready[dev] = true;
     return s;
 }
@@ -233,21 +250,17 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
     return v[0];
 }
 
-// One warp per probe; lane l owns cells l and l + 32.  With SURR, records whose bit is set in
+// Cell radiance of probe p's rays (one warp; lane l owns cells l and l + 32, ray k samples cell
+// k mod 64): L = per-cell mean of the rays that produced a sample, with the radiance backup (mean
+// over populated cells) where none did; with HITDIST also hd = the mean ray length of the cell's
+// rays that hit a surface (+inf when none did).  With SURR, records whose bit is set in
 // a.ovr_bits take their radiance from a.ovr (the surrogate's answers) instead of the cache.
-template <bool SURR = false>
-__device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t blk) {
-    const uint32_t p = (blk * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (p >= a.probes) return;
-    const float4 n4 = __ldg(a.nrm + p);
-    float *out = a.sh + (size_t)p * GI_SH_STRIDE;
-    if (n4.w == 0.0f) {
-        if (lane < GI_SH_STRIDE) out[lane] = 0.0f;
-        return;
-    }
+template <bool SURR, bool HITDIST>
+__device__ __forceinline__ void gather_cells(const IntegrateArgs &a, uint32_t p, int lane, float (&L)[2][3],
+                                             float (&hd)[2]) {
     float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     float cnt[2] = {0.f, 0.f};
+    float hs[2] = {0.f, 0.f}, hn[2] = {0.f, 0.f};
     const uint32_t *ids = a.slot_ids + (size_t)p * a.rpp;
     for (uint32_t k = lane; k < a.rpp; k += 64) {
         // rays k and k + 32 sample cells lane and lane + 32; both gathers in flight together
@@ -275,9 +288,15 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t 
         if (h1) {
             acc[1][0] += r1.x; acc[1][1] += r1.y; acc[1][2] += r1.z; cnt[1] += 1.0f;
         }
+        if (HITDIST) {
+            const size_t rec = (size_t)p * a.rpp + k;
+            const float l0 = __ldcs(a.ray_len + rec), l1 = __ldcs(a.ray_len + rec + 32);
+            if (h0 && isfinite(l0) && l0 >= 0.0f) { hs[0] += l0; hn[0] += 1.0f; }
+            if (h1 && isfinite(l1) && l1 >= 0.0f) { hs[1] += l1; hn[1] += 1.0f; }
+        }
     }
     // cell means, then the radiance backup: cells without sample take the mean of populated cells
-    float L[2][3], pop[4] = {0.f, 0.f, 0.f, 0.f};
+    float pop[4] = {0.f, 0.f, 0.f, 0.f};
     for (int h = 0; h < 2; ++h) {
         const float inv = cnt[h] > 0.f ? 1.0f / cnt[h] : 0.0f;
         for (int c = 0; c < 3; ++c) {
@@ -292,6 +311,12 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t 
     for (int h = 0; h < 2; ++h)
         if (cnt[h] == 0.f)
             for (int c = 0; c < 3; ++c) L[h][c] = pop[c] * binv;
+    for (int h = 0; h < 2; ++h) hd[h] = hn[h] > 0.f ? hs[h] / hn[h] : INFINITY;
+}
+
+// SH coefficients of the cell radiance L (lane l: cells l and l + 32) through the cells' exact
+// direction moments, rotated to world space by the probe frame of normal n4; lanes 0..27 write.
+__device__ __forceinline__ void project_cells(const float4 n4, int lane, const float (&L)[2][3], float *out) {
     // direction moments of the probe radiance (local frame): value 3 m + c = moment m, channel c
     float v[32];
 #pragma unroll
@@ -357,7 +382,57 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t 
     out[lane] = val;
 }
 
+// One warp per probe: gather then project (no intermediate atlas).
+template <bool SURR = false>
+__device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t blk) {
+    const uint32_t p = (blk * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= a.probes) return;
+    const float4 n4 = __ldg(a.nrm + p);
+    float *out = a.sh + (size_t)p * GI_SH_STRIDE;
+    if (n4.w == 0.0f) {
+        if (lane < GI_SH_STRIDE) out[lane] = 0.0f;
+        return;
+    }
+    float L[2][3], hd[2];
+    gather_cells<SURR, false>(a, p, lane, L, hd);
+    project_cells(n4, lane, L, out);
+}
+
 __global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) { integrate_body(a, blockIdx.x); }
+
+// Probe atlas: float4 per (probe, cell) = (mean radiance rgb, mean hit distance); zeros for no probe.
+__global__ void __launch_bounds__(256) k_gather(IntegrateArgs a, float4 *atlas) {
+    const uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= a.probes) return;
+    float4 *dst = atlas + (size_t)p * 64;
+    if (__ldg(a.nrm + p).w == 0.0f) {
+        dst[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        dst[lane + 32] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    float L[2][3], hd[2];
+    gather_cells<false, true>(a, p, lane, L, hd);
+    dst[lane] = make_float4(L[0][0], L[0][1], L[0][2], hd[0]);
+    dst[lane + 32] = make_float4(L[1][0], L[1][1], L[1][2], hd[1]);
+}
+
+// SH coefficients of every probe from its atlas (one warp per probe).
+__global__ void __launch_bounds__(256) k_project(const float4 *atlas, const float4 *nrm, float *sh, uint32_t probes) {
+    const uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= probes) return;
+    const float4 n4 = __ldg(nrm + p);
+    float *out = sh + (size_t)p * GI_SH_STRIDE;
+    if (n4.w == 0.0f) {
+        if (lane < GI_SH_STRIDE) out[lane] = 0.0f;
+        return;
+    }
+    const float4 c0 = __ldg(atlas + (size_t)p * 64 + lane), c1 = __ldg(atlas + (size_t)p * 64 + lane + 32);
+    const float L[2][3] = {{c0.x, c0.y, c0.z}, {c1.x, c1.y, c1.z}};
+    project_cells(n4, lane, L, out);
+}
 __global__ void __launch_bounds__(256) k_integrate_surr(IntegrateArgs a) { integrate_body<true>(a, blockIdx.x); }
 
 // ---------------------------------------------------------------- interpolation
@@ -612,6 +687,7 @@ IntegrateArgs integrate_args(gi_cache_t cache, const gi_probes *pr, const uint32
     for (int c = 0; c < 3; ++c) a.env[c] = env ? env[c] : 0.0f;
     a.ovr_bits = nullptr;
     a.ovr = nullptr;
+    a.ray_len = nullptr;
     return a;
 }
 
@@ -646,6 +722,119 @@ InterpArgs interp_args(const gi_gbuffer *gbuf, const gi_view *view, const gi_pro
     return a;
 }
 
+
+// ---------------------------------------------------------------- probe filtering (Algorithm 5)
+
+struct FilterArgs {
+    const float4 *in;
+    float4 *out;
+    const uint32_t *mask;
+    MipInfo mi;
+    const float4 *ppos;  // xyz, distance along the pixel ray
+    const float4 *pnrm;  // xyz, 1 = probe / 0 = none
+    uint32_t probes, tiles_x;
+    float dscale;        // Algorithm 6: cell_size(d) = dscale * d
+    int axis;            // 0: steps along x, 1: along y
+};
+
+// Algorithm 3 from level 0: the probe at (tx + ox, ty + oy), else up the MIP chain.
+__device__ __forceinline__ uint32_t find_probe_from_level0(const uint32_t *mask, const MipInfo &mi, int tx, int ty,
+                                                            int ox, int oy) {
+    const int x = tx + ox, y = ty + oy;
+    if (x < 0 || y < 0 || x >= mi.w[0] || y >= mi.h[0]) return GI_PROBE_NONE;
+    const uint32_t q = __ldg(mask + y * mi.w[0] + x);
+    if (q != GI_PROBE_NONE) return q;
+    return find_closest_probe(mask, mi, tx >> 1, ty >> 1, ox, oy, 1);
+}
+
+// One thread per (probe, cell), 4 probes per block (2 warps per probe): the cell's radiance and hit
+// distance blurred with the same cell of the probes found at steps -1, +1, -2, +2, -3, +3 along the
+// axis, each accepted when it lies within cell_size of the probe's plane, the cell direction is not
+// behind its normal, and the hit point seen from it (at the smaller hit distance) is within pi/50 of
+// the cell direction seen from the probe; depth weight 1 / (1 + |d_p - d_q| / cell_size(d_p)).
+// What is the same for all 64 cells of a probe -- the neighbour search, its offset from the probe,
+// the plane test and the depth weight -- lanes 0..5 of each warp compute once into shared memory;
+// every thread then issues its six neighbour loads together and takes the per-cell decisions in
+// step order (the running hit distance of one step enters the next).  The angle test avoids the
+// square root: cos(angle) >= c  <=>  d.h > 0 and (d.h)^2 >= c^2 |h|^2.
+constexpr int kFiltProbes = 4;
+__global__ void __launch_bounds__(64 * kFiltProbes) k_filter(FilterArgs a) {
+    __shared__ uint32_t s_qi[2 * kFiltProbes][6];
+    __shared__ float4 s_rel[2 * kFiltProbes][6];  // q - p (xyz), depth weight
+    __shared__ float4 s_nq[2 * kFiltProbes][6];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const uint32_t p = blockIdx.x * kFiltProbes + (t >> 6);
+    const uint32_t c = t & 63;
+    if (p >= a.probes) return;  // both warps of a probe leave together
+    const size_t self = (size_t)p * 64 + c;
+    const float4 v = __ldg(a.in + self);
+    const float4 n4 = __ldg(a.pnrm + p);
+    if (n4.w == 0.0f) {
+        a.out[self] = v;
+        return;
+    }
+    const float4 pp = __ldg(a.ppos + p);
+    const float cs = a.dscale * pp.w;
+    const float nx = n4.x, ny = n4.y, nz = n4.z;
+    if (lane < 6) {
+        const int step = (((lane & 1) << 1) - 1) * ((lane >> 1) + 1);
+        const int tx = (int)(p % a.tiles_x), ty = (int)(p / a.tiles_x);
+        const uint32_t q = find_probe_from_level0(a.mask, a.mi, tx, ty, a.axis == 0 ? step : 0, a.axis == 0 ? 0 : step);
+        uint32_t qi = GI_PROBE_NONE;
+        if (q != GI_PROBE_NONE) {
+            const uint32_t k = ((q >> 16) >> 3) * a.tiles_x + ((q & 0xFFFFu) >> 3);
+            const float4 pq = __ldg(a.ppos + k);
+            const float rx = pq.x - pp.x, ry = pq.y - pp.y, rz = pq.z - pp.z;
+            if (fabsf(rx * nx + ry * ny + rz * nz) <= cs) {  // the plane test
+                qi = k;
+                s_rel[warp][lane] = make_float4(rx, ry, rz, __fdividef(cs, cs + fabsf(pp.w - pq.w)));
+                s_nq[warp][lane] = __ldg(a.pnrm + k);
+            }
+        }
+        s_qi[warp][lane] = qi;
+    }
+    __syncwarp();
+    float4 vq[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const uint32_t qi = s_qi[warp][i];
+        vq[i] = qi != GI_PROBE_NONE ? __ldg(a.in + (size_t)qi * 64 + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // world direction of the cell centre in the probe frame (Duff et al. 2017)
+    const float sgn = copysignf(1.0f, nz);
+    const float ia = -1.0f / (sgn + nz);
+    const float bb = nx * ny * ia;
+    const float t0 = 1.0f + sgn * nx * nx * ia, t1 = sgn * bb, t2 = -sgn * nx;
+    const float b0 = bb, b1 = sgn + ny * ny * ia, b2 = -ny;
+    const float lx = c_cell_dir[c][0], ly = c_cell_dir[c][1], lz = c_cell_dir[c][2];
+    const float dx = lx * t0 + ly * b0 + lz * nx, dy = lx * t1 + ly * b1 + lz * ny, dz = lx * t2 + ly * b2 + lz * nz;
+    const float cos2 = c_filter_cos * c_filter_cos;
+    float r = v.x, gch = v.y, bch = v.z, acc_a = v.w, weight = 1.0f, hd = v.w;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        if (s_qi[warp][i] == GI_PROBE_NONE) continue;
+        const float4 nq = s_nq[warp][i];
+        if (dx * nq.x + dy * nq.y + dz * nq.z < 0.0f) continue;  // the cell points behind q
+        const float4 rel = s_rel[warp][i];
+        const float hdc = fminf(vq[i].w, hd);
+        if (isfinite(hdc)) {
+            const float hx = rel.x + dx * hdc, hy = rel.y + dy * hdc, hz = rel.z + dz * hdc;
+            const float hh = hx * hx + hy * hy + hz * hz;
+            const float dh = dx * hx + dy * hy + dz * hz;
+            // a zero vector counts as on the cell direction
+            if (hh > 0.0f && (dh <= 0.0f || dh * dh < cos2 * hh)) continue;
+        }
+        const float w = rel.w;
+        r += w * vq[i].x;
+        gch += w * vq[i].y;
+        bch += w * vq[i].z;
+        acc_a += w * hdc;
+        weight += w;
+        hd = __fdividef(acc_a, weight);
+    }
+    const float inv = __fdividef(1.0f, weight);
+    a.out[self] = make_float4(r * inv, gch * inv, bch * inv, acc_a * inv);
+}
 
 // ---------------------------------------------------------------- batched passes (many views)
 __global__ void __launch_bounds__(256) k_spawn_batched(const SpawnArgs *args, const uint32_t *prefix, uint32_t nviews) {
@@ -794,6 +983,68 @@ gi_status gi_probes_integrate_nrc(gi_cache_t cache, gi_nrc_t nrc, const gi_probe
     const unsigned blocks = (a.probes + 7) / 8;
     k_integrate_surr<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
     return cuda_status(cudaGetLastError(), "k_integrate_surr launch");
+}
+
+gi_status gi_probes_gather(gi_cache_t cache, const gi_probes *pr, const uint32_t *slot_ids, const float *ray_len,
+                           uint32_t rays_per_probe, const float env[3], float *atlas, gi_stream_t stream) {
+    gi_status s = integrate_check(cache, pr, slot_ids, rays_per_probe);
+    if (s != GI_OK) return s;
+    if ((!ray_len || !atlas) && pr->layout.num_probes > 0) {
+        set_error("gi_probes_gather: NULL ray_len or atlas");
+        return GI_ERR_INVALID_ARG;
+    }
+    if ((uintptr_t)atlas & 15) {
+        set_error("gi_probes_gather: atlas must be 16-byte aligned");
+        return GI_ERR_INVALID_ARG;
+    }
+    IntegrateArgs a = integrate_args(cache, pr, slot_ids, rays_per_probe, env);
+    if (a.probes == 0) return GI_OK;
+    a.ray_len = ray_len;
+    k_gather<<<(a.probes + 7) / 8, 256, 0, (cudaStream_t)stream>>>(a, reinterpret_cast<float4 *>(atlas));
+    return cuda_status(cudaGetLastError(), "k_gather launch");
+}
+
+gi_status gi_probes_filter(const gi_probes *pr, const gi_view *view, const float *atlas_in, float *atlas_out,
+                           uint32_t axis, gi_stream_t stream) {
+    if (!pr || !view_ok(view) || !pr->mask || !pr->pos || !pr->nrm || axis > 1 ||
+        ((!atlas_in || !atlas_out) && pr->layout.num_probes > 0) || atlas_in == atlas_out) {
+        set_error("gi_probes_filter: NULL argument, bad view or axis, or in-place atlas");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (((uintptr_t)atlas_in | (uintptr_t)atlas_out | (uintptr_t)pr->pos | (uintptr_t)pr->nrm) & 15) {
+        set_error("gi_probes_filter: atlases and probe buffers must be 16-byte aligned");
+        return GI_ERR_INVALID_ARG;
+    }
+    gi_status s = ensure_moments();
+    if (s != GI_OK) return s;
+    FilterArgs a;
+    a.in = reinterpret_cast<const float4 *>(atlas_in);
+    a.out = reinterpret_cast<float4 *>(atlas_out);
+    a.mask = pr->mask;
+    a.mi = mip_info(pr->layout);
+    a.ppos = reinterpret_cast<const float4 *>(pr->pos);
+    a.pnrm = reinterpret_cast<const float4 *>(pr->nrm);
+    a.probes = pr->layout.num_probes;
+    a.tiles_x = pr->layout.tiles_x;
+    a.dscale = (float)distance_scale(view->fov_y, view->width, view->height);
+    a.axis = (int)axis;
+    if (a.probes == 0) return GI_OK;
+    k_filter<<<(a.probes + kFiltProbes - 1) / kFiltProbes, 64 * kFiltProbes, 0, (cudaStream_t)stream>>>(a);
+    return cuda_status(cudaGetLastError(), "k_filter launch");
+}
+
+gi_status gi_probes_project(const gi_probes *pr, const float *atlas, gi_stream_t stream) {
+    if (!pr || !pr->nrm || !pr->sh || (!atlas && pr->layout.num_probes > 0) || ((uintptr_t)atlas & 15)) {
+        set_error("gi_probes_project: NULL argument or misaligned atlas");
+        return GI_ERR_INVALID_ARG;
+    }
+    gi_status s = ensure_moments();
+    if (s != GI_OK) return s;
+    const uint32_t P = pr->layout.num_probes;
+    if (P == 0) return GI_OK;
+    k_project<<<(P + 7) / 8, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float4 *>(atlas),
+                                                              reinterpret_cast<const float4 *>(pr->nrm), pr->sh, P);
+    return cuda_status(cudaGetLastError(), "k_project launch");
 }
 
 gi_status gi_probes_interpolate(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *pr, float *out,

@@ -7,9 +7,9 @@ from __future__ import annotations
 import torch
 
 from . import (GI_RESOLVED_F32, GI_SH_STRIDE, gi_batch_create, gi_batch_destroy, gi_batch_frame, gi_batch_view,
-               gi_cache_create, gi_cache_destroy, gi_cache_resolve, gi_cache_update, gi_probes_integrate,
-               gi_probes_interpolate, gi_probes_layout, gi_probes_spawn, hits_from_planes, make_gbuffer, make_probes,
-               make_view)
+               gi_cache_create, gi_cache_destroy, gi_cache_resolve, gi_cache_update, gi_probes_filter, gi_probes_gather,
+               gi_probes_integrate, gi_probes_interpolate, gi_probes_layout, gi_probes_project, gi_probes_spawn,
+               hits_from_planes, make_gbuffer, make_probes, make_view)
 
 
 def view_of(camera, frame: int):
@@ -51,6 +51,7 @@ class Pipeline:
         self.irr = torch.empty((height, width, 4), dtype=torch.float32, device=device)
         self.cache = gi_cache_create(log2_slots, cell_size, num_lods, alpha, evict_frames, max_probe, key_dir,
                                      resolved_format, rebuild_load, first_touch)
+        self.atlas = self.atlas_tmp = None
 
     def spawn(self, gbuf, view, stream=None):
         gi_probes_spawn(make_gbuffer(gbuf, self.width, self.height), view, self.probes.struct, stream)
@@ -63,6 +64,19 @@ class Pipeline:
 
     def integrate(self, env=(0.0, 0.0, 0.0), stream=None):
         gi_probes_integrate(self.cache, self.probes.struct, self.slot_ids, self.rpp, env, stream)
+
+    def integrate_filtered(self, records, view, env=(0.0, 0.0, 0.0), stream=None):
+        """Probe irradiance through the probe atlas with the separable filter (x pass, then y).
+        records: the (planes, R) record tensor of the frame (its ray-length plane is read)."""
+        if self.atlas is None:
+            P = self.probes.layout.num_probes
+            self.atlas = torch.empty((P, 64, 4), dtype=torch.float32, device=self.irr.device)
+            self.atlas_tmp = torch.empty_like(self.atlas)
+        ray_len = records[9]
+        gi_probes_gather(self.cache, self.probes.struct, self.slot_ids, ray_len, self.rpp, self.atlas, env, stream)
+        gi_probes_filter(self.probes.struct, view, self.atlas, self.atlas_tmp, 0, stream)
+        gi_probes_filter(self.probes.struct, view, self.atlas_tmp, self.atlas, 1, stream)
+        gi_probes_project(self.probes.struct, self.atlas, stream)
 
     def interpolate(self, gbuf, view, stream=None):
         gi_probes_interpolate(make_gbuffer(gbuf, self.width, self.height), view, self.probes.struct, self.irr,
