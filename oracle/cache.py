@@ -62,6 +62,10 @@ class OracleCache:
     def update(self, rec, frame: int, cam_pos, fov_y, width, height):
         """Accumulate one batch of records; returns the identity per record (0 where no hit)."""
         ident, hit = self.identities(rec, cam_pos, fov_y, width, height)
+        return self.accumulate(rec, ident, hit, frame)
+
+    def accumulate(self, rec, ident, hit, frame: int):
+        """Add the radiance of the hit records to the cells named by their identities."""
         q, bad = quantize_radiance(rec[6:9])
         self.clamped += int((bad & hit).sum())
         ids = ident[hit]
