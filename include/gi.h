@@ -90,6 +90,18 @@ typedef void *gi_stream_t; /* cudaStream_t */
  *                   resolve: fewer DRAM bursts when the table exceeds the L2), or
  *                   GI_FIRST_TOUCH_AUTO (the bitmap when the 32-byte accumulators of all
  *                   slots exceed the device's L2, else the list).  Results are identical.
+ *   tiles           0: a slot holds one cell.  1: two-level cache of Section 2.2.3 ("Prefiltering
+ *                   Radiance"): a slot holds a tile of 8 x 8 cells on the plane that drops the
+ *                   direction code's axis (in-plane cell coordinates floor-divided by 8 form the
+ *                   tile descriptor, their remainders (u mod 8) + 8 (v mod 8) the cell), plus
+ *                   box-filtered MIP levels 4x4, 2x2 and 1x1 rebuilt at every resolve that
+ *                   touches the tile.  log2_slots then counts tiles (10..22); slot ids are
+ *                   tile slot * 64 + cell; first_touch must be AUTO (tiles use a list).
+ *   min_samples     tiles only, >= 1: a cell answers queries from the finest of its levels
+ *                   (the cell, then its 4x4, 2x2 and 1x1 ancestors) whose sample count reaches
+ *                   min_samples, else from the 1x1 level.  The sample count of a cell is the
+ *                   number of samples blended into it since it last started without history;
+ *                   a MIP value averages its children that hold a value and sums their counts.
  */
 typedef struct gi_cache_config {
     uint32_t log2_slots;
@@ -102,6 +114,8 @@ typedef struct gi_cache_config {
     uint32_t resolved_format;
     float rebuild_load;
     uint32_t first_touch;
+    uint32_t tiles;
+    uint32_t min_samples;
 } gi_cache_config;
 
 /*
@@ -171,12 +185,13 @@ typedef struct gi_probes {
     float *sh;
 } gi_probes;
 
-/* Cumulative counters and table state (gi_cache_stats). */
+/* Cumulative counters and table state (gi_cache_stats).  In a tile cache slots, occupied and
+ * touched count tiles, live counts cells. */
 typedef struct gi_cache_stats_t {
     uint64_t slots;           /* N */
-    uint64_t occupied;        /* slots holding a cell, live or stale */
+    uint64_t occupied;        /* slots holding a cell (tile), live or stale */
     uint64_t live;            /* cells not evicted as of the last resolve, plus cells touched since */
-    uint64_t touched;         /* cells touched since the last resolve */
+    uint64_t touched;         /* cells (tiles) touched since the last resolve */
     uint64_t dropped;         /* hits that found no slot within max_probe (cumulative) */
     uint64_t clamped;         /* hit records whose radiance was clamped to [0, 32768] or was NaN */
     uint64_t rebuilds;        /* table compactions so far */
@@ -186,7 +201,9 @@ typedef struct gi_cache_stats_t {
     int64_t last_resolved;    /* frame of the last resolve, -1 before the first */
 } gi_cache_stats_t;
 
-/* One live cell, as exported by gi_cache_export (host memory). */
+/* One live cell, as exported by gi_cache_export (host memory).  In a tile cache the identity is
+ * (tile's home slot << 24 | tile fingerprint) << 6 | cell, value is the cell's own blended
+ * radiance (level 0) and slot is tile slot * 64 + cell. */
 typedef struct gi_cell {
     uint64_t identity;  /* home slot << 24 | 24-bit fingerprint */
     uint64_t sum[3];    /* fixed-point sums accumulated since the last resolve (2^-24 units) */
@@ -195,6 +212,20 @@ typedef struct gi_cell {
     float value[3];     /* resolved radiance */
     uint32_t slot;      /* current slot index (changes when the table is compacted) */
 } gi_cell;
+
+/* One tile of a tile cache with at least one live cell, as exported by gi_cache_export_tiles
+ * (host memory).  Values 0..63 are the cells (level 0, cell (i, j) at i + 8 j), 64..79 the 4x4
+ * level, 80..83 the 2x2 level, 84 the 1x1 level; level k + 1 value (i, j) covers level-k values
+ * (2i + di, 2j + dj).  samples = 0 marks a value that holds nothing (a cell not live, a MIP value
+ * without live cell below it).  Levels 1..3 are those of the last resolve that touched the tile. */
+#define GI_TILE_VALUES 85
+typedef struct gi_tile {
+    uint64_t identity;                 /* home slot << 24 | 24-bit fingerprint of the tile */
+    uint32_t slot;                     /* tile slot */
+    uint32_t live;                     /* live cells */
+    float value[GI_TILE_VALUES][3];
+    uint32_t samples[GI_TILE_VALUES];
+} gi_tile;
 
 /* ---------------------------------------------------------------- errors */
 /* Message of the last failed call on this host thread ("" if none). */
@@ -242,7 +273,10 @@ gi_status gi_cache_update(gi_cache_t cache, const gi_hits *hits, const gi_view *
  * v <- v + alpha (m - v); accumulators are cleared and the cell's stamp set to
  * this frame.  Cells whose last touch is E or more frames before `frame` are
  * evicted (they stay in the table until the next compaction but no longer
- * answer queries, and restart without history if hit again).
+ * answer queries, and restart without history if hit again).  A tile cache
+ * then rebuilds the MIP levels of every tile touched since the last resolve
+ * and stores, for each of its live cells, the value of the level that answers
+ * it (see min_samples): the resolved radiance that queries by slot return.
  * Errors: GI_ERR_INVALID_ARG (frame earlier than the previous resolve), GI_ERR_CUDA.
  */
 gi_status gi_cache_resolve(gi_cache_t cache, uint32_t frame, gi_stream_t stream);
@@ -277,6 +311,14 @@ gi_status gi_cache_stats(gi_cache_t cache, gi_cache_stats_t *out, gi_stream_t st
  * out may be NULL with capacity 0 to ask for the count.
  */
 gi_status gi_cache_export(gi_cache_t cache, gi_cell *out, uint64_t capacity, uint64_t *count, gi_stream_t stream);
+
+/*
+ * Tile caches: copy every tile holding a live cell, with its levels, to host memory, sorted by
+ * identity.  Synchronises `stream`.  Count and capacity as for gi_cache_export.
+ * Errors: GI_ERR_INVALID_ARG (not a tile cache, NULL argument), GI_ERR_CAPACITY, GI_ERR_CUDA.
+ */
+gi_status gi_cache_export_tiles(gi_cache_t cache, gi_tile *out, uint64_t capacity, uint64_t *count,
+                                gi_stream_t stream);
 
 /* ---------------------------------------------------------------- screen probes */
 /* Probe buffer sizes of a width x height view (host only, no device access). */
@@ -373,7 +415,8 @@ typedef struct gi_batch_tuning {
 } gi_batch_tuning;
 
 /* One view of a frame.  All pointers are device pointers owned by the caller; hits.n must equal
- * probes.layout.num_probes * rays_per_probe; every cache of a batch uses the same key_dir. */
+ * probes.layout.num_probes * rays_per_probe; every cache of a batch uses the same key_dir and
+ * holds cells, not tiles. */
 typedef struct gi_batch_view {
     gi_cache_t cache;
     gi_view view;            /* view.frame drives the spawn jitter */

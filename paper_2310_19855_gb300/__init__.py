@@ -44,7 +44,7 @@ c_u32, c_u64, c_f32, c_f64, c_vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_fl
 class gi_cache_config(ctypes.Structure):
     _fields_ = [("log2_slots", c_u32), ("cell_size", c_f32), ("num_lods", c_u32), ("alpha", c_f32),
                 ("evict_frames", c_u32), ("max_probe", c_u32), ("key_dir", c_u32), ("resolved_format", c_u32),
-                ("rebuild_load", c_f32), ("first_touch", c_u32)]
+                ("rebuild_load", c_f32), ("first_touch", c_u32), ("tiles", c_u32), ("min_samples", c_u32)]
 
 
 class gi_view(ctypes.Structure):
@@ -82,6 +82,14 @@ class gi_cell(ctypes.Structure):
                 ("slot", c_u32)]
 
 
+GI_TILE_VALUES = 85
+
+
+class gi_tile(ctypes.Structure):
+    _fields_ = [("identity", c_u64), ("slot", c_u32), ("live", c_u32), ("value", c_f32 * (3 * GI_TILE_VALUES)),
+                ("samples", c_u32 * GI_TILE_VALUES)]
+
+
 class gi_query(ctypes.Structure):
     _fields_ = [("slot_ids", c_vp), ("points", ctypes.POINTER(gi_hits)), ("view", ctypes.POINTER(gi_view)),
                 ("n", c_u64), ("env", c_f32 * 3)]
@@ -116,6 +124,9 @@ class gi_nrc_stats_t(ctypes.Structure):
 CELL_DTYPE = np.dtype([("identity", "<u8"), ("sum", "<u8", (3,)), ("count", "<u4"), ("stamp", "<u4"),
                        ("value", "<f4", (3,)), ("slot", "<u4")])
 assert CELL_DTYPE.itemsize == ctypes.sizeof(gi_cell)
+TILE_DTYPE = np.dtype([("identity", "<u8"), ("slot", "<u4"), ("live", "<u4"), ("value", "<f4", (GI_TILE_VALUES, 3)),
+                       ("samples", "<u4", (GI_TILE_VALUES,))])
+assert TILE_DTYPE.itemsize == ctypes.sizeof(gi_tile)
 
 # ---------------------------------------------------------------- library
 _LIB = None
@@ -145,6 +156,7 @@ def lib() -> ctypes.CDLL:
             "gi_cache_query": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_query), c_vp, c_vp]),
             "gi_cache_stats": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_cache_stats_t), c_vp]),
             "gi_cache_export": (ctypes.c_int, [c_vp, c_vp, c_u64, ctypes.POINTER(c_u64), c_vp]),
+            "gi_cache_export_tiles": (ctypes.c_int, [c_vp, c_vp, c_u64, ctypes.POINTER(c_u64), c_vp]),
             "gi_probes_layout": (ctypes.c_int, [c_u32, c_u32, ctypes.POINTER(gi_probe_layout)]),
             "gi_probes_spawn": (ctypes.c_int, [ctypes.POINTER(gi_gbuffer), ctypes.POINTER(gi_view),
                                                ctypes.POINTER(gi_probes), c_vp]),
@@ -267,9 +279,10 @@ def gi_cell_moments() -> np.ndarray:
 def gi_cache_create(log2_slots: int, cell_size: float = 0.05, num_lods: int = 4, alpha: float = 0.1,
                     evict_frames: int = 8, max_probe: int = 128, key_dir: int = GI_KEY_DIR_NORMAL,
                     resolved_format: int = GI_RESOLVED_F32, rebuild_load: float = 0.8,
-                    first_touch: int = GI_FIRST_TOUCH_AUTO) -> int:
+                    first_touch: int = GI_FIRST_TOUCH_AUTO, tiles: bool = False, min_samples: int = 16) -> int:
+    """tiles=True: two-level cache (8 x 8 cell tiles with MIP levels); log2_slots then counts tiles."""
     cfg = gi_cache_config(log2_slots, cell_size, num_lods, alpha, evict_frames, max_probe, key_dir,
-                          resolved_format, rebuild_load, first_touch)
+                          resolved_format, rebuild_load, first_touch, 1 if tiles else 0, min_samples)
     h = c_vp()
     check(lib().gi_cache_create(ctypes.byref(cfg), ctypes.byref(h)), "gi_cache_create")
     return h.value
@@ -318,6 +331,16 @@ def gi_cache_export(cache: int, stream=None) -> np.ndarray:
     if cnt.value:
         check(lib().gi_cache_export(cache, out.ctypes.data, cnt.value, ctypes.byref(cnt), _stream(stream)),
               "gi_cache_export")
+    return out
+
+
+def gi_cache_export_tiles(cache: int, stream=None) -> np.ndarray:
+    cnt = c_u64(0)
+    check(lib().gi_cache_export_tiles(cache, None, 0, ctypes.byref(cnt), _stream(stream)), "gi_cache_export_tiles")
+    out = np.zeros(cnt.value, TILE_DTYPE)
+    if cnt.value:
+        check(lib().gi_cache_export_tiles(cache, out.ctypes.data, cnt.value, ctypes.byref(cnt), _stream(stream)),
+              "gi_cache_export_tiles")
     return out
 
 

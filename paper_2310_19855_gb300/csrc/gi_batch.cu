@@ -90,6 +90,10 @@ static gi_status check_view(const gi_batch_view &v, uint32_t rpp, int key_dir) {
         set_error("gi_batch_frame: a view has no cache");
         return GI_ERR_INVALID_ARG;
     }
+    if (cache_tiled(v.cache)) {
+        set_error("gi_batch_frame: tile caches run through the single-view calls");
+        return GI_ERR_INVALID_ARG;
+    }
     if (cache_key_dir(v.cache) != key_dir) {
         set_error("gi_batch_frame: every cache of a batch must use the same direction descriptor");
         return GI_ERR_INVALID_ARG;

@@ -26,83 +26,11 @@
 #include <mutex>
 #include <vector>
 
-#include "gi_internal.cuh"
+#include "gi_cache_dev.cuh"
 
 namespace gi {
 
-// ---------------------------------------------------------------- hashing
-// xxHash32 of a single 4-byte word with a seed (xxHash specification).
-__device__ __forceinline__ uint32_t xxh32_word(uint32_t w, uint32_t seed) {
-    uint32_t h = seed + 0x165667B1u + 4u;
-    h += w * 0xC2B2AE3Du;
-    h = __funnelshift_l(h, h, 17) * 0x27D4EB2Fu;
-    h ^= h >> 15;
-    h *= 0x85EBCA77u;
-    h ^= h >> 13;
-    h *= 0xC2B2AE3Du;
-    h ^= h >> 16;
-    return h;
-}
-
-// Bucket ("home" slot) from the first hash, 24-bit fingerprint from the second.
-__device__ __forceinline__ void cell_of_key(unsigned long long key, uint32_t mask, uint32_t &home,
-                                            uint32_t &tag) {
-    uint32_t lo = (uint32_t)key, hi = (uint32_t)(key >> 32);
-    home = pcg_hash(lo ^ pcg_hash(hi)) & mask;
-    uint32_t fp = xxh32_word(lo, xxh32_word(hi, 0u)) >> 8;
-    fp = fp ? fp : 1u;
-    tag = (fp << 8) | (home & 0xFFu);
-}
-
-__device__ __forceinline__ float pick4(const float (&a)[4], int i) {
-    return i == 0 ? a[0] : (i == 1 ? a[1] : (i == 2 ? a[2] : a[3]));
-}
-
-// Cell descriptor (Sections 2.2.1-2.2.2): LOD from the float32 squared camera
-// distance against the Algorithm-6 thresholds, position quantised with
-// floor(p * (1/s_l)) wrapped to 19 bits, dominant-axis direction code (ties
-// x > y > z, sign bit decides), leak bit ray_len < s_l.  Every float op is an
-// explicit round-to-nearest intrinsic so that no contraction changes a bit.
-// `flip` = 1 when the direction source is the probe ray (outgoing = -ray).
-__device__ __forceinline__ unsigned long long cell_key(const KeyParams &k, float px, float py, float pz, float sx,
-                                                       float sy, float sz, float len, uint32_t flip) {
-    const int lod = key_lod(k, px, py, pz);
-    float inv = pick4(k.inv_side, lod);
-    float side = pick4(k.side, lod);
-    uint32_t qx = (uint32_t)__float2int_rd(__fmul_rn(px, inv)) & kQMask;
-    uint32_t qy = (uint32_t)__float2int_rd(__fmul_rn(py, inv)) & kQMask;
-    uint32_t qz = (uint32_t)__float2int_rd(__fmul_rn(pz, inv)) & kQMask;
-    unsigned long long leak = (len < side) ? 1ull : 0ull;
-    float ax = fabsf(sx), ay = fabsf(sy), az = fabsf(sz);
-    int axis = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
-    float comp = axis == 0 ? sx : (axis == 1 ? sy : sz);
-    uint32_t sgn = (__float_as_uint(comp) >> 31) ^ flip;
-    unsigned long long code = (unsigned long long)(2 * axis + (int)sgn);
-    return ((unsigned long long)lod << 61) | (leak << 60) | (code << 57) | ((unsigned long long)qx << 38) |
-           ((unsigned long long)qy << 19) | (unsigned long long)qz;
-}
-
-__device__ __forceinline__ bool isfinite3(float a, float b, float c) {
-    return isfinite(a) && isfinite(b) && isfinite(c);
-}
-
-// Fixed point of one channel: round-half-even(clamp(r, 0, 32768) * 2^24); NaN -> 0.
-__device__ __forceinline__ unsigned long long quantize(float r, uint32_t &bad) {
-    bad |= (r >= 0.0f && r <= kRadMax) ? 0u : 1u;
-    float c = fminf(fmaxf(r, 0.0f), kRadMax);
-    return __float2ull_rn(__fmul_rn(c, 16777216.0f));
-}
-
 // ---------------------------------------------------------------- update
-// A block takes at most kUpdBlockRecords records (one grid-strided chunk per iteration), so its
-// shared-memory list of first touches can never overflow and is flushed once, at the end, with
-// one global atomic: warps never wait for one another inside the loop.
-constexpr int kUpdThreads = 256;
-constexpr int kUpdBlockRecords = 2048;
-constexpr unsigned kFull = 0xFFFFFFFFu;
-
-
-
 // The count's returning add detects the first touch of a cell this frame.  With a.bitmap that
 // touch sets the slot's bit (a non-returning atomicOr); without, it goes to the block's
 // shared-memory list and then, once per block, to the touch list.
@@ -246,35 +174,7 @@ static inline int update_blocks(unsigned long long n) {
 }
 
 // ---------------------------------------------------------------- resolve
-constexpr int kResThreads = 256;
 
-
-__device__ __forceinline__ float3 load_resolved(const void *r, uint32_t stride, int f16, uint32_t s) {
-    r = static_cast<const char *>(r) + (size_t)s * stride;
-    if (f16) {
-        const ushort4 h = *reinterpret_cast<const ushort4 *>(r);
-        return make_float3(__half2float(__ushort_as_half(h.x)), __half2float(__ushort_as_half(h.y)),
-                           __half2float(__ushort_as_half(h.z)));
-    }
-    const float4 v = *reinterpret_cast<const float4 *>(r);
-    return make_float3(v.x, v.y, v.z);
-}
-
-// The 4th lane marks a cell resolved without history (its first resolve, or its first since an
-// eviction): 1 for such a cell, 0 otherwise.  The surrogate reads it to find cold cells.
-__device__ __forceinline__ void store_resolved(void *r, uint32_t stride, int f16, uint32_t s, float3 v, bool cold) {
-    r = static_cast<char *>(r) + (size_t)s * stride;
-    if (f16) {
-        ushort4 h;
-        h.x = __half_as_ushort(__float2half_rn(v.x));
-        h.y = __half_as_ushort(__float2half_rn(v.y));
-        h.z = __half_as_ushort(__float2half_rn(v.z));
-        h.w = cold ? (unsigned short)0x3C00u : (unsigned short)0u;
-        *reinterpret_cast<ushort4 *>(r) = h;
-    } else {
-        *reinterpret_cast<float4 *>(r) = make_float4(v.x, v.y, v.z, cold ? 1.0f : 0.0f);
-    }
-}
 
 constexpr int kResUnroll = 4;
 
@@ -324,35 +224,6 @@ __device__ __forceinline__ void resolve_slots(const ResolveArgs &a, const uint32
     }
 }
 
-// Block totals of newly occupied slots, then the last block (ticket) publishes the occupancy.
-__device__ __forceinline__ void resolve_finish(const ResolveArgs &a, uint32_t nblk, uint32_t fresh_new) {
-    __shared__ uint32_t s_new;
-    __shared__ bool s_last;
-    if (threadIdx.x == 0) s_new = 0;
-    __syncthreads();
-    fresh_new = __reduce_add_sync(kFull, fresh_new);
-    if ((threadIdx.x & 31) == 0 && fresh_new) atomicAdd(&s_new, fresh_new);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_new) atomicAdd(&a.ctr->occupied, s_new);
-        __threadfence();
-        const uint32_t t = atomicAdd(&a.ctr->ticket, 1u);
-        s_last = (t == nblk - 1u);
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        // every block has read the touch count: reset it for the next frame
-        a.ctr->touch_count = 0u;
-        a.ctr->ticket = 0u;
-        // occupancy for the host's compaction decision, then the frame it belongs to
-        if (a.occ_out) {
-            reinterpret_cast<volatile uint32_t *>(a.occ_out)[0] = atomicAdd(&a.ctr->occupied, 0u);
-            __threadfence_system();
-            reinterpret_cast<volatile uint32_t *>(a.occ_out)[1] = a.stamp_now;
-        }
-    }
-}
-
 // touch-list form: kResUnroll list entries per thread and iteration
 __device__ __forceinline__ void resolve_list_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
     const uint32_t n = __ldcg(&a.ctr->touch_count);
@@ -367,7 +238,7 @@ __device__ __forceinline__ void resolve_list_body(const ResolveArgs &a, uint32_t
         }
         resolve_slots(a, s, fresh_new);
     }
-    resolve_finish(a, nblk, fresh_new);
+    resolve_finish(a.ctr, a.occ_out, a.stamp_now, nblk, fresh_new);
 }
 
 // bitmap form: a thread takes a word (32 consecutive slots), clears it and resolves its set bits
@@ -389,7 +260,7 @@ __device__ __forceinline__ void resolve_bm_body(const ResolveArgs &a, uint32_t b
             resolve_slots(a, s, fresh_new);
         }
     }
-    resolve_finish(a, nblk, fresh_new);
+    resolve_finish(a.ctr, a.occ_out, a.stamp_now, nblk, fresh_new);
 }
 
 __device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
@@ -400,11 +271,6 @@ __device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk,
 __global__ void __launch_bounds__(kResThreads, 3) k_resolve(ResolveArgs a) { resolve_body(a, blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------- queries
-
-// a cell answers queries once resolved, until it is evicted
-__device__ __forceinline__ bool answers(uint32_t stamp, const LiveRule &r) {
-    return stamp != 0u && (!r.has_lr || (r.lr - (stamp - 1u)) < r.evict);
-}
 
 __global__ void k_query_slots(const uint32_t *slot_ids, unsigned long long n, const void *resolved, uint32_t res_stride, int f16,
                               uint32_t slots, float e0, float e1, float e2, float4 *out) {
@@ -580,6 +446,13 @@ struct gi_cache_s {
     void *resolved[2];
     uint32_t res_bytes;  // 16 (float4) or 8 (half4)
     int cur;
+    bool tiles;                  // two-level cache: a slot holds a tile of 64 cells
+    uint32_t cells;              // addressable cells: N, or 64 N for tiles
+    uint32_t *stamp[2];          // tiles: per-cell stamps, state, MIP values (gi_tiles.cu)
+    float4 *state[2];
+    float4 *mips[2];
+    unsigned long long *tmask;   // tiles: cells touched since the last resolve
+    int tres_blocks;
     uint32_t *touch;
     uint32_t *bitmap;            // touched slots since the last resolve, one bit each
     gi::Counters *ctr;
@@ -599,8 +472,19 @@ CacheView cache_view(gi_cache_t c) {
     v.resolved = c->resolved[c->cur];
     v.resolved_stride = c->res_bytes;
     v.resolved_f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
-    v.slots = c->N;
+    v.slots = c->cells;
     return v;
+}
+
+static TileArrays tile_arrays(const gi_cache_s *c, int k) {
+    TileArrays t;
+    t.tags = c->tags[k];
+    t.accum = c->accum[k];
+    t.stamp = c->stamp[k];
+    t.state = c->state[k];
+    t.resolved = c->resolved[k];
+    t.mips = c->mips[k];
+    return t;
 }
 
 static LiveRule live_rule(const gi_cache_s *c) {
@@ -623,6 +507,9 @@ static bool config_ok(const gi_cache_config *c) {
     if (c->resolved_format != GI_RESOLVED_F32 && c->resolved_format != GI_RESOLVED_F16) return false;
     if (!(c->rebuild_load >= 0.25f && c->rebuild_load <= 0.95f)) return false;
     if (c->first_touch > GI_FIRST_TOUCH_BITMAP) return false;
+    if (c->tiles > 1) return false;
+    if (c->tiles && (c->log2_slots > 22 || c->first_touch != GI_FIRST_TOUCH_AUTO || c->min_samples < 1))
+        return false;
     return true;
 }
 
@@ -672,6 +559,14 @@ static gi_status maybe_rebuild(gi_cache_s *c, cudaStream_t st) {
     const int nxt = c->cur ^ 1;
     gi_status s = cuda_status(cudaMemsetAsync(&c->ctr->occupied, 0, sizeof(uint32_t), st), "rebuild memset");
     if (s != GI_OK) return s;
+    if (c->tiles) {
+        s = tile_rebuild_launch(tile_arrays(c, c->cur), tile_arrays(c, nxt), c->tmask, c->res_bytes, c->mask,
+                                c->cfg.max_probe, live_rule(c), c->ctr, c->sms * 8, st);
+        if (s != GI_OK) return s;
+        c->cur = nxt;
+        c->rebuilds++;
+        return GI_OK;
+    }
     k_rebuild<<<c->sms * 8, 256, 0, st>>>(c->tags[c->cur], c->accum[c->cur], c->resolved[c->cur], c->tags[nxt],
                                            c->accum[nxt], c->resolved[nxt], c->res_bytes, c->mask, c->cfg.max_probe,
                                            live_rule(c), c->ctr);
@@ -717,6 +612,7 @@ gi_status cache_before_update(gi_cache_s *c, cudaStream_t st) {
 
 void cache_after_update(gi_cache_s *c) { c->touched_since_resolve = true; }
 int cache_key_dir(const gi_cache_s *c) { return (int)c->cfg.key_dir; }
+bool cache_tiled(const gi_cache_s *c) { return c->tiles; }
 int cache_device(const gi_cache_s *c) { return c->device; }
 int64_t cache_last_resolved(const gi_cache_s *c) { return c->last_resolved; }
 
@@ -725,13 +621,65 @@ static void free_cache(gi_cache_s *c) {
         cudaFree(c->tags[k]);
         cudaFree(c->accum[k]);
         cudaFree(c->resolved[k]);
+        cudaFree(c->stamp[k]);
+        cudaFree(c->state[k]);
+        cudaFree(c->mips[k]);
     }
+    cudaFree(c->tmask);
     cudaFree(c->touch);
     cudaFree(c->bitmap);
     cudaFree(c->ctr);
     cudaFree(c->scan);
     if (c->occ_host) cudaFreeHost((void *)c->occ_host);
     delete c;
+}
+
+// Host copies of a tile table (export).
+struct TileHost {
+    std::vector<SlotWord> tags;
+    std::vector<Accum> accum;
+    std::vector<uint32_t> stamp;
+    std::vector<float4> state;
+    std::vector<float4> mips;
+};
+
+static gi_status copy_tiles(const gi_cache_s *c, cudaStream_t st, TileHost &h, bool mips) {
+    const size_t N = c->N, E = c->cells;
+    h.tags.resize(N);
+    h.accum.resize(E);
+    h.stamp.resize(E);
+    h.state.resize(E);
+    gi_status s = cuda_status(cudaStreamSynchronize(st), "export sync");
+    const int k = c->cur;
+    if (s == GI_OK) s = cuda_status(cudaMemcpy(h.tags.data(), c->tags[k], N * sizeof(SlotWord), cudaMemcpyDeviceToHost), "export");
+    if (s == GI_OK) s = cuda_status(cudaMemcpy(h.accum.data(), c->accum[k], E * sizeof(Accum), cudaMemcpyDeviceToHost), "export");
+    if (s == GI_OK) s = cuda_status(cudaMemcpy(h.stamp.data(), c->stamp[k], E * sizeof(uint32_t), cudaMemcpyDeviceToHost), "export");
+    if (s == GI_OK) s = cuda_status(cudaMemcpy(h.state.data(), c->state[k], E * sizeof(float4), cudaMemcpyDeviceToHost), "export");
+    if (s == GI_OK && mips) {
+        h.mips.resize(N * kTileMips);
+        s = cuda_status(cudaMemcpy(h.mips.data(), c->mips[k], N * kTileMips * sizeof(float4), cudaMemcpyDeviceToHost),
+                        "export");
+    }
+    return s;
+}
+
+static bool host_answers(uint32_t stamp, const LiveRule &r) {
+    return stamp != 0u && (!r.has_lr || (r.lr - (stamp - 1u)) < r.evict);
+}
+
+static gi_status export_sorted(std::vector<gi_cell> &cells, gi_cell *out, uint64_t capacity, uint64_t *count,
+                               const char *who) {
+    std::sort(cells.begin(), cells.end(), [](const gi_cell &x, const gi_cell &y) { return x.identity < y.identity; });
+    *count = cells.size();
+    if (cells.size() > capacity) {
+        if (capacity > 0) {
+            set_error("%s: %zu live cells exceed capacity %llu", who, cells.size(), (unsigned long long)capacity);
+            return GI_ERR_CAPACITY;
+        }
+        return GI_OK;
+    }
+    if (!cells.empty()) memcpy(out, cells.data(), cells.size() * sizeof(gi_cell));
+    return GI_OK;
 }
 
 } // namespace gi
@@ -755,25 +703,39 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
     c->cfg = *cfg;
     c->N = 1u << cfg->log2_slots;
     c->mask = c->N - 1u;
+    c->tiles = cfg->tiles != 0;
+    c->cells = c->tiles ? c->N * (uint32_t)kTileCells : c->N;
     c->last_resolved = -1;
     c->res_bytes = cfg->resolved_format == GI_RESOLVED_F16 ? 8u : 16u;
     gi_status s = cuda_status(cudaGetDevice(&c->device), "cudaGetDevice");
     if (s == GI_OK) s = cuda_status(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device), "sm count");
-    const size_t N = c->N;
+    const size_t N = c->N, E = c->cells;
     for (int k = 0; k < 2 && s == GI_OK; ++k) {
         s = cuda_status(cudaMalloc(&c->tags[k], N * sizeof(SlotWord)), "cudaMalloc tags");
-        if (s == GI_OK) s = cuda_status(cudaMalloc(&c->accum[k], N * sizeof(Accum)), "cudaMalloc accum");
-        if (s == GI_OK) s = cuda_status(cudaMalloc(&c->resolved[k], N * c->res_bytes), "cudaMalloc resolved");
+        if (s == GI_OK) s = cuda_status(cudaMalloc(&c->accum[k], E * sizeof(Accum)), "cudaMalloc accum");
+        if (s == GI_OK) s = cuda_status(cudaMalloc(&c->resolved[k], E * c->res_bytes), "cudaMalloc resolved");
         if (s == GI_OK) s = cuda_status(cudaMemset(c->tags[k], 0, N * sizeof(SlotWord)), "memset");
-        if (s == GI_OK) s = cuda_status(cudaMemset(c->accum[k], 0, N * sizeof(Accum)), "memset");
-        if (s == GI_OK) s = cuda_status(cudaMemset(c->resolved[k], 0, N * c->res_bytes), "memset");
+        if (s == GI_OK) s = cuda_status(cudaMemset(c->accum[k], 0, E * sizeof(Accum)), "memset");
+        if (s == GI_OK) s = cuda_status(cudaMemset(c->resolved[k], 0, E * c->res_bytes), "memset");
+        if (s == GI_OK && c->tiles) {
+            s = cuda_status(cudaMalloc(&c->stamp[k], E * sizeof(uint32_t)), "cudaMalloc stamps");
+            if (s == GI_OK) s = cuda_status(cudaMalloc(&c->state[k], E * sizeof(float4)), "cudaMalloc state");
+            if (s == GI_OK) s = cuda_status(cudaMalloc(&c->mips[k], N * kTileMips * sizeof(float4)), "cudaMalloc mips");
+            if (s == GI_OK) s = cuda_status(cudaMemset(c->stamp[k], 0, E * sizeof(uint32_t)), "memset");
+            if (s == GI_OK) s = cuda_status(cudaMemset(c->state[k], 0, E * sizeof(float4)), "memset");
+            if (s == GI_OK) s = cuda_status(cudaMemset(c->mips[k], 0, N * kTileMips * sizeof(float4)), "memset");
+        }
     }
     // First touches: a slot bitmap walked in slot order by the resolve when the accumulators
     // exceed L2 (its ordered accesses then save DRAM traffic), else a touch list (cheaper updates).
     int l2 = 0;
     if (s == GI_OK) s = cuda_status(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device), "L2 size");
-    const bool use_bitmap = cfg->first_touch == GI_FIRST_TOUCH_BITMAP ||
-                            (cfg->first_touch == GI_FIRST_TOUCH_AUTO && N * sizeof(Accum) > (size_t)l2);
+    const bool use_bitmap = !c->tiles && (cfg->first_touch == GI_FIRST_TOUCH_BITMAP ||
+                                          (cfg->first_touch == GI_FIRST_TOUCH_AUTO && N * sizeof(Accum) > (size_t)l2));
+    if (s == GI_OK && c->tiles) {
+        s = cuda_status(cudaMalloc(&c->tmask, N * sizeof(unsigned long long)), "cudaMalloc tile masks");
+        if (s == GI_OK) s = cuda_status(cudaMemset(c->tmask, 0, N * sizeof(unsigned long long)), "memset");
+    }
     if (s == GI_OK && use_bitmap) {
         s = cuda_status(cudaMalloc(&c->bitmap, N / 8), "cudaMalloc bitmap");
         if (s == GI_OK) s = cuda_status(cudaMemset(c->bitmap, 0, N / 8), "memset");
@@ -799,6 +761,7 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
                         "occupancy");
         c->upd_blocks = c->sms * std::max(per_sm, 1);
         c->res_blocks = c->sms * 3;
+        c->tres_blocks = c->sms * tile_resolve_blocks_per_sm();
     }
     if (s == GI_OK) s = cuda_status(cudaDeviceSynchronize(), "create sync");
     if (s != GI_OK) {
@@ -840,6 +803,14 @@ gi_status gi_cache_update(gi_cache_t c, const gi_hits *hits, const gi_view *view
     c->updates++;
     if (hits->n == 0) return GI_OK;
     UpdateArgs a = cache_update_args(c, hits, view, slot_ids);
+    if (c->tiles) {
+        TileUpdateArgs ta;
+        ta.u = a;
+        ta.tmask = c->tmask;
+        s = tile_update_launch(ta, (int)c->cfg.key_dir, st);
+        if (s == GI_OK) c->touched_since_resolve = true;
+        return s;
+    }
     const int blocks = update_blocks(hits->n);
     if (c->cfg.key_dir == GI_KEY_DIR_NORMAL)
         k_update<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(a);
@@ -861,9 +832,29 @@ gi_status gi_cache_resolve(gi_cache_t c, uint32_t frame, gi_stream_t stream) {
         return GI_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const ResolveArgs a = cache_resolve_args(c, frame);
-    k_resolve<<<c->res_blocks, kResThreads, 0, st>>>(a);
-    gi_status s = cuda_status(cudaGetLastError(), "k_resolve launch");
+    gi_status s;
+    if (c->tiles) {
+        TileResolveArgs ta;
+        ta.t = tile_arrays(c, c->cur);
+        ta.touch = c->touch;
+        ta.tmask = c->tmask;
+        ta.ctr = c->ctr;
+        ta.res_stride = c->res_bytes;
+        ta.f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
+        ta.alpha = c->cfg.alpha;
+        ta.frame = frame;
+        ta.stamp_now = frame + 1u;
+        ta.has_lr = c->last_resolved >= 0;
+        ta.lr = c->last_resolved >= 0 ? (uint32_t)c->last_resolved : 0u;
+        ta.evict = c->cfg.evict_frames;
+        ta.min_samples = c->cfg.min_samples;
+        ta.occ_out = c->occ_dev;
+        s = tile_resolve_launch(ta, c->tres_blocks, st);
+    } else {
+        const ResolveArgs a = cache_resolve_args(c, frame);
+        k_resolve<<<c->res_blocks, kResThreads, 0, st>>>(a);
+        s = cuda_status(cudaGetLastError(), "k_resolve launch");
+    }
     if (s != GI_OK) return s;
     cache_after_resolve(c, frame);
     return GI_OK;
@@ -883,7 +874,7 @@ gi_status gi_cache_query(gi_cache_t c, const gi_query *q, float *out, gi_stream_
     const int f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
     int blocks = (int)std::min<unsigned long long>((unsigned long long)c->sms * 16, (q->n + 255) / 256);
     if (q->slot_ids) {
-        k_query_slots<<<blocks, 256, 0, st>>>(q->slot_ids, q->n, c->resolved[c->cur], c->res_bytes, f16, c->N, q->env[0],
+        k_query_slots<<<blocks, 256, 0, st>>>(q->slot_ids, q->n, c->resolved[c->cur], c->res_bytes, f16, c->cells, q->env[0],
                                               q->env[1], q->env[2], reinterpret_cast<float4 *>(out));
     } else {
         if (!q->points || !hits_ok(q->points, c->cfg.key_dir) || q->points->n < q->n || !view_ok(q->view)) {
@@ -892,6 +883,13 @@ gi_status gi_cache_query(gi_cache_t c, const gi_query *q, float *out, gi_stream_
         }
         UpdateArgs a = cache_update_args(c, q->points, q->view, nullptr);
         a.n = q->n;
+        if (c->tiles) {
+            TileUpdateArgs ta;
+            ta.u = a;
+            ta.tmask = c->tmask;
+            return tile_query_points_launch(ta, tile_arrays(c, c->cur), c->res_bytes, f16, live_rule(c),
+                                            reinterpret_cast<float4 *>(out), blocks, (int)c->cfg.key_dir, st);
+        }
         if (c->cfg.key_dir == GI_KEY_DIR_NORMAL)
             k_query_points<GI_KEY_DIR_NORMAL><<<blocks, 256, 0, st>>>(a, c->resolved[c->cur], c->res_bytes, f16, live_rule(c),
                                                                       reinterpret_cast<float4 *>(out));
@@ -910,8 +908,13 @@ gi_status gi_cache_stats(gi_cache_t c, gi_cache_stats_t *out, gi_stream_t stream
     cudaStream_t st = (cudaStream_t)stream;
     gi_status s = cuda_status(cudaMemsetAsync(c->scan, 0, 3 * sizeof(unsigned long long), st), "stats memset");
     if (s != GI_OK) return s;
-    k_scan_stats<<<c->sms * 4, 256, 0, st>>>(c->tags[c->cur], c->accum[c->cur], c->bitmap, c->N, live_rule(c), c->scan);
-    s = cuda_status(cudaGetLastError(), "k_scan_stats launch");
+    if (c->tiles) {
+        s = tile_scan_launch(tile_arrays(c, c->cur), c->N, live_rule(c), c->scan, c->sms * 4, st);
+    } else {
+        k_scan_stats<<<c->sms * 4, 256, 0, st>>>(c->tags[c->cur], c->accum[c->cur], c->bitmap, c->N, live_rule(c),
+                                                 c->scan);
+        s = cuda_status(cudaGetLastError(), "k_scan_stats launch");
+    }
     if (s != GI_OK) return s;
     Counters h;
     unsigned long long sc[3];
@@ -943,6 +946,35 @@ gi_status gi_cache_export(gi_cache_t c, gi_cell *out, uint64_t capacity, uint64_
         return GI_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if (c->tiles) {
+        TileHost h;
+        gi_status s = copy_tiles(c, st, h, false);
+        if (s != GI_OK) return s;
+        const LiveRule r = live_rule(c);
+        std::vector<gi_cell> cells;
+        for (uint32_t i = 0; i < c->N; ++i) {
+            const uint32_t t = h.tags[i];
+            if (t == kEmpty) continue;
+            const uint32_t home = (i - ((i - (t & 0xFFu)) & 0xFFu)) & c->mask;
+            const uint64_t tid = ((uint64_t)home << 24) | (uint64_t)(t >> 8);
+            for (uint32_t k = 0; k < (uint32_t)kTileCells; ++k) {
+                const size_t e = (size_t)i * kTileCells + k;
+                const Accum &a = h.accum[e];
+                if (!(a.count > 0 || host_answers(h.stamp[e], r))) continue;
+                gi_cell cell;
+                cell.identity = (tid << 6) | k;
+                for (int q = 0; q < 3; ++q) cell.sum[q] = a.sum[q];
+                cell.count = a.count;
+                cell.stamp = h.stamp[e];
+                cell.value[0] = h.state[e].x;
+                cell.value[1] = h.state[e].y;
+                cell.value[2] = h.state[e].z;
+                cell.slot = (uint32_t)e;
+                cells.push_back(cell);
+            }
+        }
+        return export_sorted(cells, out, capacity, count, "gi_cache_export");
+    }
     const size_t N = c->N;
     const int f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
     std::vector<SlotWord> tags(N);
@@ -979,17 +1011,62 @@ gi_status gi_cache_export(gi_cache_t c, gi_cell *out, uint64_t capacity, uint64_
         cell.slot = i;
         cells.push_back(cell);
     }
-    std::sort(cells.begin(), cells.end(), [](const gi_cell &x, const gi_cell &y) { return x.identity < y.identity; });
-    *count = cells.size();
-    if (cells.size() > capacity) {
+    return export_sorted(cells, out, capacity, count, "gi_cache_export");
+}
+
+gi_status gi_cache_export_tiles(gi_cache_t c, gi_tile *out, uint64_t capacity, uint64_t *count, gi_stream_t stream) {
+    if (!c || !count || (capacity > 0 && !out)) {
+        set_error("gi_cache_export_tiles: NULL argument");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (!c->tiles) {
+        set_error("gi_cache_export_tiles: the cache holds cells, not tiles");
+        return GI_ERR_INVALID_ARG;
+    }
+    TileHost h;
+    gi_status s = copy_tiles(c, (cudaStream_t)stream, h, true);
+    if (s != GI_OK) return s;
+    const LiveRule r = live_rule(c);
+    std::vector<gi_tile> tiles;
+    for (uint32_t i = 0; i < c->N; ++i) {
+        const uint32_t t = h.tags[i];
+        if (t == kEmpty) continue;
+        gi_tile tile;
+        memset(&tile, 0, sizeof tile);
+        for (uint32_t k = 0; k < (uint32_t)kTileCells; ++k) {
+            const size_t e = (size_t)i * kTileCells + k;
+            if (h.accum[e].count > 0) ++tile.live;
+            if (!host_answers(h.stamp[e], r)) continue;
+            if (h.accum[e].count == 0) ++tile.live;
+            tile.value[k][0] = h.state[e].x;
+            tile.value[k][1] = h.state[e].y;
+            tile.value[k][2] = h.state[e].z;
+            memcpy(&tile.samples[k], &h.state[e].w, sizeof(uint32_t));
+        }
+        if (!tile.live) continue;
+        for (uint32_t k = 0; k < (uint32_t)kTileMips; ++k) {
+            const float4 &m = h.mips[(size_t)i * kTileMips + k];
+            tile.value[kTileCells + k][0] = m.x;
+            tile.value[kTileCells + k][1] = m.y;
+            tile.value[kTileCells + k][2] = m.z;
+            memcpy(&tile.samples[kTileCells + k], &m.w, sizeof(uint32_t));
+        }
+        const uint32_t home = (i - ((i - (t & 0xFFu)) & 0xFFu)) & c->mask;
+        tile.identity = ((uint64_t)home << 24) | (uint64_t)(t >> 8);
+        tile.slot = i;
+        tiles.push_back(tile);
+    }
+    std::sort(tiles.begin(), tiles.end(), [](const gi_tile &x, const gi_tile &y) { return x.identity < y.identity; });
+    *count = tiles.size();
+    if (tiles.size() > capacity) {
         if (capacity > 0) {
-            set_error("gi_cache_export: %zu live cells exceed capacity %llu", cells.size(),
+            set_error("gi_cache_export_tiles: %zu tiles exceed capacity %llu", tiles.size(),
                       (unsigned long long)capacity);
             return GI_ERR_CAPACITY;
         }
         return GI_OK;
     }
-    if (!cells.empty()) memcpy(out, cells.data(), cells.size() * sizeof(gi_cell));
+    if (!tiles.empty()) memcpy(out, tiles.data(), tiles.size() * sizeof(gi_tile));
     return GI_OK;
 }
 

@@ -176,6 +176,50 @@ struct InterpArgs {
     float4 *out;
 };
 
+// ---------------------------------------------------------------- tile table (gi_tiles.cu)
+// Two-level cache (Section 2.2.3): a slot holds a tile of 8 x 8 cells; cell e = slot * 64 + cell.
+constexpr int kTileCells = 64;
+constexpr int kTileMips = 21;  // 4x4 + 2x2 + 1x1 values above the cells
+
+struct TileArrays {
+    SlotWord *tags;              // [T] tile tags
+    Accum *accum;                // [T * 64] sums and count since the last resolve (stamp field unused)
+    uint32_t *stamp;             // [T * 64] 1 + frame of the last resolve with samples; 0 = never
+    float4 *state;               // [T * 64] blended radiance; w = sample count (u32 bits)
+    void *resolved;              // [T * 64] answer of each live cell (float4 or half4, w = cold)
+    float4 *mips;                // [T * 21] MIP values; w = sample count (u32 bits), 0 = none
+};
+
+struct TileUpdateArgs {
+    UpdateArgs u;                // u.tags / u.accum / u.mask / u.touch of the tile table
+    unsigned long long *tmask;   // [T] cells touched since the last resolve (one table for both copies)
+};
+
+struct TileResolveArgs {
+    TileArrays t;
+    const uint32_t *touch;       // tiles first touched since the last resolve
+    unsigned long long *tmask;
+    Counters *ctr;
+    uint32_t res_stride;
+    int f16;
+    float alpha;
+    uint32_t frame, stamp_now;   // frame and frame + 1
+    uint32_t has_lr, lr, evict;  // previous resolve (for the no-history test) and E
+    uint32_t min_samples;
+    uint32_t *occ_out;
+};
+
+gi_status tile_update_launch(const TileUpdateArgs &a, int key_dir, cudaStream_t st);
+gi_status tile_resolve_launch(const TileResolveArgs &a, int blocks, cudaStream_t st);
+int tile_resolve_blocks_per_sm();
+gi_status tile_query_points_launch(const TileUpdateArgs &a, const TileArrays &t, uint32_t res_stride, int f16,
+                                   LiveRule rule, float4 *out, int blocks, int key_dir, cudaStream_t st);
+gi_status tile_rebuild_launch(const TileArrays &from, const TileArrays &to, unsigned long long *tmask,
+                              uint32_t res_bytes, uint32_t mask, uint32_t max_probe, LiveRule rule, Counters *ctr,
+                              int blocks, cudaStream_t st);
+gi_status tile_scan_launch(const TileArrays &t, uint32_t tiles, LiveRule rule, unsigned long long *out, int blocks,
+                           cudaStream_t st);
+
 // Cache internals needed by the probe kernels.
 struct CacheView {
     const void *resolved;      // resolved radiance of slot 0: float4, or half4 (ushort4)
@@ -196,6 +240,7 @@ void cache_after_update(gi_cache_t c);
 ResolveArgs cache_resolve_args(gi_cache_t c, uint32_t frame);
 void cache_after_resolve(gi_cache_t c, uint32_t frame);
 int cache_key_dir(const gi_cache_s *c);
+bool cache_tiled(const gi_cache_s *c);
 int cache_device(const gi_cache_s *c);
 int64_t cache_last_resolved(const gi_cache_s *c);
 

@@ -43,14 +43,15 @@ class ProbeBuffers:
 class Pipeline:
     def __init__(self, width: int, height: int, rays_per_probe: int, log2_slots: int, cell_size=0.05,
                  num_lods=4, alpha=0.1, evict_frames=8, max_probe=128, key_dir=0,
-                 resolved_format=GI_RESOLVED_F32, rebuild_load=0.8, first_touch=0, device="cuda"):
+                 resolved_format=GI_RESOLVED_F32, rebuild_load=0.8, first_touch=0, tiles=False, min_samples=16,
+                 device="cuda"):
         self.width, self.height, self.rpp = width, height, rays_per_probe
         self.probes = ProbeBuffers(width, height, device)
         self.n_records = self.probes.layout.num_probes * rays_per_probe
         self.slot_ids = torch.empty(self.n_records, dtype=torch.int32, device=device)
         self.irr = torch.empty((height, width, 4), dtype=torch.float32, device=device)
         self.cache = gi_cache_create(log2_slots, cell_size, num_lods, alpha, evict_frames, max_probe, key_dir,
-                                     resolved_format, rebuild_load, first_touch)
+                                     resolved_format, rebuild_load, first_touch, tiles, min_samples)
         self.atlas = self.atlas_tmp = None
 
     def spawn(self, gbuf, view, stream=None):

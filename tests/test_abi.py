@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 STRUCTS = ["gi_cache_config", "gi_view", "gi_hits", "gi_gbuffer", "gi_probe_layout", "gi_probes",
-           "gi_cache_stats_t", "gi_cell", "gi_query", "gi_batch_tuning", "gi_batch_view", "gi_nrc_config",
+           "gi_cache_stats_t", "gi_cell", "gi_tile", "gi_query", "gi_batch_tuning", "gi_batch_view", "gi_nrc_config",
            "gi_points", "gi_nrc_stats_t"]
 
 
@@ -100,6 +100,14 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
     bad = gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, 3)  # unknown first-touch record
     assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    # tile caches: at most 2^22 tiles, first touches always listed, min_samples >= 1, tiles in {0, 1}
+    for bad in (gi.gi_cache_config(23, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, 0, 1, 16),
+                gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, gi.GI_FIRST_TOUCH_BITMAP, 1, 16),
+                gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, 0, 1, 0),
+                gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, 0, 2, 16)):
+        assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    cnt = ctypes.c_uint64()
+    assert lib.gi_cache_export_tiles(None, None, 0, ctypes.byref(cnt), None) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_cache_create(None, ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_cache_update(None, None, None, None, None) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_cache_resolve(None, 0, None) == gi.GI_ERR_INVALID_ARG
