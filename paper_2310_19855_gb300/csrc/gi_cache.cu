@@ -451,7 +451,10 @@ struct gi_cache_s {
     uint32_t *stamp[2];          // tiles: per-cell stamps, state, MIP values (gi_tiles.cu)
     float4 *state[2];
     float4 *mips[2];
+    unsigned long long *omask[2];
     unsigned long long *tmask;   // tiles: cells touched since the last resolve
+    uint32_t *cidx;              // tiles: accumulator block of each touched tile
+    uint32_t *tlist;             // tiles: tile of each accumulator block
     int tres_blocks;
     uint32_t *touch;
     uint32_t *bitmap;            // touched slots since the last resolve, one bit each
@@ -484,6 +487,7 @@ static TileArrays tile_arrays(const gi_cache_s *c, int k) {
     t.state = c->state[k];
     t.resolved = c->resolved[k];
     t.mips = c->mips[k];
+    t.omask = c->omask[k];
     return t;
 }
 
@@ -624,8 +628,11 @@ static void free_cache(gi_cache_s *c) {
         cudaFree(c->stamp[k]);
         cudaFree(c->state[k]);
         cudaFree(c->mips[k]);
+        cudaFree(c->omask[k]);
     }
     cudaFree(c->tmask);
+    cudaFree(c->cidx);
+    cudaFree(c->tlist);
     cudaFree(c->touch);
     cudaFree(c->bitmap);
     cudaFree(c->ctr);
@@ -651,8 +658,18 @@ static gi_status copy_tiles(const gi_cache_s *c, cudaStream_t st, TileHost &h, b
     h.state.resize(E);
     gi_status s = cuda_status(cudaStreamSynchronize(st), "export sync");
     const int k = c->cur;
+    std::vector<Accum> blocks(E);
+    std::vector<uint32_t> cidx(N);
     if (s == GI_OK) s = cuda_status(cudaMemcpy(h.tags.data(), c->tags[k], N * sizeof(SlotWord), cudaMemcpyDeviceToHost), "export");
-    if (s == GI_OK) s = cuda_status(cudaMemcpy(h.accum.data(), c->accum[k], E * sizeof(Accum), cudaMemcpyDeviceToHost), "export");
+    if (s == GI_OK) s = cuda_status(cudaMemcpy(blocks.data(), c->accum[k], E * sizeof(Accum), cudaMemcpyDeviceToHost), "export");
+    if (s == GI_OK) s = cuda_status(cudaMemcpy(cidx.data(), c->cidx, N * sizeof(uint32_t), cudaMemcpyDeviceToHost), "export");
+    // accumulators in slot order: a touched tile's block, zeros for the others
+    if (s == GI_OK) {
+        memset(h.accum.data(), 0, E * sizeof(Accum));
+        for (size_t i = 0; i < N; ++i)
+            if (cidx[i] < N)
+                memcpy(&h.accum[i * kTileCells], &blocks[(size_t)cidx[i] * kTileCells], kTileCells * sizeof(Accum));
+    }
     if (s == GI_OK) s = cuda_status(cudaMemcpy(h.stamp.data(), c->stamp[k], E * sizeof(uint32_t), cudaMemcpyDeviceToHost), "export");
     if (s == GI_OK) s = cuda_status(cudaMemcpy(h.state.data(), c->state[k], E * sizeof(float4), cudaMemcpyDeviceToHost), "export");
     if (s == GI_OK && mips) {
@@ -724,6 +741,8 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
             if (s == GI_OK) s = cuda_status(cudaMemset(c->stamp[k], 0, E * sizeof(uint32_t)), "memset");
             if (s == GI_OK) s = cuda_status(cudaMemset(c->state[k], 0, E * sizeof(float4)), "memset");
             if (s == GI_OK) s = cuda_status(cudaMemset(c->mips[k], 0, N * kTileMips * sizeof(float4)), "memset");
+            if (s == GI_OK) s = cuda_status(cudaMalloc(&c->omask[k], N * sizeof(unsigned long long)), "cudaMalloc omask");
+            if (s == GI_OK) s = cuda_status(cudaMemset(c->omask[k], 0, N * sizeof(unsigned long long)), "memset");
         }
     }
     // First touches: a slot bitmap walked in slot order by the resolve when the accumulators
@@ -735,11 +754,14 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
     if (s == GI_OK && c->tiles) {
         s = cuda_status(cudaMalloc(&c->tmask, N * sizeof(unsigned long long)), "cudaMalloc tile masks");
         if (s == GI_OK) s = cuda_status(cudaMemset(c->tmask, 0, N * sizeof(unsigned long long)), "memset");
+        if (s == GI_OK) s = cuda_status(cudaMalloc(&c->cidx, N * sizeof(uint32_t)), "cudaMalloc tile blocks");
+        if (s == GI_OK) s = cuda_status(cudaMemset(c->cidx, 0xFF, N * sizeof(uint32_t)), "memset");
+        if (s == GI_OK) s = cuda_status(cudaMalloc(&c->tlist, N * sizeof(uint32_t)), "cudaMalloc tile list");
     }
     if (s == GI_OK && use_bitmap) {
         s = cuda_status(cudaMalloc(&c->bitmap, N / 8), "cudaMalloc bitmap");
         if (s == GI_OK) s = cuda_status(cudaMemset(c->bitmap, 0, N / 8), "memset");
-    } else if (s == GI_OK) {
+    } else if (s == GI_OK && !c->tiles) {
         s = cuda_status(cudaMalloc(&c->touch, N * 4), "cudaMalloc touch");
     }
     if (s == GI_OK) s = cuda_status(cudaMalloc(&c->ctr, sizeof(Counters)), "cudaMalloc counters");
@@ -807,6 +829,8 @@ gi_status gi_cache_update(gi_cache_t c, const gi_hits *hits, const gi_view *view
         TileUpdateArgs ta;
         ta.u = a;
         ta.tmask = c->tmask;
+        ta.cidx = c->cidx;
+        ta.tlist = c->tlist;
         s = tile_update_launch(ta, (int)c->cfg.key_dir, st);
         if (s == GI_OK) c->touched_since_resolve = true;
         return s;
@@ -836,8 +860,10 @@ gi_status gi_cache_resolve(gi_cache_t c, uint32_t frame, gi_stream_t stream) {
     if (c->tiles) {
         TileResolveArgs ta;
         ta.t = tile_arrays(c, c->cur);
-        ta.touch = c->touch;
+        ta.tiles = c->N;
         ta.tmask = c->tmask;
+        ta.cidx = c->cidx;
+        ta.tlist = c->tlist;
         ta.ctr = c->ctr;
         ta.res_stride = c->res_bytes;
         ta.f16 = c->cfg.resolved_format == GI_RESOLVED_F16;
@@ -887,6 +913,8 @@ gi_status gi_cache_query(gi_cache_t c, const gi_query *q, float *out, gi_stream_
             TileUpdateArgs ta;
             ta.u = a;
             ta.tmask = c->tmask;
+            ta.cidx = c->cidx;
+            ta.tlist = c->tlist;
             return tile_query_points_launch(ta, tile_arrays(c, c->cur), c->res_bytes, f16, live_rule(c),
                                             reinterpret_cast<float4 *>(out), blocks, (int)c->cfg.key_dir, st);
         }
@@ -909,7 +937,7 @@ gi_status gi_cache_stats(gi_cache_t c, gi_cache_stats_t *out, gi_stream_t stream
     gi_status s = cuda_status(cudaMemsetAsync(c->scan, 0, 3 * sizeof(unsigned long long), st), "stats memset");
     if (s != GI_OK) return s;
     if (c->tiles) {
-        s = tile_scan_launch(tile_arrays(c, c->cur), c->N, live_rule(c), c->scan, c->sms * 4, st);
+        s = tile_scan_launch(tile_arrays(c, c->cur), c->tmask, c->N, live_rule(c), c->scan, c->sms * 4, st);
     } else {
         k_scan_stats<<<c->sms * 4, 256, 0, st>>>(c->tags[c->cur], c->accum[c->cur], c->bitmap, c->N, live_rule(c),
                                                  c->scan);
@@ -926,7 +954,7 @@ gi_status gi_cache_stats(gi_cache_t c, gi_cache_stats_t *out, gi_stream_t stream
     out->slots = c->N;
     out->occupied = sc[0];
     out->live = sc[1];
-    out->touched = c->bitmap ? sc[2] : h.touch_count;
+    out->touched = (c->bitmap || c->tiles) ? sc[2] : h.touch_count;
     out->dropped = h.dropped;
     out->clamped = h.clamped;
     out->rebuilds = c->rebuilds;

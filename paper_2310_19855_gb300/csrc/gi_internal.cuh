@@ -188,17 +188,22 @@ struct TileArrays {
     float4 *state;               // [T * 64] blended radiance; w = sample count (u32 bits)
     void *resolved;              // [T * 64] answer of each live cell (float4 or half4, w = cold)
     float4 *mips;                // [T * 21] MIP values; w = sample count (u32 bits), 0 = none
+    unsigned long long *omask;   // [T] cells live after the tile's last resolve
 };
 
 struct TileUpdateArgs {
-    UpdateArgs u;                // u.tags / u.accum / u.mask / u.touch of the tile table
-    unsigned long long *tmask;   // [T] cells touched since the last resolve (one table for both copies)
+    UpdateArgs u;                // u.tags / u.accum / u.mask / u.ctr of the tile table
+    unsigned long long *tmask;   // [T] cells touched since the last resolve (one array for both copies)
+    uint32_t *cidx;              // [T] accumulator block of each touched tile (one array for both copies)
+    uint32_t *tlist;             // [T] tile of each block
 };
 
 struct TileResolveArgs {
     TileArrays t;
-    const uint32_t *touch;       // tiles first touched since the last resolve
+    uint32_t tiles;              // T (a multiple of 32)
     unsigned long long *tmask;
+    uint32_t *cidx;
+    uint32_t *tlist;
     Counters *ctr;
     uint32_t res_stride;
     int f16;
@@ -217,8 +222,8 @@ gi_status tile_query_points_launch(const TileUpdateArgs &a, const TileArrays &t,
 gi_status tile_rebuild_launch(const TileArrays &from, const TileArrays &to, unsigned long long *tmask,
                               uint32_t res_bytes, uint32_t mask, uint32_t max_probe, LiveRule rule, Counters *ctr,
                               int blocks, cudaStream_t st);
-gi_status tile_scan_launch(const TileArrays &t, uint32_t tiles, LiveRule rule, unsigned long long *out, int blocks,
-                           cudaStream_t st);
+gi_status tile_scan_launch(const TileArrays &t, const unsigned long long *tmask, uint32_t tiles, LiveRule rule,
+                           unsigned long long *out, int blocks, cudaStream_t st);
 
 // Cache internals needed by the probe kernels.
 struct CacheView {

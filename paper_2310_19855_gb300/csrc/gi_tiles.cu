@@ -11,15 +11,26 @@
 //
 // Layout (T tile slots, cell e = slot * 64 + cell):
 //   tags     u32[T]          tile fingerprint << 8 | (home mod 256); 0 = empty
-//   tmask    u64[T]          cells touched since the last resolve (set by the update, cleared by
-//                            the resolve); its first bit in a frame lists the tile for the resolve
-//   accum    Accum[T * 64]   fixed-point sums and count since the last resolve
+//   tmask    u64[T]          cells touched since the last resolve (set by the update, walked in
+//                            slot order and cleared by the resolve: the touched tiles are its
+//                            non-zero words)
+//   omask    u64[T]          cells live after the last resolve that touched the tile (a superset of
+//                            its live cells until the next one: cells only die without a touch)
+//   cidx     u32[T]          accumulator block of a tile touched since the last resolve, in the
+//                            order the update handed them out; GI_SLOT_NONE otherwise
+//   accum    Accum[T * 64]   block b holds the fixed-point sums and counts of the 64 cells of the
+//                            tile whose cidx is b, since the last resolve
 //   stamp    u32[T * 64]     1 + frame of the last resolve that found samples; 0 = never
 //   state    float4[T * 64]  blended radiance, w = samples since the cell last started without history
 //   resolved [T * 64]        the answer of each live cell (float4 or half4; w = resolved without history)
 //   mips     float4[T * 21]  levels 1..3 (16 + 4 + 1 values), w = summed sample count, 0 = no value
-// The per-cell arrays of one tile are contiguous: the resolve of a tile is one warp reading 256 B
-// of stamps and 1 KB of state, the accumulators of touched cells only.
+//   tlist    u32[T]          the touched tiles in block order (entry b = the tile of block b)
+// The per-cell arrays of one tile are contiguous.  The update issues no returning atomic but one
+// counter add per CTA of the compaction: sums, counts and the touched bit are reductions.  The
+// resolve of a tile is one warp that issues the loads of all its cells at once: 256 B of stamps,
+// the state of the cells in omask | tmask, the accumulators of the touched cells.
+#include <algorithm>
+
 #include "gi_cache_dev.cuh"
 
 namespace gi {
@@ -52,17 +63,20 @@ __device__ __forceinline__ unsigned long long tile_key(const KeyParams &k, float
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) { return a > 0xFFFFFFFFu - b ? 0xFFFFFFFFu : a + b; }
 
 // ---------------------------------------------------------------- update
-// Per record: tile descriptor, bucket + fingerprint of the tile, cell.  Hits of a warp naming the
-// same cell are merged (integer sums, order-free); the group leader finds or inserts the tile by
-// linear probing, adds the sums into the cell's accumulator and sets the cell's bit in the tile's
-// touched mask; the add that finds the mask empty lists the tile for the resolve.
+// Three launches.  (1) k_tile_key: per record the tile descriptor, bucket + fingerprint of the
+// tile and the cell; the leader of each group of same-cell hits in a warp finds or inserts the
+// tile by linear probing and sets the cell's bit in the tile's touched mask (a reduction); the
+// record's slot id is tile slot * 64 + cell.  (2) k_tile_compact: every tile touched since the
+// last resolve that has no accumulator block yet gets the next one (a per-frame index, cidx).
+// (3) k_tile_accumulate: per record the fixed-point radiance, merged per cell within the warp
+// and added into the cell's accumulator of its tile's block with reductions.  The accumulator
+// blocks of one frame are contiguous (touched tiles x 2 KB), so the reductions of a frame span
+// that range only, not the whole table: the cost of scattered reductions grows with the span.
 template <int KEY_DIR>
-__global__ void __launch_bounds__(kUpdThreads, 8) k_tile_update(TileUpdateArgs ta) {
+__global__ void __launch_bounds__(kUpdThreads, 8) k_tile_key(TileUpdateArgs ta) {
     const UpdateArgs &a = ta.u;
-    __shared__ uint32_t s_touch[kUpdBlockRecords];
-    __shared__ uint32_t s_n, s_base, s_clamped, s_maxp, s_new;
+    __shared__ uint32_t s_clamped, s_maxp, s_new;
     if (threadIdx.x == 0) {
-        s_n = 0;
         s_clamped = 0;
         s_maxp = 0;
         s_new = 0;
@@ -71,6 +85,7 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_update(TileUpdateArgs t
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * kUpdThreads;
     uint32_t my_clamped = 0, my_maxp = 0, my_new = 0;
+    unsigned long long my_dropped = 0;
     for (unsigned long long base = (unsigned long long)blockIdx.x * kUpdThreads; base < a.n; base += stride) {
         const unsigned long long i = base + threadIdx.x;
         const bool inr = i < a.n;
@@ -83,7 +98,6 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_update(TileUpdateArgs t
         }
         const bool hit = inr && isfinite(len) && len >= 0.0f && isfinite3(px, py, pz);
         const bool miss = inr && len == INFINITY;
-        unsigned long long q0 = 0, q1 = 0, q2 = 0;
         uint32_t home = 0, tag = 0, cell = 0;
         if (hit) {
             float sx, sy, sz;
@@ -97,9 +111,9 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_update(TileUpdateArgs t
                 sz = __ldcs(a.dir[2] + i);
             }
             uint32_t bad = 0;
-            q0 = quantize(__ldcs(a.rad[0] + i), bad);
-            q1 = quantize(__ldcs(a.rad[1] + i), bad);
-            q2 = quantize(__ldcs(a.rad[2] + i), bad);
+            quantize(__ldg(a.rad[0] + i), bad);
+            quantize(__ldg(a.rad[1] + i), bad);
+            quantize(__ldg(a.rad[2] + i), bad);
             my_clamped += bad;
             const unsigned long long key =
                 tile_key(a.kp, px, py, pz, sx, sy, sz, len, KEY_DIR == GI_KEY_DIR_NORMAL ? 0u : 1u, cell);
@@ -109,24 +123,6 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_update(TileUpdateArgs t
         const unsigned hm = __ballot_sync(kFull, hit);
         unsigned peers = 0;
         if (hit) peers = __match_any_sync(hm, ((unsigned long long)(home | (cell << 26)) << 32) | tag);
-        const unsigned above = peers & (0xFFFFFFFEu << lane);
-        int nxt = above ? (__ffs(above) - 1) : -1;
-        uint32_t cnt = hit ? 1u : 0u;
-        while (__any_sync(kFull, nxt >= 0)) {
-            const int src = nxt >= 0 ? nxt : lane;
-            const unsigned long long o0 = __shfl_sync(kFull, q0, src);
-            const unsigned long long o1 = __shfl_sync(kFull, q1, src);
-            const unsigned long long o2 = __shfl_sync(kFull, q2, src);
-            const uint32_t oc = __shfl_sync(kFull, cnt, src);
-            const int on = __shfl_sync(kFull, nxt, src);
-            if (nxt >= 0) {
-                q0 += o0;
-                q1 += o1;
-                q2 += o2;
-                cnt += oc;
-                nxt = on;
-            }
-        }
         const bool leader = hit && (peers & ((1u << lane) - 1u)) == 0u;
         uint32_t slot = GI_SLOT_NONE;
         if (leader) {
@@ -148,16 +144,8 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_update(TileUpdateArgs t
                 s = (s + 1u) & a.mask;
             }
             my_maxp = max(my_maxp, k + 1u);
-            if (slot != GI_SLOT_NONE) {
-                Accum *ac = a.accum + (size_t)slot * kTileCells + cell;
-                atomicAdd(&ac->sum[0], q0);
-                atomicAdd(&ac->sum[1], q1);
-                atomicAdd(&ac->sum[2], q2);
-                atomicAdd(&ac->count, cnt);
-                if (atomicOr(ta.tmask + slot, 1ull << cell) == 0ull) s_touch[atomicAdd(&s_n, 1u)] = slot;
-            } else {
-                atomicAdd(&a.ctr->dropped, (unsigned long long)cnt);
-            }
+            if (slot != GI_SLOT_NONE) atomicOr(ta.tmask + slot, 1ull << cell);
+            else my_dropped += (unsigned long long)__popc(peers);
         }
         const int lead = hit ? (__ffs(peers) - 1) : lane;
         const uint32_t my_slot = __shfl_sync(kFull, slot, lead);
@@ -168,6 +156,7 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_update(TileUpdateArgs t
     my_clamped = __reduce_add_sync(kFull, my_clamped);
     my_maxp = __reduce_max_sync(kFull, my_maxp);
     my_new = __reduce_add_sync(kFull, my_new);
+    if (my_dropped) atomicAdd(&a.ctr->dropped, my_dropped);
     if (lane == 0) {
         if (my_clamped) atomicAdd(&s_clamped, my_clamped);
         if (my_new) atomicAdd(&s_new, my_new);
@@ -175,150 +164,290 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_update(TileUpdateArgs t
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        s_base = s_n ? atomicAdd(&a.ctr->touch_count, s_n) : 0u;
         if (s_clamped) atomicAdd(&a.ctr->clamped, (unsigned long long)s_clamped);
         if (s_maxp) atomicMax(&a.ctr->max_probe, s_maxp);
         if (s_new) atomicAdd(&a.ctr->occupied, s_new);
     }
+}
+
+constexpr int kCompactThreads = 256;
+
+// One warp per 32 tile slots: the touched tiles without a block take the next indices (one
+// counter add per CTA) and are listed at that index.  ctr->touch_count counts the blocks handed
+// out since the last resolve.
+__global__ void __launch_bounds__(kCompactThreads) k_tile_compact(const unsigned long long *tmask, uint32_t *cidx,
+                                                                  uint32_t *tlist, uint32_t tiles, Counters *ctr) {
+    __shared__ uint32_t s_cnt[kCompactThreads / 32];
+    __shared__ uint32_t s_base;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t t = blockIdx.x * kCompactThreads + threadIdx.x;
+    bool need = false;
+    if (t < tiles) need = __ldcg(tmask + t) != 0ull && __ldcg(cidx + t) == GI_SLOT_NONE;
+    const unsigned b = __ballot_sync(kFull, need);
+    if (lane == 0) s_cnt[w] = (uint32_t)__popc(b);
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < s_n; j += kUpdThreads) a.touch[s_base + j] = s_touch[j];
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int k = 0; k < kCompactThreads / 32; ++k) {
+            const uint32_t c = s_cnt[k];
+            s_cnt[k] = tot;
+            tot += c;
+        }
+        s_base = tot ? atomicAdd(&ctr->touch_count, tot) : 0u;
+    }
+    __syncthreads();
+    if (need) {
+        const uint32_t k = s_base + s_cnt[w] + (uint32_t)__popc(b & ((1u << lane) - 1u));
+        cidx[t] = k;
+        tlist[k] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kUpdThreads, 8) k_tile_accumulate(const uint32_t *slot_ids, const float *r0,
+                                                                    const float *r1, const float *r2,
+                                                                    unsigned long long n, const uint32_t *cidx,
+                                                                    uint32_t cells, Accum *accum) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const unsigned long long i = base + threadIdx.x;
+        const uint32_t id = i < n ? __ldcs(slot_ids + i) : GI_SLOT_NONE;
+        bool ok = id < cells;
+        unsigned long long q0 = 0, q1 = 0, q2 = 0;
+        uint32_t blk = 0;
+        if (ok) {
+            uint32_t bad = 0;
+            q0 = quantize(__ldcs(r0 + i), bad);
+            q1 = quantize(__ldcs(r1 + i), bad);
+            q2 = quantize(__ldcs(r2 + i), bad);
+            blk = __ldcg(cidx + id / kTileCells);
+        }
+        // a tile with a slot id always has a block (the compaction ran after the keys); a missing
+        // one would be a broken invariant: the record is skipped rather than written out of range
+        ok = ok && blk < cells / kTileCells;
+        const unsigned vm = __ballot_sync(kFull, ok);
+        unsigned peers = 0;
+        if (ok) peers = __match_any_sync(vm, id);
+        const unsigned above = peers & (0xFFFFFFFEu << lane);
+        int nxt = above ? (__ffs(above) - 1) : -1;
+        uint32_t cnt = ok ? 1u : 0u;
+        while (__any_sync(kFull, nxt >= 0)) {
+            const int src = nxt >= 0 ? nxt : lane;
+            const unsigned long long o0 = __shfl_sync(kFull, q0, src);
+            const unsigned long long o1 = __shfl_sync(kFull, q1, src);
+            const unsigned long long o2 = __shfl_sync(kFull, q2, src);
+            const uint32_t oc = __shfl_sync(kFull, cnt, src);
+            const int on = __shfl_sync(kFull, nxt, src);
+            if (nxt >= 0) {
+                q0 += o0;
+                q1 += o1;
+                q2 += o2;
+                cnt += oc;
+                nxt = on;
+            }
+        }
+        if (ok && (peers & ((1u << lane) - 1u)) == 0u) {
+            Accum *ac = accum + (size_t)blk * kTileCells + (id % kTileCells);
+            atomicAdd(&ac->sum[0], q0);
+            atomicAdd(&ac->sum[1], q1);
+            atomicAdd(&ac->sum[2], q2);
+            atomicAdd(&ac->count, cnt);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- resolve
-// Sum of a value over the lanes lane ^ {0, o1, o2, o1 ^ o2}: every lane of the group gets the same
-// bits (each add is commutative).
-struct Box {
-    float3 s;
-    uint32_t k, n;
-};
-
-__device__ __forceinline__ Box box_xor(Box b, int o) {
-    Box r;
-    r.s.x = b.s.x + __shfl_xor_sync(kFull, b.s.x, o);
-    r.s.y = b.s.y + __shfl_xor_sync(kFull, b.s.y, o);
-    r.s.z = b.s.z + __shfl_xor_sync(kFull, b.s.z, o);
-    r.k = b.k + __shfl_xor_sync(kFull, b.k, o);
-    r.n = sat_add(b.n, __shfl_xor_sync(kFull, b.n, o));
-    return r;
-}
-
-__device__ __forceinline__ Box box_of(bool has, float3 v, uint32_t n) {
-    Box b;
-    b.s = has ? v : make_float3(0.f, 0.f, 0.f);
-    b.k = has ? 1u : 0u;
-    b.n = has ? n : 0u;
-    return b;
-}
-
-// mean of the children holding a value (their count k), zero when none does
-__device__ __forceinline__ float3 box_mean(const Box &b) {
-    if (!b.k) return make_float3(0.f, 0.f, 0.f);
-    const float fk = (float)b.k;
-    return make_float3(__fdiv_rn(b.s.x, fk), __fdiv_rn(b.s.y, fk), __fdiv_rn(b.s.z, fk));
-}
-
-__device__ __forceinline__ float4 mip_word(const Box &b) {
-    const float3 m = box_mean(b);
-    return make_float4(m.x, m.y, m.z, __uint_as_float(b.k ? b.n : 0u));
-}
-
 constexpr int kTileResThreads = 256;
+constexpr int kTileResWarps = kTileResThreads / 32;
 
-// One warp per touched tile; lane l holds cells l and l + 32 (rows 0..3 and 4..7).  Cell (i, j)
-// = i + 8 j, so the level-1 siblings of a cell differ in lane bits 0 and 3, level-2 siblings (of
-// level-1 values) in bits 1 and 4, level-3 siblings in bit 2 and in the half.
+__device__ __forceinline__ float recip_children(uint32_t k) {
+    // 1 / k for the children holding a value (k <= 4): exact for 1, 2, 4, within half an ulp for 3
+    return k == 1u ? 1.0f : (k == 2u ? 0.5f : (k == 3u ? 0.333333343f : (k == 4u ? 0.25f : 0.0f)));
+}
+
+// One MIP value from four values of the level below (xyz, w = sample count bits; count 0 = no
+// value): the mean of those holding a value and their summed (saturating) count.
+__device__ __forceinline__ float4 box4(const float4 &a, const float4 &b, const float4 &c, const float4 &d) {
+    const uint32_t na = __float_as_uint(a.w), nb = __float_as_uint(b.w), nc = __float_as_uint(c.w),
+                   nd = __float_as_uint(d.w);
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    uint32_t k = 0, n = 0;
+    if (na) {
+        sx += a.x;
+        sy += a.y;
+        sz += a.z;
+        ++k;
+        n = sat_add(n, na);
+    }
+    if (nb) {
+        sx += b.x;
+        sy += b.y;
+        sz += b.z;
+        ++k;
+        n = sat_add(n, nb);
+    }
+    if (nc) {
+        sx += c.x;
+        sy += c.y;
+        sz += c.z;
+        ++k;
+        n = sat_add(n, nc);
+    }
+    if (nd) {
+        sx += d.x;
+        sy += d.y;
+        sz += d.z;
+        ++k;
+        n = sat_add(n, nd);
+    }
+    const float r = recip_children(k);
+    return make_float4(sx * r, sy * r, sz * r, __uint_as_float(n));
+}
+
+// The touched tiles are listed in block order by the compaction; warps take entries i, i + warps,
+// ... (the next entry's tile and masks are loaded before the current one is computed).  A tile is
+// resolved by one warp, lane l holding cells l and l + 32: the blended cells go to shared memory,
+// lanes 0..15 build the 4x4 level, lanes 0..3 the 2x2 level and lane 0 the 1x1 level, each value
+// from its four children; then each live cell takes the finest level with enough samples.
+// Completion is counted per warp, so warps never wait for one another.
 __global__ void __launch_bounds__(kTileResThreads) k_tile_resolve(TileResolveArgs a) {
-    const uint32_t n = __ldcg(&a.ctr->touch_count);
-    const int lane = threadIdx.x & 31;
+    __shared__ float4 s_lv[kTileResWarps][kTileCells + kTileMips];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float4 *lv = s_lv[w];
     const uint32_t warp = (blockIdx.x * kTileResThreads + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * kTileResThreads) >> 5;
-    for (uint32_t ti = warp; ti < n; ti += nwarps) {
-        const uint32_t t = __ldcs(a.touch + ti);
-        const unsigned long long m = __ldcg(a.tmask + t);
-        __syncwarp();
-        if (lane == 0) a.tmask[t] = 0ull;
+    const uint32_t n = __ldcg(&a.ctr->touch_count);
+    uint32_t i = warp;
+    uint32_t t = 0;
+    unsigned long long m = 0, o = 0;
+    if (i < n) {
+        t = __ldcg(a.tlist + i);
+        m = __ldcg(a.tmask + t);
+        o = __ldcg(a.t.omask + t);
+    }
+    while (i < n) {
         const size_t base = (size_t)t * kTileCells;
-        float3 v[2];
-        uint32_t ns[2];
+        Accum *acc = a.t.accum + (size_t)i * kTileCells;
+        const unsigned long long want = m | o;
+        // every load of the tile: stamps, state of the cells that may hold a value, accumulators
+        uint32_t st[2];
+        float4 sv[2];
+        uint4 lo[2], hi[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t c = (uint32_t)lane + 32u * h;
+            st[h] = __ldcg(a.t.stamp + base + c);
+            sv[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if ((want >> c) & 1ull) sv[h] = __ldcg(a.t.state + base + c);
+            if ((m >> c) & 1ull) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(acc + c);
+                lo[h] = __ldcg(src);
+                hi[h] = __ldcg(src + 1);
+            }
+        }
+        // the next entry's tile and masks
+        const uint32_t inext = i + nwarps;
+        uint32_t tn = 0;
+        unsigned long long mn = 0, on = 0;
+        if (inext < n) {
+            tn = __ldcg(a.tlist + inext);
+            mn = __ldcg(a.tmask + tn);
+            on = __ldcg(a.t.omask + tn);
+        }
         bool live[2], cold[2];
+        float4 cv[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint32_t c = (uint32_t)lane + 32u * h;
             const size_t e = base + c;
-            const uint32_t st = __ldcg(a.t.stamp + e);
-            v[h] = make_float3(0.f, 0.f, 0.f);
-            ns[h] = 0;
-            live[h] = false;
+            cv[h] = sv[h];
             cold[h] = false;
             if ((m >> c) & 1ull) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(a.t.accum + e);
-                const uint4 lo = __ldcg(src), hi = __ldcg(src + 1);
                 // no history: never resolved, or evicted by an earlier resolve (untouched E frames)
-                const bool fresh = st == 0u || (a.has_lr && (a.lr - (st - 1u)) >= a.evict);
-                const unsigned long long s0 = ((unsigned long long)lo.y << 32) | lo.x;
-                const unsigned long long s1 = ((unsigned long long)lo.w << 32) | lo.z;
-                const unsigned long long s2 = ((unsigned long long)hi.y << 32) | hi.x;
-                const float fc = (float)hi.z;
-                float3 val = make_float3(__fdiv_rn(__ull2float_rn(s0), fc) * 5.9604644775390625e-8f,
-                                         __fdiv_rn(__ull2float_rn(s1), fc) * 5.9604644775390625e-8f,
-                                         __fdiv_rn(__ull2float_rn(s2), fc) * 5.9604644775390625e-8f);
-                uint32_t samples = hi.z;
+                const bool fresh = st[h] == 0u || (a.has_lr && (a.lr - (st[h] - 1u)) >= a.evict);
+                const unsigned long long s0 = ((unsigned long long)lo[h].y << 32) | lo[h].x;
+                const unsigned long long s1 = ((unsigned long long)lo[h].w << 32) | lo[h].z;
+                const unsigned long long s2 = ((unsigned long long)hi[h].y << 32) | hi[h].x;
+                // mean = sum / (count 2^24): one reciprocal, three products (within an ulp of the quotient)
+                const float rc = __frcp_rn((float)hi[h].z) * 5.9604644775390625e-8f;
+                float3 val = make_float3(__ull2float_rn(s0) * rc, __ull2float_rn(s1) * rc, __ull2float_rn(s2) * rc);
+                uint32_t samples = hi[h].z;
                 if (!fresh) {
-                    const float4 o = __ldcg(a.t.state + e);
-                    val = make_float3(o.x + a.alpha * (val.x - o.x), o.y + a.alpha * (val.y - o.y),
-                                      o.z + a.alpha * (val.z - o.z));
-                    samples = sat_add(__float_as_uint(o.w), samples);
+                    val = make_float3(sv[h].x + a.alpha * (val.x - sv[h].x), sv[h].y + a.alpha * (val.y - sv[h].y),
+                                      sv[h].z + a.alpha * (val.z - sv[h].z));
+                    samples = sat_add(__float_as_uint(sv[h].w), samples);
                 }
-                a.t.state[e] = make_float4(val.x, val.y, val.z, __uint_as_float(samples));
+                cv[h] = make_float4(val.x, val.y, val.z, __uint_as_float(samples));
+                a.t.state[e] = cv[h];
                 a.t.stamp[e] = a.stamp_now;
-                uint4 *dst = reinterpret_cast<uint4 *>(a.t.accum + e);
+                uint4 *dst = reinterpret_cast<uint4 *>(acc + c);
                 dst[0] = make_uint4(0u, 0u, 0u, 0u);
                 dst[1] = make_uint4(0u, 0u, 0u, 0u);
-                v[h] = val;
-                ns[h] = samples;
                 live[h] = true;
                 cold[h] = fresh;
-            } else if (st != 0u && (a.frame - (st - 1u)) < a.evict) {
-                const float4 o = __ldcg(a.t.state + e);
-                v[h] = make_float3(o.x, o.y, o.z);
-                ns[h] = __float_as_uint(o.w);
-                live[h] = true;
+            } else {
+                live[h] = st[h] != 0u && (a.frame - (st[h] - 1u)) < a.evict;
             }
+            // a live cell's sample count is >= 1, so count 0 marks "no value" in the levels
+            if (!live[h]) cv[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            lv[c] = cv[h];
         }
-        // level 1 (4x4): siblings at lane ^ 1 and lane ^ 8
-        Box b1[2], b2[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) b1[h] = box_xor(box_xor(box_of(live[h], v[h], ns[h]), 1), 8);
-        // level 2 (2x2): level-1 siblings at lane ^ 2 and lane ^ 16
-#pragma unroll
-        for (int h = 0; h < 2; ++h) b2[h] = box_xor(box_xor(box_of(b1[h].k > 0, box_mean(b1[h]), b1[h].n), 2), 16);
-        // level 3 (1x1): level-2 siblings at lane ^ 4 and in the other half
-        Box c3[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) c3[h] = box_xor(box_of(b2[h].k > 0, box_mean(b2[h]), b2[h].n), 4);
-        Box b3;
-        b3.s = make_float3(c3[0].s.x + c3[1].s.x, c3[0].s.y + c3[1].s.y, c3[0].s.z + c3[1].s.z);
-        b3.k = c3[0].k + c3[1].k;
-        b3.n = sat_add(c3[0].n, c3[1].n);
-        const float3 m3 = box_mean(b3);
-        float4 *mips = a.t.mips + (size_t)t * kTileMips;
+        __syncwarp();
+        if (lane < 16) {  // 4x4 value (I, J) = (lane & 3, lane >> 2): cells 2I + 16J + {0, 1, 8, 9}
+            const int c0 = 2 * (lane & 3) + 16 * (lane >> 2);
+            lv[kTileCells + lane] = box4(lv[c0], lv[c0 + 1], lv[c0 + 8], lv[c0 + 9]);
+        }
+        __syncwarp();
+        if (lane < 4) {  // 2x2 value (I, J) = (lane & 1, lane >> 1): 4x4 values 2I + 8J + {0, 1, 4, 5}
+            const int c0 = kTileCells + 2 * (lane & 1) + 8 * (lane >> 1);
+            lv[kTileCells + 16 + lane] = box4(lv[c0], lv[c0 + 1], lv[c0 + 4], lv[c0 + 5]);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const int c0 = kTileCells + 16;
+            lv[kTileCells + 20] = box4(lv[c0], lv[c0 + 1], lv[c0 + 2], lv[c0 + 3]);
+        }
+        __syncwarp();
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint32_t c = (uint32_t)lane + 32u * h;
-            if (live[h]) {
-                // finest level with enough samples; a live cell has a value at every level above it
-                float3 ans = m3;
-                if (ns[h] >= a.min_samples) ans = v[h];
-                else if (b1[h].n >= a.min_samples) ans = box_mean(b1[h]);
-                else if (b2[h].n >= a.min_samples) ans = box_mean(b2[h]);
-                store_resolved(a.t.resolved, a.res_stride, a.f16, (uint32_t)(base + c), ans, cold[h]);
-            }
-            if ((c & 9u) == 0u) mips[((c & 7u) >> 1) + 4u * (c >> 4)] = mip_word(b1[h]);
-            if ((c & 27u) == 0u) mips[16u + ((c >> 2) & 1u) + 2u * (c >> 5)] = mip_word(b2[h]);
+            if (!live[h]) continue;
+            // finest level with enough samples; a live cell has a value at every level above it
+            const float4 l1 = lv[kTileCells + ((c & 7u) >> 1) + 4u * (c >> 4)];
+            const float4 l2 = lv[kTileCells + 16u + ((c >> 2) & 1u) + 2u * (c >> 5)];
+            float4 ans = lv[kTileCells + 20];
+            if (__float_as_uint(cv[h].w) >= a.min_samples) ans = cv[h];
+            else if (__float_as_uint(l1.w) >= a.min_samples) ans = l1;
+            else if (__float_as_uint(l2.w) >= a.min_samples) ans = l2;
+            store_resolved(a.t.resolved, a.res_stride, a.f16, (uint32_t)(base + c), make_float3(ans.x, ans.y, ans.z),
+                           cold[h]);
         }
-        if (lane == 0) mips[20] = mip_word(b3);
+        if (lane < kTileMips) a.t.mips[(size_t)t * kTileMips + lane] = lv[kTileCells + lane];
+        const unsigned live0 = __ballot_sync(kFull, live[0]), live1 = __ballot_sync(kFull, live[1]);
+        if (lane == 0) {
+            a.t.omask[t] = ((unsigned long long)live1 << 32) | live0;
+            a.tmask[t] = 0ull;
+            a.cidx[t] = GI_SLOT_NONE;
+        }
+        __syncwarp();
+        i = inext;
+        t = tn;
+        m = mn;
+        o = on;
     }
-    resolve_finish(a.ctr, a.occ_out, a.stamp_now, gridDim.x, 0u);
+    // the last warp to finish resets the block counter and publishes the occupancy
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(&a.ctr->ticket, 1u) == nwarps - 1u) {
+            a.ctr->touch_count = 0u;
+            a.ctr->ticket = 0u;
+            if (a.occ_out) {
+                reinterpret_cast<volatile uint32_t *>(a.occ_out)[0] = atomicAdd(&a.ctr->occupied, 0u);
+                __threadfence_system();
+                reinterpret_cast<volatile uint32_t *>(a.occ_out)[1] = a.stamp_now;
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------- lookup by point
@@ -405,7 +534,10 @@ __global__ void k_tile_rebuild(TileArrays from, TileArrays to, unsigned long lon
                 }
                 if (lane < kTileMips)
                     to.mips[(size_t)ns * kTileMips + lane] = from.mips[(size_t)s * kTileMips + lane];
-                if (lane == 0) ++live_tiles;
+                if (lane == 0) {
+                    to.omask[ns] = ((unsigned long long)live1 << 32) | live0;
+                    ++live_tiles;
+                }
             } else if (lane == 0) {
                 dropped += (uint32_t)(__popc(live0) + __popc(live1));
             }
@@ -415,6 +547,7 @@ __global__ void k_tile_rebuild(TileArrays from, TileArrays to, unsigned long lon
         __syncwarp();
         if (lane == 0) {
             from.tags[s] = kEmpty;
+            from.omask[s] = 0ull;
             tmask[s] = 0ull;
         }
     }
@@ -427,21 +560,25 @@ __global__ void k_tile_rebuild(TileArrays from, TileArrays to, unsigned long lon
 }
 
 // ---------------------------------------------------------------- table scan for stats
-__global__ void k_tile_scan(TileArrays t, uint32_t tiles, LiveRule rule, unsigned long long *out /* occupied, live */) {
-    unsigned long long occ = 0, live = 0;
+__global__ void k_tile_scan(TileArrays t, const unsigned long long *tmask, uint32_t tiles, LiveRule rule,
+                            unsigned long long *out /* occupied, live, touched tiles */) {
+    unsigned long long occ = 0, live = 0, touched = 0;
     const size_t cells = (size_t)tiles * kTileCells;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < cells; e += (size_t)gridDim.x * blockDim.x) {
+        if ((e % kTileCells) == 0 && tmask[e / kTileCells]) ++touched;
         if (t.tags[e / kTileCells] == kEmpty) continue;
         if ((e % kTileCells) == 0) ++occ;
-        if (t.accum[e].count > 0u || answers(t.stamp[e], rule)) ++live;
+        if (((tmask[e / kTileCells] >> (e % kTileCells)) & 1ull) || answers(t.stamp[e], rule)) ++live;
     }
     for (int o = 16; o; o >>= 1) {
         occ += __shfl_xor_sync(kFull, occ, o);
         live += __shfl_xor_sync(kFull, live, o);
+        touched += __shfl_xor_sync(kFull, touched, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(out, occ);
         atomicAdd(out + 1, live);
+        atomicAdd(out + 2, touched);
     }
 }
 
@@ -450,10 +587,19 @@ gi_status tile_update_launch(const TileUpdateArgs &a, int key_dir, cudaStream_t 
     const int blocks = (int)((a.u.n + kUpdBlockRecords - 1) / kUpdBlockRecords);
     if (blocks == 0) return GI_OK;
     if (key_dir == GI_KEY_DIR_NORMAL)
-        k_tile_update<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(a);
+        k_tile_key<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(a);
     else
-        k_tile_update<GI_KEY_DIR_RAY><<<blocks, kUpdThreads, 0, st>>>(a);
-    return cuda_status(cudaGetLastError(), "k_tile_update launch");
+        k_tile_key<GI_KEY_DIR_RAY><<<blocks, kUpdThreads, 0, st>>>(a);
+    gi_status s = cuda_status(cudaGetLastError(), "k_tile_key launch");
+    if (s != GI_OK) return s;
+    const uint32_t tiles = a.u.mask + 1u;
+    k_tile_compact<<<(tiles + kCompactThreads - 1) / kCompactThreads, kCompactThreads, 0, st>>>(a.tmask, a.cidx,
+                                                                                                a.tlist, tiles, a.u.ctr);
+    s = cuda_status(cudaGetLastError(), "k_tile_compact launch");
+    if (s != GI_OK) return s;
+    k_tile_accumulate<<<blocks, kUpdThreads, 0, st>>>(a.u.slot_ids, a.u.rad[0], a.u.rad[1], a.u.rad[2], a.u.n, a.cidx,
+                                                      tiles * (uint32_t)kTileCells, a.u.accum);
+    return cuda_status(cudaGetLastError(), "k_tile_accumulate launch");
 }
 
 int tile_resolve_blocks_per_sm() {
@@ -464,6 +610,8 @@ int tile_resolve_blocks_per_sm() {
 }
 
 gi_status tile_resolve_launch(const TileResolveArgs &a, int blocks, cudaStream_t st) {
+    // no more warps than tiles
+    blocks = std::min<int>(blocks, (int)((a.tiles + kTileResWarps - 1) / kTileResWarps));
     k_tile_resolve<<<blocks, kTileResThreads, 0, st>>>(a);
     return cuda_status(cudaGetLastError(), "k_tile_resolve launch");
 }
@@ -484,9 +632,9 @@ gi_status tile_rebuild_launch(const TileArrays &from, const TileArrays &to, unsi
     return cuda_status(cudaGetLastError(), "k_tile_rebuild launch");
 }
 
-gi_status tile_scan_launch(const TileArrays &t, uint32_t tiles, LiveRule rule, unsigned long long *out, int blocks,
-                           cudaStream_t st) {
-    k_tile_scan<<<blocks, 256, 0, st>>>(t, tiles, rule, out);
+gi_status tile_scan_launch(const TileArrays &t, const unsigned long long *tmask, uint32_t tiles, LiveRule rule,
+                           unsigned long long *out, int blocks, cudaStream_t st) {
+    k_tile_scan<<<blocks, 256, 0, st>>>(t, tmask, tiles, rule, out);
     return cuda_status(cudaGetLastError(), "k_tile_scan launch");
 }
 
