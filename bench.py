@@ -345,6 +345,9 @@ def run_native(args, rank, world, local_rank):
     torch.cuda.synchronize()
     f_ms = np.array([[f_ev[j][i].elapsed_time(f_ev[j][i + 1]) for i in range(4)] for j in range(f_steps)]).mean(axis=0)
 
+    # ---- the two-level cache (Section 2.2.3): the same frames through a tile cache
+    tiles = run_tiles(args, gi, Pipeline, frames, dev_rec, dev_gb, views, flush, stream, cfg, R)
+
     # ---- max over ranks
     tot = np.array(max_over_ranks([window_ms.sum(), frame_ms.sum(), t_wall, e2e_ms.sum()], world, "cuda"))
     if rank != 0:
@@ -422,11 +425,103 @@ def run_native(args, rank, world, local_rank):
                   "max_probe_seen": int(st["max_probe_seen"]), "rebuilds_total": int(st["rebuilds"])},
         "rebuilds_in_timed_region": int(rebuilds),
         "probe_filter": probe_filter,
+        "tiles": tiles,
         "clocks": clk,
         "wall_s_timed": float(tot[2]),
     }
+    if tiles is not None:
+        for k in ("update", "resolve"):
+            r = tiles["roofline"][k]
+            r["peak"] = peak
+            r["frac"] = r["achieved"] / peak
     print(json.dumps(line), flush=True)
     pl.close()
+
+
+TILE_LOG2 = 18      # tile slots of the two-level cache at 1080p (64 cells each)
+TILE_MIN_SAMPLES = 16
+
+
+def run_tiles(args, gi, Pipeline, frames, dev_rec, dev_gb, views, flush, stream, cfg, R):
+    """Update + resolve + probe irradiance through a tile cache (8 x 8 cells with MIP levels),
+    per pass, L2 flushed before each frame; the resolve's algorithmic bytes from one frame's
+    touched tiles, touched cells and live cells in the touched tiles."""
+    import torch
+
+    fr0 = frames[0]
+    W, H = fr0.camera.width, fr0.camera.height
+    n_frames = len(frames)
+    pt = Pipeline(W, H, fr0.rays_per_probe, TILE_LOG2, resolved_format=cfg["resolved_format"], tiles=True,
+                  min_samples=TILE_MIN_SAMPLES)
+    try:
+        def frame(i, ev=None):
+            k = i % n_frames
+            pt.spawn(dev_gb[k], views[k], stream)
+            if ev is not None:
+                ev[0].record(stream)
+            gi.gi_cache_update(pt.cache, gi.hits_from_planes(dev_rec[k], R), views[k], pt.slot_ids, stream)
+            if ev is not None:
+                ev[1].record(stream)
+            pt.resolve(i, stream)
+            if ev is not None:
+                ev[2].record(stream)
+            pt.integrate((0.0, 0.0, 0.0), stream)
+            if ev is not None:
+                ev[3].record(stream)
+
+        for i in range(args.warmup):
+            frame(i)
+        steps = max(3, args.steps)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        torch.cuda.synchronize()
+        for j in range(steps):
+            flush.zero_()
+            frame(args.warmup + j, evs[j])
+        torch.cuda.synchronize()
+        ms = np.array([[evs[j][i].elapsed_time(evs[j][i + 1]) for i in range(3)] for j in range(steps)]).mean(axis=0)
+        # one more frame, counted: touched tiles and cells, live cells of the touched tiles
+        i = args.warmup + steps
+        k = i % n_frames
+        gi.gi_cache_update(pt.cache, gi.hits_from_planes(dev_rec[k], R), views[k], pt.slot_ids, stream)
+        st = gi.gi_cache_stats(pt.cache, stream)
+        ids = pt.slot_ids.cpu().numpy().view(np.uint32)
+        cells_total = (1 << TILE_LOG2) * 64
+        ids = ids[ids < cells_total]
+        touched_tiles = np.unique(ids >> 6)
+        touched_cells = int(np.unique(ids).size)
+        pt.resolve(i, stream)
+        ex = gi.gi_cache_export(pt.cache)
+        live_in_touched = int(np.isin(ex["slot"] >> 6, touched_tiles).sum())
+        res_b = 8 if cfg["resolved_format"] == 1 else 16
+        Tt = float(touched_tiles.size)
+        T_slots = float(1 << TILE_LOG2)
+        # update (k_tile_key + k_tile_compact + k_tile_accumulate): records 40 B in and the slot id
+        # 4 B out, then slot id + radiance 16 B in again; per touched tile a 32 B tag sector, its 8 B
+        # mask set, its block index and list entry 8 B written; per touched cell the 32 B
+        # accumulator read and written; the compaction scans 12 B (mask + block index) per slot
+        upd_b = R * (44 + 16) + Tt * (32 + 8 + 8) + touched_cells * 64 + T_slots * 12
+        # resolve: per touched tile the list entry 4 B, masks 8 + 8 B read and 8 + 8 B + 4 B index
+        # written, 256 B of stamps, 336 B of MIP values written; per touched cell the accumulator
+        # read + cleared, state and stamp written; per live cell of a touched tile its state read
+        # and its answer written
+        res_bytes = Tt * (4 + 16 + 20 + 256 + 336) + touched_cells * (64 + 20) + live_in_touched * (16 + res_b)
+        return {
+            "note": "gi_cache_create(tiles=1): 2^%d tile slots of 8 x 8 cells, min_samples %d; spawn untimed, "
+                    "update + resolve + probe irradiance per pass, L2 flushed per frame" % (TILE_LOG2, TILE_MIN_SAMPLES),
+            "pass_ms": {"update": float(ms[0]), "resolve": float(ms[1]), "integrate": float(ms[2])},
+            "window_records_per_s_M": R / (ms.sum() * 1e-3) / 1e6,
+            "touched_tiles": int(Tt), "touched_cells": touched_cells, "live_cells_in_touched_tiles": live_in_touched,
+            "table": {"slots": int(st["slots"]), "occupied": int(st["occupied"]), "rebuilds": int(st["rebuilds"]),
+                      "dropped": int(st["dropped"])},
+            "roofline": {
+                "update": {"kernel": "k_tile_key + k_tile_compact + k_tile_accumulate", "bound": "hbm",
+                           "algorithmic_bytes_per_launch": upd_b,
+                           "achieved": upd_b / (ms[0] * 1e-3) / 1e9, "unit": "GB/s"},
+                "resolve": {"kernel": "k_tile_resolve", "bound": "hbm", "algorithmic_bytes_per_launch": res_bytes,
+                            "achieved": res_bytes / (ms[1] * 1e-3) / 1e9, "unit": "GB/s"}},
+        }
+    finally:
+        pt.close()
 
 
 # ------------------------------------------------------------------ batched arm (many views)
