@@ -331,9 +331,63 @@ gi_status gi_probes_layout(uint32_t width, uint32_t height, gi_probe_layout *out
  * Writes mask level 0 and its MIP chain (Section 2.1.5: first valid probe of
  * each 2x2 block in the order (0,0), (1,0), (0,1), (1,1)), positions rebuilt
  * from the G-buffer distance and the camera, normals from the G-buffer.
+ * Positions: the camera ray through the pixel centre times the distance, in
+ * float32 round-to-nearest operations in a fixed order (sx = (2(x+0.5)/W - 1)
+ * tan(fov/2) W/H, sy = (1 - 2(y+0.5)/H) tan(fov/2), dir = (fwd + sx right) + sy up,
+ * world = cam + dir (d / |dir|)), so that they are reproducible bit for bit.
  * `probes` must have been laid out for the view size.
  */
 gi_status gi_probes_spawn(const gi_gbuffer *gbuf, const gi_view *view, const gi_probes *probes, gi_stream_t stream);
+
+/* ---------------------------------------------------------------- temporal path */
+#define GI_MAX_UPSCALE 8
+
+/*
+ * Spawn with temporal upscale u (Section 2.1.1, "Temporal Upscale"): spawn tiles of 8u x 8u
+ * pixels share the jitter j = (floor(8u H_2(f+1)), floor(8u H_3(f+1))); the probe pixel of spawn
+ * tile S is min(8u S + j, (W-1, H-1)) and the 8x8 tile containing it receives a fresh probe
+ * (position and normal as gi_probes_spawn) unless the pixel is sky.  keep = 0: every other tile
+ * gets no probe (u = 1, keep = 0 is gi_probes_spawn).  keep != 0: every other tile, and a tile
+ * whose spawn pixel is sky, keeps its level-0 mask, position and normal (those written by
+ * gi_probes_reproject).  Then the MIP chain.  1 <= u <= GI_MAX_UPSCALE.
+ * The frame's hit records belong to the spawn tiles, row by row: probe S traces records
+ * S * rays_per_probe ... (S + 1) * rays_per_probe - 1.
+ */
+gi_status gi_probes_spawn_upscaled(const gi_gbuffer *gbuf, const gi_view *view, uint32_t upscale, uint32_t keep,
+                                   const gi_probes *probes, gi_stream_t stream);
+
+/*
+ * Screen-probe reprojection (Algorithm 1) into `cur` from the previous frame's probes `prev`
+ * (same layout, distinct buffers).  motion: device float2 per pixel (row-major, 8-byte aligned),
+ * the offset in pixels from the pixel centre to where its surface point was in the previous
+ * frame.  Per 8x8 tile, each non-sky pixel p looks up q = floor(p + 0.5 + motion(p)); if q is in
+ * the image and the previous level-0 mask has a probe at q's tile, that probe bids when
+ * |dot(pos_probe - pos_p, n_p)| < cell_size(d_p) (Algorithm 6's distance_scale x d_p) and
+ * dot(n_probe, n_p) > 0.95, with the score (half(|pos_probe - pos_p|) << 16) | lane, lane =
+ * 8 ly + lx; the smallest score places the tile's probe on its pixel (position and normal of that
+ * pixel), src[tile] = the previous probe's index.  A tile without bid gets no probe and
+ * src = GI_PROBE_NONE.  All decisions in float32 round-to-nearest operations (positions as in
+ * gi_probes_spawn).  Writes cur's level-0 mask, pos, nrm; the MIP chain comes with the spawn
+ * that follows (gi_probes_spawn_upscaled with keep).  src: device u32[num_probes].
+ */
+gi_status gi_probes_reproject(const gi_gbuffer *gbuf, const gi_view *view, const float *motion,
+                              const gi_probes *prev, const gi_probes *cur, uint32_t *src, gi_stream_t stream);
+
+/*
+ * The frame's probe atlas (float4[num_probes * 64], (radiance rgb, mean hit distance)) for the
+ * temporal path.  A tile whose fresh probe exists this frame (see gi_probes_spawn_upscaled)
+ * gathers its spawn tile's rays as gi_probes_gather does; when src[tile] names a previous probe,
+ * each cell's radiance is then blended with that probe's same cell in prev_atlas by the biased
+ * temporal hysteresis of Algorithm 4 (l = mean of rgb; alpha = max(l1 - l2 - min(l1, l2), 0) /
+ * max(l1, l2, 1e-4), clamped to [0, 0.95] and squared; lerp(current, previous, alpha)), keeping
+ * the fresh hit distance.  A tile with a reprojected probe and no fresh one copies the source's
+ * 64 cells; a tile with neither gets zeros.  slot_ids / ray_len: the spawn tiles' records.
+ * prev_atlas and atlas are distinct, 16-byte aligned.  gi_probes_project then gives the SH.
+ */
+gi_status gi_probes_gather_temporal(gi_cache_t cache, const gi_gbuffer *gbuf, const gi_view *view, uint32_t upscale,
+                                    const gi_probes *probes, const uint32_t *slot_ids, const float *ray_len,
+                                    uint32_t rays_per_probe, const uint32_t *src, const float *prev_atlas,
+                                    float *atlas, const float env[3], gi_stream_t stream);
 
 /*
  * Probe irradiance (Sections 2.1.4, 2.4.2): ray k of probe p is record

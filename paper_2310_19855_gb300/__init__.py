@@ -170,6 +170,13 @@ def lib() -> ctypes.CDLL:
             "gi_probes_filter": (ctypes.c_int, [ctypes.POINTER(gi_probes), ctypes.POINTER(gi_view), c_vp, c_vp, c_u32,
                                                 c_vp]),
             "gi_probes_project": (ctypes.c_int, [ctypes.POINTER(gi_probes), c_vp, c_vp]),
+            "gi_probes_spawn_upscaled": (ctypes.c_int, [ctypes.POINTER(gi_gbuffer), ctypes.POINTER(gi_view), c_u32,
+                                                        c_u32, ctypes.POINTER(gi_probes), c_vp]),
+            "gi_probes_reproject": (ctypes.c_int, [ctypes.POINTER(gi_gbuffer), ctypes.POINTER(gi_view), c_vp,
+                                                   ctypes.POINTER(gi_probes), ctypes.POINTER(gi_probes), c_vp, c_vp]),
+            "gi_probes_gather_temporal": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_gbuffer), ctypes.POINTER(gi_view),
+                                                         c_u32, ctypes.POINTER(gi_probes), c_vp, c_vp, c_u32, c_vp,
+                                                         c_vp, c_vp, ctypes.POINTER(c_f32), c_vp]),
             "gi_batch_create": (ctypes.c_int, [c_u32, c_u32, ctypes.POINTER(gi_batch_tuning), ctypes.POINTER(c_vp)]),
             "gi_batch_set_tuning": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_batch_tuning)]),
             "gi_batch_frame": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_batch_view), c_u32, c_vp]),
@@ -243,6 +250,7 @@ def hits_from_planes(planes, n: int) -> gi_hits:
     """gi_hits from a device float32 array of 13 contiguous planes of n records
     (pos xyz, nrm xyz, rad rgb, ray_len, ray_dir xyz) or from 13 plane pointers."""
     h = gi_hits()
+    h._keep = planes  # the struct holds raw pointers: keep the arrays alive as long as it lives
     if isinstance(planes, (list, tuple)):
         ptrs = [_ptr(p) for p in planes]
     else:
@@ -266,6 +274,7 @@ def make_probes(layout: gi_probe_layout, mask, pos, nrm, sh) -> gi_probes:
     p = gi_probes()
     p.layout = layout
     p.mask, p.pos, p.nrm, p.sh = _ptr(mask), _ptr(pos), _ptr(nrm), _ptr(sh)
+    p._keep = (mask, pos, nrm, sh)
     return p
 
 
@@ -379,9 +388,35 @@ def gi_probes_project(probes: gi_probes, atlas, stream=None) -> None:
     check(lib().gi_probes_project(ctypes.byref(probes), _ptr(atlas), _stream(stream)), "gi_probes_project")
 
 
+def gi_probes_spawn_upscaled(gbuf: gi_gbuffer, view: gi_view, upscale: int, keep: bool, probes: gi_probes,
+                             stream=None) -> None:
+    """Spawn with temporal upscale (one fresh probe per spawn tile of 8u x 8u pixels)."""
+    check(lib().gi_probes_spawn_upscaled(ctypes.byref(gbuf), ctypes.byref(view), int(upscale), 1 if keep else 0,
+                                         ctypes.byref(probes), _stream(stream)), "gi_probes_spawn_upscaled")
+
+
+def gi_probes_reproject(gbuf: gi_gbuffer, view: gi_view, motion, prev: gi_probes, cur: gi_probes, src,
+                        stream=None) -> None:
+    """Screen-probe reprojection (Algorithm 1) of prev into cur; src[tile] = source probe index."""
+    check(lib().gi_probes_reproject(ctypes.byref(gbuf), ctypes.byref(view), _ptr(motion), ctypes.byref(prev),
+                                    ctypes.byref(cur), _ptr(src), _stream(stream)), "gi_probes_reproject")
+
+
+def gi_probes_gather_temporal(cache: int, gbuf: gi_gbuffer, view: gi_view, upscale: int, probes: gi_probes,
+                              slot_ids, ray_len, rays_per_probe: int, src, prev_atlas, atlas, env=(0.0, 0.0, 0.0),
+                              stream=None) -> None:
+    """The frame's probe atlas: fresh probes gathered and blended by Algorithm 4, reprojected ones carried."""
+    e = (c_f32 * 3)(*[float(x) for x in env])
+    check(lib().gi_probes_gather_temporal(cache, ctypes.byref(gbuf), ctypes.byref(view), int(upscale),
+                                          ctypes.byref(probes), _ptr(slot_ids), _ptr(ray_len), int(rays_per_probe),
+                                          _ptr(src), _ptr(prev_atlas), _ptr(atlas), e, _stream(stream)),
+          "gi_probes_gather_temporal")
+
+
 def make_gbuffer(nd, width: int, height: int) -> gi_gbuffer:
     g = gi_gbuffer()
     g.nd, g.width, g.height = _ptr(nd), int(width), int(height)
+    g._keep = nd
     return g
 
 
@@ -496,6 +531,7 @@ def make_points(pos_planes, nrm_planes, n: int) -> gi_points:
         p.pos[a] = _ptr(pos_planes[a])
         p.nrm[a] = _ptr(nrm_planes[a])
     p.n = int(n)
+    p._keep = (pos_planes, nrm_planes)
     return p
 
 

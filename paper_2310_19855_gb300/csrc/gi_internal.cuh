@@ -138,13 +138,30 @@ struct SpawnArgs {
     const float4 *gbuf;
     uint32_t width, height;
     CamParams cam;
-    int jx, jy;
+    int jx, jy;            // jitter inside the spawn tile of 8 upscale x 8 upscale pixels
+    uint32_t upscale;      // 1: every 8x8 tile spawns; u: one tile per spawn tile
+    uint32_t keep;         // tiles without a fresh probe keep their level-0 mask, position, normal
     uint32_t *mask;
     float4 *pos;
     float4 *nrm;
     uint32_t tiles_x, tiles_y;
     MipInfo mi;
 };
+
+// Screen-probe reprojection (Algorithm 1).
+struct ReprojArgs {
+    const float4 *gbuf;
+    const float2 *motion;  // per pixel: offset to the previous frame's position of its surface point
+    uint32_t width, height, tiles_x, tiles_y;
+    CamParams cam;
+    float dscale;          // cell_size(d) = dscale * d
+    const uint32_t *prev_mask;
+    const float4 *prev_pos, *prev_nrm;
+    uint32_t *mask;
+    float4 *pos, *nrm;
+    uint32_t *src;         // source probe of each tile (GI_PROBE_NONE: none)
+};
+
 
 struct IntegrateArgs {
     const uint32_t *slot_ids;
@@ -160,6 +177,18 @@ struct IntegrateArgs {
     const uint32_t *ovr_bits;  // surrogate answers: bit r set -> record r takes ovr[r] (or NULL)
     const float4 *ovr;
     const float *ray_len;      // ray lengths of the records (probe atlas: mean hit distance per cell)
+};
+
+// Frame atlas of the temporal path: fresh probes gather their spawn tile's rays (blended with the
+// tile's reprojected probe by Algorithm 4), reprojected-only probes carry their source's cells.
+struct TemporalArgs {
+    IntegrateArgs g;       // records of the spawn tiles (g.probes = spawn tiles)
+    const float4 *gbuf;
+    uint32_t width, height, tiles_x, probes, upscale, spawn_x;
+    int jx, jy;
+    const uint32_t *src;
+    const float4 *prev_atlas;
+    float4 *atlas;
 };
 
 struct InterpArgs {
@@ -297,6 +326,23 @@ __device__ __forceinline__ void load_view_args(T &dst, const T *src) {
     const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
     uint32_t *d = reinterpret_cast<uint32_t *>(&dst);
     for (uint32_t i = threadIdx.x; i < sizeof(T) / 4; i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+// World position of pixel (x, y) at distance d along its camera ray, every operation in float32
+// round-to-nearest in a fixed order (no contraction): probe positions and the reprojection's
+// decisions are then reproducible bit for bit.
+__device__ __forceinline__ float3 pixel_world_exact(const CamParams &c, uint32_t x, uint32_t y, float d) {
+    const float sx = __fmul_rn(__fsub_rn(__fmul_rn(__fmul_rn(2.0f, __fadd_rn((float)x, 0.5f)), c.inv_w), 1.0f),
+                               c.sx_scale);
+    const float sy = __fmul_rn(__fsub_rn(1.0f, __fmul_rn(__fmul_rn(2.0f, __fadd_rn((float)y, 0.5f)), c.inv_h)),
+                               c.sy_scale);
+    const float dx = __fadd_rn(__fadd_rn(c.fwd[0], __fmul_rn(sx, c.right[0])), __fmul_rn(sy, c.up[0]));
+    const float dy = __fadd_rn(__fadd_rn(c.fwd[1], __fmul_rn(sx, c.right[1])), __fmul_rn(sy, c.up[1]));
+    const float dz = __fadd_rn(__fadd_rn(c.fwd[2], __fmul_rn(sx, c.right[2])), __fmul_rn(sy, c.up[2]));
+    const float ln = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
+    const float s = __fdiv_rn(d, ln);
+    return make_float3(__fadd_rn(c.pos[0], __fmul_rn(dx, s)), __fadd_rn(c.pos[1], __fmul_rn(dy, s)),
+                       __fadd_rn(c.pos[2], __fmul_rn(dz, s)));
 }
 
 __device__ __forceinline__ float3 cam_ray_dir(const CamParams &c, float x, float y) {

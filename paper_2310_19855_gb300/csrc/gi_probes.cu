@@ -144,29 +144,39 @@ gi_status ensure_moments() {
 
 // ---------------------------------------------------------------- spawn
 
-// Block of 16x16 tiles: level 0 plus levels 1..4 of its region, built in shared memory.
+// Block of 16x16 tiles: level 0 plus levels 1..4 of its region, built in shared memory.  With
+// temporal upscale u, the 8x8 tile holding the probe pixel min(8u S + jitter, image) of its spawn
+// tile S = tile / u receives the fresh probe (Section 2.1.1); with keep, the other tiles (and a
+// fresh tile whose pixel is sky) keep what level 0 holds (the reprojected probes).
 __device__ __forceinline__ void spawn_body(const SpawnArgs &a, uint32_t bx, uint32_t by) {
     __shared__ uint32_t s_lvl[2][16][16];
     const int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
     const uint32_t tx = bx * 16 + lx, ty = by * 16 + ly;
     uint32_t m = GI_PROBE_NONE;
     if (tx < a.tiles_x && ty < a.tiles_y) {
-        const uint32_t px = min(8u * tx + (uint32_t)a.jx, a.width - 1u);
-        const uint32_t py = min(8u * ty + (uint32_t)a.jy, a.height - 1u);
-        const float4 nd = __ldg(a.gbuf + (size_t)py * a.width + px);
-        const bool valid = isfinite(nd.w) && nd.w >= 0.0f;
+        const uint32_t st = 8u * a.upscale;
+        const uint32_t px = min(st * (tx / a.upscale) + (uint32_t)a.jx, a.width - 1u);
+        const uint32_t py = min(st * (ty / a.upscale) + (uint32_t)a.jy, a.height - 1u);
         const uint32_t p = ty * a.tiles_x + tx;
-        if (valid) {
+        bool fresh = false;
+        float4 nd = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((px >> 3) == tx && (py >> 3) == ty) {
+            nd = __ldg(a.gbuf + (size_t)py * a.width + px);
+            fresh = isfinite(nd.w) && nd.w >= 0.0f;
+        }
+        if (fresh) {
             m = (py << 16) | px;
-            const float3 d = cam_ray_dir(a.cam, (float)px, (float)py);
-            a.pos[p] = make_float4(a.cam.pos[0] + d.x * nd.w, a.cam.pos[1] + d.y * nd.w, a.cam.pos[2] + d.z * nd.w,
-                                   nd.w);
+            const float3 w = pixel_world_exact(a.cam, px, py, nd.w);
+            a.pos[p] = make_float4(w.x, w.y, w.z, nd.w);
             a.nrm[p] = make_float4(nd.x, nd.y, nd.z, 1.0f);
+            a.mask[p] = m;
+        } else if (a.keep) {
+            m = a.mask[p];
         } else {
             a.pos[p] = make_float4(0.f, 0.f, 0.f, 0.f);
             a.nrm[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+            a.mask[p] = m;
         }
-        a.mask[ty * a.tiles_x + tx] = m;
     }
     s_lvl[0][ly][lx] = m;
     __syncthreads();
@@ -435,6 +445,118 @@ __global__ void __launch_bounds__(256) k_project(const float4 *atlas, const floa
 }
 __global__ void __launch_bounds__(256) k_integrate_surr(IntegrateArgs a) { integrate_body<true>(a, blockIdx.x); }
 
+// ---------------------------------------------------------------- temporal path
+constexpr uint32_t kScoreNone = (0x7BFFu << 16) | 0xFFFFu;  // half(65504) << 16 | 0xFFFF
+
+__device__ __forceinline__ float dot3_rn(float ax, float ay, float az, float bx, float by, float bz) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(ax, bx), __fmul_rn(ay, by)), __fmul_rn(az, bz));
+}
+
+// Algorithm 1: four 8x8 tiles per block (one thread per pixel, lane = 8 ly + lx).  A pixel whose
+// previous position q falls on a previous probe that lies within cell_size of the pixel's plane
+// and faces within 0.95 of its normal bids (half(distance) << 16 | lane); the smallest bid places
+// the tile's probe on its pixel, carrying that previous probe.
+__global__ void __launch_bounds__(256) k_reproject(ReprojArgs a) {
+    __shared__ uint32_t s_score[4];
+    const uint32_t tl = threadIdx.x >> 6, lane = threadIdx.x & 63;
+    const uint32_t t = blockIdx.x * 4u + tl;
+    const uint32_t tx = t % a.tiles_x, ty = t / a.tiles_x;
+    if (lane == 0) s_score[tl] = kScoreNone;
+    __syncthreads();
+    const uint32_t x = 8u * tx + (lane & 7u), y = 8u * ty + (lane >> 3);
+    uint32_t my = kScoreNone, tq = 0;
+    float3 w = make_float3(0.f, 0.f, 0.f);
+    float4 nd = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ty < a.tiles_y && x < a.width && y < a.height) {
+        nd = __ldg(a.gbuf + (size_t)y * a.width + x);
+        if (isfinite(nd.w) && nd.w >= 0.0f) {
+            const float2 mv = __ldg(a.motion + (size_t)y * a.width + x);
+            const float fx = floorf(__fadd_rn(__fadd_rn((float)x, 0.5f), mv.x));
+            const float fy = floorf(__fadd_rn(__fadd_rn((float)y, 0.5f), mv.y));
+            if (fx >= 0.0f && fy >= 0.0f && fx < (float)a.width && fy < (float)a.height) {
+                tq = ((uint32_t)fy >> 3) * a.tiles_x + ((uint32_t)fx >> 3);
+                if (__ldg(a.prev_mask + tq) != GI_PROBE_NONE) {
+                    w = pixel_world_exact(a.cam, x, y, nd.w);
+                    const float4 pp = __ldg(a.prev_pos + tq), pn = __ldg(a.prev_nrm + tq);
+                    const float vx = __fsub_rn(pp.x, w.x), vy = __fsub_rn(pp.y, w.y), vz = __fsub_rn(pp.z, w.z);
+                    const float plane = fabsf(dot3_rn(vx, vy, vz, nd.x, nd.y, nd.z));
+                    const float ncheck = dot3_rn(pn.x, pn.y, pn.z, nd.x, nd.y, nd.z);
+                    if (plane < __fmul_rn(a.dscale, nd.w) && ncheck > 0.95f) {
+                        const float dist = __fsqrt_rn(dot3_rn(vx, vy, vz, vx, vy, vz));
+                        my = ((uint32_t)__half_as_ushort(__float2half_rn(dist)) << 16) | lane;
+                        atomicMin(&s_score[tl], my);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (ty >= a.tiles_y) return;
+    const uint32_t best = s_score[tl];
+    if (best == kScoreNone) {
+        if (lane == 0) {
+            a.mask[t] = GI_PROBE_NONE;
+            a.pos[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            a.nrm[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            a.src[t] = GI_PROBE_NONE;
+        }
+    } else if (my == best) {
+        a.mask[t] = (y << 16) | x;
+        a.pos[t] = make_float4(w.x, w.y, w.z, nd.w);
+        a.nrm[t] = make_float4(nd.x, nd.y, nd.z, 1.0f);
+        a.src[t] = tq;
+    }
+}
+
+// Algorithm 4 on one cell: alpha from the normalised luminance difference, squared after the clamp.
+__device__ __forceinline__ float3 temporal_blend(float3 c, float3 p) {
+    const float l1 = (c.x + c.y + c.z) * (1.0f / 3.0f);
+    const float l2 = (p.x + p.y + p.z) * (1.0f / 3.0f);
+    float al = fmaxf(l1 - l2 - fminf(l1, l2), 0.0f) / fmaxf(fmaxf(l1, l2), 1e-4f);
+    al = fminf(fmaxf(al, 0.0f), 0.95f);
+    al *= al;
+    return make_float3(c.x + al * (p.x - c.x), c.y + al * (p.y - c.y), c.z + al * (p.z - c.z));
+}
+
+// One warp per 8x8 tile: a fresh probe gathers its spawn tile's rays (the cells' radiance and hit
+// distance, as k_gather) and blends each cell with the same cell of the tile's reprojected probe;
+// a reprojected-only probe copies its source's cells; a tile without probe gets zeros.
+__global__ void __launch_bounds__(256) k_gather_temporal(TemporalArgs a) {
+    const uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= a.probes) return;
+    const uint32_t tx = t % a.tiles_x, ty = t / a.tiles_x;
+    const uint32_t st = 8u * a.upscale, sx = tx / a.upscale, sy = ty / a.upscale;
+    const uint32_t px = min(st * sx + (uint32_t)a.jx, a.width - 1u);
+    const uint32_t py = min(st * sy + (uint32_t)a.jy, a.height - 1u);
+    bool fresh = false;
+    if ((px >> 3) == tx && (py >> 3) == ty) {
+        const float d = __ldg(&a.gbuf[(size_t)py * a.width + px].w);
+        fresh = isfinite(d) && d >= 0.0f;
+    }
+    const uint32_t src = __ldg(a.src + t);
+    float4 *dst = a.atlas + (size_t)t * 64;
+    float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
+    if (fresh) {
+        float L[2][3], hd[2];
+        gather_cells<false, true>(a.g, sy * a.spawn_x + sx, lane, L, hd);
+        float3 c0 = make_float3(L[0][0], L[0][1], L[0][2]), c1 = make_float3(L[1][0], L[1][1], L[1][2]);
+        if (src != GI_PROBE_NONE) {
+            const float4 p0 = __ldg(a.prev_atlas + (size_t)src * 64 + lane);
+            const float4 p1 = __ldg(a.prev_atlas + (size_t)src * 64 + lane + 32);
+            c0 = temporal_blend(c0, make_float3(p0.x, p0.y, p0.z));
+            c1 = temporal_blend(c1, make_float3(p1.x, p1.y, p1.z));
+        }
+        o0 = make_float4(c0.x, c0.y, c0.z, hd[0]);
+        o1 = make_float4(c1.x, c1.y, c1.z, hd[1]);
+    } else if (src != GI_PROBE_NONE) {
+        o0 = __ldg(a.prev_atlas + (size_t)src * 64 + lane);
+        o1 = __ldg(a.prev_atlas + (size_t)src * 64 + lane + 32);
+    }
+    dst[lane] = o0;
+    dst[lane + 32] = o1;
+}
+
 // ---------------------------------------------------------------- interpolation
 
 // Algorithm 3 from MIP level m0 on: probe-space position (tx, ty) at that level plus the
@@ -616,15 +738,15 @@ static bool layout_matches(const gi_probe_layout &l, uint32_t w, uint32_t h) {
            l.mip_count >= 1 && l.mip_count <= GI_MAX_MIPS;
 }
 
-static int halton_times8(uint32_t i, uint32_t base) {
-    // floor(8 * radical_inverse_base(i)) with exact integer arithmetic
+static int halton_scaled(uint32_t i, uint32_t base, uint32_t scale) {
+    // floor(scale * radical_inverse_base(i)) with exact integer arithmetic
     uint64_t num = 0, den = 1;
     while (i) {
         num = num * base + i % base;
         den *= base;
         i /= base;
     }
-    return (int)((8 * num) / den);
+    return (int)((scale * num) / den);
 }
 
 
@@ -648,8 +770,10 @@ SpawnArgs spawn_args(const gi_gbuffer *gbuf, const gi_view *view, const gi_probe
     a.width = view->width;
     a.height = view->height;
     a.cam = cam_params(view);
-    a.jx = halton_times8(view->frame + 1u, 2);
-    a.jy = halton_times8(view->frame + 1u, 3);
+    a.jx = halton_scaled(view->frame + 1u, 2, 8u);
+    a.jy = halton_scaled(view->frame + 1u, 3, 8u);
+    a.upscale = 1u;
+    a.keep = 0u;
     a.mask = pr->mask;
     a.pos = reinterpret_cast<float4 *>(pr->pos);
     a.nrm = reinterpret_cast<float4 *>(pr->nrm);
@@ -950,6 +1074,99 @@ gi_status gi_probes_spawn(const gi_gbuffer *gbuf, const gi_view *view, const gi_
         s = cuda_status(cudaGetLastError(), "k_mip_tail launch");
     }
     return s;
+}
+
+gi_status gi_probes_spawn_upscaled(const gi_gbuffer *gbuf, const gi_view *view, uint32_t upscale, uint32_t keep,
+                                   const gi_probes *pr, gi_stream_t stream) {
+    gi_status s = spawn_check(gbuf, view, pr);
+    if (s != GI_OK) return s;
+    if (upscale < 1 || upscale > GI_MAX_UPSCALE) {
+        set_error("gi_probes_spawn_upscaled: upscale must be in 1..%d", GI_MAX_UPSCALE);
+        return GI_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    SpawnArgs a = spawn_args(gbuf, view, pr);
+    a.upscale = upscale;
+    a.keep = keep ? 1u : 0u;
+    a.jx = halton_scaled(view->frame + 1u, 2, 8u * upscale);
+    a.jy = halton_scaled(view->frame + 1u, 3, 8u * upscale);
+    dim3 grid((a.tiles_x + 15) / 16, (a.tiles_y + 15) / 16);
+    k_spawn<<<grid, 256, 0, st>>>(a);
+    s = cuda_status(cudaGetLastError(), "k_spawn launch");
+    if (s == GI_OK && a.mi.count > 5) {
+        k_mip_tail<<<1, 1024, 0, st>>>(pr->mask, a.mi);
+        s = cuda_status(cudaGetLastError(), "k_mip_tail launch");
+    }
+    return s;
+}
+
+gi_status gi_probes_reproject(const gi_gbuffer *gbuf, const gi_view *view, const float *motion,
+                              const gi_probes *prev, const gi_probes *cur, uint32_t *src, gi_stream_t stream) {
+    gi_status s = spawn_check(gbuf, view, cur);
+    if (s != GI_OK) return s;
+    if (!motion || !src || !prev || !prev->mask || !prev->pos || !prev->nrm || ((uintptr_t)motion & 7) ||
+        ((uintptr_t)prev->pos & 15) || ((uintptr_t)prev->nrm & 15) ||
+        prev->layout.num_probes != cur->layout.num_probes || prev->layout.tiles_x != cur->layout.tiles_x ||
+        prev->mask == cur->mask || prev->pos == cur->pos || prev->nrm == cur->nrm) {
+        set_error("gi_probes_reproject: NULL or misaligned argument, or prev and cur not two distinct probe "
+                  "buffers of the same layout");
+        return GI_ERR_INVALID_ARG;
+    }
+    ReprojArgs a;
+    a.gbuf = reinterpret_cast<const float4 *>(gbuf->nd);
+    a.motion = reinterpret_cast<const float2 *>(motion);
+    a.width = view->width;
+    a.height = view->height;
+    a.tiles_x = cur->layout.tiles_x;
+    a.tiles_y = cur->layout.tiles_y;
+    a.cam = cam_params(view);
+    a.dscale = (float)distance_scale(view->fov_y, view->width, view->height);
+    a.prev_mask = prev->mask;
+    a.prev_pos = reinterpret_cast<const float4 *>(prev->pos);
+    a.prev_nrm = reinterpret_cast<const float4 *>(prev->nrm);
+    a.mask = cur->mask;
+    a.pos = reinterpret_cast<float4 *>(cur->pos);
+    a.nrm = reinterpret_cast<float4 *>(cur->nrm);
+    a.src = src;
+    const uint32_t P = cur->layout.num_probes;
+    k_reproject<<<(P + 3) / 4, 256, 0, (cudaStream_t)stream>>>(a);
+    return cuda_status(cudaGetLastError(), "k_reproject launch");
+}
+
+gi_status gi_probes_gather_temporal(gi_cache_t cache, const gi_gbuffer *gbuf, const gi_view *view, uint32_t upscale,
+                                    const gi_probes *pr, const uint32_t *slot_ids, const float *ray_len,
+                                    uint32_t rays_per_probe, const uint32_t *src, const float *prev_atlas,
+                                    float *atlas, const float env[3], gi_stream_t stream) {
+    gi_status s = integrate_check(cache, pr, slot_ids, rays_per_probe);
+    if (s != GI_OK) return s;
+    if (!gbuf || !gbuf->nd || !view_ok(view) || gbuf->width != view->width || gbuf->height != view->height ||
+        !layout_matches(pr->layout, view->width, view->height) || !ray_len || !src || !prev_atlas || !atlas ||
+        prev_atlas == atlas || ((uintptr_t)prev_atlas & 15) || ((uintptr_t)atlas & 15) ||
+        ((uintptr_t)gbuf->nd & 15) || upscale < 1 || upscale > GI_MAX_UPSCALE) {
+        set_error("gi_probes_gather_temporal: NULL, aliased or misaligned buffer, size mismatch or bad upscale");
+        return GI_ERR_INVALID_ARG;
+    }
+    TemporalArgs a;
+    a.g = integrate_args(cache, pr, slot_ids, rays_per_probe, env);
+    a.g.ray_len = ray_len;
+    const uint32_t su = 8u * upscale;
+    a.spawn_x = (view->width + su - 1) / su;
+    a.g.probes = a.spawn_x * ((view->height + su - 1) / su);
+    a.gbuf = reinterpret_cast<const float4 *>(gbuf->nd);
+    a.width = view->width;
+    a.height = view->height;
+    a.tiles_x = pr->layout.tiles_x;
+    a.probes = pr->layout.num_probes;
+    a.upscale = upscale;
+    a.jx = halton_scaled(view->frame + 1u, 2, su);
+    a.jy = halton_scaled(view->frame + 1u, 3, su);
+    a.src = src;
+    a.prev_atlas = reinterpret_cast<const float4 *>(prev_atlas);
+    a.atlas = reinterpret_cast<float4 *>(atlas);
+    const uint32_t blocks = (a.probes + 7) / 8;
+    if (blocks == 0) return GI_OK;
+    k_gather_temporal<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    return cuda_status(cudaGetLastError(), "k_gather_temporal launch");
 }
 
 gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *pr, const uint32_t *slot_ids,

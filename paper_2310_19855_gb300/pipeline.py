@@ -8,8 +8,9 @@ import torch
 
 from . import (GI_RESOLVED_F32, GI_SH_STRIDE, gi_batch_create, gi_batch_destroy, gi_batch_frame, gi_batch_view,
                gi_cache_create, gi_cache_destroy, gi_cache_resolve, gi_cache_update, gi_probes_filter, gi_probes_gather,
-               gi_probes_integrate, gi_probes_interpolate, gi_probes_layout, gi_probes_project, gi_probes_spawn,
-               hits_from_planes, make_gbuffer, make_probes, make_view)
+               gi_probes_gather_temporal, gi_probes_integrate, gi_probes_interpolate, gi_probes_layout,
+               gi_probes_project, gi_probes_reproject, gi_probes_spawn, gi_probes_spawn_upscaled, hits_from_planes,
+               make_gbuffer, make_probes, make_view)
 
 
 def view_of(camera, frame: int):
@@ -151,6 +152,66 @@ class BatchPipeline:
             if st.get("cache"):
                 gi_cache_destroy(st["cache"])
                 st["cache"] = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TemporalPipeline:
+    """The screen-probe temporal path of one view (Sections 2.1.1-2.1.4): per frame, reprojection of
+    the previous probes (Algorithm 1), spawn with temporal upscale u, cache update + resolve on the
+    spawn tiles' rays, the frame atlas (fresh probes blended with their reprojected history by
+    Algorithm 4, reprojected probes carried), SH projection and per-pixel interpolation.  Probe
+    buffers and atlases alternate between frames."""
+
+    def __init__(self, width: int, height: int, rays_per_probe: int, log2_slots: int, upscale: int = 2,
+                 device="cuda", **cache_kw):
+        self.width, self.height, self.rpp, self.upscale = width, height, rays_per_probe, upscale
+        self.bufs = [ProbeBuffers(width, height, device), ProbeBuffers(width, height, device)]
+        for b in self.bufs:
+            b.mask.fill_(-1)
+            b.pos.zero_()
+            b.nrm.zero_()
+        P = self.bufs[0].layout.num_probes
+        self.atlases = [torch.zeros((P, 64, 4), dtype=torch.float32, device=device) for _ in range(2)]
+        self.src = torch.empty(P, dtype=torch.int32, device=device)
+        su = 8 * upscale
+        self.spawn_tiles = ((width + su - 1) // su) * ((height + su - 1) // su)
+        self.n_records = self.spawn_tiles * rays_per_probe
+        self.slot_ids = torch.empty(self.n_records, dtype=torch.int32, device=device)
+        self.irr = torch.empty((height, width, 4), dtype=torch.float32, device=device)
+        self.cache = gi_cache_create(log2_slots, **cache_kw)
+        self.k = 0
+
+    @property
+    def probes(self):
+        """The probe buffers of the latest frame."""
+        return self.bufs[self.k ^ 1]
+
+    @property
+    def atlas(self):
+        return self.atlases[self.k ^ 1]
+
+    def frame(self, gbuf, records, motion, view, env=(0.0, 0.0, 0.0), stream=None):
+        cur, prev = self.bufs[self.k], self.bufs[self.k ^ 1]
+        g = make_gbuffer(gbuf, self.width, self.height)
+        gi_probes_reproject(g, view, motion, prev.struct, cur.struct, self.src, stream)
+        gi_probes_spawn_upscaled(g, view, self.upscale, True, cur.struct, stream)
+        gi_cache_update(self.cache, hits_from_planes(records, self.n_records), view, self.slot_ids, stream)
+        gi_cache_resolve(self.cache, view.frame, stream)
+        gi_probes_gather_temporal(self.cache, g, view, self.upscale, cur.struct, self.slot_ids, records[9], self.rpp,
+                                  self.src, self.atlases[self.k ^ 1], self.atlases[self.k], env, stream)
+        gi_probes_project(cur.struct, self.atlases[self.k], stream)
+        gi_probes_interpolate(g, view, cur.struct, self.irr, stream)
+        self.k ^= 1
+
+    def close(self):
+        if self.cache:
+            gi_cache_destroy(self.cache)
+            self.cache = None
 
     def __del__(self):
         try:

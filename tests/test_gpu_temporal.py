@@ -1,0 +1,173 @@
+"""GPU parity of the screen-probe temporal path (temporal upscale, Algorithm 1, Algorithm 4) against
+oracle/temporal.py, through the C ABI.
+
+Bit-exact: probe masks (every MIP level), reprojection sources, probe positions and normals (the
+positions are float32 operation-by-operation on both sides, so every decision of Algorithm 1 is
+taken from identical values).  Within 1e-4 relative: the frame atlas (the cache's float32 radiance
+against the float64 oracle, then the continuous Algorithm 4 blend) and the probes' SH."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2310_19855_gb300 as gi
+import workload as wl
+from oracle import probes as OP
+from oracle import temporal as OT
+from oracle.cache import OracleCache
+from oracle.frame import ray_radiance
+from paper_2310_19855_gb300.pipeline import ProbeBuffers, TemporalPipeline, view_of
+
+from _gpu_util import close, dev, require_gpu, u32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+CFG = dict(wl.CONFIGS[2], width=320, height=184, n_boxes=512, room=(24.0, 8.0, 24.0), frames=8)
+SEED = wl.scene.SEED_BASE + 4300
+
+
+@pytest.fixture(scope="module")
+def frames():
+    scene = wl.make_scene(CFG, SEED)
+    return [wl.make_frame(CFG, f, scene, seed_base=SEED, upscale=2, motion=True) for f in range(5)]
+
+
+def _upload_state(st, pb: ProbeBuffers):
+    m = np.full(pb.layout.mask_words, OT.SENTINEL, np.uint32)
+    mips = OP.build_mips(st["mask"])
+    for k, lv in enumerate(mips):
+        off = pb.layout.mip_offset[k]
+        m[off:off + lv.size] = lv.reshape(-1)
+    pb.mask.copy_(torch.from_numpy(m.view(np.int32)))
+    pb.pos.copy_(torch.from_numpy(st["pos"]))
+    pb.nrm.copy_(torch.from_numpy(st["nrm"]))
+
+
+def _levels(pb: ProbeBuffers):
+    return pb.mask_levels()
+
+
+def _oracle_chain(frames, upscale=2, upto=None):
+    """Oracle states, atlases and SH of each frame (the plain cache on the spawn tiles' rays)."""
+    fr0 = frames[0]
+    st = OT.empty_state(fr0.tiles_x, fr0.tiles_y)
+    atlas = np.zeros((st["pos"].shape[0], 64, 4))
+    oc = OracleCache(18)
+    out = []
+    for fr in frames[:upto]:
+        cam = fr.camera
+        prev = st
+        st = OT.reproject(prev, fr.gbuffer, cam, fr.motion)
+        rep = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in st.items()}
+        ft = OT.spawn_fresh(st, fr.gbuffer, cam, fr.frame, upscale)
+        ident = oc.update(fr.records, fr.frame, cam.pos, cam.fov_y, cam.width, cam.height)
+        oc.resolve(fr.frame)
+        rad, has = ray_radiance(oc, fr.records, ident)
+        S = ft.size
+        atlas = OT.temporal_atlas(st, atlas, ft, rad.reshape(S, fr.rays_per_probe, 3),
+                                  has.reshape(S, fr.rays_per_probe), fr.records[9])
+        valid = OT.probe_valid(st)
+        sh = OP.project(valid, st["nrm"][:, 0:3].astype(np.float64), atlas)
+        out.append(dict(prev=prev, reproj=rep, state={k: (v.copy() if isinstance(v, np.ndarray) else v)
+                                                      for k, v in st.items()}, atlas=atlas.copy(), sh=sh, fresh=ft))
+    return out
+
+
+def test_reprojection_matches_oracle_bit_exact(frames):
+    ref = _oracle_chain(frames, upto=4)
+    fr0 = frames[0]
+    W, H = fr0.camera.width, fr0.camera.height
+    prev, cur = ProbeBuffers(W, H), ProbeBuffers(W, H)
+    src = torch.empty(prev.layout.num_probes, dtype=torch.int32, device="cuda")
+    for fr, r in zip(frames[1:4], ref[1:4]):
+        _upload_state(r["prev"], prev)
+        g = gi.make_gbuffer(dev(fr.gbuffer), W, H)
+        gi.gi_probes_reproject(g, view_of(fr.camera, fr.frame), dev(fr.motion), prev.struct, cur.struct, src)
+        torch.cuda.synchronize()
+        want = r["reproj"]
+        got_mask = cur.mask.cpu().numpy().view(np.uint32)[:cur.layout.num_probes]
+        assert np.array_equal(got_mask, want["mask"].reshape(-1))
+        assert np.array_equal(u32(src), want["src"])
+        ok = want["mask"].reshape(-1) != OT.SENTINEL
+        assert ok.sum() > 0.3 * ok.size  # the camera moves: most tiles still find a probe
+        assert np.array_equal(cur.pos.cpu().numpy()[ok], want["pos"][ok])
+        assert np.array_equal(cur.nrm.cpu().numpy()[ok], want["nrm"][ok])
+
+
+@pytest.mark.parametrize("upscale", [1, 2, 3])
+def test_spawn_upscaled_over_reprojected_tiles(frames, upscale):
+    fr = frames[2]
+    W, H = fr.camera.width, fr.camera.height
+    ref = _oracle_chain(frames, upto=3)[2]["reproj"]
+    pb = ProbeBuffers(W, H)
+    _upload_state(ref, pb)
+    g = gi.make_gbuffer(dev(fr.gbuffer), W, H)
+    gi.gi_probes_spawn_upscaled(g, view_of(fr.camera, fr.frame), upscale, True, pb.struct)
+    st = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in ref.items()}
+    ft = OT.spawn_fresh(st, fr.gbuffer, fr.camera, fr.frame, upscale)
+    assert (ft >= 0).any()
+    for got, want in zip(_levels(pb), OP.build_mips(st["mask"])):
+        assert np.array_equal(got, want)
+    ok = st["mask"].reshape(-1) != OT.SENTINEL
+    assert np.array_equal(pb.pos.cpu().numpy()[ok], st["pos"][ok])
+    assert np.array_equal(pb.nrm.cpu().numpy()[ok], st["nrm"][ok])
+
+
+def test_upscale_one_without_keep_is_the_plain_spawn(frames):
+    fr = frames[1]
+    W, H = fr.camera.width, fr.camera.height
+    a, b = ProbeBuffers(W, H), ProbeBuffers(W, H)
+    g = gi.make_gbuffer(dev(fr.gbuffer), W, H)
+    v = view_of(fr.camera, fr.frame)
+    gi.gi_probes_spawn(g, v, a.struct)
+    b.mask.fill_(7)
+    gi.gi_probes_spawn_upscaled(g, v, 1, False, b.struct)
+    torch.cuda.synchronize()
+    assert torch.equal(a.mask, b.mask) and torch.equal(a.pos, b.pos) and torch.equal(a.nrm, b.nrm)
+
+
+def test_temporal_chain_matches_oracle(frames):
+    ref = _oracle_chain(frames)
+    fr0 = frames[0]
+    W, H = fr0.camera.width, fr0.camera.height
+    tp = TemporalPipeline(W, H, fr0.rays_per_probe, 18, upscale=2)
+    try:
+        for fr, r in zip(frames, ref):
+            tp.frame(dev(fr.gbuffer), dev(fr.records), dev(fr.motion), view_of(fr.camera, fr.frame))
+            torch.cuda.synchronize()
+            pb = tp.probes
+            for got, want in zip(_levels(pb), OP.build_mips(r["state"]["mask"])):
+                assert np.array_equal(got, want)
+            assert np.array_equal(u32(tp.src), r["state"]["src"])
+            valid = OT.probe_valid(r["state"])
+            got_atlas = tp.atlas.cpu().numpy().astype(np.float64)
+            ok = close(got_atlas[..., :3], r["atlas"][..., :3])
+            assert ok.all(), (np.count_nonzero(~ok), np.abs(got_atlas[..., :3] - r["atlas"][..., :3]).max())
+            hd_g, hd_w = got_atlas[..., 3], r["atlas"][..., 3]
+            both_inf = np.isinf(hd_g) & np.isinf(hd_w)
+            assert (both_inf | close(hd_g, hd_w, rel=1e-6)).all()
+            sh = pb.sh.cpu().numpy()[:, :27].reshape(-1, 9, 3)
+            scale = np.abs(r["sh"][:, 0, :]).max(axis=1)[:, None, None]
+            err = (np.abs(sh - r["sh"]) / np.maximum(scale, 1e-12)).max(axis=(1, 2))
+            assert err[valid].max() < 1e-4
+        # after five frames of 2x2 upscale under camera motion most tiles hold a probe
+        assert valid.mean() > 0.75
+    finally:
+        tp.close()
+
+
+def test_reprojection_argument_checks(frames):
+    fr = frames[0]
+    W, H = fr.camera.width, fr.camera.height
+    pb = ProbeBuffers(W, H)
+    src = torch.empty(pb.layout.num_probes, dtype=torch.int32, device="cuda")
+    g = gi.make_gbuffer(dev(fr.gbuffer), W, H)
+    with pytest.raises(gi.GiError):  # prev and cur must be distinct buffers
+        gi.gi_probes_reproject(g, view_of(fr.camera, 0), dev(fr.motion), pb.struct, pb.struct, src)
+    with pytest.raises(gi.GiError):
+        gi.gi_probes_spawn_upscaled(g, view_of(fr.camera, 0), 0, True, pb.struct)

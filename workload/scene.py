@@ -337,16 +337,40 @@ def render_gbuffer(scene: Scene, cam: Camera):
 
 
 # --------------------------------------------------------------------------- probes
-def halton_jitter(frame: int) -> tuple[int, int]:
-    """(floor(8 H_2(frame+1)), floor(8 H_3(frame+1))) with exact integer digit reversal."""
-    def f8(i: int, b: int) -> int:
+def halton_jitter(frame: int, upscale: int = 1) -> tuple[int, int]:
+    """(floor(8u H_2(frame+1)), floor(8u H_3(frame+1))) with exact integer digit reversal: the
+    jitter inside a spawn tile of 8u x 8u pixels."""
+    def fs(i: int, b: int) -> int:
         num, den = 0, 1
         while i > 0:
             i, dgt = divmod(i, b)
             num = num * b + dgt
             den *= b
-        return (8 * num) // den
-    return f8(frame + 1, 2), f8(frame + 1, 3)
+        return (8 * upscale * num) // den
+    return fs(frame + 1, 2), fs(frame + 1, 3)
+
+
+def motion_vectors(gbuf: np.ndarray, cam: Camera, prev: Camera) -> np.ndarray:
+    """Per pixel the offset (float32, pixels) from the pixel centre to the centre position of its
+    surface point in the previous camera (static geometry); zero for sky pixels."""
+    H, W = gbuf.shape[:2]
+    d = camera_rays(cam).reshape(H, W, 3).astype(np.float64)
+    dist = gbuf[..., 3].astype(np.float64)
+    ok = np.isfinite(dist)
+    X = cam.pos.astype(np.float64) + d * np.where(ok, dist, 0.0)[..., None]
+    v = X - prev.pos.astype(np.float64)
+    z = v @ prev.fwd.astype(np.float64)
+    th = math.tan(0.5 * prev.fov_y)
+    sx = (v @ prev.right.astype(np.float64)) / (z * th * prev.width / prev.height)
+    sy = (v @ prev.up.astype(np.float64)) / (z * th)
+    xp = (sx + 1.0) * 0.5 * prev.width
+    yp = (1.0 - sy) * 0.5 * prev.height
+    ys, xs = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    mv = np.zeros((H, W, 2), np.float32)
+    good = ok & (z > 0)
+    mv[..., 0] = np.where(good, xp - (xs + 0.5), 0.0)
+    mv[..., 1] = np.where(good, yp - (ys + 0.5), 0.0)
+    return mv
 
 
 def _onb(n: np.ndarray):
@@ -394,6 +418,10 @@ class Frame:
     probe_valid: np.ndarray  # (P,) bool: the tracer found a surface under the probe pixel
     light_pos: np.ndarray
     light_I: np.ndarray
+    upscale: int = 1         # spawn tiles of 8u x 8u pixels: records belong to the spawn tiles
+    spawn_x: int = 0         # spawn tiles per row / column (the tile grid when upscale is 1)
+    spawn_y: int = 0
+    motion: np.ndarray | None = None  # (H, W, 2) float32 motion vectors to the previous frame
 
     @property
     def n_records(self) -> int:
@@ -401,9 +429,11 @@ class Frame:
 
 
 def make_frame(config, f: int, scene: Scene | None = None, rays_per_probe: int | None = None,
-               seed_base: int | None = None) -> Frame:
+               seed_base: int | None = None, upscale: int = 1, motion: bool = False) -> Frame:
     """Frame f of a configuration number or of a configuration dict (then seed_base is required;
-    the frame's random draws use seed_base + f)."""
+    the frame's random draws use seed_base + f).  With upscale u one probe per spawn tile of
+    8u x 8u pixels traces rays (records are spawn-tile major); with motion the frame carries the
+    motion vectors to frame f - 1 (zero at f = 0)."""
     cfg = CONFIGS[config] if isinstance(config, int) else config
     if seed_base is None:
         seed_base = SEED_BASE + 1000 * config
@@ -417,10 +447,12 @@ def make_frame(config, f: int, scene: Scene | None = None, rays_per_probe: int |
     rpp = rays_per_probe or cfg["rays_per_probe"]
     W, H = cam.width, cam.height
     tx_n, ty_n = (W + 7) // 8, (H + 7) // 8
-    jx, jy = halton_jitter(f)
-    tx, ty = np.meshgrid(np.arange(tx_n), np.arange(ty_n))
-    px = np.minimum(8 * tx + jx, W - 1).reshape(-1)
-    py = np.minimum(8 * ty + jy, H - 1).reshape(-1)
+    st = 8 * upscale
+    sx_n, sy_n = (W + st - 1) // st, (H + st - 1) // st
+    jx, jy = halton_jitter(f, upscale)
+    tx, ty = np.meshgrid(np.arange(sx_n), np.arange(sy_n))
+    px = np.minimum(st * tx + jx, W - 1).reshape(-1)
+    py = np.minimum(st * ty + jy, H - 1).reshape(-1)
     P = px.size
     dist = gb[py, px, 3]
     valid = np.isfinite(dist)
@@ -464,8 +496,12 @@ def make_frame(config, f: int, scene: Scene | None = None, rays_per_probe: int |
     rec[6:9] = rad.T
     rec[9] = ln
     rec[10:13] = d.T
+    mv = None
+    if motion:
+        prev_cam = _camera(scene.at_frame(max(f - 1, 0), frames), cfg, max(f - 1, 0) if cfg["moving_camera"] else 0)
+        mv = motion_vectors(gb, cam, prev_cam)
     return Frame(config if isinstance(config, int) else -1, f, cam, gb, np.ascontiguousarray(rec), rpp, tx_n, ty_n,
-                 (jx, jy), valid, lp, li)
+                 (jx, jy), valid, lp, li, upscale, sx_n, sy_n, mv)
 
 
 def make_frames(config: int, frames: int | None = None, start: int = 0, **kw):
