@@ -524,6 +524,223 @@ def run_tiles(args, gi, Pipeline, frames, dev_rec, dev_gb, views, flush, stream,
         pt.close()
 
 
+# ------------------------------------------------------------------ temporal arm (configuration 6)
+def oracle_temporal_window(frames, steps):
+    """Times the oracle's frame of the temporal path: reprojection, upscaled spawn, cache update +
+    resolve on the spawn tiles' rays, the frame atlas (Algorithm 4) and SH projection."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle.cache import OracleCache
+    from oracle import probes as OP
+    from oracle import temporal as OT
+    from oracle.frame import ray_radiance
+    import workload as wl
+    cfg = wl.CONFIGS[CONFIG]
+    oc = OracleCache(cfg["log2_slots"])
+    fr0 = frames[0]
+    st = OT.empty_state(fr0.tiles_x, fr0.tiles_y)
+    atlas = np.zeros((st["pos"].shape[0], 64, 4))
+    times = []
+    for i in range(steps):
+        fr = frames[i % len(frames)]
+        cam = fr.camera
+        t0 = time.perf_counter()
+        st = OT.reproject(st, fr.gbuffer, cam, fr.motion)
+        ft = OT.spawn_fresh(st, fr.gbuffer, cam, fr.frame, fr.upscale)
+        ident = oc.update(fr.records, i, cam.pos, cam.fov_y, cam.width, cam.height)
+        oc.resolve(i)
+        rad, has = ray_radiance(oc, fr.records, ident)
+        S = ft.size
+        atlas = OT.temporal_atlas(st, atlas, ft, rad.reshape(S, fr.rays_per_probe, 3),
+                                  has.reshape(S, fr.rays_per_probe), fr.records[9])
+        OP.project(OT.probe_valid(st), st["nrm"][:, 0:3].astype(np.float64), atlas)
+        times.append(time.perf_counter() - t0)
+    return fr0.n_records, times
+
+
+def run_temporal(args, rank, world, local_rank):
+    """Configuration 6: the 1080p boxes workload at 2x2 temporal upscale.  Per frame: reprojection
+    (Algorithm 1), upscaled spawn, cache update + resolve on the spawn tiles' rays (a quarter of
+    the probes trace), the frame atlas (fresh probes blended with their history by Algorithm 4,
+    reprojected probes carried), SH projection, per-pixel interpolation."""
+    import torch
+    import paper_2310_19855_gb300 as gi
+    from paper_2310_19855_gb300.build import build
+    from paper_2310_19855_gb300.pipeline import TemporalPipeline, view_of
+    from paper_2310_19855_gb300.replicas import aggregate_rate, barrier, max_over_ranks
+    import workload as wl
+    import workload.scene as wscene
+
+    build()
+    wscene.build_tracer()
+    torch.cuda.set_device(local_rank)
+    cfg = wl.CONFIGS[CONFIG]
+    n_frames = min(args.frames, args.steps + args.warmup)
+    frames = make_frames(n_frames, rank)
+    fr0 = frames[0]
+    W, H, R = fr0.camera.width, fr0.camera.height, fr0.n_records
+    u = fr0.upscale
+    tp = TemporalPipeline(W, H, fr0.rays_per_probe, cfg["log2_slots"], upscale=u,
+                          resolved_format=cfg["resolved_format"])
+    dev_rec = [torch.from_numpy(np.ascontiguousarray(f.records[:10])).cuda() for f in frames]
+    dev_gb = [torch.from_numpy(f.gbuffer).cuda() for f in frames]
+    dev_mv = [torch.from_numpy(f.motion).cuda() for f in frames]
+    views = [view_of(f.camera, f.frame) for f in frames]
+    gbs = [gi.make_gbuffer(g, W, H) for g in dev_gb]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    names = ["reproject", "spawn", "update", "resolve", "gather_temporal", "project", "interpolate"]
+
+    def step(i, ev=None, rec=None, gb=None, mv=None):
+        k = i % n_frames
+        rec = dev_rec[k] if rec is None else rec
+        g = gbs[k] if gb is None else gb
+        mv = dev_mv[k] if mv is None else mv
+        v = views[k]
+        cur, prev = tp.bufs[tp.k], tp.bufs[tp.k ^ 1]
+
+        def mark(j):
+            if ev is not None:
+                ev[j].record(stream)
+        mark(0)
+        gi.gi_probes_reproject(g, v, mv, prev.struct, cur.struct, tp.src, stream)
+        mark(1)
+        gi.gi_probes_spawn_upscaled(g, v, u, True, cur.struct, stream)
+        mark(2)
+        gi.gi_cache_update(tp.cache, gi.hits_from_planes(rec, R), v, tp.slot_ids, stream)
+        mark(3)
+        gi.gi_cache_resolve(tp.cache, i, stream)
+        mark(4)
+        gi.gi_probes_gather_temporal(tp.cache, g, v, u, cur.struct, tp.slot_ids, rec[9], tp.rpp, tp.src,
+                                     tp.atlases[tp.k ^ 1], tp.atlases[tp.k], stream=stream)
+        mark(5)
+        gi.gi_probes_project(cur.struct, tp.atlases[tp.k], stream)
+        mark(6)
+        gi.gi_probes_interpolate(g, v, cur.struct, tp.irr, stream)
+        mark(7)
+        tp.k ^= 1
+
+    U = distinct_cells(frames, cfg["log2_slots"], cfg["resolved_format"])
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    rebuilds0 = gi.gi_cache_stats(tp.cache)["rebuilds"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.5)
+    torch.cuda.synchronize()
+    t_start = time.perf_counter()
+    t_start_wall = time.time()
+    for j in range(args.steps):
+        flush.zero_()
+        step(args.warmup + j, evs[j])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_start
+    clk = clocks.stop(t_start_wall, time.time())
+    barrier(world)
+    per = np.array([[evs[j][k].elapsed_time(evs[j][k + 1]) for k in range(7)] for j in range(args.steps)])
+    frame_ms = per.sum(axis=1)
+    window_ms = per[:, 2:6].sum(axis=1)  # update, resolve, gather_temporal, project
+    st = gi.gi_cache_stats(tp.cache)
+    rebuilds = st["rebuilds"] - rebuilds0
+    valid = int((tp.probes.mask[:tp.probes.layout.num_probes] != -1).sum().item())
+    reproj = int((tp.src != -1).sum().item())
+
+    # ---- end to end: records, G-buffer and motion vectors from pinned host memory, irradiance back
+    h_rec = [torch.from_numpy(np.ascontiguousarray(f.records[:10])).pin_memory() for f in frames[:2]]
+    h_gb = [torch.from_numpy(f.gbuffer).pin_memory() for f in frames[:2]]
+    h_mv = [torch.from_numpy(f.motion).pin_memory() for f in frames[:2]]
+    h_out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+    d_rec, d_gb, d_mv = torch.empty_like(dev_rec[0]), torch.empty_like(dev_gb[0]), torch.empty_like(dev_mv[0])
+    d_g = gi.make_gbuffer(d_gb, W, H)
+    e_steps = max(3, min(args.steps, 10))
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e_steps)]
+    base = args.warmup + args.steps
+    for j in range(e_steps):
+        k = j % 2
+        flush.zero_()
+        e_ev[j][0].record(stream)
+        d_rec.copy_(h_rec[k], non_blocking=True)
+        d_gb.copy_(h_gb[k], non_blocking=True)
+        d_mv.copy_(h_mv[k], non_blocking=True)
+        step(base + j, None, d_rec, d_g, d_mv)
+        h_out.copy_(tp.irr, non_blocking=True)
+        e_ev[j][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = np.array([a.elapsed_time(b) for a, b in e_ev])
+    h2d = h_rec[0].numel() * 4 + h_gb[0].numel() * 4 + h_mv[0].numel() * 4
+    d2h = h_out.numel() * 4
+
+    tot = np.array(max_over_ranks([window_ms.sum(), frame_ms.sum(), t_wall, e2e_ms.sum()], world, "cuda"))
+    if rank != 0:
+        tp.close()
+        return
+    value = aggregate_rate(R, world, args.steps, tot[0] / 1e3) / 1e6
+    e2e_value = aggregate_rate(R, world, e_steps, tot[3] / 1e3) / 1e6
+    pass_ms = per.mean(axis=0)
+    peak, peak_src = _peaks()
+    P = fr0.tiles_x * fr0.tiles_y
+    X = W * H
+    S = fr0.spawn_x * fr0.spawn_y
+    alg = {
+        # per pixel the 16 B G-buffer and 8 B motion vector; per tile the previous probe (mask 4 B,
+        # position 16 B, normal 16 B) and the new one (36 B + 4 B source)
+        "reproject": X * 24 + P * (36 + 40),
+        # per tile the 16 B G-buffer texel of a fresh probe and 36 B written, the mask chain
+        "spawn": P * 52,
+        # as configuration 2, with the measured touched-cell count U of these frames
+        "update": R * 44 + float(np.mean(U)) * (32 + 64 + 4),
+        "resolve": float(np.mean(U)) * (4 + 64 + 2 * (8 if cfg["resolved_format"] == 1 else 16)),
+        # per spawn-tile ray its slot id 4 B, ray length 4 B and a 16 B resolved gather; per tile the
+        # previous atlas 1 KB read and the new one 1 KB written
+        "gather_temporal": R * 24 + P * 2048,
+        "project": P * (1024 + 16 + 112),
+        "interpolate": X * 32 + P * 144,
+    }
+    dominant = max((n for n in names if alg[n] > 0), key=lambda n: pass_ms[names.index(n)])
+    d_ms = pass_ms[names.index(dominant)]
+    achieved = alg[dominant] / (d_ms * 1e-3) / 1e9
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        Rs, ct = oracle_temporal_window(frames[:4], 3)
+        cpu = {"value": Rs * len(ct) / sum(ct) / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"3 whole frames ({Rs} records each): reprojection, upscaled spawn, update + resolve, "
+                         "frame atlas with Algorithm 4, SH projection; numpy float64 (float32 where the "
+                         "reprojection's decisions need it), one thread"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(tot[1] / args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{cfg['name']}: {W}x{H} G-buffer, 2x2 temporal upscale: {S} spawn tiles x "
+                               f"{fr0.rays_per_probe} rays = {R} hit records/frame for {P} probe tiles, "
+                               f"{cfg['n_boxes']} boxes, 2^{cfg['log2_slots']} slots; motion vectors from the "
+                               f"analytic camera ({n_frames} frames cycled)",
+                   "records_per_step": R, "pixels_per_step": X,
+                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "note": "value over update + resolve + temporal gather + SH projection; ms_per_step is the "
+                           "whole frame (reprojection ... interpolation)"},
+        "window_ms_per_step": float(tot[0] / args.steps),
+        "pass_ms": {n: float(m) for n, m in zip(names, pass_ms)},
+        "probes_valid_last_frame": valid, "probes_reprojected_last_frame": reproj, "probe_tiles": P,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": dominant, "algorithmic_bytes_per_launch": alg[dominant],
+                     "peak_source": peak_src},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": float(tot[3] / e_steps)},
+        # k_reproject, k_spawn, k_mip_tail, k_update, k_resolve, k_gather_temporal, k_project, k_interpolate
+        "gpu_launches": int(args.steps * 8 + rebuilds),
+        "rebuilds_in_timed_region": int(rebuilds),
+        "dropped_hits": int(st["dropped"]),
+        "clocks": clk,
+        "wall_s_timed": float(tot[2]),
+    }
+    print(json.dumps(line), flush=True)
+    tp.close()
+
+
 # ------------------------------------------------------------------ batched arm (many views)
 def run_batched(args, rank, world, local_rank):
     """16 views of uneven resolution per frame: batched passes replayed from a CUDA graph (launch
@@ -878,9 +1095,10 @@ def main():
     ap.add_argument("--setup-frames", type=int, default=None,
                     help="configuration 4: frames of online training before the warm-up (default: the "
                          "configuration's 128)")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5, 6],
                     help="2: boxes at 1080p (default); 3: 16 batched views; 4: Cornell box at 1080p with the "
-                         "learned surrogate; 5: boxes at 4K, 2^24 slots, FP16 resolved radiance")
+                         "learned surrogate; 5: boxes at 4K, 2^24 slots, FP16 resolved radiance; 6: boxes at "
+                         "1080p with 2x2 temporal upscale, probe reprojection and hysteresis")
     args = ap.parse_args()
     global CONFIG
     CONFIG = args.config
@@ -899,6 +1117,8 @@ def main():
             run_batched(args, rank, world, local_rank)
         elif CONFIG == 4:
             run_surrogate(args, rank, world, local_rank)
+        elif CONFIG == 6:
+            run_temporal(args, rank, world, local_rank)
         else:
             run_native(args, rank, world, local_rank)
     finally:

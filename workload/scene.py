@@ -55,6 +55,10 @@ CONFIGS = {
             evict_frames=8, frames=64, moving_camera=True, n_boxes=16384,
             room=(96.0, 20.0, 96.0), moving_emitters=3, resolved_format=1),
 }
+# The 1080p boxes workload at the paper's quarter-sample operating point: 2x2 temporal upscale (one
+# probe per 16x16 spawn tile traces 64 rays), probes reprojected from the previous frame along the
+# camera's motion vectors.
+CONFIGS[6] = dict(CONFIGS[2], name="boxes-1080p-upscale2", upscale=2, motion=True)
 
 
 # Configuration 3: 16 independent views of uneven resolution, each its own seeded scene (Cornell
@@ -429,7 +433,7 @@ class Frame:
 
 
 def make_frame(config, f: int, scene: Scene | None = None, rays_per_probe: int | None = None,
-               seed_base: int | None = None, upscale: int = 1, motion: bool = False) -> Frame:
+               seed_base: int | None = None, upscale: int | None = None, motion: bool | None = None) -> Frame:
     """Frame f of a configuration number or of a configuration dict (then seed_base is required;
     the frame's random draws use seed_base + f).  With upscale u one probe per spawn tile of
     8u x 8u pixels traces rays (records are spawn-tile major); with motion the frame carries the
@@ -439,6 +443,8 @@ def make_frame(config, f: int, scene: Scene | None = None, rays_per_probe: int |
         seed_base = SEED_BASE + 1000 * config
     if scene is None:
         scene = make_scene(config, seed_base)
+    upscale = cfg.get("upscale", 1) if upscale is None else upscale
+    motion = cfg.get("motion", False) if motion is None else motion
     frames = cfg["frames"]
     sc = scene.at_frame(f, frames)
     cam = _camera(sc, cfg, f if cfg["moving_camera"] else 0)
