@@ -40,10 +40,11 @@ REFERENCE_BUDGET_S = 90.0
 # DRAM traffic per launch of the dominant kernel from an ncu capture (profiles/), keyed by
 # "configuration:kernel" and by the source it was taken on; null when the source has changed since.
 NCU_TRAFFIC = {
-    # k_update, boxes-1080p (profiles/k_update_boxes-1080p.md): 159.6 MB read + 22.1 MB written
-    "2:update": {"bytes_per_launch": 181652736, "source": "gi_cache.cu", "source_sha": "d54abd387582618e"},
+    # k_update, boxes-1080p (profiles/k_update_boxes-1080p.md): 159.6 MB read + 21.4 MB written
+    "2:update": {"bytes_per_launch": 180966912, "sources": ("gi_cache.cu", "gi_cache_dev.cuh", "gi_internal.cuh"),
+                 "source_sha": "af27052fbc1da58c"},
     # k_nrc_adam_table, Cornell 1080p (profiles/nrc_training_cornell-1080p.md): 3.22 TB/s x 40.16 us
-    "4:adam_table": {"bytes_per_launch": 129501000, "source": "gi_nrc.cu", "source_sha": "94a0221974ed412e"},
+    "4:adam_table": {"bytes_per_launch": 129501000, "sources": ("gi_nrc.cu",), "source_sha": "94a0221974ed412e"},
 }
 
 
@@ -51,12 +52,15 @@ def ncu_traffic(key):
     tr = NCU_TRAFFIC.get(key)
     if not tr:
         return None
-    src = os.path.join(ROOT, "paper_2310_19855_gb300", "csrc", tr["source"])
-    return tr["bytes_per_launch"] if _source_sha(src) == tr["source_sha"] else None
+    srcs = [os.path.join(ROOT, "paper_2310_19855_gb300", "csrc", f) for f in tr["sources"]]
+    return tr["bytes_per_launch"] if _source_sha(srcs) == tr["source_sha"] else None
 
 
-def _source_sha(path):
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+def _source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
