@@ -459,6 +459,22 @@ def run_native(args, rank, world, local_rank):
 
 
 TILE_LOG2 = 18      # tile slots of the two-level cache at 1080p (64 cells each)
+
+
+def tile_bytes(R, touched_tiles, touched_cells, live_in_touched, res_b, tile_slots):
+    """Algorithmic bytes of the tile cache's update (k_tile_key + k_tile_compact +
+    k_tile_accumulate) and resolve (k_tile_resolve) for one frame."""
+    # update: records 40 B in and the slot id 4 B out, then slot id + radiance 16 B in again; per
+    # touched tile a 32 B tag sector, its 8 B mask set, its block index and list entry 8 B written;
+    # per touched cell the 32 B accumulator read and written; the compaction scans 12 B (mask +
+    # block index) per slot
+    upd = R * (44 + 16) + touched_tiles * (32 + 8 + 8) + touched_cells * 64 + tile_slots * 12
+    # resolve: per touched tile the list entry 4 B, masks 8 + 8 B read and 8 + 8 B + 4 B index
+    # written, 256 B of stamps, 336 B of MIP values written; per touched cell the accumulator read +
+    # cleared, state and stamp written; per live cell of a touched tile its state read and its
+    # answer written
+    res = touched_tiles * (4 + 16 + 20 + 256 + 336) + touched_cells * (64 + 20) + live_in_touched * (16 + res_b)
+    return upd, res
 TILE_MIN_SAMPLES = 16
 
 
@@ -514,17 +530,7 @@ def run_tiles(args, gi, Pipeline, frames, dev_rec, dev_gb, views, flush, stream,
         live_in_touched = int(np.isin(ex["slot"] >> 6, touched_tiles).sum())
         res_b = 8 if cfg["resolved_format"] == 1 else 16
         Tt = float(touched_tiles.size)
-        T_slots = float(1 << TILE_LOG2)
-        # update (k_tile_key + k_tile_compact + k_tile_accumulate): records 40 B in and the slot id
-        # 4 B out, then slot id + radiance 16 B in again; per touched tile a 32 B tag sector, its 8 B
-        # mask set, its block index and list entry 8 B written; per touched cell the 32 B
-        # accumulator read and written; the compaction scans 12 B (mask + block index) per slot
-        upd_b = R * (44 + 16) + Tt * (32 + 8 + 8) + touched_cells * 64 + T_slots * 12
-        # resolve: per touched tile the list entry 4 B, masks 8 + 8 B read and 8 + 8 B + 4 B index
-        # written, 256 B of stamps, 336 B of MIP values written; per touched cell the accumulator
-        # read + cleared, state and stamp written; per live cell of a touched tile its state read
-        # and its answer written
-        res_bytes = Tt * (4 + 16 + 20 + 256 + 336) + touched_cells * (64 + 20) + live_in_touched * (16 + res_b)
+        upd_b, res_bytes = tile_bytes(R, Tt, touched_cells, live_in_touched, res_b, float(1 << TILE_LOG2))
         return {
             "note": "gi_cache_create(tiles=1): 2^%d tile slots of 8 x 8 cells, min_samples %d; spawn untimed, "
                     "update + resolve + probe irradiance per pass, L2 flushed per frame" % (TILE_LOG2, TILE_MIN_SAMPLES),
@@ -599,8 +605,13 @@ def run_temporal(args, rank, world, local_rank):
     fr0 = frames[0]
     W, H, R = fr0.camera.width, fr0.camera.height, fr0.n_records
     u = fr0.upscale
-    tp = TemporalPipeline(W, H, fr0.rays_per_probe, cfg["log2_slots"], upscale=u,
-                          resolved_format=cfg["resolved_format"])
+    tiles = bool(cfg.get("tiles", False))
+    filtered = bool(cfg.get("filtered", False))
+    log2 = cfg["log2_tiles"] if tiles else cfg["log2_slots"]
+    cache_kw = dict(resolved_format=cfg["resolved_format"])
+    if tiles:
+        cache_kw.update(tiles=True, min_samples=cfg["min_samples"])
+    tp = TemporalPipeline(W, H, fr0.rays_per_probe, log2, upscale=u, filtered=filtered, **cache_kw)
     dev_rec = [torch.from_numpy(np.ascontiguousarray(f.records[:10])).cuda() for f in frames]
     dev_gb = [torch.from_numpy(f.gbuffer).cuda() for f in frames]
     dev_mv = [torch.from_numpy(f.motion).cuda() for f in frames]
@@ -608,7 +619,10 @@ def run_temporal(args, rank, world, local_rank):
     gbs = [gi.make_gbuffer(g, W, H) for g in dev_gb]
     flush = L2Flush(torch)
     stream = torch.cuda.current_stream()
-    names = ["reproject", "spawn", "update", "resolve", "gather_temporal", "project", "interpolate"]
+    names = ["reproject", "spawn", "update", "resolve", "gather_temporal"]
+    names += ["filter_x", "filter_y"] if filtered else []
+    names += ["project", "interpolate"]
+    n_ev = len(names) + 1
 
     def step(i, ev=None, rec=None, gb=None, mv=None):
         k = i % n_frames
@@ -633,10 +647,17 @@ def run_temporal(args, rank, world, local_rank):
         gi.gi_probes_gather_temporal(tp.cache, g, v, u, cur.struct, tp.slot_ids, rec[9], tp.rpp, tp.src,
                                      tp.atlases[tp.k ^ 1], tp.atlases[tp.k], stream=stream)
         mark(5)
-        gi.gi_probes_project(cur.struct, tp.atlases[tp.k], stream)
-        mark(6)
+        shown, j = tp.atlases[tp.k], 6
+        if filtered:
+            gi.gi_probes_filter(cur.struct, v, shown, tp.filt[0], 0, stream)
+            mark(6)
+            gi.gi_probes_filter(cur.struct, v, tp.filt[0], tp.filt[1], 1, stream)
+            mark(7)
+            shown, j = tp.filt[1], 8
+        gi.gi_probes_project(cur.struct, shown, stream)
+        mark(j)
         gi.gi_probes_interpolate(g, v, cur.struct, tp.irr, stream)
-        mark(7)
+        mark(j + 1)
         tp.k ^= 1
 
     U = distinct_cells(frames, cfg["log2_slots"], cfg["resolved_format"])
@@ -644,7 +665,7 @@ def run_temporal(args, rank, world, local_rank):
         step(i)
     torch.cuda.synchronize()
     rebuilds0 = gi.gi_cache_stats(tp.cache)["rebuilds"]
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
     clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     barrier(world)
     torch.cuda.synchronize()
@@ -660,9 +681,10 @@ def run_temporal(args, rank, world, local_rank):
     t_wall = time.perf_counter() - t_start
     clk = clocks.stop(t_start_wall, time.time())
     barrier(world)
-    per = np.array([[evs[j][k].elapsed_time(evs[j][k + 1]) for k in range(7)] for j in range(args.steps)])
+    per = np.array([[evs[j][k].elapsed_time(evs[j][k + 1]) for k in range(len(names))] for j in range(args.steps)])
     frame_ms = per.sum(axis=1)
-    window_ms = per[:, 2:6].sum(axis=1)  # update, resolve, gather_temporal, project
+    # update, resolve, temporal gather (+ filter), projection
+    window_ms = per[:, names.index("update"):names.index("project") + 1].sum(axis=1)
     st = gi.gi_cache_stats(tp.cache)
     rebuilds = st["rebuilds"] - rebuilds0
     valid = int((tp.probes.mask[:tp.probes.layout.num_probes] != -1).sum().item())
@@ -719,6 +741,26 @@ def run_temporal(args, rank, world, local_rank):
         "project": P * (1024 + 16 + 112),
         "interpolate": X * 32 + P * 144,
     }
+    if filtered:
+        # per probe and cell the 16 B atlas entry read and written, 32 B of probe data per probe
+        alg["filter_x"] = alg["filter_y"] = P * 64 * 32 + P * 32
+    if tiles:
+        # one more frame, counted: touched tiles and cells, live cells of the touched tiles
+        i = args.warmup + args.steps + e_steps
+        k = i % n_frames
+        cur, prev = tp.bufs[tp.k], tp.bufs[tp.k ^ 1]
+        gi.gi_probes_reproject(gbs[k], views[k], dev_mv[k], prev.struct, cur.struct, tp.src, stream)
+        gi.gi_probes_spawn_upscaled(gbs[k], views[k], u, True, cur.struct, stream)
+        gi.gi_cache_update(tp.cache, gi.hits_from_planes(dev_rec[k], R), views[k], tp.slot_ids, stream)
+        ids = tp.slot_ids.cpu().numpy().view(np.uint32)
+        ids = ids[ids < (1 << log2) * 64]
+        touched_tiles = np.unique(ids >> 6)
+        gi.gi_cache_resolve(tp.cache, i, stream)
+        ex = gi.gi_cache_export(tp.cache)
+        live_in = int(np.isin(ex["slot"] >> 6, touched_tiles).sum())
+        ub, rb = tile_bytes(R, float(touched_tiles.size), int(np.unique(ids).size), live_in,
+                            8 if cfg["resolved_format"] == 1 else 16, float(1 << log2))
+        alg["update"], alg["resolve"] = ub, rb
     dominant = max((n for n in names if alg[n] > 0), key=lambda n: pass_ms[names.index(n)])
     d_ms = pass_ms[names.index(dominant)]
     achieved = alg[dominant] / (d_ms * 1e-3) / 1e9
@@ -735,12 +777,15 @@ def run_temporal(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{cfg['name']}: {W}x{H} G-buffer, 2x2 temporal upscale: {S} spawn tiles x "
                                f"{fr0.rays_per_probe} rays = {R} hit records/frame for {P} probe tiles, "
-                               f"{cfg['n_boxes']} boxes, 2^{cfg['log2_slots']} slots; motion vectors from the "
-                               f"analytic camera ({n_frames} frames cycled)",
+                               f"{cfg['n_boxes']} boxes, "
+                               + (f"two-level cache of 2^{log2} tiles (min_samples {cfg['min_samples']}), "
+                                  if tiles else f"2^{log2} slots, ")
+                               + ("probe filter (Algorithm 5), " if filtered else "")
+                               + f"motion vectors from the analytic camera ({n_frames} frames cycled)",
                    "records_per_step": R, "pixels_per_step": X,
                    "l2": L2_NOTE,
-                   "note": "value over update + resolve + temporal gather + SH projection; ms_per_step is the "
-                           "whole frame (reprojection ... interpolation)"},
+                   "note": "value over update + resolve + temporal gather (+ filter) + SH projection; "
+                           "ms_per_step is the whole frame (reprojection ... interpolation)"},
         "window_ms_per_step": float(tot[0] / args.steps),
         "pass_ms": {n: float(m) for n, m in zip(names, pass_ms)},
         "probes_valid_last_frame": valid, "probes_reprojected_last_frame": reproj, "probe_tiles": P,
@@ -750,8 +795,9 @@ def run_temporal(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": float(tot[3] / e_steps)},
-        # k_reproject, k_spawn, k_mip_tail, k_update, k_resolve, k_gather_temporal, k_project, k_interpolate
-        "gpu_launches": int(args.steps * 8 + rebuilds),
+        # k_reproject, k_spawn, k_mip_tail, the update (1 kernel, or 3 for tiles), the resolve,
+        # k_gather_temporal, (2 x k_filter,) k_project, k_interpolate
+        "gpu_launches": int(args.steps * (8 + (2 if tiles else 0) + (2 if filtered else 0)) + rebuilds),
         "rebuilds_in_timed_region": int(rebuilds),
         "dropped_hits": int(st["dropped"]),
         "clocks": clk,
@@ -1115,10 +1161,11 @@ def main():
     ap.add_argument("--setup-frames", type=int, default=None,
                     help="configuration 4: frames of online training before the warm-up (default: the "
                          "configuration's 128)")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5, 6],
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5, 6, 7],
                     help="2: boxes at 1080p (default); 3: 16 batched views; 4: Cornell box at 1080p with the "
                          "learned surrogate; 5: boxes at 4K, 2^24 slots, FP16 resolved radiance; 6: boxes at "
-                         "1080p with 2x2 temporal upscale, probe reprojection and hysteresis")
+                         "1080p with 2x2 temporal upscale, probe reprojection and hysteresis; 7: as 6 with the "
+                         "two-level tile cache and the probe filter (the paper's whole chain)")
     args = ap.parse_args()
     global CONFIG
     CONFIG = args.config
@@ -1137,7 +1184,7 @@ def main():
             run_batched(args, rank, world, local_rank)
         elif CONFIG == 4:
             run_surrogate(args, rank, world, local_rank)
-        elif CONFIG == 6:
+        elif CONFIG in (6, 7):
             run_temporal(args, rank, world, local_rank)
         else:
             run_native(args, rank, world, local_rank)

@@ -168,8 +168,12 @@ class TemporalPipeline:
     buffers and atlases alternate between frames."""
 
     def __init__(self, width: int, height: int, rays_per_probe: int, log2_slots: int, upscale: int = 2,
-                 device="cuda", **cache_kw):
+                 filtered: bool = False, device="cuda", **cache_kw):
+        """filtered: the frame atlas goes through the probe filter (Algorithm 5, an x then a y pass)
+        before the SH projection; the unfiltered atlas stays the next frame's history.  cache_kw
+        go to gi_cache_create (tiles=True gives the two-level cache, log2_slots then counts tiles)."""
         self.width, self.height, self.rpp, self.upscale = width, height, rays_per_probe, upscale
+        self.filtered = filtered
         self.bufs = [ProbeBuffers(width, height, device), ProbeBuffers(width, height, device)]
         for b in self.bufs:
             b.mask.fill_(-1)
@@ -177,6 +181,7 @@ class TemporalPipeline:
             b.nrm.zero_()
         P = self.bufs[0].layout.num_probes
         self.atlases = [torch.zeros((P, 64, 4), dtype=torch.float32, device=device) for _ in range(2)]
+        self.filt = [torch.zeros((P, 64, 4), dtype=torch.float32, device=device) for _ in range(2)] if filtered else None
         self.src = torch.empty(P, dtype=torch.int32, device=device)
         su = 8 * upscale
         self.spawn_tiles = ((width + su - 1) // su) * ((height + su - 1) // su)
@@ -204,7 +209,12 @@ class TemporalPipeline:
         gi_cache_resolve(self.cache, view.frame, stream)
         gi_probes_gather_temporal(self.cache, g, view, self.upscale, cur.struct, self.slot_ids, records[9], self.rpp,
                                   self.src, self.atlases[self.k ^ 1], self.atlases[self.k], env, stream)
-        gi_probes_project(cur.struct, self.atlases[self.k], stream)
+        shown = self.atlases[self.k]
+        if self.filtered:
+            gi_probes_filter(cur.struct, view, shown, self.filt[0], 0, stream)
+            gi_probes_filter(cur.struct, view, self.filt[0], self.filt[1], 1, stream)
+            shown = self.filt[1]
+        gi_probes_project(cur.struct, shown, stream)
         gi_probes_interpolate(g, view, cur.struct, self.irr, stream)
         self.k ^= 1
 

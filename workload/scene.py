@@ -59,6 +59,10 @@ CONFIGS = {
 # probe per 16x16 spawn tile traces 64 rays), probes reprojected from the previous frame along the
 # camera's motion vectors.
 CONFIGS[6] = dict(CONFIGS[2], name="boxes-1080p-upscale2", upscale=2, motion=True)
+# The paper's whole chain at that operating point: configuration 6 with the two-level world cache
+# (8x8 tiles with MIP levels, 2^18 tile slots, min_samples 16) and the probe filter (Algorithm 5).
+CONFIGS[7] = dict(CONFIGS[6], name="boxes-1080p-upscale2-tiles-filtered", tiles=True, log2_tiles=18,
+                  min_samples=16, filtered=True)
 
 
 # Configuration 3: 16 independent views of uneven resolution, each its own seeded scene (Cornell
