@@ -106,7 +106,9 @@ static void cell_moments_closed_form(int c, double out[10]) {
 }
 
 // Local unit direction of each cell's centre (u, v) = (-1 + (i + 1/2)/4, -1 + (j + 1/2)/4), cell 8 j + i.
-__constant__ float c_cell_dir[64][3];
+// In global memory (read through the read-only cache): the filter reads it at a different index in
+// every lane, which the constant cache would serialise.
+__device__ float g_cell_dir[64][3];
 // cos(pi / 50): the angle-error threshold of the probe filter (Algorithm 5)
 __constant__ float c_filter_cos;
 
@@ -136,7 +138,7 @@ gi_status ensure_moments() {
         dirs[c][2] = (float)(z / n);
     }
     const float fc = (float)cos(3.14159265358979323846 / 50.0);
-    if (s == GI_OK) s = cuda_status(cudaMemcpyToSymbol(c_cell_dir, dirs, sizeof dirs), "upload cell directions");
+    if (s == GI_OK) s = cuda_status(cudaMemcpyToSymbol(g_cell_dir, dirs, sizeof dirs), "upload cell directions");
     if (s == GI_OK) s = cuda_status(cudaMemcpyToSymbol(c_filter_cos, &fc, sizeof fc), "upload filter threshold");
     if (s == GI_OK && dev >= 0 && dev < 64) g_moments_ready[dev] = true;
     return s;
@@ -930,7 +932,7 @@ __global__ void __launch_bounds__(64 * kFiltProbes) k_filter(FilterArgs a) {
     const float bb = nx * ny * ia;
     const float t0 = 1.0f + sgn * nx * nx * ia, t1 = sgn * bb, t2 = -sgn * nx;
     const float b0 = bb, b1 = sgn + ny * ny * ia, b2 = -ny;
-    const float lx = c_cell_dir[c][0], ly = c_cell_dir[c][1], lz = c_cell_dir[c][2];
+    const float lx = __ldg(&g_cell_dir[c][0]), ly = __ldg(&g_cell_dir[c][1]), lz = __ldg(&g_cell_dir[c][2]);
     const float dx = lx * t0 + ly * b0 + lz * nx, dy = lx * t1 + ly * b1 + lz * ny, dz = lx * t2 + ly * b2 + lz * nz;
     const float cos2 = c_filter_cos * c_filter_cos;
     float r = v.x, gch = v.y, bch = v.z, acc_a = v.w, weight = 1.0f, hd = v.w;
