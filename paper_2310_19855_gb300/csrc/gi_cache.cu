@@ -238,7 +238,7 @@ __device__ __forceinline__ void resolve_list_body(const ResolveArgs &a, uint32_t
         }
         resolve_slots(a, s, fresh_new);
     }
-    resolve_finish(a.ctr, a.occ_out, a.stamp_now, nblk, fresh_new);
+    resolve_finish(a.ctr, a.occ_out, a.stamp_now, nblk * (kResThreads / 32), fresh_new);
 }
 
 // bitmap form: a thread takes a word (32 consecutive slots), clears it and resolves its set bits
@@ -260,7 +260,7 @@ __device__ __forceinline__ void resolve_bm_body(const ResolveArgs &a, uint32_t b
             resolve_slots(a, s, fresh_new);
         }
     }
-    resolve_finish(a.ctr, a.occ_out, a.stamp_now, nblk, fresh_new);
+    resolve_finish(a.ctr, a.occ_out, a.stamp_now, nblk * (kResThreads / 32), fresh_new);
 }
 
 __device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {

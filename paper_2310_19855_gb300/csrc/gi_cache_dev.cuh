@@ -113,33 +113,25 @@ __device__ __forceinline__ bool answers(uint32_t stamp, const LiveRule &r) {
     return stamp != 0u && (!r.has_lr || (r.lr - (stamp - 1u)) < r.evict);
 }
 
-// Block totals of newly occupied slots, then the last block (ticket) resets the touch count and
-// publishes the occupancy, followed by the frame it belongs to, to host-mapped memory.
-__device__ __forceinline__ void resolve_finish(Counters *ctr, uint32_t *occ_out, uint32_t stamp_now, uint32_t nblk,
+// Newly occupied slots added per warp, then the last warp to finish (a ticket over all nwarps
+// warps of the launch) resets the touch count and publishes the occupancy, followed by the frame it
+// belongs to, to host-mapped memory.  No block barrier: a warp never waits for the others.
+__device__ __forceinline__ void resolve_finish(Counters *ctr, uint32_t *occ_out, uint32_t stamp_now, uint32_t nwarps,
                                                uint32_t fresh_new) {
-    __shared__ uint32_t s_new;
-    __shared__ bool s_last;
-    if (threadIdx.x == 0) s_new = 0;
-    __syncthreads();
     fresh_new = __reduce_add_sync(kFull, fresh_new);
-    if ((threadIdx.x & 31) == 0 && fresh_new) atomicAdd(&s_new, fresh_new);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_new) atomicAdd(&ctr->occupied, s_new);
+    if ((threadIdx.x & 31) == 0) {
+        if (fresh_new) atomicAdd(&ctr->occupied, fresh_new);
         __threadfence();
-        const uint32_t t = atomicAdd(&ctr->ticket, 1u);
-        s_last = (t == nblk - 1u);
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        // every block has read the touch count: reset it for the next frame
-        ctr->touch_count = 0u;
-        ctr->ticket = 0u;
-        // occupancy for the host's compaction decision, then the frame it belongs to
-        if (occ_out) {
-            reinterpret_cast<volatile uint32_t *>(occ_out)[0] = atomicAdd(&ctr->occupied, 0u);
-            __threadfence_system();
-            reinterpret_cast<volatile uint32_t *>(occ_out)[1] = stamp_now;
+        if (atomicAdd(&ctr->ticket, 1u) == nwarps - 1u) {
+            // every warp has read the touch count: reset it for the next frame
+            ctr->touch_count = 0u;
+            ctr->ticket = 0u;
+            // occupancy for the host's compaction decision, then the frame it belongs to
+            if (occ_out) {
+                reinterpret_cast<volatile uint32_t *>(occ_out)[0] = atomicAdd(&ctr->occupied, 0u);
+                __threadfence_system();
+                reinterpret_cast<volatile uint32_t *>(occ_out)[1] = stamp_now;
+            }
         }
     }
 }

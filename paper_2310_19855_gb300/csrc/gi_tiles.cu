@@ -436,18 +436,7 @@ __global__ void __launch_bounds__(kTileResThreads) k_tile_resolve(TileResolveArg
         o = on;
     }
     // the last warp to finish resets the block counter and publishes the occupancy
-    if (lane == 0) {
-        __threadfence();
-        if (atomicAdd(&a.ctr->ticket, 1u) == nwarps - 1u) {
-            a.ctr->touch_count = 0u;
-            a.ctr->ticket = 0u;
-            if (a.occ_out) {
-                reinterpret_cast<volatile uint32_t *>(a.occ_out)[0] = atomicAdd(&a.ctr->occupied, 0u);
-                __threadfence_system();
-                reinterpret_cast<volatile uint32_t *>(a.occ_out)[1] = a.stamp_now;
-            }
-        }
-    }
+    resolve_finish(a.ctr, a.occ_out, a.stamp_now, nwarps, 0u);
 }
 
 // ---------------------------------------------------------------- lookup by point
