@@ -584,6 +584,26 @@ __device__ __forceinline__ uint32_t pick_u4(const uint32_t (&v)[4], int i) {
     return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
 }
 
+// Terms of neighbour probe q (packed pixel) for a pixel with normal n: its distance along n from
+// the camera, t_q (d_q . n), through the camera basis projected on n (fn, rn, un), and the
+// normal weight max(0, n . n_q)^8.
+__device__ __forceinline__ void neighbour_terms(const InterpArgs &a, uint32_t q, float nx, float ny, float nz, float fn,
+                                                float rn, float un, float &qn, float &n8) {
+    const uint32_t pidx = (q >> 19) * a.tiles_x + ((q & 0xFFFFu) >> 3);
+    const float tq = __ldg(a.ppos + pidx).w;
+    const float4 nq = __ldg(a.pnrm + pidx);
+    const float qpx = (float)(q & 0xFFFFu), qpy = (float)(q >> 16);
+    const float sxq = (2.0f * (qpx + 0.5f) * a.cam.inv_w - 1.0f) * a.cam.sx_scale;
+    const float syq = (1.0f - 2.0f * (qpy + 0.5f) * a.cam.inv_h) * a.cam.sy_scale;
+    const float vx = a.cam.fwd[0] + sxq * a.cam.right[0] + syq * a.cam.up[0];
+    const float vy = a.cam.fwd[1] + sxq * a.cam.right[1] + syq * a.cam.up[1];
+    const float vz = a.cam.fwd[2] + sxq * a.cam.right[2] + syq * a.cam.up[2];
+    qn = tq * (fn + sxq * rn + syq * un) * rsqrtf(vx * vx + vy * vy + vz * vz);
+    const float nd1 = fmaxf(nx * nq.x + ny * nq.y + nz * nq.z, 0.0f);
+    const float n2 = nd1 * nd1, n4 = n2 * n2;
+    n8 = n4 * n4;
+}
+
 // Block = 16x16 pixels starting at (16 bx - 4, 16 by - 4); warp = 8x4 pixels that
 // share one base tile, so the four neighbour probes are warp-uniform loads.
 __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t bx, uint32_t by) {
@@ -672,10 +692,6 @@ __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t b
                 for (int cc = 0; cc < 3; ++cc) Eo[oo][cc] += Yb[k] * c[3 * k + cc];
         }
     }
-    if (!act) {
-        if (inb) __stcs(a.out + pix, make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
-        return;
-    }
     // Plane distance of neighbour q from the pixel's plane, relative to the camera (the camera
     // origin cancels): (P_q - P_p) . n_p = t_q (d_q . n_p) - t_p (d_p . n_p), with
     // d = v / |v|, v = fwd + sx right + sy up.  Only the projections of fwd, right and up on n_p
@@ -683,6 +699,23 @@ __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t b
     const float fn = a.cam.fwd[0] * nx + a.cam.fwd[1] * ny + a.cam.fwd[2] * nz;
     const float rn = a.cam.right[0] * nx + a.cam.right[1] * ny + a.cam.right[2] * nz;
     const float un = a.cam.up[0] * nx + a.cam.up[1] * ny + a.cam.up[2] * nz;
+    // a uniform warp (one normal, the same four neighbours) computes the neighbours' terms once, in
+    // lanes 0..3, and broadcasts them (while every lane of the warp is still here)
+    float qn_s[4] = {0.f, 0.f, 0.f, 0.f}, n8_s[4] = {0.f, 0.f, 0.f, 0.f};
+    if (uniform) {
+        float qn_u = 0.f, n8_u = 0.f;
+        const uint32_t qo = pick_u4(qs, lane & 3);
+        if (lane < 4 && qo != GI_PROBE_NONE) neighbour_terms(a, qo, nx, ny, nz, fn, rn, un, qn_u, n8_u);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            qn_s[o] = __shfl_sync(kFullMask, qn_u, o);
+            n8_s[o] = __shfl_sync(kFullMask, n8_u, o);
+        }
+    }
+    if (!act) {
+        if (inb) __stcs(a.out + pix, make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
+        return;
+    }
     const float inv_cs = 1.0f / (a.dscale * nd.w);
     float pn;  // t_p (d_p . n_p)
     {
@@ -696,20 +729,10 @@ __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t b
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
         if (q[o] == GI_PROBE_NONE) continue;
-        const uint32_t pidx = (q[o] >> 19) * a.tiles_x + ((q[o] & 0xFFFFu) >> 3);
-        const float tq = __ldg(a.ppos + pidx).w;
-        const float4 nq = __ldg(a.pnrm + pidx);
+        float qn = qn_s[o], n8 = n8_s[o];
+        if (!uniform) neighbour_terms(a, q[o], nx, ny, nz, fn, rn, un, qn, n8);
         const int ox = o & 1, oy = o >> 1;
-        const float qpx = (float)(q[o] & 0xFFFFu), qpy = (float)(q[o] >> 16);
-        const float sxq = (2.0f * (qpx + 0.5f) * a.cam.inv_w - 1.0f) * a.cam.sx_scale;
-        const float syq = (1.0f - 2.0f * (qpy + 0.5f) * a.cam.inv_h) * a.cam.sy_scale;
-        const float vx = a.cam.fwd[0] + sxq * a.cam.right[0] + syq * a.cam.up[0];
-        const float vy = a.cam.fwd[1] + sxq * a.cam.right[1] + syq * a.cam.up[1];
-        const float vz = a.cam.fwd[2] + sxq * a.cam.right[2] + syq * a.cam.up[2];
-        const float qn = tq * (fn + sxq * rn + syq * un) * rsqrtf(vx * vx + vy * vy + vz * vz);
         const float bil = (ox ? fx : 1.0f - fx) * (oy ? fy : 1.0f - fy);
-        const float nd1 = fmaxf(nx * nq.x + ny * nq.y + nz * nq.z, 0.0f);
-        const float n2 = nd1 * nd1, n4 = n2 * n2, n8 = n4 * n4;
         const float wd = fmaxf(1.0f - fabsf(qn - pn) * inv_cs, 0.0f);
         const float w = bil * n8 * wd;
         wsum += w;
