@@ -507,7 +507,6 @@ def run_native(args, rank, world, local_rank):
     pl.close()
 
 
-TILE_LOG2 = 18      # tile slots of the two-level cache at 1080p (64 cells each)
 
 
 def tile_bytes(R, touched_tiles, touched_cells, live_in_touched, res_b, tile_slots):
@@ -536,7 +535,8 @@ def run_tiles(args, gi, Pipeline, frames, dev_rec, dev_gb, views, flush, stream,
     fr0 = frames[0]
     W, H = fr0.camera.width, fr0.camera.height
     n_frames = len(frames)
-    pt = Pipeline(W, H, fr0.rays_per_probe, TILE_LOG2, resolved_format=cfg["resolved_format"], tiles=True,
+    log2_tiles = cfg["log2_tiles"]  # 2^18 tile slots of 64 cells at 1080p, 2^20 at 4K
+    pt = Pipeline(W, H, fr0.rays_per_probe, log2_tiles, resolved_format=cfg["resolved_format"], tiles=True,
                   min_samples=TILE_MIN_SAMPLES)
     try:
         def frame(i, ev=None):
@@ -570,7 +570,7 @@ def run_tiles(args, gi, Pipeline, frames, dev_rec, dev_gb, views, flush, stream,
         gi.gi_cache_update(pt.cache, gi.hits_from_planes(dev_rec[k], R), views[k], pt.slot_ids, stream)
         st = gi.gi_cache_stats(pt.cache, stream)
         ids = pt.slot_ids.cpu().numpy().view(np.uint32)
-        cells_total = (1 << TILE_LOG2) * 64
+        cells_total = (1 << log2_tiles) * 64
         ids = ids[ids < cells_total]
         touched_tiles = np.unique(ids >> 6)
         touched_cells = int(np.unique(ids).size)
@@ -579,10 +579,10 @@ def run_tiles(args, gi, Pipeline, frames, dev_rec, dev_gb, views, flush, stream,
         live_in_touched = int(np.isin(ex["slot"] >> 6, touched_tiles).sum())
         res_b = 8 if cfg["resolved_format"] == 1 else 16
         Tt = float(touched_tiles.size)
-        upd_b, res_bytes = tile_bytes(R, Tt, touched_cells, live_in_touched, res_b, float(1 << TILE_LOG2))
+        upd_b, res_bytes = tile_bytes(R, Tt, touched_cells, live_in_touched, res_b, float(1 << log2_tiles))
         return {
             "note": "gi_cache_create(tiles=1): 2^%d tile slots of 8 x 8 cells, min_samples %d; spawn untimed, "
-                    "update + resolve + probe irradiance per pass, L2 flushed per frame" % (TILE_LOG2, TILE_MIN_SAMPLES),
+                    "update + resolve + probe irradiance per pass, L2 flushed per frame" % (log2_tiles, TILE_MIN_SAMPLES),
             "pass_ms": {"update": float(ms[0]), "resolve": float(ms[1]), "integrate": float(ms[2])},
             "window_records_per_s_M": R / (ms.sum() * 1e-3) / 1e6,
             "touched_tiles": int(Tt), "touched_cells": touched_cells, "live_cells_in_touched_tiles": live_in_touched,

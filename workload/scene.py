@@ -49,11 +49,11 @@ CONFIGS = {
     2: dict(name="boxes-1080p", scene="boxes", width=1920, height=1080, fov_deg=60.0,
             rays_per_probe=64, log2_slots=22, cell_size=0.05, num_lods=4, alpha=0.1,
             evict_frames=8, frames=64, moving_camera=True, n_boxes=4096,
-            room=(64.0, 16.0, 64.0), moving_emitters=0, resolved_format=0),
+            room=(64.0, 16.0, 64.0), moving_emitters=0, resolved_format=0, log2_tiles=18),
     5: dict(name="boxes-4k", scene="boxes", width=3840, height=2160, fov_deg=60.0,
             rays_per_probe=64, log2_slots=24, cell_size=0.05, num_lods=4, alpha=0.1,
             evict_frames=8, frames=64, moving_camera=True, n_boxes=16384,
-            room=(96.0, 20.0, 96.0), moving_emitters=3, resolved_format=1),
+            room=(96.0, 20.0, 96.0), moving_emitters=3, resolved_format=1, log2_tiles=20),
 }
 # The 1080p boxes workload at the paper's quarter-sample operating point: 2x2 temporal upscale (one
 # probe per 16x16 spawn tile traces 64 rays), probes reprojected from the previous frame along the
@@ -61,8 +61,8 @@ CONFIGS = {
 CONFIGS[6] = dict(CONFIGS[2], name="boxes-1080p-upscale2", upscale=2, motion=True)
 # The paper's whole chain at that operating point: configuration 6 with the two-level world cache
 # (8x8 tiles with MIP levels, 2^18 tile slots, min_samples 16) and the probe filter (Algorithm 5).
-CONFIGS[7] = dict(CONFIGS[6], name="boxes-1080p-upscale2-tiles-filtered", tiles=True, log2_tiles=18,
-                  min_samples=16, filtered=True)
+CONFIGS[7] = dict(CONFIGS[6], name="boxes-1080p-upscale2-tiles-filtered", tiles=True, min_samples=16,
+                  filtered=True)
 
 
 # Configuration 3: 16 independent views of uneven resolution, each its own seeded scene (Cornell
