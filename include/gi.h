@@ -96,7 +96,8 @@ typedef void *gi_stream_t; /* cudaStream_t */
  *                   tile descriptor, their remainders (u mod 8) + 8 (v mod 8) the cell), plus
  *                   box-filtered MIP levels 4x4, 2x2 and 1x1 rebuilt at every resolve that
  *                   touches the tile.  log2_slots then counts tiles (10..22); slot ids are
- *                   tile slot * 64 + cell; first_touch must be AUTO (tiles use a list).
+ *                   tile slot * 64 + cell; first_touch must be AUTO (a tile cache records the
+ *                   cells touched since the last resolve in a 64-bit mask per tile).
  *   min_samples     tiles only, >= 1: a cell answers queries from the finest of its levels
  *                   (the cell, then its 4x4, 2x2 and 1x1 ancestors) whose sample count reaches
  *                   min_samples, else from the 1x1 level.  The sample count of a cell is the
