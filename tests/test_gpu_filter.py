@@ -153,3 +153,25 @@ def test_filtered_chain_matches_oracle():
     valid = sp["valid"]
     bad = valid & (err > 1e-4)
     assert np.count_nonzero(bad) <= 0.01 * np.count_nonzero(valid), (np.count_nonzero(bad), err[valid].max())
+
+
+def test_full_size_1080p_filter_pass():
+    # one filter pass of the 1080p workload at full size (32,400 probes) on the oracle's atlas
+    fr = wl.make_frame(2, 0)
+    ls = wl.CONFIGS[2]["log2_slots"]
+    sp, atlas = _oracle_frame(fr, ls)
+    a32 = atlas.astype(np.float32)
+    pl, view, R = _gpu_frame(fr, ls)
+    try:
+        src = dev(a32)
+        dst = torch.empty_like(src)
+        gi.gi_probes_filter(pl.probes.struct, view, src, dst, 0)
+        got = dst.cpu().numpy()
+    finally:
+        pl.close()
+    want, margin = OP.filter_pass(a32.astype(np.float64), sp, fr.camera, 0)
+    robust = margin > MARGIN
+    _atlas_close(got[robust], want[robust], rel=2e-6, atol=1e-7)
+    cell_ok = _close_mask(got, want, 2e-6, 1e-7).all(axis=-1)
+    valid = sp["valid"][:, None].repeat(64, axis=1)
+    assert np.count_nonzero(~cell_ok & valid) <= 0.005 * np.count_nonzero(valid)

@@ -236,3 +236,33 @@ def test_full_chain_with_tiles_and_filter_matches_oracle(frames):
         assert gi.gi_cache_stats(tp.cache)["dropped"] == 0
     finally:
         tp.close()
+
+
+def test_full_size_1080p_temporal_frames():
+    # bench configuration 6 at full size (1920 x 1080, 8,160 spawn tiles x 64 rays) for three
+    # frames: reprojection and spawn bit-exact at every MIP level, atlas and SH within 1e-4
+    scene = wl.make_scene(6)
+    frames = [wl.make_frame(6, f, scene) for f in range(3)]
+    ref = _oracle_chain(frames)
+    fr0 = frames[0]
+    W, H = fr0.camera.width, fr0.camera.height
+    tp = TemporalPipeline(W, H, fr0.rays_per_probe, 22, upscale=2)
+    try:
+        for fr, r in zip(frames, ref):
+            gb, rec, mv = dev(fr.gbuffer), dev(fr.records), dev(fr.motion)
+            tp.frame(gb, rec, mv, view_of(fr.camera, fr.frame))
+            torch.cuda.synchronize()
+            for got, want in zip(_levels(tp.probes), OP.build_mips(r["state"]["mask"])):
+                assert np.array_equal(got, want)
+            assert np.array_equal(u32(tp.src), r["state"]["src"])
+            ok = r["state"]["mask"].reshape(-1) != OT.SENTINEL
+            assert np.array_equal(tp.probes.pos.cpu().numpy()[ok], r["state"]["pos"][ok])
+            got_atlas = tp.atlas.cpu().numpy().astype(np.float64)
+            assert close(got_atlas[..., :3], r["atlas"][..., :3]).all()
+            sh = tp.probes.sh.cpu().numpy()[:, :27].reshape(-1, 9, 3)
+            scale = np.abs(r["sh"][:, 0, :]).max(axis=1)[:, None, None]
+            err = (np.abs(sh - r["sh"]) / np.maximum(scale, 1e-12)).max(axis=(1, 2))
+            assert err[OT.probe_valid(r["state"])].max() < 1e-4
+        assert gi.gi_cache_stats(tp.cache)["dropped"] == 0
+    finally:
+        tp.close()
