@@ -254,7 +254,7 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
             update_blocks_for(bv.hits.n, b->tuning.update_records_per_block),
             std::max<uint32_t>(1u, (uint32_t)((double)res_total * (double)bv.hits.n / (double)std::max(1ull, total_records))),
             (bv.probes.layout.num_probes * 32u + b->tuning.integrate_threads - 1u) / b->tuning.integrate_threads,
-            ((bv.view.width + 4u + 15u) / 16u) * ((bv.view.height + 4u + 15u) / 16u)};
+            interp_grid_x(bv.view.width) * interp_grid_y(bv.view.height)};
         for (int k = 0; k < 5; ++k) pre[k][v + 1] = pre[k][v] + cnt[k];
         reinterpret_cast<UpdateArgs *>(h + L.upd)[v] = cache_update_args(bv.cache, &bv.hits, &bv.view, bv.slot_ids);
         reinterpret_cast<ResolveArgs *>(h + L.res)[v] = cache_resolve_args(bv.cache, bv.resolve_frame);

@@ -254,6 +254,11 @@ gi_status tile_rebuild_launch(const TileArrays &from, const TileArrays &to, unsi
 gi_status tile_scan_launch(const TileArrays &t, const unsigned long long *tmask, uint32_t tiles, LiveRule rule,
                            unsigned long long *out, int blocks, cudaStream_t st);
 
+// Grid of the interpolation: blocks of 32x16 pixels starting at (-4, -4), one 8x8-pixel region
+// sharing a base tile per warp.
+__host__ __device__ inline uint32_t interp_grid_x(uint32_t width) { return (width + 4u + 31u) / 32u; }
+__host__ __device__ inline uint32_t interp_grid_y(uint32_t height) { return (height + 4u + 15u) / 16u; }
+
 // Cache internals needed by the probe kernels.
 struct CacheView {
     const void *resolved;      // resolved radiance of slot 0: float4, or half4 (ushort4)

@@ -604,117 +604,66 @@ __device__ __forceinline__ void neighbour_terms(const InterpArgs &a, uint32_t q,
     n8 = n4 * n4;
 }
 
-// Block = 16x16 pixels starting at (16 bx - 4, 16 by - 4); warp = 8x4 pixels that
-// share one base tile, so the four neighbour probes are warp-uniform loads.
-__device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t bx, uint32_t by) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x = (int)bx * 16 - 4 + 8 * (warp & 1) + (lane & 7);
-    const int y = (int)by * 16 - 4 + 4 * (warp >> 1) + (lane >> 3);
-    const bool inb = x >= 0 && y >= 0 && x < (int)a.width && y < (int)a.height;
-    const size_t pix = inb ? (size_t)y * a.width + x : 0;
-    const int tx = (x - 4) >> 3, ty = (y - 4) >> 3;
-    // the G-buffer texel and the four level-0 mask entries are independent: issue them together
-    const float4 nd = inb ? __ldcs(a.gbuf + pix) : make_float4(0.f, 0.f, 0.f, -1.0f);
-    uint32_t q[4];
+// E_q(n) of one neighbour for one pixel: sum_k A_l Y_k(n) c_qk, the probe's 27 coefficients read
+// as seven 16-byte vectors.
+__device__ __forceinline__ void eval_neighbour(const InterpArgs &a, uint32_t q, const float (&Yb)[9], float (&E)[3]) {
+    E[0] = E[1] = E[2] = 0.f;
+    if (q == GI_PROBE_NONE) return;
+    const uint32_t pidx = (q >> 19) * a.tiles_x + ((q & 0xFFFFu) >> 3);
+    const float4 *c4 = reinterpret_cast<const float4 *>(a.sh + (size_t)pidx * GI_SH_STRIDE);
+    float c[28];
 #pragma unroll
-    for (int o = 0; o < 4; ++o) {
-        const int qx = tx + (o & 1), qy = ty + (o >> 1);
-        const bool in0 = inb && qx >= 0 && qy >= 0 && qx < a.mi.w[0] && qy < a.mi.h[0];
-        q[o] = in0 ? __ldg(a.mask + qy * a.mi.w[0] + qx) : GI_PROBE_NONE;
-        // Algorithm 3 continues above level 0 only where level 0 holds no probe
-        if (in0 && q[o] == GI_PROBE_NONE) q[o] = find_closest_probe(a.mask, a.mi, tx >> 1, ty >> 1, o & 1, o >> 1, 1);
+    for (int k = 0; k < 7; ++k) {
+        const float4 v = __ldg(c4 + k);
+        c[4 * k] = v.x;
+        c[4 * k + 1] = v.y;
+        c[4 * k + 2] = v.z;
+        c[4 * k + 3] = v.w;
     }
-    const bool sky = inb && !(isfinite(nd.w) && nd.w >= 0.0f);
-    const bool act = inb && !sky;
-    const unsigned am = __ballot_sync(kFullMask, act);
-    if (am == 0u) {  // the whole warp is sky or outside the image
-        if (inb) __stcs(a.out + pix, make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
-        return;
-    }
-    // the pixel's normal, or the first active lane's for inactive lanes (they only help the warp)
-    const int src = __ffs(am) - 1;
-    const float sx_ = __shfl_sync(kFullMask, nd.x, src), sy_ = __shfl_sync(kFullMask, nd.y, src),
-                sz_ = __shfl_sync(kFullMask, nd.z, src);
-    const float nx = act ? nd.x : sx_, ny = act ? nd.y : sy_, nz = act ? nd.z : sz_;
-    uint32_t qs[4];
 #pragma unroll
-    for (int o = 0; o < 4; ++o) qs[o] = __shfl_sync(kFullMask, q[o], src);
-    const bool same = !act || (__float_as_uint(nd.x) == __float_as_uint(sx_) && __float_as_uint(nd.y) == __float_as_uint(sy_) &&
-                               __float_as_uint(nd.z) == __float_as_uint(sz_) && q[0] == qs[0] && q[1] == qs[1] &&
-                               q[2] == qs[2] && q[3] == qs[3]);
-    const bool uniform = __all_sync(kFullMask, same);
-    // A_l Y_lm(n_p)
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) E[cc] += Yb[k] * c[3 * k + cc];
+}
+
+// A_l Y_lm(n) for the 9 coefficients of bands 0..2.
+__device__ __forceinline__ void sh_lobe(float nx, float ny, float nz, float (&Yb)[9]) {
     const float PI = 3.14159265358979f;
     const float A0 = PI, A1 = 2.0f * PI / 3.0f, A2 = 0.25f * PI;
-    const float Yb[9] = {A0 * 0.28209479177387814f,
-                         A1 * 0.4886025119029199f * ny,
-                         A1 * 0.4886025119029199f * nz,
-                         A1 * 0.4886025119029199f * nx,
-                         A2 * 1.0925484305920792f * nx * ny,
-                         A2 * 1.0925484305920792f * ny * nz,
-                         A2 * 0.31539156525252005f * (3.0f * nz * nz - 1.0f),
-                         A2 * 1.0925484305920792f * nx * nz,
-                         A2 * 0.5462742152960396f * (nx * nx - ny * ny)};
-    // E_q(n) = sum_k A_l Y_k(n) c_qk for the four neighbours
-    float Eo[4][3];
-    if (uniform) {
-        // lane 3 o + ch evaluates neighbour o, channel ch for the whole warp
-        const int o = lane / 3, ch = lane - 3 * (lane / 3);
-        float e = 0.f;
-        const uint32_t qo = pick_u4(qs, o < 4 ? o : 0);
-        if (lane < 12 && qo != GI_PROBE_NONE) {
-            const float *c = a.sh + (size_t)((qo >> 19) * a.tiles_x + ((qo & 0xFFFFu) >> 3)) * GI_SH_STRIDE + ch;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) e += Yb[k] * __ldg(c + 3 * k);
-        }
-#pragma unroll
-        for (int oo = 0; oo < 4; ++oo)
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) Eo[oo][cc] = __shfl_sync(kFullMask, e, 3 * oo + cc);
-    } else {
-#pragma unroll
-        for (int oo = 0; oo < 4; ++oo) {
-            // keep each neighbour's 28 SH loads inside its own iteration (register pressure)
-            asm volatile("" ::: "memory");
-            Eo[oo][0] = Eo[oo][1] = Eo[oo][2] = 0.f;
-            if (q[oo] == GI_PROBE_NONE) continue;
-            const uint32_t pidx = (q[oo] >> 19) * a.tiles_x + ((q[oo] & 0xFFFFu) >> 3);
-            const float4 *c4 = reinterpret_cast<const float4 *>(a.sh + (size_t)pidx * GI_SH_STRIDE);
-            float c[28];
-#pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                const float4 v = __ldg(c4 + k);
-                c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
-            }
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) Eo[oo][cc] += Yb[k] * c[3 * k + cc];
-        }
-    }
-    // Plane distance of neighbour q from the pixel's plane, relative to the camera (the camera
-    // origin cancels): (P_q - P_p) . n_p = t_q (d_q . n_p) - t_p (d_p . n_p), with
-    // d = v / |v|, v = fwd + sx right + sy up.  Only the projections of fwd, right and up on n_p
-    // are needed per neighbour.
-    const float fn = a.cam.fwd[0] * nx + a.cam.fwd[1] * ny + a.cam.fwd[2] * nz;
-    const float rn = a.cam.right[0] * nx + a.cam.right[1] * ny + a.cam.right[2] * nz;
-    const float un = a.cam.up[0] * nx + a.cam.up[1] * ny + a.cam.up[2] * nz;
-    // a uniform warp (one normal, the same four neighbours) computes the neighbours' terms once, in
-    // lanes 0..3, and broadcasts them (while every lane of the warp is still here)
-    float qn_s[4] = {0.f, 0.f, 0.f, 0.f}, n8_s[4] = {0.f, 0.f, 0.f, 0.f};
-    if (uniform) {
-        float qn_u = 0.f, n8_u = 0.f;
-        const uint32_t qo = pick_u4(qs, lane & 3);
-        if (lane < 4 && qo != GI_PROBE_NONE) neighbour_terms(a, qo, nx, ny, nz, fn, rn, un, qn_u, n8_u);
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            qn_s[o] = __shfl_sync(kFullMask, qn_u, o);
-            n8_s[o] = __shfl_sync(kFullMask, n8_u, o);
-        }
-    }
+    Yb[0] = A0 * 0.28209479177387814f;
+    Yb[1] = A1 * 0.4886025119029199f * ny;
+    Yb[2] = A1 * 0.4886025119029199f * nz;
+    Yb[3] = A1 * 0.4886025119029199f * nx;
+    Yb[4] = A2 * 1.0925484305920792f * nx * ny;
+    Yb[5] = A2 * 1.0925484305920792f * ny * nz;
+    Yb[6] = A2 * 0.31539156525252005f * (3.0f * nz * nz - 1.0f);
+    Yb[7] = A2 * 1.0925484305920792f * nx * nz;
+    Yb[8] = A2 * 0.5462742152960396f * (nx * nx - ny * ny);
+}
+
+// One pixel of the interpolation: weights of the four neighbours (bilinear x normal x plane
+// distance) and the weighted irradiance, or the relaxed / none / sky flags.  UNIFORM: the
+// neighbours' irradiance and plane terms come from the warp (Eu, qn_s, n8_s); otherwise each is
+// evaluated for this pixel's normal.
+template <bool UNIFORM>
+__device__ __forceinline__ void interp_pixel(const InterpArgs &a, int x, int y, int tx, int ty, const float4 nd,
+                                             size_t pix, bool inb, bool act, const uint32_t (&q)[4],
+                                             const float (&Eu)[4][3], const float (&qn_s)[4], const float (&n8_s)[4]) {
+    if (!inb) return;
     if (!act) {
-        if (inb) __stcs(a.out + pix, make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
+        __stcs(a.out + pix, make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
         return;
+    }
+    const float nx = nd.x, ny = nd.y, nz = nd.z;
+    // Plane distance of neighbour q from the pixel's plane, relative to the camera (the camera
+    // origin cancels): (P_q - P_p) . n_p = t_q (d_q . n_p) - t_p (d_p . n_p), with d = v / |v|,
+    // v = fwd + sx right + sy up.  Only the projections of fwd, right and up on n_p are needed
+    // per neighbour.
+    float fn = 0.f, rn = 0.f, un = 0.f;
+    if (!UNIFORM) {
+        fn = a.cam.fwd[0] * nx + a.cam.fwd[1] * ny + a.cam.fwd[2] * nz;
+        rn = a.cam.right[0] * nx + a.cam.right[1] * ny + a.cam.right[2] * nz;
+        un = a.cam.up[0] * nx + a.cam.up[1] * ny + a.cam.up[2] * nz;
     }
     const float inv_cs = 1.0f / (a.dscale * nd.w);
     float pn;  // t_p (d_p . n_p)
@@ -724,13 +673,26 @@ __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t b
     }
     const float fx = ((float)((x - 4) - 8 * tx) + 0.5f) * 0.125f;
     const float fy = ((float)((y - 4) - 8 * ty) + 0.5f) * 0.125f;
+    float Yb[9];
+    if (!UNIFORM) sh_lobe(nx, ny, nz, Yb);
     float wsum = 0.f, es[3] = {0.f, 0.f, 0.f}, er[3] = {0.f, 0.f, 0.f};
     int nfound = 0;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
         if (q[o] == GI_PROBE_NONE) continue;
-        float qn = qn_s[o], n8 = n8_s[o];
-        if (!uniform) neighbour_terms(a, q[o], nx, ny, nz, fn, rn, un, qn, n8);
+        float qn, n8, E[3];
+        if (UNIFORM) {
+            qn = qn_s[o];
+            n8 = n8_s[o];
+            E[0] = Eu[o][0];
+            E[1] = Eu[o][1];
+            E[2] = Eu[o][2];
+        } else {
+            // keep each neighbour's 28 SH loads inside its own iteration (register pressure)
+            asm volatile("" ::: "memory");
+            neighbour_terms(a, q[o], nx, ny, nz, fn, rn, un, qn, n8);
+            eval_neighbour(a, q[o], Yb, E);
+        }
         const int ox = o & 1, oy = o >> 1;
         const float bil = (ox ? fx : 1.0f - fx) * (oy ? fy : 1.0f - fy);
         const float wd = fmaxf(1.0f - fabsf(qn - pn) * inv_cs, 0.0f);
@@ -738,8 +700,8 @@ __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t b
         wsum += w;
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-            es[ch] += w * Eo[o][ch];
-            er[ch] += Eo[o][ch];
+            es[ch] += w * E[ch];
+            er[ch] += E[ch];
         }
         ++nfound;
     }
@@ -756,7 +718,100 @@ __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t b
     __stcs(a.out + pix, r);
 }
 
-__global__ void __launch_bounds__(256, 4) k_interpolate(InterpArgs a) { interpolate_body(a, blockIdx.x, blockIdx.y); }
+// Block = 32x16 pixels starting at (32 bx - 4, 16 by - 4); warp = the 8x8 pixels that share one
+// base tile floor((p - 4) / 8): lane l holds column l & 7 of rows l >> 3 and 4 + (l >> 3).  The
+// four neighbour probes are therefore the same for the whole warp, and a warp whose active pixels
+// share one normal evaluates the neighbours' irradiance and plane terms once for its 64 pixels.
+__device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t bx, uint32_t by) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = (int)bx * 32 - 4 + 8 * (warp & 3) + (lane & 7);
+    const int y0 = (int)by * 16 - 4 + 8 * (warp >> 2) + (lane >> 3);
+    const int tx = (x - 4) >> 3, ty = (y0 - 4) >> 3;  // the same for y0 and y0 + 4
+    // the neighbours (Algorithm 3 from the four tiles around the base tile), the same in every lane
+    uint32_t q[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        const int qx = tx + (o & 1), qy = ty + (o >> 1);
+        const bool in0 = qx >= 0 && qy >= 0 && qx < a.mi.w[0] && qy < a.mi.h[0];
+        q[o] = in0 ? __ldg(a.mask + qy * a.mi.w[0] + qx) : GI_PROBE_NONE;
+        // Algorithm 3 continues above level 0 only where level 0 holds no probe
+        if (in0 && q[o] == GI_PROBE_NONE) q[o] = find_closest_probe(a.mask, a.mi, tx >> 1, ty >> 1, o & 1, o >> 1, 1);
+    }
+    bool inb[2], act[2];
+    float4 nd[2];
+    size_t pix[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int y = y0 + 4 * h;
+        inb[h] = x >= 0 && y >= 0 && x < (int)a.width && y < (int)a.height;
+        pix[h] = inb[h] ? (size_t)y * a.width + x : 0;
+        nd[h] = inb[h] ? __ldcs(a.gbuf + pix[h]) : make_float4(0.f, 0.f, 0.f, -1.0f);
+        act[h] = inb[h] && isfinite(nd[h].w) && nd[h].w >= 0.0f;
+    }
+    const unsigned am0 = __ballot_sync(kFullMask, act[0]), am1 = __ballot_sync(kFullMask, act[1]);
+    if ((am0 | am1) == 0u) {  // the whole warp is sky or outside the image
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (inb[h]) __stcs(a.out + pix[h], make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
+        return;
+    }
+    // the first active pixel's normal stands in for inactive pixels (they only help the warp)
+    const int sh_ = am0 ? 0 : 1;
+    const int src = __ffs(am0 ? am0 : am1) - 1;
+    const float4 ns = sh_ == 0 ? nd[0] : nd[1];
+    const float sx_ = __shfl_sync(kFullMask, ns.x, src), sy_ = __shfl_sync(kFullMask, ns.y, src),
+                sz_ = __shfl_sync(kFullMask, ns.z, src);
+    bool same = true;
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        same = same && (!act[h] || (__float_as_uint(nd[h].x) == __float_as_uint(sx_) &&
+                                    __float_as_uint(nd[h].y) == __float_as_uint(sy_) &&
+                                    __float_as_uint(nd[h].z) == __float_as_uint(sz_)));
+    const bool uniform = __all_sync(kFullMask, same);
+    // uniform warp: lane 3 o + ch evaluates neighbour o, channel ch; lanes 0..3 the plane and
+    // normal terms of neighbour `lane`; every lane then has all four
+    float Eu[4][3] = {}, qn_s[4] = {}, n8_s[4] = {};
+    if (uniform) {
+        float Yb[9];
+        sh_lobe(sx_, sy_, sz_, Yb);
+        const int o = lane / 3, ch = lane - 3 * (lane / 3);
+        float e = 0.f;
+        const uint32_t qo = pick_u4(q, o < 4 ? o : 0);
+        if (lane < 12 && qo != GI_PROBE_NONE) {
+            const float *c = a.sh + (size_t)((qo >> 19) * a.tiles_x + ((qo & 0xFFFFu) >> 3)) * GI_SH_STRIDE + ch;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) e += Yb[k] * __ldg(c + 3 * k);
+        }
+        const float fn = a.cam.fwd[0] * sx_ + a.cam.fwd[1] * sy_ + a.cam.fwd[2] * sz_;
+        const float rn = a.cam.right[0] * sx_ + a.cam.right[1] * sy_ + a.cam.right[2] * sz_;
+        const float un = a.cam.up[0] * sx_ + a.cam.up[1] * sy_ + a.cam.up[2] * sz_;
+        float qn_u = 0.f, n8_u = 0.f;
+        const uint32_t q4 = pick_u4(q, lane & 3);
+        if (lane < 4 && q4 != GI_PROBE_NONE) neighbour_terms(a, q4, sx_, sy_, sz_, fn, rn, un, qn_u, n8_u);
+#pragma unroll
+        for (int oo = 0; oo < 4; ++oo) {
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) Eu[oo][cc] = __shfl_sync(kFullMask, e, 3 * oo + cc);
+            qn_s[oo] = __shfl_sync(kFullMask, qn_u, oo);
+            n8_s[oo] = __shfl_sync(kFullMask, n8_u, oo);
+        }
+    }
+    // the two pixels one after the other (selects, not indexing: the arrays stay in registers); the
+    // uniform and the per-pixel forms in separate loops, so that each keeps only its own state live
+    if (uniform) {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h)
+            interp_pixel<true>(a, x, y0 + 4 * h, tx, ty, h ? nd[1] : nd[0], h ? pix[1] : pix[0], h ? inb[1] : inb[0],
+                               h ? act[1] : act[0], q, Eu, qn_s, n8_s);
+    } else {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h)
+            interp_pixel<false>(a, x, y0 + 4 * h, tx, ty, h ? nd[1] : nd[0], h ? pix[1] : pix[0], h ? inb[1] : inb[0],
+                                h ? act[1] : act[0], q, Eu, qn_s, n8_s);
+    }
+}
+
+__global__ void __launch_bounds__(256, 3) k_interpolate(InterpArgs a) { interpolate_body(a, blockIdx.x, blockIdx.y); }
 
 static bool layout_matches(const gi_probe_layout &l, uint32_t w, uint32_t h) {
     return l.tiles_x == (w + 7) / 8 && l.tiles_y == (h + 7) / 8 && l.num_probes == l.tiles_x * l.tiles_y &&
@@ -1012,13 +1067,13 @@ __global__ void __launch_bounds__(256) k_integrate_batched(const IntegrateArgs *
     integrate_body(sa, blockIdx.x - __ldg(prefix + v));
 }
 
-__global__ void __launch_bounds__(256, 4) k_interpolate_batched(const InterpArgs *args, const uint32_t *prefix,
+__global__ void __launch_bounds__(256, 3) k_interpolate_batched(const InterpArgs *args, const uint32_t *prefix,
                                                                 uint32_t nviews) {
     __shared__ InterpArgs sa;
     const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
     load_view_args(sa, args + v);
     __syncthreads();
-    const uint32_t b = blockIdx.x - __ldg(prefix + v), gx = (sa.width + 4 + 15) / 16;
+    const uint32_t b = blockIdx.x - __ldg(prefix + v), gx = interp_grid_x(sa.width);
     interpolate_body(sa, b % gx, b / gx);
 }
 
@@ -1294,7 +1349,7 @@ gi_status gi_probes_interpolate(const gi_gbuffer *gbuf, const gi_view *view, con
     gi_status s = interp_check(gbuf, view, pr, out);
     if (s != GI_OK) return s;
     const InterpArgs a = interp_args(gbuf, view, pr, out);
-    dim3 grid((view->width + 4 + 15) / 16, (view->height + 4 + 15) / 16);
+    dim3 grid(interp_grid_x(view->width), interp_grid_y(view->height));
     k_interpolate<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
     return cuda_status(cudaGetLastError(), "k_interpolate launch");
 }
