@@ -584,46 +584,37 @@ __device__ __forceinline__ uint32_t pick_u4(const uint32_t (&v)[4], int i) {
     return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
 }
 
-// Terms of neighbour probe q (packed pixel) for a pixel with normal n: its distance along n from
-// the camera, t_q (d_q . n), through the camera basis projected on n (fn, rn, un), and the
-// normal weight max(0, n . n_q)^8.
-__device__ __forceinline__ void neighbour_terms(const InterpArgs &a, uint32_t q, float nx, float ny, float nz, float fn,
-                                                float rn, float un, float &qn, float &n8) {
-    const uint32_t pidx = (q >> 19) * a.tiles_x + ((q & 0xFFFFu) >> 3);
-    const float tq = __ldg(a.ppos + pidx).w;
-    const float4 nq = __ldg(a.pnrm + pidx);
-    const float qpx = (float)(q & 0xFFFFu), qpy = (float)(q >> 16);
-    const float sxq = (2.0f * (qpx + 0.5f) * a.cam.inv_w - 1.0f) * a.cam.sx_scale;
-    const float syq = (1.0f - 2.0f * (qpy + 0.5f) * a.cam.inv_h) * a.cam.sy_scale;
-    const float vx = a.cam.fwd[0] + sxq * a.cam.right[0] + syq * a.cam.up[0];
-    const float vy = a.cam.fwd[1] + sxq * a.cam.right[1] + syq * a.cam.up[1];
-    const float vz = a.cam.fwd[2] + sxq * a.cam.right[2] + syq * a.cam.up[2];
-    qn = tq * (fn + sxq * rn + syq * un) * rsqrtf(vx * vx + vy * vy + vz * vz);
-    const float nd1 = fmaxf(nx * nq.x + ny * nq.y + nz * nq.z, 0.0f);
-    const float n2 = nd1 * nd1, n4 = n2 * n2;
-    n8 = n4 * n4;
+// Per-warp copy of the four neighbours' data in shared memory: SH coefficients (27 + pad, seven
+// float4), the position relative to the camera t_q d_q and the normal.
+struct InterpNb {
+    float4 c[4][7];
+    float4 pos[4];
+    float4 nrm[4];
+    float4 eu[4];  // uniform warp: neighbour o's irradiance (xyz) and plane term (w)
+    float4 n8;     // uniform warp: the four normal weights
+};
+
+// Terms of neighbour o for a pixel with normal n: its distance along n from the camera,
+// (t_q d_q) . n, and the normal weight max(0, n . n_q)^8.
+__device__ __forceinline__ void nb_terms(const InterpNb &s, int o, float nx, float ny, float nz, float &qn, float &n8) {
+    const float4 P = s.pos[o], N = s.nrm[o];
+    qn = P.x * nx + P.y * ny + P.z * nz;
+    const float d = fmaxf(nx * N.x + ny * N.y + nz * N.z, 0.0f);
+    const float d2 = d * d, d4 = d2 * d2;
+    n8 = d4 * d4;
 }
 
-// E_q(n) of one neighbour for one pixel: sum_k A_l Y_k(n) c_qk, the probe's 27 coefficients read
-// as seven 16-byte vectors.
-__device__ __forceinline__ void eval_neighbour(const InterpArgs &a, uint32_t q, const float (&Yb)[9], float (&E)[3]) {
+// E_q(n) of neighbour o: sum_k A_l Y_k(n) c_qk (coefficient 3 k + channel), read four at a time.
+__device__ __forceinline__ void nb_irradiance(const InterpNb &s, int o, const float (&Yb)[9], float (&E)[3]) {
     E[0] = E[1] = E[2] = 0.f;
-    if (q == GI_PROBE_NONE) return;
-    const uint32_t pidx = (q >> 19) * a.tiles_x + ((q & 0xFFFFu) >> 3);
-    const float4 *c4 = reinterpret_cast<const float4 *>(a.sh + (size_t)pidx * GI_SH_STRIDE);
-    float c[28];
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
-        const float4 v = __ldg(c4 + k);
-        c[4 * k] = v.x;
-        c[4 * k + 1] = v.y;
-        c[4 * k + 2] = v.z;
-        c[4 * k + 3] = v.w;
+        const float4 v = s.c[o][k];
+        const float t[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (4 * k + j < 27) E[(4 * k + j) % 3] += Yb[(4 * k + j) / 3] * t[j];
     }
-#pragma unroll
-    for (int k = 0; k < 9; ++k)
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) E[cc] += Yb[k] * c[3 * k + cc];
 }
 
 // A_l Y_lm(n) for the 9 coefficients of bands 0..2.
@@ -642,13 +633,13 @@ __device__ __forceinline__ void sh_lobe(float nx, float ny, float nz, float (&Yb
 }
 
 // One pixel of the interpolation: weights of the four neighbours (bilinear x normal x plane
-// distance) and the weighted irradiance, or the relaxed / none / sky flags.  UNIFORM: the
-// neighbours' irradiance and plane terms come from the warp (Eu, qn_s, n8_s); otherwise each is
-// evaluated for this pixel's normal.
+// distance) and the weighted irradiance, or the relaxed / none / sky flags.  (fx, fy) is the
+// pixel's bilinear position between the neighbours.  UNIFORM: the neighbours' irradiance and
+// plane and normal terms were evaluated once for the warp (s.eu, s.n8); otherwise each is
+// evaluated for this pixel's normal from the warp's shared copy.
 template <bool UNIFORM>
-__device__ __forceinline__ void interp_pixel(const InterpArgs &a, int x, int y, int tx, int ty, const float4 nd,
-                                             size_t pix, bool inb, bool act, const uint32_t (&q)[4],
-                                             const float (&Eu)[4][3], const float (&qn_s)[4], const float (&n8_s)[4]) {
+__device__ __forceinline__ void interp_pixel(const InterpArgs &a, const InterpNb &s, int x, int y, float fx, float fy,
+                                             const float4 nd, size_t pix, bool inb, bool act, const uint32_t (&q)[4]) {
     if (!inb) return;
     if (!act) {
         __stcs(a.out + pix, make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
@@ -656,53 +647,40 @@ __device__ __forceinline__ void interp_pixel(const InterpArgs &a, int x, int y, 
     }
     const float nx = nd.x, ny = nd.y, nz = nd.z;
     // Plane distance of neighbour q from the pixel's plane, relative to the camera (the camera
-    // origin cancels): (P_q - P_p) . n_p = t_q (d_q . n_p) - t_p (d_p . n_p), with d = v / |v|,
-    // v = fwd + sx right + sy up.  Only the projections of fwd, right and up on n_p are needed
-    // per neighbour.
-    float fn = 0.f, rn = 0.f, un = 0.f;
-    if (!UNIFORM) {
-        fn = a.cam.fwd[0] * nx + a.cam.fwd[1] * ny + a.cam.fwd[2] * nz;
-        rn = a.cam.right[0] * nx + a.cam.right[1] * ny + a.cam.right[2] * nz;
-        un = a.cam.up[0] * nx + a.cam.up[1] * ny + a.cam.up[2] * nz;
-    }
-    const float inv_cs = 1.0f / (a.dscale * nd.w);
-    float pn;  // t_p (d_p . n_p)
-    {
-        const float3 d = cam_ray_dir(a.cam, (float)x, (float)y);
-        pn = nd.w * (d.x * nx + d.y * ny + d.z * nz);
-    }
-    const float fx = ((float)((x - 4) - 8 * tx) + 0.5f) * 0.125f;
-    const float fy = ((float)((y - 4) - 8 * ty) + 0.5f) * 0.125f;
+    // origin cancels): (P_q - P_p) . n_p = (t_q d_q) . n_p - t_p (d_p . n_p).
+    const float3 d = cam_ray_dir(a.cam, (float)x, (float)y);
+    // (products rounded on their own: no contraction into the differences below, so that every
+    // kernel instantiating this body rounds alike)
+    const float pn = __fmul_rn(nd.w, d.x * nx + d.y * ny + d.z * nz);
+    // the plane weight max(1 - |plane distance| / cs, 0) is taken times cs, which cancels in
+    // es / wsum and keeps the sign of every weight
+    const float cs = __fmul_rn(a.dscale, nd.w);
     float Yb[9];
     if (!UNIFORM) sh_lobe(nx, ny, nz, Yb);
-    float wsum = 0.f, es[3] = {0.f, 0.f, 0.f}, er[3] = {0.f, 0.f, 0.f};
+    float wsum = 0.f, es[3] = {0.f, 0.f, 0.f};
     int nfound = 0;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
         if (q[o] == GI_PROBE_NONE) continue;
         float qn, n8, E[3];
         if (UNIFORM) {
-            qn = qn_s[o];
-            n8 = n8_s[o];
-            E[0] = Eu[o][0];
-            E[1] = Eu[o][1];
-            E[2] = Eu[o][2];
+            const float4 u = s.eu[o];
+            const float4 n8v = s.n8;
+            qn = u.w;
+            n8 = o == 0 ? n8v.x : (o == 1 ? n8v.y : (o == 2 ? n8v.z : n8v.w));
+            E[0] = u.x;
+            E[1] = u.y;
+            E[2] = u.z;
         } else {
-            // keep each neighbour's 28 SH loads inside its own iteration (register pressure)
-            asm volatile("" ::: "memory");
-            neighbour_terms(a, q[o], nx, ny, nz, fn, rn, un, qn, n8);
-            eval_neighbour(a, q[o], Yb, E);
+            nb_terms(s, o, nx, ny, nz, qn, n8);
+            nb_irradiance(s, o, Yb, E);
         }
-        const int ox = o & 1, oy = o >> 1;
-        const float bil = (ox ? fx : 1.0f - fx) * (oy ? fy : 1.0f - fy);
-        const float wd = fmaxf(1.0f - fabsf(qn - pn) * inv_cs, 0.0f);
+        const float bil = ((o & 1) ? fx : 1.0f - fx) * ((o >> 1) ? fy : 1.0f - fy);
+        const float wd = fmaxf(cs - fabsf(qn - pn), 0.0f);
         const float w = bil * n8 * wd;
         wsum += w;
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            es[ch] += w * E[ch];
-            er[ch] += E[ch];
-        }
+        for (int ch = 0; ch < 3; ++ch) es[ch] += w * E[ch];
         ++nfound;
     }
     float4 r;
@@ -712,31 +690,45 @@ __device__ __forceinline__ void interp_pixel(const InterpArgs &a, int x, int y, 
         const float inv = 1.0f / wsum;
         r = make_float4(es[0] * inv, es[1] * inv, es[2] * inv, (float)GI_INTERP_OK);
     } else {
+        // relaxed: the plain mean of the neighbours found (rare: every weight vanished)
+        float er[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            if (q[o] == GI_PROBE_NONE) continue;
+            float E[3];
+            if (UNIFORM) {
+                const float4 u = s.eu[o];
+                E[0] = u.x;
+                E[1] = u.y;
+                E[2] = u.z;
+            } else {
+                nb_irradiance(s, o, Yb, E);
+            }
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) er[ch] += E[ch];
+        }
         const float inv = 1.0f / (float)nfound;
         r = make_float4(er[0] * inv, er[1] * inv, er[2] * inv, (float)GI_INTERP_RELAXED);
     }
     __stcs(a.out + pix, r);
 }
 
+constexpr int kInterpWarps = 8;  // 32 x 16 pixels per 256-thread block
+
 // Block = 32x16 pixels starting at (32 bx - 4, 16 by - 4); warp = the 8x8 pixels that share one
 // base tile floor((p - 4) / 8): lane l holds column l & 7 of rows l >> 3 and 4 + (l >> 3).  The
-// four neighbour probes are therefore the same for the whole warp, and a warp whose active pixels
-// share one normal evaluates the neighbours' irradiance and plane terms once for its 64 pixels.
+// four neighbour probes are therefore the same for the whole warp: lanes 0..3 run Algorithm 3
+// for one neighbour each, and the warp copies the neighbours' data to shared memory once (28 lanes
+// one SH float4 each, 4 lanes a position and normal).  A warp whose active pixels share one normal
+// evaluates the neighbours' irradiance and plane terms once for its 64 pixels.
 __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t bx, uint32_t by) {
+    __shared__ InterpNb s_nb[kInterpWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    InterpNb &s = s_nb[warp];
     const int x = (int)bx * 32 - 4 + 8 * (warp & 3) + (lane & 7);
     const int y0 = (int)by * 16 - 4 + 8 * (warp >> 2) + (lane >> 3);
     const int tx = (x - 4) >> 3, ty = (y0 - 4) >> 3;  // the same for y0 and y0 + 4
-    // the neighbours (Algorithm 3 from the four tiles around the base tile), the same in every lane
-    uint32_t q[4];
-#pragma unroll
-    for (int o = 0; o < 4; ++o) {
-        const int qx = tx + (o & 1), qy = ty + (o >> 1);
-        const bool in0 = qx >= 0 && qy >= 0 && qx < a.mi.w[0] && qy < a.mi.h[0];
-        q[o] = in0 ? __ldg(a.mask + qy * a.mi.w[0] + qx) : GI_PROBE_NONE;
-        // Algorithm 3 continues above level 0 only where level 0 holds no probe
-        if (in0 && q[o] == GI_PROBE_NONE) q[o] = find_closest_probe(a.mask, a.mi, tx >> 1, ty >> 1, o & 1, o >> 1, 1);
-    }
+    // the G-buffer of the lane's two pixels (independent of the probes)
     bool inb[2], act[2];
     float4 nd[2];
     size_t pix[2];
@@ -746,8 +738,22 @@ __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t b
         inb[h] = x >= 0 && y >= 0 && x < (int)a.width && y < (int)a.height;
         pix[h] = inb[h] ? (size_t)y * a.width + x : 0;
         nd[h] = inb[h] ? __ldcs(a.gbuf + pix[h]) : make_float4(0.f, 0.f, 0.f, -1.0f);
-        act[h] = inb[h] && isfinite(nd[h].w) && nd[h].w >= 0.0f;
     }
+    // neighbour `lane` (lanes 0..3): Algorithm 3 from the tile (tx + (lane & 1), ty + (lane >> 1)),
+    // continued above level 0 only where level 0 holds no probe
+    uint32_t qo = GI_PROBE_NONE;
+    if (lane < 4) {
+        const int qx = tx + (lane & 1), qy = ty + (lane >> 1);
+        if (qx >= 0 && qy >= 0 && qx < a.mi.w[0] && qy < a.mi.h[0]) {
+            qo = __ldg(a.mask + qy * a.mi.w[0] + qx);
+            if (qo == GI_PROBE_NONE) qo = find_closest_probe(a.mask, a.mi, tx >> 1, ty >> 1, lane & 1, lane >> 1, 1);
+        }
+    }
+    uint32_t q[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) q[o] = __shfl_sync(kFullMask, qo, o);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) act[h] = inb[h] && isfinite(nd[h].w) && nd[h].w >= 0.0f;
     const unsigned am0 = __ballot_sync(kFullMask, act[0]), am1 = __ballot_sync(kFullMask, act[1]);
     if ((am0 | am1) == 0u) {  // the whole warp is sky or outside the image
 #pragma unroll
@@ -755,10 +761,33 @@ __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t b
             if (inb[h]) __stcs(a.out + pix[h], make_float4(0.f, 0.f, 0.f, (float)GI_INTERP_SKY));
         return;
     }
+    // the neighbours' data into the warp's shared copy
+    {
+        const int o = lane < 28 ? lane / 7 : lane - 28;
+        const uint32_t qq = pick_u4(q, o);
+        if (qq != GI_PROBE_NONE) {
+            const uint32_t pidx = (qq >> 19) * a.tiles_x + ((qq & 0xFFFFu) >> 3);
+            if (lane < 28) {
+                const int k = lane - 7 * o;
+                s.c[o][k] = __ldg(reinterpret_cast<const float4 *>(a.sh + (size_t)pidx * GI_SH_STRIDE) + k);
+            } else {
+                const float tq = __ldg(a.ppos + pidx).w;
+                const float qpx = (float)(qq & 0xFFFFu), qpy = (float)(qq >> 16);
+                const float sxq = (2.0f * (qpx + 0.5f) * a.cam.inv_w - 1.0f) * a.cam.sx_scale;
+                const float syq = (1.0f - 2.0f * (qpy + 0.5f) * a.cam.inv_h) * a.cam.sy_scale;
+                const float vx = a.cam.fwd[0] + sxq * a.cam.right[0] + syq * a.cam.up[0];
+                const float vy = a.cam.fwd[1] + sxq * a.cam.right[1] + syq * a.cam.up[1];
+                const float vz = a.cam.fwd[2] + sxq * a.cam.right[2] + syq * a.cam.up[2];
+                const float t = tq * rsqrtf(vx * vx + vy * vy + vz * vz);
+                s.pos[o] = make_float4(t * vx, t * vy, t * vz, 0.f);
+                s.nrm[o] = __ldg(a.pnrm + pidx);
+            }
+        }
+    }
+    __syncwarp();
     // the first active pixel's normal stands in for inactive pixels (they only help the warp)
-    const int sh_ = am0 ? 0 : 1;
     const int src = __ffs(am0 ? am0 : am1) - 1;
-    const float4 ns = sh_ == 0 ? nd[0] : nd[1];
+    const float4 ns = am0 ? nd[0] : nd[1];
     const float sx_ = __shfl_sync(kFullMask, ns.x, src), sy_ = __shfl_sync(kFullMask, ns.y, src),
                 sz_ = __shfl_sync(kFullMask, ns.z, src);
     bool same = true;
@@ -768,50 +797,42 @@ __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t b
                                     __float_as_uint(nd[h].y) == __float_as_uint(sy_) &&
                                     __float_as_uint(nd[h].z) == __float_as_uint(sz_)));
     const bool uniform = __all_sync(kFullMask, same);
-    // uniform warp: lane 3 o + ch evaluates neighbour o, channel ch; lanes 0..3 the plane and
-    // normal terms of neighbour `lane`; every lane then has all four
-    float Eu[4][3] = {}, qn_s[4] = {}, n8_s[4] = {};
+    const float fx = ((float)(lane & 7) + 0.5f) * 0.125f;
+    // uniform warp: lane 3 o + ch evaluates neighbour o, channel ch; lanes 12..15 the plane and
+    // normal terms of neighbour lane - 12; the results go to the warp's shared copy
     if (uniform) {
-        float Yb[9];
-        sh_lobe(sx_, sy_, sz_, Yb);
-        const int o = lane / 3, ch = lane - 3 * (lane / 3);
-        float e = 0.f;
-        const uint32_t qo = pick_u4(q, o < 4 ? o : 0);
-        if (lane < 12 && qo != GI_PROBE_NONE) {
-            const float *c = a.sh + (size_t)((qo >> 19) * a.tiles_x + ((qo & 0xFFFFu) >> 3)) * GI_SH_STRIDE + ch;
+        if (lane < 12) {
+            const int o = lane / 3, ch = lane - 3 * (lane / 3);
+            float e = 0.f;
+            if (pick_u4(q, o) != GI_PROBE_NONE) {
+                float Yb[9];
+                sh_lobe(sx_, sy_, sz_, Yb);
+                const float *c = reinterpret_cast<const float *>(s.c[o]) + ch;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) e += Yb[k] * __ldg(c + 3 * k);
+                for (int k = 0; k < 9; ++k) e += Yb[k] * c[3 * k];
+            }
+            reinterpret_cast<float *>(s.eu)[4 * o + ch] = e;
+        } else if (lane < 16) {
+            const int o = lane - 12;
+            float qn_u = 0.f, n8_u = 0.f;
+            if (pick_u4(q, o) != GI_PROBE_NONE) nb_terms(s, o, sx_, sy_, sz_, qn_u, n8_u);
+            reinterpret_cast<float *>(s.eu)[4 * o + 3] = qn_u;
+            reinterpret_cast<float *>(&s.n8)[o] = n8_u;
         }
-        const float fn = a.cam.fwd[0] * sx_ + a.cam.fwd[1] * sy_ + a.cam.fwd[2] * sz_;
-        const float rn = a.cam.right[0] * sx_ + a.cam.right[1] * sy_ + a.cam.right[2] * sz_;
-        const float un = a.cam.up[0] * sx_ + a.cam.up[1] * sy_ + a.cam.up[2] * sz_;
-        float qn_u = 0.f, n8_u = 0.f;
-        const uint32_t q4 = pick_u4(q, lane & 3);
-        if (lane < 4 && q4 != GI_PROBE_NONE) neighbour_terms(a, q4, sx_, sy_, sz_, fn, rn, un, qn_u, n8_u);
-#pragma unroll
-        for (int oo = 0; oo < 4; ++oo) {
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) Eu[oo][cc] = __shfl_sync(kFullMask, e, 3 * oo + cc);
-            qn_s[oo] = __shfl_sync(kFullMask, qn_u, oo);
-            n8_s[oo] = __shfl_sync(kFullMask, n8_u, oo);
-        }
-    }
-    // the two pixels one after the other (selects, not indexing: the arrays stay in registers); the
-    // uniform and the per-pixel forms in separate loops, so that each keeps only its own state live
-    if (uniform) {
+        __syncwarp();
 #pragma unroll 1
         for (int h = 0; h < 2; ++h)
-            interp_pixel<true>(a, x, y0 + 4 * h, tx, ty, h ? nd[1] : nd[0], h ? pix[1] : pix[0], h ? inb[1] : inb[0],
-                               h ? act[1] : act[0], q, Eu, qn_s, n8_s);
+            interp_pixel<true>(a, s, x, y0 + 4 * h, fx, ((float)((lane >> 3) + 4 * h) + 0.5f) * 0.125f,
+                               h ? nd[1] : nd[0], h ? pix[1] : pix[0], h ? inb[1] : inb[0], h ? act[1] : act[0], q);
     } else {
 #pragma unroll 1
         for (int h = 0; h < 2; ++h)
-            interp_pixel<false>(a, x, y0 + 4 * h, tx, ty, h ? nd[1] : nd[0], h ? pix[1] : pix[0], h ? inb[1] : inb[0],
-                                h ? act[1] : act[0], q, Eu, qn_s, n8_s);
+            interp_pixel<false>(a, s, x, y0 + 4 * h, fx, ((float)((lane >> 3) + 4 * h) + 0.5f) * 0.125f,
+                                h ? nd[1] : nd[0], h ? pix[1] : pix[0], h ? inb[1] : inb[0], h ? act[1] : act[0], q);
     }
 }
 
-__global__ void __launch_bounds__(256, 3) k_interpolate(InterpArgs a) { interpolate_body(a, blockIdx.x, blockIdx.y); }
+__global__ void __launch_bounds__(256, 4) k_interpolate(InterpArgs a) { interpolate_body(a, blockIdx.x, blockIdx.y); }
 
 static bool layout_matches(const gi_probe_layout &l, uint32_t w, uint32_t h) {
     return l.tiles_x == (w + 7) / 8 && l.tiles_y == (h + 7) / 8 && l.num_probes == l.tiles_x * l.tiles_y &&
@@ -1067,7 +1088,7 @@ __global__ void __launch_bounds__(256) k_integrate_batched(const IntegrateArgs *
     integrate_body(sa, blockIdx.x - __ldg(prefix + v));
 }
 
-__global__ void __launch_bounds__(256, 3) k_interpolate_batched(const InterpArgs *args, const uint32_t *prefix,
+__global__ void __launch_bounds__(256, 4) k_interpolate_batched(const InterpArgs *args, const uint32_t *prefix,
                                                                 uint32_t nviews) {
     __shared__ InterpArgs sa;
     const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
