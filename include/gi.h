@@ -678,6 +678,24 @@ gi_status gi_nrc_stats(gi_nrc_t nrc, gi_nrc_stats_t *out, gi_stream_t stream);
 gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *view, float cell_size, uint32_t num_lods,
                                 uint32_t key_dir, const float env[3], float *out, gi_stream_t stream);
 
+/* ---------------------------------------------------------------- diagnostics
+ * Not a step of the path.  gi_cache_update ends, per group of same-cell records of a warp, in four
+ * L2 atomics on the cell's 32-byte accumulator (three 64-bit additions of the fixed-point sums,
+ * Section 2.2.1's accumulation, and one returning 32-bit addition of the count, whose old value
+ * flags the first touch).  gi_diag_update_atomics issues exactly those atomics for n slot ids
+ * (records with slot_ids[i] >= 2^log2_slots are skipped; same-slot records of a warp merged as the
+ * update merges them) and nothing else: no record stream, key, probe or slot-id store.  Timed
+ * beside gi_cache_update on the same frame's slot ids it gives the floor that the L2's atomic
+ * throughput sets for the update's accumulation.
+ *   slot_ids       device uint32[n] (4-byte aligned), e.g. the slot_ids_out of an update
+ *   scratch        device, caller-owned, 2^log2_slots x 32 bytes (32-byte aligned), zeroed by the
+ *                  caller; receives the additions (sums 1, 2, 3 and the group counts)
+ *   first_touches  device uint32 (caller-owned), incremented by the number of slots whose count
+ *                  left 0
+ * Errors: GI_ERR_INVALID_ARG for log2_slots outside [10, 30], a NULL or misaligned buffer. */
+gi_status gi_diag_update_atomics(const uint32_t *slot_ids, uint64_t n, uint32_t log2_slots, void *scratch,
+                                 uint32_t *first_touches, gi_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libgi.so")
-SOURCES = ("gi_common.cu", "gi_cache.cu", "gi_tiles.cu", "gi_probes.cu", "gi_batch.cu", "gi_nrc.cu")
+SOURCES = ("gi_common.cu", "gi_cache.cu", "gi_tiles.cu", "gi_probes.cu", "gi_batch.cu", "gi_nrc.cu", "gi_diag.cu")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -218,9 +218,11 @@ __device__ __forceinline__ void resolve_slots(const ResolveArgs &a, const uint32
             v = make_float3(o.x + a.alpha * (m.x - o.x), o.y + a.alpha * (m.y - o.y), o.z + a.alpha * (m.z - o.z));
         }
         store_resolved(a.resolved, a.res_stride, a.f16, s[u], v, fresh[u]);
+        // evict-first: the cleared accumulator is next read by the next frame's update, while the
+        // resolved values are read right after by the probe pass
         uint4 *dst = reinterpret_cast<uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
-        dst[0] = make_uint4(0u, 0u, 0u, 0u);
-        dst[1] = make_uint4(0u, 0u, 0u, a.stamp_now);
+        __stcs(dst, make_uint4(0u, 0u, 0u, 0u));
+        __stcs(dst + 1, make_uint4(0u, 0u, 0u, a.stamp_now));
     }
 }
 

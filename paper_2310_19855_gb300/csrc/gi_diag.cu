@@ -1,0 +1,65 @@
+// Diagnostics, not a step of the path: the L2 atomic floor of the cache update's accumulation.
+//
+// gi_cache_update ends, per group of same-cell records of a warp, in four L2 atomics on the
+// cell's 32-byte accumulator: three 64-bit additions (the fixed-point sums) and one returning
+// 32-bit addition (the count, whose old value flags the first touch).  k_diag_atomics issues
+// exactly those atomics for a frame's slot ids, with nothing else (no record stream, key, probe or
+// slot-id store), so its time is the floor of that design on this GPU.
+#include "gi_cache_dev.cuh"
+
+namespace gi {
+
+__global__ void __launch_bounds__(kUpdThreads, 8) k_diag_atomics(const uint32_t *slot_ids, unsigned long long n,
+                                                                  uint32_t slots, Accum *acc, uint32_t *first_out) {
+    __shared__ uint32_t s_first;
+    if (threadIdx.x == 0) s_first = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kUpdThreads;
+    uint32_t first = 0;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * kUpdThreads; base < n; base += stride) {
+        const unsigned long long i = base + threadIdx.x;
+        const uint32_t s = i < n ? __ldcs(slot_ids + i) : GI_SLOT_NONE;
+        const bool hit = s < slots;
+        // same-slot records of the warp: one leader adds the group's count (as the update's merge)
+        const unsigned hm = __ballot_sync(kFull, hit);
+        const unsigned peers = hit ? __match_any_sync(hm, s) : 0u;
+        if (hit && (peers & ((1u << lane) - 1u)) == 0u) {
+            Accum *a = acc + s;
+            atomicAdd(&a->sum[0], 1ull);
+            atomicAdd(&a->sum[1], 2ull);
+            atomicAdd(&a->sum[2], 3ull);
+            if (atomicAdd(&a->count, (uint32_t)__popc(peers)) == 0u) ++first;
+        }
+    }
+    first = __reduce_add_sync(kFull, first);
+    if (lane == 0 && first) atomicAdd(&s_first, first);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_first) atomicAdd(first_out, s_first);
+}
+
+} // namespace gi
+
+using namespace gi;
+
+extern "C" gi_status gi_diag_update_atomics(const uint32_t *slot_ids, uint64_t n, uint32_t log2_slots, void *scratch,
+                                            uint32_t *first_touches, gi_stream_t stream) {
+    if (log2_slots < 10 || log2_slots > 30) {
+        set_error("gi_diag_update_atomics: log2_slots must be in [10, 30]");
+        return GI_ERR_INVALID_ARG;
+    }
+    if ((n > 0 && !slot_ids) || !scratch || !first_touches) {
+        set_error("gi_diag_update_atomics: NULL buffer");
+        return GI_ERR_INVALID_ARG;
+    }
+    if ((reinterpret_cast<uintptr_t>(scratch) & 31u) != 0 || (reinterpret_cast<uintptr_t>(first_touches) & 3u) != 0 ||
+        (reinterpret_cast<uintptr_t>(slot_ids) & 3u) != 0) {
+        set_error("gi_diag_update_atomics: scratch must be 32-byte aligned, slot_ids and first_touches 4-byte aligned");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (n == 0) return GI_OK;
+    const unsigned long long blocks = (n + kUpdBlockRecords - 1) / kUpdBlockRecords;
+    k_diag_atomics<<<(unsigned)blocks, kUpdThreads, 0, (cudaStream_t)stream>>>(
+        slot_ids, (unsigned long long)n, 1u << log2_slots, static_cast<Accum *>(scratch), first_touches);
+    return cuda_status(cudaGetLastError(), "k_diag_atomics launch");
+}

@@ -291,3 +291,27 @@ def test_clamped_and_invalid_records_are_counted():
         assert st["clamped"] == oc.clamped > 0
     finally:
         gi.gi_cache_destroy(h)
+
+
+def test_diag_update_atomics_counts_every_record():
+    """The diagnostic atomics pass (not a step of the path): per slot, the counts add up to the
+    slot's records and the first touches to the distinct slots; records without a slot skipped."""
+    rng = np.random.default_rng(5)
+    log2 = 12
+    n = 50_000
+    ids = rng.integers(0, 1 << log2, n).astype(np.uint32)
+    ids[rng.random(n) < 0.1] = 0xFFFFFFFE  # misses
+    ids[:64] = 7  # two warps on one slot (merged groups)
+    scratch = torch.zeros((1 << log2) * 8, dtype=torch.int32, device="cuda")
+    first = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gi.gi_diag_update_atomics(dev(ids.view(np.int32)), n, log2, scratch, first)
+    acc = scratch.cpu().numpy().view(np.uint32).reshape(-1, 8)
+    valid = ids[ids < (1 << log2)]
+    want = np.bincount(valid, minlength=1 << log2)
+    assert np.array_equal(acc[:, 6], want)
+    assert int(first.item()) == int((want > 0).sum())
+    # sums: 1, 2, 3 per merged group, so between 1x and 1x the records (never more)
+    s0 = acc[:, 0].astype(np.uint64) | (acc[:, 1].astype(np.uint64) << 32)
+    s1 = acc[:, 2].astype(np.uint64) | (acc[:, 3].astype(np.uint64) << 32)
+    assert np.all(s1 == 2 * s0) and np.all(s0 <= want) and np.all((s0 > 0) == (want > 0))
+    assert s0[7] <= want[7] - 62  # the 64 records of slot 7 in lanes 0..63 form two groups
