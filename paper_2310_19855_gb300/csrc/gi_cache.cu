@@ -176,7 +176,8 @@ static inline int update_blocks(unsigned long long n) {
 // ---------------------------------------------------------------- resolve
 
 
-constexpr int kResUnroll = 4;
+constexpr int kResUnroll = 2;
+constexpr int kResBlocksPerSm = 4;  // resident blocks of k_resolve per SM (its persistent grid)
 
 // Resolve up to kResUnroll touched slots (0xFFFFFFFF = none), their loads issued together:
 // mean = sum / (count 2^24); a cell without history (never resolved, or evicted by an earlier
@@ -206,11 +207,9 @@ __device__ __forceinline__ void resolve_slots(const ResolveArgs &a, const uint32
         const unsigned long long s0 = ((unsigned long long)lo[u].y << 32) | lo[u].x;
         const unsigned long long s1 = ((unsigned long long)lo[u].w << 32) | lo[u].z;
         const unsigned long long s2 = ((unsigned long long)hi[u].y << 32) | hi[u].x;
-        const float fc = (float)hi[u].z;
-        // mean = sum / (count 2^24)
-        const float3 m = make_float3(__fdiv_rn(__ull2float_rn(s0), fc) * 5.9604644775390625e-8f,
-                                     __fdiv_rn(__ull2float_rn(s1), fc) * 5.9604644775390625e-8f,
-                                     __fdiv_rn(__ull2float_rn(s2), fc) * 5.9604644775390625e-8f);
+        // mean = sum / (count 2^24): one reciprocal, three products (within an ulp of the quotient)
+        const float rc = __frcp_rn((float)hi[u].z) * 5.9604644775390625e-8f;
+        const float3 m = make_float3(__ull2float_rn(s0) * rc, __ull2float_rn(s1) * rc, __ull2float_rn(s2) * rc);
         fresh_new += hi[u].w == 0u ? 1u : 0u;
         float3 v = m;
         if (!fresh[u]) {
@@ -270,7 +269,7 @@ __device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk,
     else resolve_list_body(a, blk, nblk);
 }
 
-__global__ void __launch_bounds__(kResThreads, 3) k_resolve(ResolveArgs a) { resolve_body(a, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(kResThreads, kResBlocksPerSm) k_resolve(ResolveArgs a) { resolve_body(a, blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------- queries
 
@@ -784,7 +783,7 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
         s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<0>, kUpdThreads, 0),
                         "occupancy");
         c->upd_blocks = c->sms * std::max(per_sm, 1);
-        c->res_blocks = c->sms * 3;
+        c->res_blocks = c->sms * kResBlocksPerSm;
         c->tres_blocks = c->sms * tile_resolve_blocks_per_sm();
     }
     if (s == GI_OK) s = cuda_status(cudaDeviceSynchronize(), "create sync");
