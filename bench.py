@@ -61,11 +61,14 @@ class L2Flush:
 REFERENCE_BUDGET_S = 90.0
 
 # DRAM traffic per launch of the dominant kernel from an ncu capture (profiles/), keyed by
-# "configuration:kernel" and by the source it was taken on; null when the source has changed since.
+# "configuration:kernel" and by the source it was taken on; null when that source has changed
+# since.  A source is a file of csrc/, or (file, first line, line after the last) for one section.
+UPDATE_SECTION = ("gi_cache.cu", "// ---------------------------------------------------------------- update",
+                  "// ---------------------------------------------------------------- resolve")
 NCU_TRAFFIC = {
-    # k_update, boxes-1080p (profiles/k_update_boxes-1080p.md): 159.6 MB read + 21.4 MB written
-    "2:update": {"bytes_per_launch": 180966912, "sources": ("gi_cache.cu", "gi_cache_dev.cuh", "gi_internal.cuh"),
-                 "source_sha": "af27052fbc1da58c"},
+    # k_update, boxes-1080p (profiles/k_update_boxes-1080p.md): 159.6 MB read + 21.9 MB written
+    "2:update": {"bytes_per_launch": 181539072, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
+                 "source_sha": "f1061c0841969a2d"},
     # k_nrc_adam_table, Cornell 1080p (profiles/nrc_training_cornell-1080p.md): 3.22 TB/s x 40.16 us
     "4:adam_table": {"bytes_per_launch": 129501000, "sources": ("gi_nrc.cu",), "source_sha": "94a0221974ed412e"},
 }
@@ -75,14 +78,18 @@ def ncu_traffic(key):
     tr = NCU_TRAFFIC.get(key)
     if not tr:
         return None
-    srcs = [os.path.join(ROOT, "paper_2310_19855_gb300", "csrc", f) for f in tr["sources"]]
-    return tr["bytes_per_launch"] if _source_sha(srcs) == tr["source_sha"] else None
+    return tr["bytes_per_launch"] if _source_sha(tr["sources"]) == tr["source_sha"] else None
 
 
-def _source_sha(paths):
+def _source_sha(sources):
     h = hashlib.sha256()
-    for p in paths:
-        h.update(open(p, "rb").read())
+    for src in sources:
+        name = src if isinstance(src, str) else src[0]
+        text = open(os.path.join(ROOT, "paper_2310_19855_gb300", "csrc", name), "rb").read()
+        if not isinstance(src, str):
+            a = text.index(src[1].encode())
+            text = text[a:text.index(src[2].encode(), a)]
+        h.update(text)
     return h.hexdigest()[:16]
 
 

@@ -176,33 +176,38 @@ static inline int update_blocks(unsigned long long n) {
 // ---------------------------------------------------------------- resolve
 
 
-constexpr int kResUnroll = 2;
-constexpr int kResBlocksPerSm = 4;  // resident blocks of k_resolve per SM (its persistent grid)
+// Touch-list form: 2 list entries per thread and iteration, 4 resident blocks per SM (56
+// registers); bitmap form: a word's set bits 4 at a time, 3 blocks per SM.  (Sweeps at 1080p and
+// 4K: the list form within 45-48 us for 3 to 8 blocks and 1 to 4 entries, the bitmap form 126 us
+// at 4 bits and 3 blocks against 135 us at 2 and 4.)
+constexpr int kResListUnroll = 2, kResListBlocksPerSm = 4;
+constexpr int kResBmUnroll = 4, kResBmBlocksPerSm = 3;
 
-// Resolve up to kResUnroll touched slots (0xFFFFFFFF = none), their loads issued together:
+// Resolve up to U touched slots (0xFFFFFFFF = none), their loads issued together:
 // mean = sum / (count 2^24); a cell without history (never resolved, or evicted by an earlier
 // resolve) takes the mean, the others blend; accumulator cleared, stamp = frame + 1.
-__device__ __forceinline__ void resolve_slots(const ResolveArgs &a, const uint32_t (&s)[kResUnroll], uint32_t &fresh_new) {
-    uint4 lo[kResUnroll], hi[kResUnroll];
+template <int U>
+__device__ __forceinline__ void resolve_slots(const ResolveArgs &a, const uint32_t (&s)[U], uint32_t &fresh_new) {
+    uint4 lo[U], hi[U];
 #pragma unroll
-    for (int u = 0; u < kResUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
         if (s[u] != 0xFFFFFFFFu) {
             const uint4 *src = reinterpret_cast<const uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
             lo[u] = __ldcg(src);
             hi[u] = __ldcg(src + 1);
         }
     }
-    bool fresh[kResUnroll];
-    float3 old[kResUnroll];
+    bool fresh[U];
+    float3 old[U];
 #pragma unroll
-    for (int u = 0; u < kResUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
         const uint32_t stamp = hi[u].w;
         // no history: never resolved, or evicted by an earlier resolve (untouched E frames)
         fresh[u] = stamp == 0u || (a.has_lr && (a.lr - (stamp - 1u)) >= a.evict);
         if (s[u] != 0xFFFFFFFFu && !fresh[u]) old[u] = load_resolved(a.resolved, a.res_stride, a.f16, s[u]);
     }
 #pragma unroll
-    for (int u = 0; u < kResUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
         if (s[u] == 0xFFFFFFFFu) continue;
         const unsigned long long s0 = ((unsigned long long)lo[u].y << 32) | lo[u].x;
         const unsigned long long s1 = ((unsigned long long)lo[u].w << 32) | lo[u].z;
@@ -225,25 +230,27 @@ __device__ __forceinline__ void resolve_slots(const ResolveArgs &a, const uint32
     }
 }
 
-// touch-list form: kResUnroll list entries per thread and iteration
+// touch-list form: U list entries per thread and iteration
+template <int U>
 __device__ __forceinline__ void resolve_list_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
     const uint32_t n = __ldcg(&a.ctr->touch_count);
     const uint32_t stride = nblk * kResThreads;
     uint32_t fresh_new = 0;
-    for (uint32_t i0 = blk * kResThreads + threadIdx.x; i0 < n; i0 += kResUnroll * stride) {
-        uint32_t s[kResUnroll];
+    for (uint32_t i0 = blk * kResThreads + threadIdx.x; i0 < n; i0 += U * stride) {
+        uint32_t s[U];
 #pragma unroll
-        for (int u = 0; u < kResUnroll; ++u) {
+        for (int u = 0; u < U; ++u) {
             const uint32_t i = i0 + u * stride;
             s[u] = i < n ? __ldcs(a.touch + i) : 0xFFFFFFFFu;
         }
-        resolve_slots(a, s, fresh_new);
+        resolve_slots<U>(a, s, fresh_new);
     }
     resolve_finish(a.ctr, a.occ_out, a.stamp_now, nblk * (kResThreads / 32), fresh_new);
 }
 
 // bitmap form: a thread takes a word (32 consecutive slots), clears it and resolves its set bits
-// kResUnroll at a time, in slot order
+// U at a time, in slot order
+template <int U>
 __device__ __forceinline__ void resolve_bm_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
     const uint32_t stride = nblk * kResThreads;
     uint32_t fresh_new = 0;
@@ -252,24 +259,29 @@ __device__ __forceinline__ void resolve_bm_body(const ResolveArgs &a, uint32_t b
         if (!bits) continue;
         a.bitmap[w] = 0u;
         while (bits) {
-            uint32_t s[kResUnroll];
+            uint32_t s[U];
 #pragma unroll
-            for (int u = 0; u < kResUnroll; ++u) {
+            for (int u = 0; u < U; ++u) {
                 s[u] = bits ? w * 32u + (uint32_t)(__ffs(bits) - 1) : 0xFFFFFFFFu;
                 bits &= bits - 1u;
             }
-            resolve_slots(a, s, fresh_new);
+            resolve_slots<U>(a, s, fresh_new);
         }
     }
     resolve_finish(a.ctr, a.occ_out, a.stamp_now, nblk * (kResThreads / 32), fresh_new);
 }
 
 __device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
-    if (a.bitmap) resolve_bm_body(a, blk, nblk);
-    else resolve_list_body(a, blk, nblk);
+    if (a.bitmap) resolve_bm_body<kResBmUnroll>(a, blk, nblk);
+    else resolve_list_body<kResListUnroll>(a, blk, nblk);
 }
 
-__global__ void __launch_bounds__(kResThreads, kResBlocksPerSm) k_resolve(ResolveArgs a) { resolve_body(a, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(kResThreads, kResListBlocksPerSm) k_resolve(ResolveArgs a) {
+    resolve_list_body<kResListUnroll>(a, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(kResThreads, kResBmBlocksPerSm) k_resolve_bitmap(ResolveArgs a) {
+    resolve_bm_body<kResBmUnroll>(a, blockIdx.x, gridDim.x);
+}
 
 // ---------------------------------------------------------------- queries
 
@@ -783,7 +795,7 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
         s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<0>, kUpdThreads, 0),
                         "occupancy");
         c->upd_blocks = c->sms * std::max(per_sm, 1);
-        c->res_blocks = c->sms * kResBlocksPerSm;
+        c->res_blocks = c->sms * (c->bitmap ? kResBmBlocksPerSm : kResListBlocksPerSm);
         c->tres_blocks = c->sms * tile_resolve_blocks_per_sm();
     }
     if (s == GI_OK) s = cuda_status(cudaDeviceSynchronize(), "create sync");
@@ -879,7 +891,10 @@ gi_status gi_cache_resolve(gi_cache_t c, uint32_t frame, gi_stream_t stream) {
         s = tile_resolve_launch(ta, c->tres_blocks, st);
     } else {
         const ResolveArgs a = cache_resolve_args(c, frame);
-        k_resolve<<<c->res_blocks, kResThreads, 0, st>>>(a);
+        if (a.bitmap)
+            k_resolve_bitmap<<<c->res_blocks, kResThreads, 0, st>>>(a);
+        else
+            k_resolve<<<c->res_blocks, kResThreads, 0, st>>>(a);
         s = cuda_status(cudaGetLastError(), "k_resolve launch");
     }
     if (s != GI_OK) return s;
