@@ -496,10 +496,10 @@ def run_native(args, rank, world, local_rank):
                      "algorithmic_bytes_per_launch": alg[dominant], "peak_source": peak_src},
         "update_atomic_floor": {
             "kernel": "k_diag_atomics (gi_diag_update_atomics)", "ms": floor_ms, "update_ms": float(pass_ms[1]),
-            "update_over_floor": float(pass_ms[1]) / floor_ms, "first_touches": floor_first,
-            "note": "the update's four accumulator atomics per merged record group (3 x 64-bit add + returning "
-                    "32-bit count add) on a frame's own slot ids, nothing else, L2 flushed before each launch: "
-                    "the floor the L2's atomic throughput sets for k_update"},
+            "update_over_floor": float(pass_ms[1]) / floor_ms, "touched_slots": floor_first,
+            "note": "the update's accumulation alone (bitmap form: one 32-byte bulk reduction of the sums and count "
+                    "plus a bitmap bit per merged record group) on a frame's own slot ids, nothing else, L2 flushed "
+                    "before each launch: the floor the L2 sets for k_update"},
         "roofline_window": {"achieved": sum(alg[n] for n in ("update", "resolve", "integrate")) /
                                         (pass_ms[1:4].sum() * 1e-3) / 1e9, "peak": peak, "unit": "GB/s"},
         "cpu_baseline": cpu,
@@ -527,25 +527,27 @@ def run_native(args, rank, world, local_rank):
 
 
 def update_atomic_floor(gi, torch, slot_ids, R, log2_slots, flush, stream, steps):
-    """gi_diag_update_atomics on one frame's slot ids (the update's accumulator atomics and
-    nothing else) into a zeroed table of the cache's size, L2 flushed before each launch: mean
-    event-timed ms over the launches after 3 warm-up ones, and the first touches counted."""
-    scratch = torch.zeros((1 << log2_slots) * 8, dtype=torch.int32, device="cuda")
-    first = torch.zeros(1, dtype=torch.int32, device="cuda")
+    """gi_diag_update_atomics on one frame's slot ids (the update's accumulation in the form the
+    cache uses by default, the bitmap form, and nothing else) into a zeroed table of the cache's
+    size, L2 flushed before each launch: mean event-timed ms over the launches after 3 warm-up
+    ones, and the slots touched (bits set)."""
+    slots = 1 << log2_slots
+    scratch = torch.zeros(slots * 8 + slots // 32, dtype=torch.int32, device="cuda")
     n = max(3, min(steps, 50))
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n + 3)]
     for j in range(n + 3):
         scratch.zero_()
-        first.zero_()
         flush.zero_()
         ev[j][0].record(stream)
-        gi.gi_diag_update_atomics(slot_ids, R, log2_slots, scratch, first, stream)
+        gi.gi_diag_update_atomics(slot_ids, R, log2_slots, scratch, first_touch=gi.GI_FIRST_TOUCH_BITMAP,
+                                  stream=stream)
         ev[j][1].record(stream)
     torch.cuda.synchronize()
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev[3:]]))
-    out = (ms, int(first.item()))
+    bits = scratch[slots * 8:].cpu().numpy().view(np.uint32)
+    touched = int(np.unpackbits(bits.view(np.uint8)).sum())
     del scratch
-    return out
+    return ms, touched
 
 
 def tile_bytes(R, touched_tiles, touched_cells, live_in_touched, res_b, tile_slots):

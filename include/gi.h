@@ -84,12 +84,15 @@ typedef void *gi_stream_t; /* cudaStream_t */
  *   resolved_format GI_RESOLVED_F32 (16 B per slot) or GI_RESOLVED_F16 (8 B)
  *   rebuild_load    fraction of slots occupied (live + stale cells) above which the
  *                   next update first compacts the table, in [0.25, 0.95]
- *   first_touch     how the slots touched since the last resolve are recorded:
- *                   GI_FIRST_TOUCH_LIST (a list, appended per block: cheapest update),
- *                   GI_FIRST_TOUCH_BITMAP (one bit per slot, walked in slot order by the
- *                   resolve: fewer DRAM bursts when the table exceeds the L2), or
- *                   GI_FIRST_TOUCH_AUTO (the bitmap when the 32-byte accumulators of all
- *                   slots exceed the device's L2, else the list).  Results are identical.
+ *   first_touch     how the update accumulates and records the slots touched since the
+ *                   last resolve: GI_FIRST_TOUCH_LIST (per group of same-cell records of a warp,
+ *                   three 64-bit additions and a returning count addition; the first toucher of
+ *                   a slot appends it to a list, staged per block), GI_FIRST_TOUCH_BITMAP (the
+ *                   group's sums and count in one 32-byte bulk reduction from shared memory,
+ *                   cp.reduce.async.bulk, and a non-returning set of the slot's bit in a bitmap
+ *                   of one bit per slot that the resolve walks in slot order: fewer L2
+ *                   operations per record), or GI_FIRST_TOUCH_AUTO (the bitmap).  Results are
+ *                   identical.
  *   tiles           0: a slot holds one cell.  1: two-level cache of Section 2.2.3 ("Prefiltering
  *                   Radiance"): a slot holds a tile of 8 x 8 cells on the plane that drops the
  *                   direction code's axis (in-plane cell coordinates floor-divided by 8 form the
@@ -679,22 +682,27 @@ gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *view, float 
                                 uint32_t key_dir, const float env[3], float *out, gi_stream_t stream);
 
 /* ---------------------------------------------------------------- diagnostics
- * Not a step of the path.  gi_cache_update ends, per group of same-cell records of a warp, in four
- * L2 atomics on the cell's 32-byte accumulator (three 64-bit additions of the fixed-point sums,
- * Section 2.2.1's accumulation, and one returning 32-bit addition of the count, whose old value
- * flags the first touch).  gi_diag_update_atomics issues exactly those atomics for n slot ids
- * (records with slot_ids[i] >= 2^log2_slots are skipped; same-slot records of a warp merged as the
- * update merges them) and nothing else: no record stream, key, probe or slot-id store.  Timed
- * beside gi_cache_update on the same frame's slot ids it gives the floor that the L2's atomic
- * throughput sets for the update's accumulation.
+ * Not a step of the path.  gi_cache_update ends, per group of same-cell records of a warp, in L2
+ * operations on the cell's 32-byte accumulator (Section 2.2.1's accumulation in 64-bit fixed
+ * point): in the list form (GI_FIRST_TOUCH_LIST) three 64-bit additions of the sums and one
+ * returning 32-bit addition of the count, whose old value flags the first touch; in the bitmap
+ * form (GI_FIRST_TOUCH_BITMAP, and AUTO) one 32-byte bulk reduction of the sums and count from
+ * shared memory and a non-returning set of the slot's bit.  gi_diag_update_atomics issues exactly
+ * those operations of the given form for n slot ids (records with slot_ids[i] >= 2^log2_slots are
+ * skipped; same-slot records of a warp merged as the update merges them) and nothing else: no
+ * record stream, key, probe or slot-id store.  Timed beside gi_cache_update on the same frame's
+ * slot ids it gives the floor that the L2 sets for the update's accumulation.
  *   slot_ids       device uint32[n] (4-byte aligned), e.g. the slot_ids_out of an update
- *   scratch        device, caller-owned, 2^log2_slots x 32 bytes (32-byte aligned), zeroed by the
- *                  caller; receives the additions (sums 1, 2, 3 and the group counts)
- *   first_touches  device uint32 (caller-owned), incremented by the number of slots whose count
- *                  left 0
- * Errors: GI_ERR_INVALID_ARG for log2_slots outside [10, 30], a NULL or misaligned buffer. */
-gi_status gi_diag_update_atomics(const uint32_t *slot_ids, uint64_t n, uint32_t log2_slots, void *scratch,
-                                 uint32_t *first_touches, gi_stream_t stream);
+ *   first_touch    the form: GI_FIRST_TOUCH_LIST, GI_FIRST_TOUCH_BITMAP or AUTO (the bitmap)
+ *   scratch        device, caller-owned, zeroed by the caller, 32-byte aligned: 2^log2_slots
+ *                  32-byte accumulators (receiving sums 1, 2, 3 and the group counts), followed
+ *                  in the bitmap form by the bitmap, 2^log2_slots / 8 bytes
+ *   first_touches  list form: device uint32 (caller-owned), incremented by the number of slots
+ *                  whose count left 0; unused (may be NULL) in the bitmap form
+ * Errors: GI_ERR_INVALID_ARG for log2_slots outside [10, 30], an unknown form, a NULL or
+ * misaligned buffer. */
+gi_status gi_diag_update_atomics(const uint32_t *slot_ids, uint64_t n, uint32_t log2_slots, uint32_t first_touch,
+                                 void *scratch, uint32_t *first_touches, gi_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -200,7 +200,7 @@ def lib() -> ctypes.CDLL:
             "gi_probes_integrate_nrc": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(gi_probes), c_vp, c_u32,
                                                        ctypes.POINTER(c_f32), c_vp]),
             "gi_nrc_stats": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_nrc_stats_t), c_vp]),
-            "gi_diag_update_atomics": (ctypes.c_int, [c_vp, c_u64, c_u32, c_vp, c_vp, c_vp]),
+            "gi_diag_update_atomics": (ctypes.c_int, [c_vp, c_u64, c_u32, c_u32, c_vp, c_vp, c_vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -430,11 +430,13 @@ def gi_cell_means_noalloc(hits: gi_hits, view: gi_view, out, cell_size: float = 
                                       int(key_dir), e, _ptr(out), _stream(stream)), "gi_cell_means_noalloc")
 
 
-def gi_diag_update_atomics(slot_ids, n: int, log2_slots: int, scratch, first_touches, stream=None) -> None:
-    """Diagnostics (see gi.h): the update's accumulator atomics alone for these slot ids, into the
-    caller's zeroed scratch (2^log2_slots x 32 bytes); first_touches: device uint32 counter."""
-    check(lib().gi_diag_update_atomics(_ptr(slot_ids), int(n), int(log2_slots), _ptr(scratch), _ptr(first_touches),
-                                       _stream(stream)), "gi_diag_update_atomics")
+def gi_diag_update_atomics(slot_ids, n: int, log2_slots: int, scratch, first_touches=None,
+                           first_touch: int = GI_FIRST_TOUCH_AUTO, stream=None) -> None:
+    """Diagnostics (see gi.h): the update's accumulation alone, in the given form, for these slot
+    ids, into the caller's zeroed scratch (2^log2_slots x 32 bytes of accumulators, then in the
+    bitmap form 2^log2_slots / 8 bytes of bitmap); first_touches: device uint32 counter (list form)."""
+    check(lib().gi_diag_update_atomics(_ptr(slot_ids), int(n), int(log2_slots), int(first_touch), _ptr(scratch),
+                                       _ptr(first_touches), _stream(stream)), "gi_diag_update_atomics")
 
 
 def gi_batch_create(n_views: int, rays_per_probe: int, tuning: gi_batch_tuning | None = None) -> int:

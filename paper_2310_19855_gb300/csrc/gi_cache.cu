@@ -31,12 +31,20 @@
 namespace gi {
 
 // ---------------------------------------------------------------- update
-// The count's returning add detects the first touch of a cell this frame.  With a.bitmap that
-// touch sets the slot's bit (a non-returning atomicOr); without, it goes to the block's
-// shared-memory list and then, once per block, to the touch list.
+// Touch list (a.bitmap NULL): three 64-bit reductions of the sums and a returning add of the
+// count, whose old value 0 marks the first touch of the cell this frame; first touches go to the
+// block's shared-memory list and then, once per block, to the touch list.
+// Bitmap: the group's sums and count in one 32-byte bulk reduction from the thread's 32-byte
+// shared-memory slot (rewritten only once its previous reduction has read it), and the slot's bit
+// set by a non-returning atomicOr.  The block's shared buffer is the first-touch list in the one
+// form and the reduction slots in the other.  (1080p: 76 us against 80 us for the list form; a
+// plain load skipping the atomicOr when the bit is already set, 78 us; two slots per thread, 76 us.)
+static_assert(kUpdBlockRecords * 4 == kUpdThreads * 32, "one 32-byte reduction slot per thread");
 template <int KEY_DIR>
 __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, uint32_t nblk) {
-    __shared__ uint32_t s_touch[kUpdBlockRecords];
+    __shared__ __align__(32) unsigned long long s_buf[kUpdBlockRecords / 2];
+    uint32_t *s_touch = reinterpret_cast<uint32_t *>(s_buf);
+    unsigned long long *s_red = s_buf + 4 * threadIdx.x;
     const bool bitmap = a.bitmap != nullptr;
     __shared__ uint32_t s_n, s_base, s_clamped, s_maxp;
     if (threadIdx.x == 0) {
@@ -128,13 +136,21 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
             my_maxp = max(my_maxp, k + 1u);
             if (slot != GI_SLOT_NONE) {
                 Accum *ac = a.accum + (size_t)slot * a.acc_stride;
-                atomicAdd(&ac->sum[0], q0);
-                atomicAdd(&ac->sum[1], q1);
-                atomicAdd(&ac->sum[2], q2);
-                // the count was cleared by the last resolve: the first adder this frame records the slot
-                if (atomicAdd(&ac->count, cnt) == 0u) {
-                    if (bitmap) atomicOr(a.bitmap + (slot >> 5), 1u << (slot & 31u));
-                    else s_touch[atomicAdd(&s_n, 1u)] = slot;
+                if (bitmap) {
+                    bulk_wait_read();  // the previous reduction has read the slot
+                    s_red[0] = q0;
+                    s_red[1] = q1;
+                    s_red[2] = q2;
+                    s_red[3] = cnt;
+                    bulk_add_accum(ac, s_red);
+                    const uint32_t bit = 1u << (slot & 31u);
+                    atomicOr(a.bitmap + (slot >> 5), bit);
+                } else {
+                    atomicAdd(&ac->sum[0], q0);
+                    atomicAdd(&ac->sum[1], q1);
+                    atomicAdd(&ac->sum[2], q2);
+                    // the count was cleared by the last resolve: the first adder this frame records the slot
+                    if (atomicAdd(&ac->count, cnt) == 0u) s_touch[atomicAdd(&s_n, 1u)] = slot;
                 }
             } else {
                 atomicAdd(&a.ctr->dropped, (unsigned long long)cnt);
@@ -144,6 +160,8 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
         const uint32_t my_slot = __shfl_sync(kFull, slot, lead);
         if (inr) __stcs(a.slot_ids + i, hit ? my_slot : (miss ? GI_SLOT_MISS : GI_SLOT_NONE));
     }
+    // the bulk reductions complete (their sums visible) before the block ends
+    if (bitmap) bulk_wait_all();
     // block totals of the statistics, one global atomic each
     my_clamped = __reduce_add_sync(kFull, my_clamped);
     my_maxp = __reduce_max_sync(kFull, my_maxp);
@@ -760,10 +778,7 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
     }
     // First touches: a slot bitmap walked in slot order by the resolve when the accumulators
     // exceed L2 (its ordered accesses then save DRAM traffic), else a touch list (cheaper updates).
-    int l2 = 0;
-    if (s == GI_OK) s = cuda_status(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device), "L2 size");
-    const bool use_bitmap = !c->tiles && (cfg->first_touch == GI_FIRST_TOUCH_BITMAP ||
-                                          (cfg->first_touch == GI_FIRST_TOUCH_AUTO && N * sizeof(Accum) > (size_t)l2));
+    const bool use_bitmap = !c->tiles && cfg->first_touch != GI_FIRST_TOUCH_LIST;
     if (s == GI_OK && c->tiles) {
         s = cuda_status(cudaMalloc(&c->tmask, N * sizeof(unsigned long long)), "cudaMalloc tile masks");
         if (s == GI_OK) s = cuda_status(cudaMemset(c->tmask, 0, N * sizeof(unsigned long long)), "memset");

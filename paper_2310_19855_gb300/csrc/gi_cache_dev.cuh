@@ -18,6 +18,24 @@ constexpr int kUpdBlockRecords = 2048;
 constexpr int kResThreads = 256;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// ---------------------------------------------------------------- bulk reductions
+// A cell's whole 32-byte accumulator {u64 r, g, b; u32 count; u32 stamp} in one L2 operation:
+// the thread writes {r, g, b, count} to a 32-byte shared-memory slot and the bulk-copy unit adds
+// it to global memory as four 64-bit lanes (cp.reduce.async.bulk .add.u64; the count lands in the
+// low half of the last lane, where it cannot carry into the stamp: a frame adds far fewer than
+// 2^32 to a count and every resolve clears it).  Both addresses 32-byte aligned.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_add_accum(void *dst, const unsigned long long *src_smem) {
+    // the generic-proxy writes of the slot become visible to the bulk-copy (async) proxy
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(src_smem);
+    const unsigned long long ga = (unsigned long long)__cvta_generic_to_global(dst);
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], 32;" ::"l"(ga), "r"(sa)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- hashing
 // xxHash32 of a single 4-byte word with a seed (xxHash specification).
 __device__ __forceinline__ uint32_t xxh32_word(uint32_t w, uint32_t seed) {

@@ -121,9 +121,10 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.gi_probes_gather(None, None, None, None, 64, None, None, None) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_probes_filter(None, None, None, None, 0, None) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_probes_project(None, None, None) == gi.GI_ERR_INVALID_ARG
-    assert lib.gi_diag_update_atomics(None, 0, 9, None, None, None) == gi.GI_ERR_INVALID_ARG
-    assert lib.gi_diag_update_atomics(None, 0, 31, None, None, None) == gi.GI_ERR_INVALID_ARG
-    assert lib.gi_diag_update_atomics(None, 16, 16, None, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_diag_update_atomics(None, 0, 9, 0, None, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_diag_update_atomics(None, 0, 31, 0, None, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_diag_update_atomics(None, 0, 16, 3, None, None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_diag_update_atomics(None, 16, 16, 0, None, None, None) == gi.GI_ERR_INVALID_ARG
 
 
 def test_surrogate_arguments_are_rejected_on_the_host(lib):

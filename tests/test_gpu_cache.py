@@ -293,25 +293,36 @@ def test_clamped_and_invalid_records_are_counted():
         gi.gi_cache_destroy(h)
 
 
-def test_diag_update_atomics_counts_every_record():
-    """The diagnostic atomics pass (not a step of the path): per slot, the counts add up to the
-    slot's records and the first touches to the distinct slots; records without a slot skipped."""
+@pytest.mark.parametrize("form", [gi.GI_FIRST_TOUCH_LIST, gi.GI_FIRST_TOUCH_BITMAP])
+def test_diag_update_atomics_counts_every_record(form):
+    """The diagnostic accumulation pass (not a step of the path), in either form: per slot, the
+    counts add up to the slot's records; the first touches (list) or the bits (bitmap) mark exactly
+    the distinct slots; records without a slot skipped."""
     rng = np.random.default_rng(5)
     log2 = 12
     n = 50_000
     ids = rng.integers(0, 1 << log2, n).astype(np.uint32)
     ids[rng.random(n) < 0.1] = 0xFFFFFFFE  # misses
     ids[:64] = 7  # two warps on one slot (merged groups)
-    scratch = torch.zeros((1 << log2) * 8, dtype=torch.int32, device="cuda")
+    slots = 1 << log2
+    scratch = torch.zeros(slots * 8 + slots // 32, dtype=torch.int32, device="cuda")
     first = torch.zeros(1, dtype=torch.int32, device="cuda")
-    gi.gi_diag_update_atomics(dev(ids.view(np.int32)), n, log2, scratch, first)
-    acc = scratch.cpu().numpy().view(np.uint32).reshape(-1, 8)
-    valid = ids[ids < (1 << log2)]
-    want = np.bincount(valid, minlength=1 << log2)
+    gi.gi_diag_update_atomics(dev(ids.view(np.int32)), n, log2, scratch, first, first_touch=form)
+    raw = scratch.cpu().numpy().view(np.uint32)
+    acc = raw[: slots * 8].reshape(-1, 8)
+    valid = ids[ids < slots]
+    want = np.bincount(valid, minlength=slots)
     assert np.array_equal(acc[:, 6], want)
-    assert int(first.item()) == int((want > 0).sum())
-    # sums: 1, 2, 3 per merged group, so between 1x and 1x the records (never more)
+    assert np.all(acc[:, 7] == 0)  # the stamp word is never touched
+    if form == gi.GI_FIRST_TOUCH_LIST:
+        assert int(first.item()) == int((want > 0).sum())
+    else:
+        bits = np.unpackbits(raw[slots * 8:].view(np.uint8), bitorder="little").astype(bool)
+        assert np.array_equal(bits, want > 0)
+    # sums: 1, 2, 3 per merged group, so at most one group per record
     s0 = acc[:, 0].astype(np.uint64) | (acc[:, 1].astype(np.uint64) << 32)
     s1 = acc[:, 2].astype(np.uint64) | (acc[:, 3].astype(np.uint64) << 32)
-    assert np.all(s1 == 2 * s0) and np.all(s0 <= want) and np.all((s0 > 0) == (want > 0))
+    s2 = acc[:, 4].astype(np.uint64) | (acc[:, 5].astype(np.uint64) << 32)
+    assert np.all(s1 == 2 * s0) and np.all(s2 == 3 * s0)
+    assert np.all(s0 <= want) and np.all((s0 > 0) == (want > 0))
     assert s0[7] <= want[7] - 62  # the 64 records of slot 7 in lanes 0..63 form two groups
