@@ -1193,10 +1193,9 @@ __global__ void k_noalloc_means(const uint32_t *slot_ids, unsigned long long n, 
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (s < kNoAllocSlots) {
             const Accum a = accum[s];
-            const float fc = (float)a.count;
-            o = make_float4(__fdiv_rn(__ull2float_rn(a.sum[0]), fc) * 5.9604644775390625e-8f,
-                            __fdiv_rn(__ull2float_rn(a.sum[1]), fc) * 5.9604644775390625e-8f,
-                            __fdiv_rn(__ull2float_rn(a.sum[2]), fc) * 5.9604644775390625e-8f, 1.0f);
+            const float rc = __frcp_rn((float)a.count) * 5.9604644775390625e-8f;
+            o = make_float4(__ull2float_rn(a.sum[0]) * rc, __ull2float_rn(a.sum[1]) * rc, __ull2float_rn(a.sum[2]) * rc,
+                            1.0f);
         } else if (s == GI_SLOT_MISS) {
             o = make_float4(e0, e1, e2, 1.0f);
         }
