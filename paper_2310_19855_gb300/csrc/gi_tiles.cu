@@ -69,7 +69,7 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) { return a >
 // record's slot id is tile slot * 64 + cell.  (2) k_tile_compact: every tile touched since the
 // last resolve that has no accumulator block yet gets the next one (a per-frame index, cidx).
 // (3) k_tile_accumulate: per record the fixed-point radiance, merged per cell within the warp
-// and added into the cell's accumulator of its tile's block with reductions.  The accumulator
+// and added into the cell's accumulator of its tile's block with one 32-byte bulk reduction.  The accumulator
 // blocks of one frame are contiguous (touched tiles x 2 KB), so the reductions of a frame span
 // that range only, not the whole table: the cost of scattered reductions grows with the span.
 template <int KEY_DIR>
@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_accumulate(const uint32
                                                                     const float *r1, const float *r2,
                                                                     unsigned long long n, const uint32_t *cidx,
                                                                     uint32_t cells, Accum *accum) {
+    __shared__ __align__(32) unsigned long long s_red[kUpdThreads][4];
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -247,13 +248,18 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_accumulate(const uint32
             }
         }
         if (ok && (peers & ((1u << lane) - 1u)) == 0u) {
+            // the group's sums and count in one 32-byte bulk reduction (the stamp half of the
+            // last lane is unused in the blocks)
             Accum *ac = accum + (size_t)blk * kTileCells + (id % kTileCells);
-            atomicAdd(&ac->sum[0], q0);
-            atomicAdd(&ac->sum[1], q1);
-            atomicAdd(&ac->sum[2], q2);
-            atomicAdd(&ac->count, cnt);
+            bulk_wait_read();  // the previous reduction has read the slot
+            s_red[threadIdx.x][0] = q0;
+            s_red[threadIdx.x][1] = q1;
+            s_red[threadIdx.x][2] = q2;
+            s_red[threadIdx.x][3] = cnt;
+            bulk_add_accum(ac, s_red[threadIdx.x]);
         }
     }
+    bulk_wait_all();
 }
 
 // ---------------------------------------------------------------- resolve
