@@ -243,8 +243,10 @@ uint32_t gi_version(void);
 /*
  * Create a cache (Section 2.2.1): allocates the slot table (fingerprints,
  * 32-byte fixed-point accumulators, resolved radiance), a spare table for
- * compaction, the touch list and counters, on the current CUDA device.  The
- * library owns this memory until gi_cache_destroy.  Synchronous.
+ * compaction, the record of touched slots (a bitmap of one bit per slot, or a
+ * touch list of 4 bytes per slot in the list form) and counters, on the
+ * current CUDA device.  The library owns this memory until gi_cache_destroy.
+ * Synchronous.
  * Errors: GI_ERR_INVALID_ARG (cfg out of range), GI_ERR_OOM, GI_ERR_CUDA.
  */
 gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out);
