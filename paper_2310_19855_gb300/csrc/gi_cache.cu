@@ -863,7 +863,10 @@ gi_status gi_cache_update(gi_cache_t c, const gi_hits *hits, const gi_view *view
         if (s == GI_OK) c->touched_since_resolve = true;
         return s;
     }
-    const int blocks = update_blocks(hits->n);
+    // the bitmap form stages nothing per block: a resident grid strides over the records
+    const int blocks = c->bitmap ? (int)std::min<unsigned long long>((unsigned long long)c->upd_blocks,
+                                                                      (hits->n + kUpdThreads - 1) / kUpdThreads)
+                                 : update_blocks(hits->n);
     if (c->cfg.key_dir == GI_KEY_DIR_NORMAL)
         k_update<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(a);
     else
