@@ -859,7 +859,7 @@ gi_status gi_cache_update(gi_cache_t c, const gi_hits *hits, const gi_view *view
         ta.tmask = c->tmask;
         ta.cidx = c->cidx;
         ta.tlist = c->tlist;
-        s = tile_update_launch(ta, (int)c->cfg.key_dir, st);
+        s = tile_update_launch(ta, (int)c->cfg.key_dir, c->upd_blocks, st);
         if (s == GI_OK) c->touched_since_resolve = true;
         return s;
     }

@@ -243,7 +243,7 @@ struct TileResolveArgs {
     uint32_t *occ_out;
 };
 
-gi_status tile_update_launch(const TileUpdateArgs &a, int key_dir, cudaStream_t st);
+gi_status tile_update_launch(const TileUpdateArgs &a, int key_dir, int resident_blocks, cudaStream_t st);
 gi_status tile_resolve_launch(const TileResolveArgs &a, int blocks, cudaStream_t st);
 int tile_resolve_blocks_per_sm();
 gi_status tile_query_points_launch(const TileUpdateArgs &a, const TileArrays &t, uint32_t res_stride, int f16,

@@ -578,8 +578,10 @@ __global__ void k_tile_scan(TileArrays t, const unsigned long long *tmask, uint3
 }
 
 // ---------------------------------------------------------------- launchers
-gi_status tile_update_launch(const TileUpdateArgs &a, int key_dir, cudaStream_t st) {
-    const int blocks = (int)((a.u.n + kUpdBlockRecords - 1) / kUpdBlockRecords);
+gi_status tile_update_launch(const TileUpdateArgs &a, int key_dir, int resident_blocks, cudaStream_t st) {
+    // neither pass stages anything per block: resident grids stride over the records
+    const int blocks =
+        (int)std::min<unsigned long long>((unsigned long long)resident_blocks, (a.u.n + kUpdThreads - 1) / kUpdThreads);
     if (blocks == 0) return GI_OK;
     if (key_dir == GI_KEY_DIR_NORMAL)
         k_tile_key<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(a);
