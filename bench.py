@@ -66,9 +66,9 @@ REFERENCE_BUDGET_S = 90.0
 UPDATE_SECTION = ("gi_cache.cu", "// ---------------------------------------------------------------- update",
                   "// ---------------------------------------------------------------- resolve")
 NCU_TRAFFIC = {
-    # k_update, boxes-1080p (profiles/k_update_boxes-1080p.md): 158.5 MB read + 20.0 MB written
-    "2:update": {"bytes_per_launch": 178548736, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
-                 "source_sha": "3db383f21331d54b"},
+    # k_update, boxes-1080p (profiles/k_update_boxes-1080p.md): 158.5 MB read + 21.0 MB written
+    "2:update": {"bytes_per_launch": 179567104, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
+                 "source_sha": "7878ce80b2d3d135"},
     # k_nrc_adam_table, Cornell 1080p (profiles/nrc_training_cornell-1080p.md): 3.22 TB/s x 40.16 us
     "4:adam_table": {"bytes_per_launch": 129501000, "sources": ("gi_nrc.cu",), "source_sha": "94a0221974ed412e"},
 }
