@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -68,9 +69,9 @@ UPDATE_SECTION = ("gi_cache.cu", "// -------------------------------------------
 NCU_TRAFFIC = {
     # k_update, boxes-1080p (profiles/k_update_boxes-1080p.md): 158.5 MB read + 21.0 MB written
     "2:update": {"bytes_per_launch": 179567104, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
-                 "source_sha": "7878ce80b2d3d135"},
+                 "source_sha": "5c0f819bafd5d881"},
     # k_nrc_adam_table, Cornell 1080p (profiles/nrc_training_cornell-1080p.md): 3.22 TB/s x 40.16 us
-    "4:adam_table": {"bytes_per_launch": 129501000, "sources": ("gi_nrc.cu",), "source_sha": "94a0221974ed412e"},
+    "4:adam_table": {"bytes_per_launch": 129501000, "sources": ("gi_nrc.cu",), "source_sha": "dc778f1ceac58713"},
 }
 
 
@@ -82,14 +83,17 @@ def ncu_traffic(key):
 
 
 def _source_sha(sources):
+    """Hash of the code of the sources, comments and layout left out (a comment edit keeps it)."""
     h = hashlib.sha256()
     for src in sources:
         name = src if isinstance(src, str) else src[0]
-        text = open(os.path.join(ROOT, "paper_2310_19855_gb300", "csrc", name), "rb").read()
+        text = open(os.path.join(ROOT, "paper_2310_19855_gb300", "csrc", name), encoding="utf-8").read()
         if not isinstance(src, str):
-            a = text.index(src[1].encode())
-            text = text[a:text.index(src[2].encode(), a)]
-        h.update(text)
+            a = text.index(src[1])
+            text = text[a:text.index(src[2], a)]
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
