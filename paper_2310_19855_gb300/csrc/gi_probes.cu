@@ -820,7 +820,7 @@ __device__ __forceinline__ void interpolate_body(const InterpArgs &a, uint32_t b
             reinterpret_cast<float *>(&s.n8)[o] = n8_u;
         }
         __syncwarp();
-#pragma unroll 1
+#pragma unroll
         for (int h = 0; h < 2; ++h)
             interp_pixel<true>(a, s, x, y0 + 4 * h, fx, ((float)((lane >> 3) + 4 * h) + 0.5f) * 0.125f,
                                h ? nd[1] : nd[0], h ? pix[1] : pix[0], h ? inb[1] : inb[0], h ? act[1] : act[0], q);
