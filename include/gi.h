@@ -264,8 +264,9 @@ gi_status gi_cache_destroy(gi_cache_t cache);
  * atomics (see first_touch for the two forms of the accumulation).  Between two
  * resolves a cell takes fewer than 2^32 records (its 32-bit count) and sums
  * below 2^64 (2^25 records at the clamp radiance 32768): the records of many
- * frames, far above what a frame brings.  slot_ids (device, n u32, caller-owned) receives each record's
- * slot, GI_SLOT_MISS or GI_SLOT_NONE: the cached index of Section 2.2.1, valid
+ * frames, far above what a frame brings.  slot_ids (device, n u32,
+ * caller-owned) receives each record's slot, GI_SLOT_MISS or GI_SLOT_NONE: the
+ * cached index of Section 2.2.1, valid
  * until the next gi_cache_update.  Several updates may precede one resolve.
  * If the previous resolve left the table fuller than rebuild_load, this call
  * first compacts it (live cells only; slot indices change).
