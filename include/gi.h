@@ -266,8 +266,8 @@ gi_status gi_cache_destroy(gi_cache_t cache);
  * below 2^64 (2^25 records at the clamp radiance 32768): the records of many
  * frames, far above what a frame brings.  slot_ids (device, n u32,
  * caller-owned) receives each record's slot, GI_SLOT_MISS or GI_SLOT_NONE: the
- * cached index of Section 2.2.1, valid
- * until the next gi_cache_update.  Several updates may precede one resolve.
+ * cached index of Section 2.2.1, valid until the next gi_cache_update.
+ * Several updates may precede one resolve.
  * If the previous resolve left the table fuller than rebuild_load, this call
  * first compacts it (live cells only; slot indices change).
  * Errors: GI_ERR_INVALID_ARG (NULL record plane, NULL slot_ids with n > 0,
