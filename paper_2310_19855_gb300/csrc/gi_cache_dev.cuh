@@ -10,9 +10,10 @@
 
 namespace gi {
 
-// A block of the update takes at most kUpdBlockRecords records (one grid-strided chunk per
-// iteration), so its shared-memory list of first touches can never overflow and is flushed once,
-// at the end, with one global atomic: warps never wait for one another inside the loop.
+// In the touch-list form a block of the update takes at most kUpdBlockRecords records (one
+// grid-strided chunk per iteration), so its shared-memory list of first touches can never
+// overflow and is flushed once, at the end, with one global atomic: warps never wait for one
+// another inside the loop.  The bitmap form stages nothing and runs a resident grid.
 constexpr int kUpdThreads = 256;
 constexpr int kUpdBlockRecords = 2048;
 constexpr int kResThreads = 256;
