@@ -2,7 +2,8 @@
 (in-plane floor division by 8 with negative coordinates, the main axis from the direction, the cell
 index), a dense patch brute-forced into exactly its tiles, level-0 values equal to the plain
 cache's cells record by record (same quantised cell, so the same samples and blend), MIP closed
-forms (constant field, a single live cell, a hand-averaged 2x2 block) and the level rule."""
+forms (constant field, a single live cell, a hand-averaged 2x2 block), the level rule, and an
+expired cell leaving its tile's levels at the resolve that evicts it."""
 import math
 
 import numpy as np
@@ -129,3 +130,34 @@ def test_mip_box_filter_and_level_rule_by_hand():
         want = 0 if (int(cid[r]) & 63) == 8 else 1
         assert lv[r] == want
     assert np.allclose(v[lv == 1], 3.0) and np.allclose(v[lv == 0], 6.0)
+
+
+def test_expired_cell_leaves_the_levels_of_its_tile():
+    # cells A = (0, 0) and B = (1, 0) of one tile; B is hit in frame 0 only, A in every frame.
+    # B is evicted at the resolve of frame 8 (8 untouched frames, E = 8): from then on the tile's
+    # levels are A alone, with A's sample count, and B no longer answers.
+    s = 0.05
+    a = ((0.5 * s, 0.5 * s, 0.3),)
+    b = ((1.5 * s, 0.5 * s, 0.3),)
+    tc = T.OracleTileCache(10, min_samples=1000)
+    fov = math.radians(60)
+    ca = tc.update(_rec(a, (0, 0, 1), rad=(1.0, 1.0, 1.0)), 0, (0, 0, 0), fov, 1920, 1080)
+    cb = tc.update(_rec(b, (0, 0, 1), rad=(5.0, 5.0, 5.0)), 0, (0, 0, 0), fov, 1920, 1080)
+    tc.resolve(0)
+    tile = int(ca[0]) >> 6
+    assert int(cb[0]) >> 6 == tile
+    vals, n, has = tc.mips[tile]
+    assert np.allclose(vals[64], 3.0) and n[64] == 2  # level 1 holds both cells: (1 + 5) / 2
+    for f in range(1, 9):
+        tc.update(_rec(a, (0, 0, 1), rad=(1.0, 1.0, 1.0)), f, (0, 0, 0), fov, 1920, 1080)
+        tc.resolve(f)
+        vals, n, has = tc.mips[tile]
+        if f < 8:  # B is still live: it keeps its value in the levels
+            assert np.allclose(vals[64], 3.0) and n[64] == f + 2
+    cell_a = int(ca[0]) & 63
+    for lv in range(4):
+        k = int(T.mip_index(cell_a, lv))
+        assert has[k] and np.allclose(vals[k], 1.0) and n[k] == 9
+    assert has.sum() == 4
+    v, lv, found = tc.radiance(np.array([ca[0], cb[0]], np.uint64))
+    assert found[0] and not found[1] and np.allclose(v[0], 1.0)
