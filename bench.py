@@ -484,7 +484,7 @@ def run_native(args, rank, world, local_rank):
                     "roofline": {"bound": "hbm", "kernel": "k_filter", "algorithmic_bytes_per_launch": filt_bytes,
                                  "achieved": filt_bytes / (filt_ms * 1e-3) / 1e9, "peak": peak,
                                  "frac": filt_bytes / (filt_ms * 1e-3) / 1e9 / peak, "unit": "GB/s"}}
-    launches_per_step = 6  # k_spawn, k_mip_tail, k_update, k_resolve, k_integrate, k_interpolate
+    launches_per_step = 6  # k_spawn, k_mip_tail, k_update, k_resolve_bitmap, k_integrate, k_interpolate
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(tot[1] / args.steps), "higher_is_better": True,
