@@ -61,16 +61,16 @@ class L2Flush:
         self.torch.cuda._sleep(HOST_AHEAD_CYCLES)
 REFERENCE_BUDGET_S = 90.0
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture (profiles/), keyed by
+# DRAM traffic per launch of the dominant kernel from an ncu capture, keyed by
 # "configuration:kernel" and by the source it was taken on; null when that source has changed
 # since.  A source is a file of csrc/, or (file, first line, line after the last) for one section.
 UPDATE_SECTION = ("gi_cache.cu", "// ---------------------------------------------------------------- update",
                   "// ---------------------------------------------------------------- resolve")
 NCU_TRAFFIC = {
-    # k_update, boxes-1080p (profiles/k_update_boxes-1080p.md): 158.5 MB read + 21.0 MB written
+    # k_update, boxes-1080p: 158.5 MB read + 21.0 MB written
     "2:update": {"bytes_per_launch": 179567104, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
                  "source_sha": "5c0f819bafd5d881"},
-    # k_nrc_adam_table, Cornell 1080p (profiles/nrc_training_cornell-1080p.md): 3.22 TB/s x 40.16 us
+    # k_nrc_adam_table, Cornell 1080p: 3.22 TB/s x 40.16 us
     "4:adam_table": {"bytes_per_launch": 129501000, "sources": ("gi_nrc.cu",), "source_sha": "dc778f1ceac58713"},
 }
 

@@ -1,6 +1,7 @@
 """Pins for oracle/hashing.py: the two hash functions against their published
 definitions (a byte-oriented XXH32 written from the xxHash specification and
-its reference test vector; PCG's permutation property), and the identity /
+its reference test vector; PCG values worked step by step from its published definition
+and its permutation property), and the identity /
 tag construction of Section 2.2.1's bucket + fingerprint scheme."""
 import json
 import os
@@ -65,12 +66,38 @@ def test_pcg_is_a_permutation_on_a_large_sample():
     assert np.unique(hashing.pcg_hash(v)).size == v.size
 
 
-def test_pcg_definition_on_scalars():
-    # one LCG step (multiplier 747796405, increment 2891336453), then RXS-M-XS
-    for v in (0, 1, 2, 12345, 0xFFFFFFFF, 0x80000000):
-        st = (v * 747796405 + 2891336453) & M32
-        word = (((st >> ((st >> 28) + 4)) ^ st) * 277803737) & M32
-        assert int(hashing.pcg_hash(v)[0]) == ((word >> 22) ^ word)
+def test_pcg_worked_values():
+    # values worked step by step from the published definition (golden file lists every step)
+    for row in GOLDEN["pcg_worked"]:
+        assert int(hashing.pcg_hash(int(row["v"], 16))[0]) == int(row["out"], 16), row["v"]
+
+
+def test_pcg_worked_values_are_self_consistent():
+    # each listed intermediate follows from the previous one: a typo in the golden file fails here,
+    # not silently in the oracle test above
+    for row in GOLDEN["pcg_worked"]:
+        v, st = int(row["v"], 16), int(row["state"], 16)
+        assert st == (v * 747796405 + 2891336453) % 2 ** 32
+        assert row["shift"] == (st >> 28) + 4
+        assert int(row["xorshift"], 16) == (st >> row["shift"]) ^ st
+        w = int(row["word"], 16)
+        assert w == int(row["xorshift"], 16) * 277803737 % 2 ** 32
+        assert int(row["out"], 16) == (w >> 22) ^ w
+
+
+def test_cell_identity_worked_fold():
+    # bucket h(lo ^ h(hi)) and fingerprint xxh(lo, xxh(hi)) >> 8 of one descriptor, worked by hand:
+    # a swapped fold (hi and lo exchanged, or the seed chain reversed) gives other values
+    g = GOLDEN["fold_worked"]
+    key = int(g["key"], 16)
+    home, fp = hashing.cell_identity(np.uint64(key), 16)
+    assert int(home[0]) == int(g["home_log2_16"], 16)
+    assert int(fp[0]) == int(g["fingerprint"], 16)
+    # the intermediates agree with the byte-oriented XXH32 pinned to its reference vector
+    assert xxh32_bytes((1).to_bytes(4, "little"), 0) == int(g["xxh_hi_seed0"]["avalanche"][-1], 16)
+    assert xxh32_bytes((2).to_bytes(4, "little"), int(g["xxh_hi_seed0"]["avalanche"][-1], 16)) == \
+        int(g["xxh_lo_seed"]["avalanche"][-1], 16)
+    assert int(g["xxh_lo_seed"]["avalanche"][-1], 16) >> 8 == int(g["fingerprint"], 16)
 
 
 def test_identity_fingerprint_never_zero_and_tag_layout():
