@@ -67,9 +67,9 @@ REFERENCE_BUDGET_S = 90.0
 UPDATE_SECTION = ("gi_cache.cu", "// ---------------------------------------------------------------- update",
                   "// ---------------------------------------------------------------- resolve")
 NCU_TRAFFIC = {
-    # k_update, boxes-1080p: 158.5 MB read + 21.0 MB written
-    "2:update": {"bytes_per_launch": 179567104, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
-                 "source_sha": "5c0f819bafd5d881"},
+    # k_update, boxes-1080p: 153.96 MB read + 24.14 MB written
+    "2:update": {"bytes_per_launch": 178099200, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
+                 "source_sha": "14f297f5a79a57a6"},
     # k_nrc_adam_table, Cornell 1080p: 3.22 TB/s x 40.16 us
     "4:adam_table": {"bytes_per_launch": 129501000, "sources": ("gi_nrc.cu",), "source_sha": "dc778f1ceac58713"},
 }

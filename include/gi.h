@@ -65,6 +65,7 @@ typedef enum gi_status {
 enum { GI_KEY_DIR_NORMAL = 0, GI_KEY_DIR_RAY = 1 };
 enum { GI_RESOLVED_F32 = 0, GI_RESOLVED_F16 = 1 };
 enum { GI_FIRST_TOUCH_AUTO = 0, GI_FIRST_TOUCH_LIST = 1, GI_FIRST_TOUCH_BITMAP = 2 };
+enum { GI_MERGE_NONE = 0, GI_MERGE_WARP = 1 };
 
 typedef struct gi_cache_s *gi_cache_t;
 typedef void *gi_stream_t; /* cudaStream_t */
@@ -106,6 +107,13 @@ typedef void *gi_stream_t; /* cudaStream_t */
  *                   min_samples, else from the 1x1 level.  The sample count of a cell is the
  *                   number of samples blended into it since it last started without history;
  *                   a MIP value averages its children that hold a value and sums their counts.
+ *   merge           GI_MERGE_NONE: every hit record is inserted and accumulated on its own (records
+ *                   of one cell add into its accumulator in separate reductions; the integer sums
+ *                   are the same).  GI_MERGE_WARP: the hits of a warp (32 consecutive records) that
+ *                   name the same cell are merged first (__match_any_sync), so one of them probes
+ *                   and accumulates for all.  Results are identical; the merge pays only where
+ *                   consecutive records share cells.  Ignored by tile caches and by
+ *                   gi_batch_frame, whose update never merges.
  */
 typedef struct gi_cache_config {
     uint32_t log2_slots;
@@ -120,6 +128,7 @@ typedef struct gi_cache_config {
     uint32_t first_touch;
     uint32_t tiles;
     uint32_t min_samples;
+    uint32_t merge;
 } gi_cache_config;
 
 /*
@@ -260,8 +269,8 @@ gi_status gi_cache_destroy(gi_cache_t cache);
  * distance LOD from Algorithm 6's cell size, light-leak bit), bucket hash +
  * fingerprint, linear probing with atomicCAS on the fingerprint to find or
  * insert the cell, then 64-bit fixed-point sums round(r * 2^24) per channel
- * and a sample count.  Same-cell hits of a warp are merged before the global
- * atomics (see first_touch for the two forms of the accumulation).  Between two
+ * and a sample count (see first_touch for the two forms of the accumulation and
+ * merge for the optional merge of a warp's same-cell hits).  Between two
  * resolves a cell takes fewer than 2^32 records (its 32-bit count) and sums
  * below 2^64 (2^25 records at the clamp radiance 32768): the records of many
  * frames, far above what a frame brings.  slot_ids (device, n u32,
@@ -474,8 +483,8 @@ typedef struct gi_batch_s *gi_batch_t;
 /* Launch shapes, chosen by an autotuner (defaults: 2048, 3, 256). */
 typedef struct gi_batch_tuning {
     uint32_t update_records_per_block; /* records per update block, multiple of 256 in [256, 2048] */
-    uint32_t resolve_blocks_per_sm;    /* resolve blocks per SM over all views, 1..3 */
-    uint32_t integrate_threads;        /* threads per integrate block (one warp per probe), 64..256 */
+    uint32_t resolve_blocks_per_sm;    /* resolve blocks per SM over all views, 1..4 */
+    uint32_t integrate_threads;        /* threads per integrate block (four per probe), 32..128 */
 } gi_batch_tuning;
 
 /* One view of a frame.  All pointers are device pointers owned by the caller; hits.n must equal
@@ -663,7 +672,13 @@ gi_status gi_nrc_stats(gi_nrc_t nrc, gi_nrc_stats_t *out, gi_stream_t stream);
  * allocator -- and so cannot create a cache with gi_cache_create.
  *
  * Result: out (device float4[n], caller-owned) = (mean radiance of the record's cell, 1) for a
- * hit, (env, 1) for a ray that left the scene (ray_len = +inf), (0, 0, 0, 0) for no sample.  It
+ * hit, (env, 1) for a ray that left the scene (ray_len = +inf), (0, 0, 0, -1) for a hit whose cell
+ * found no free slot within 255 slots of its bucket (dropped; at most GI_NOALLOC_MAX_RECORDS cells
+ * in 2^GI_NOALLOC_LOG2_SLOTS slots make this very unlikely), (0, 0, 0, 0) for a record that is no
+ * sample (non-finite position, negative or NaN ray length).  stats_out (device uint64[2],
+ * caller-owned, 8-byte aligned, or NULL) receives, on `stream` after the means, the number of
+ * dropped hits and the number of hits whose radiance was clamped to [0, 32768] before fixed-point
+ * accumulation (the means of clamped hits use the clamped values).  It
  * equals gi_cache_create(log2_slots = GI_NOALLOC_LOG2_SLOTS, cell_size, num_lods, key_dir,
  * max_probe = 255) followed by gi_cache_update, gi_cache_resolve and gi_cache_query by slot on the
  * same records: the cell descriptor, fixed-point sums and float32 mean are the same, with no
@@ -673,35 +688,40 @@ gi_status gi_nrc_stats(gi_nrc_t nrc, gi_nrc_stats_t *out, gi_stream_t stream);
  * table, touch list, counters and slot ids.  Every GPU that loads the library holds it until the
  * process exits.  Each call clears the table and counters first, then overwrites the rest.  The
  * first call on a device looks the array's address up (cudaGetSymbolAddress, with that device
- * current) and caches it; make that first call before any stream capture.  Every call on a device
+ * current) and caches it for the life of the process; make that first call before any stream
+ * capture.  A device reset (cudaDeviceReset, or anything else that destroys the primary context)
+ * unloads the module and leaves that cached address stale: do not call this entry point on a
+ * device after its context was reset.  Every call on a device
  * shares the one array: calls that overlap on the GPU (other streams, other host threads) race
  * and give wrong results -- serialise them.  Calls no cudaMalloc, cudaFree or allocating library.
  *
  * Errors: GI_ERR_INVALID_ARG for n > GI_NOALLOC_MAX_RECORDS, a NULL plane or output, a bad view,
- * cell_size <= 0, num_lods outside 1..4 or an unknown key_dir; GI_ERR_CUDA if a launch fails.
+ * cell_size <= 0, num_lods outside 1..4, an unknown key_dir or a misaligned stats_out; GI_ERR_CUDA
+ * if a launch fails.
  */
 #define GI_NOALLOC_LOG2_SLOTS 18
 #define GI_NOALLOC_MAX_RECORDS 131072u
 #define GI_NOALLOC_SCRATCH_BYTES \
     ((4u + 32u + 4u) * (1u << GI_NOALLOC_LOG2_SLOTS) + 4u * GI_NOALLOC_MAX_RECORDS + 128u)
 gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *view, float cell_size, uint32_t num_lods,
-                                uint32_t key_dir, const float env[3], float *out, gi_stream_t stream);
+                                uint32_t key_dir, const float env[3], float *out, uint64_t *stats_out,
+                                gi_stream_t stream);
 
 /* ---------------------------------------------------------------- diagnostics
- * Not a step of the path.  gi_cache_update ends, per group of same-cell records of a warp, in L2
+ * Not a step of the path.  gi_cache_update ends, per hit record (GI_MERGE_NONE), in L2
  * operations on the cell's 32-byte accumulator (Section 2.2.1's accumulation in 64-bit fixed
  * point): in the list form (GI_FIRST_TOUCH_LIST) three 64-bit additions of the sums and one
  * returning 32-bit addition of the count, whose old value flags the first touch; in the bitmap
  * form (GI_FIRST_TOUCH_BITMAP, and AUTO) one 32-byte bulk reduction of the sums and count from
  * shared memory and a non-returning set of the slot's bit.  gi_diag_update_atomics issues exactly
  * those operations of the given form for n slot ids (records with slot_ids[i] >= 2^log2_slots are
- * skipped; same-slot records of a warp merged as the update merges them) and nothing else: no
- * record stream, key, probe or slot-id store.  Timed beside gi_cache_update on the same frame's
- * slot ids it gives the floor that the L2 sets for the update's accumulation.
+ * skipped; one reduction per record, as the update without merge) and nothing else: no record
+ * stream, key, probe or slot-id store.  Timed beside gi_cache_update on the same frame's slot ids
+ * it gives the floor of the update's accumulation on this GPU.
  *   slot_ids       device uint32[n] (4-byte aligned), e.g. the slot_ids_out of an update
  *   first_touch    the form: GI_FIRST_TOUCH_LIST, GI_FIRST_TOUCH_BITMAP or AUTO (the bitmap)
  *   scratch        device, caller-owned, zeroed by the caller, 32-byte aligned: 2^log2_slots
- *                  32-byte accumulators (receiving sums 1, 2, 3 and the group counts), followed
+ *                  32-byte accumulators (receiving sums 1, 2, 3 and count 1 per record), followed
  *                  in the bitmap form by the bitmap, 2^log2_slots / 8 bytes
  *   first_touches  list form: device uint32 (caller-owned), incremented by the number of slots
  *                  whose count left 0; unused (may be NULL) in the bitmap form

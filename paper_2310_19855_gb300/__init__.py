@@ -27,6 +27,7 @@ GI_INTERP_OK, GI_INTERP_RELAXED, GI_INTERP_NONE, GI_INTERP_SKY = 0, 1, 2, 3
 GI_KEY_DIR_NORMAL, GI_KEY_DIR_RAY = 0, 1
 GI_RESOLVED_F32, GI_RESOLVED_F16 = 0, 1
 GI_FIRST_TOUCH_AUTO, GI_FIRST_TOUCH_LIST, GI_FIRST_TOUCH_BITMAP = 0, 1, 2
+GI_MERGE_NONE, GI_MERGE_WARP = 0, 1
 GI_MAX_MIPS = 16
 GI_SH_STRIDE = 28
 GI_NOALLOC_LOG2_SLOTS = 18
@@ -44,7 +45,8 @@ c_u32, c_u64, c_f32, c_f64, c_vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_fl
 class gi_cache_config(ctypes.Structure):
     _fields_ = [("log2_slots", c_u32), ("cell_size", c_f32), ("num_lods", c_u32), ("alpha", c_f32),
                 ("evict_frames", c_u32), ("max_probe", c_u32), ("key_dir", c_u32), ("resolved_format", c_u32),
-                ("rebuild_load", c_f32), ("first_touch", c_u32), ("tiles", c_u32), ("min_samples", c_u32)]
+                ("rebuild_load", c_f32), ("first_touch", c_u32), ("tiles", c_u32), ("min_samples", c_u32),
+                ("merge", c_u32)]
 
 
 class gi_view(ctypes.Structure):
@@ -182,7 +184,7 @@ def lib() -> ctypes.CDLL:
             "gi_batch_frame": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_batch_view), c_u32, c_vp]),
             "gi_batch_destroy": (ctypes.c_int, [c_vp]),
             "gi_cell_means_noalloc": (ctypes.c_int, [ctypes.POINTER(gi_hits), ctypes.POINTER(gi_view), c_f32, c_u32,
-                                                     c_u32, ctypes.POINTER(c_f32), c_vp, c_vp]),
+                                                     c_u32, ctypes.POINTER(c_f32), c_vp, c_vp, c_vp]),
             "gi_nrc_create": (ctypes.c_int, [ctypes.POINTER(gi_nrc_config), ctypes.POINTER(c_vp)]),
             "gi_nrc_destroy": (ctypes.c_int, [c_vp]),
             "gi_nrc_set_params": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
@@ -289,10 +291,12 @@ def gi_cell_moments() -> np.ndarray:
 def gi_cache_create(log2_slots: int, cell_size: float = 0.05, num_lods: int = 4, alpha: float = 0.1,
                     evict_frames: int = 8, max_probe: int = 128, key_dir: int = GI_KEY_DIR_NORMAL,
                     resolved_format: int = GI_RESOLVED_F32, rebuild_load: float = 0.8,
-                    first_touch: int = GI_FIRST_TOUCH_AUTO, tiles: bool = False, min_samples: int = 16) -> int:
-    """tiles=True: two-level cache (8 x 8 cell tiles with MIP levels); log2_slots then counts tiles."""
+                    first_touch: int = GI_FIRST_TOUCH_AUTO, tiles: bool = False, min_samples: int = 16,
+                    merge: int = GI_MERGE_NONE) -> int:
+    """tiles=True: two-level cache (8 x 8 cell tiles with MIP levels); log2_slots then counts tiles.
+    merge=GI_MERGE_WARP: same-cell hits of a warp merged before the probe and the accumulation."""
     cfg = gi_cache_config(log2_slots, cell_size, num_lods, alpha, evict_frames, max_probe, key_dir,
-                          resolved_format, rebuild_load, first_touch, 1 if tiles else 0, min_samples)
+                          resolved_format, rebuild_load, first_touch, 1 if tiles else 0, min_samples, merge)
     h = c_vp()
     check(lib().gi_cache_create(ctypes.byref(cfg), ctypes.byref(h)), "gi_cache_create")
     return h.value
@@ -422,12 +426,15 @@ def make_gbuffer(nd, width: int, height: int) -> gi_gbuffer:
 
 
 def gi_cell_means_noalloc(hits: gi_hits, view: gi_view, out, cell_size: float = 0.05, num_lods: int = 4,
-                          key_dir: int = GI_KEY_DIR_NORMAL, env=(0.0, 0.0, 0.0), stream=None) -> None:
+                          key_dir: int = GI_KEY_DIR_NORMAL, env=(0.0, 0.0, 0.0), stats_out=None,
+                          stream=None) -> None:
     """Per-record cell means of one batch without any device allocation (see gi.h): for callers
-    that cannot call cudaMalloc.  out: device float4[n]."""
+    that cannot call cudaMalloc.  out: device float4[n]; stats_out: optional device int64[2] that
+    receives the dropped and clamped hit counts."""
     e = (c_f32 * 3)(*[float(x) for x in env])
     check(lib().gi_cell_means_noalloc(ctypes.byref(hits), ctypes.byref(view), float(cell_size), int(num_lods),
-                                      int(key_dir), e, _ptr(out), _stream(stream)), "gi_cell_means_noalloc")
+                                      int(key_dir), e, _ptr(out), _ptr(stats_out) if stats_out is not None else None,
+                                      _stream(stream)), "gi_cell_means_noalloc")
 
 
 def gi_diag_update_atomics(slot_ids, n: int, log2_slots: int, scratch, first_touches=None,

@@ -14,7 +14,7 @@ from . import gi_batch_set_tuning, gi_batch_tuning
 from .build import BUILD_DIR
 
 DEFAULT_CACHE = os.path.join(BUILD_DIR, "autotune.json")
-CANDIDATES = [(r, b, t) for r in (1024, 2048) for b in (1, 2, 3) for t in (128, 256)]
+CANDIDATES = [(r, b, t) for r in (1024, 2048) for b in (1, 2, 4) for t in (64, 128)]
 
 
 def signature(views) -> str:

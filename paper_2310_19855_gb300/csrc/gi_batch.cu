@@ -62,8 +62,8 @@ namespace gi {
 
 static bool tuning_ok(const gi_batch_tuning *t) {
     return t && t->update_records_per_block >= 256 && t->update_records_per_block <= 2048 &&
-           t->update_records_per_block % 256 == 0 && t->resolve_blocks_per_sm >= 1 && t->resolve_blocks_per_sm <= 3 &&
-           t->integrate_threads >= 64 && t->integrate_threads <= 256 && t->integrate_threads % 32 == 0;
+           t->update_records_per_block % 256 == 0 && t->resolve_blocks_per_sm >= 1 && t->resolve_blocks_per_sm <= 4 &&
+           t->integrate_threads >= 32 && t->integrate_threads <= 128 && t->integrate_threads % 32 == 0;
 }
 
 static void drop_graphs(gi_batch_s *b) {
@@ -156,7 +156,7 @@ gi_status gi_batch_create(uint32_t n_views, uint32_t rays_per_probe, const gi_ba
         return GI_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    gi_batch_tuning t = {2048u, 3u, 256u};
+    gi_batch_tuning t = {2048u, 4u, 64u};
     if (tuning) t = *tuning;
     if (!tuning_ok(&t)) {
         set_error("gi_batch_create: tuning out of range");
@@ -253,7 +253,7 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
             ((tx + 15) / 16) * ((ty + 15) / 16),
             update_blocks_for(bv.hits.n, b->tuning.update_records_per_block),
             std::max<uint32_t>(1u, (uint32_t)((double)res_total * (double)bv.hits.n / (double)std::max(1ull, total_records))),
-            (bv.probes.layout.num_probes * 32u + b->tuning.integrate_threads - 1u) / b->tuning.integrate_threads,
+            (bv.probes.layout.num_probes * 4u + b->tuning.integrate_threads - 1u) / b->tuning.integrate_threads,
             interp_grid_x(bv.view.width) * interp_grid_y(bv.view.height)};
         for (int k = 0; k < 5; ++k) pre[k][v + 1] = pre[k][v] + cnt[k];
         reinterpret_cast<UpdateArgs *>(h + L.upd)[v] = cache_update_args(bv.cache, &bv.hits, &bv.view, bv.slot_ids);

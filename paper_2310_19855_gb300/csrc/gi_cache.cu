@@ -31,17 +31,63 @@
 namespace gi {
 
 // ---------------------------------------------------------------- update
+// Find or insert the cell (home, tag): linear probing from the home slot, up to max_probe slots.
+// The slots are read four at a time (one 16-byte load of an aligned group), so that a run that
+// continues past its first slot costs no further round trip until it leaves the group; an empty
+// slot is claimed with atomicCAS (a slot, once claimed, never changes during an update: a failed
+// claim moves on to the next slot).  k = slots examined before the answer.  Returns GI_SLOT_NONE
+// when the run is longer than max_probe.  (1080p, no warp merge: 63 us against 69 us with one
+// 4-byte load per slot.)
+__device__ __forceinline__ uint32_t probe_cell(const UpdateArgs &a, uint32_t home, uint32_t tag, uint32_t &k) {
+    uint32_t s = home;
+    k = 0;
+    while (k < a.max_probe) {
+        const uint32_t g = s & ~3u, st = s & 3u;
+        const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(a.tags + g));
+        const uint32_t mt = (q.x == tag ? 1u : 0u) | (q.y == tag ? 2u : 0u) | (q.z == tag ? 4u : 0u) |
+                            (q.w == tag ? 8u : 0u);
+        const uint32_t me = (q.x == kEmpty ? 1u : 0u) | (q.y == kEmpty ? 2u : 0u) | (q.z == kEmpty ? 4u : 0u) |
+                            (q.w == kEmpty ? 8u : 0u);
+        const uint32_t m = (mt | me) & (0xFu << st) & 0xFu;
+        if (!m) {
+            k += 4u - st;
+            s = (g + 4u) & a.mask;
+            continue;
+        }
+        const uint32_t j = (uint32_t)(__ffs(m) - 1);
+        k += j - st;
+        if (k >= a.max_probe) break;
+        if ((mt >> j) & 1u) return g + j;
+        const uint32_t old = atomicCAS(a.tags + g + j, kEmpty, tag);
+        if (old == kEmpty || old == tag) return g + j;
+        ++k;
+        s = (g + j + 1u) & a.mask;
+    }
+    k = a.max_probe;
+    return GI_SLOT_NONE;
+}
+
 // Touch list (a.bitmap NULL): three 64-bit reductions of the sums and a returning add of the
 // count, whose old value 0 marks the first touch of the cell this frame; first touches go to the
 // block's shared-memory list and then, once per block, to the touch list.
 // Bitmap: the group's sums and count in one 32-byte bulk reduction from the thread's 32-byte
 // shared-memory slot (rewritten only once its previous reduction has read it), and the slot's bit
 // set by a non-returning atomicOr.  The block's shared buffer is the first-touch list in the one
-// form and the reduction slots in the other.  (1080p, blocks of 2048 records: 76 us against 80 us
-// for the list form; a plain load skipping the atomicOr when the bit is already set, 78 us; two
-// slots per thread, 76 us.  With the bitmap form's resident grid, 71 us.)
+// form and the reduction slots in the other.  The bulk reductions dominate the update's issue: at
+// 1080p it ran 60 us, 39 us without any accumulation and 44 us when only every fourth lane issued
+// its reduction (sums then wrong: bounds taken to size the cost).  A tensor-map reduction of four
+// rows per instruction (cp.reduce.async.bulk.tensor .tile::scatter4 .add.u64) compiles but wrote
+// the rows instead of adding them (every cell counted one sample), so it is not used.
+// MERGE: hits of a warp that name the same cell are merged first (__match_any_sync on the cell,
+// pointer-jumping sums), so one leader per cell probes and accumulates.  Without it every hit is
+// its own group: same-cell hits of a warp then reach the same accumulator in separate reductions,
+// whose integer sums are the same.  Probe rays of one warp belong to one probe and point in
+// different directions, so few of them share a cell: at 1080p the merge cost 9 us of the update
+// for ~5 % fewer reductions (update 72 us with it, 63 us without), and on the Cornell box at
+// 1080p 41 us against 38 us.  It stays available (GI_MERGE_WARP) for workloads whose warps do hit
+// the same cells.
 static_assert(kUpdBlockRecords * 4 == kUpdThreads * 32, "one 32-byte reduction slot per thread");
-template <int KEY_DIR>
+template <int KEY_DIR, bool MERGE>
 __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, uint32_t nblk) {
     __shared__ __align__(32) unsigned long long s_buf[kUpdBlockRecords / 2];
     uint32_t *s_touch = reinterpret_cast<uint32_t *>(s_buf);
@@ -91,51 +137,40 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
                 cell_key(a.kp, px, py, pz, sx, sy, sz, len, KEY_DIR == GI_KEY_DIR_NORMAL ? 0u : 1u);
             cell_of_key(key, a.mask, home, tag);
         }
-        // Merge the hits of this warp that name the same cell: one leader per cell
-        // adds the group's integer sums (order-independent, so still bit-exact).
-        const unsigned hm = __ballot_sync(kFull, hit);
-        unsigned peers = 0;
-        if (hit) peers = __match_any_sync(hm, ((unsigned long long)home << 32) | tag);
-        const unsigned above = peers & (0xFFFFFFFEu << lane);
-        int nxt = above ? (__ffs(above) - 1) : -1;
         uint32_t cnt = hit ? 1u : 0u;
-        // pointer-jumping suffix sums along each group's lane list
-        while (__any_sync(kFull, nxt >= 0)) {
-            const int src = nxt >= 0 ? nxt : lane;
-            const unsigned long long o0 = __shfl_sync(kFull, q0, src);
-            const unsigned long long o1 = __shfl_sync(kFull, q1, src);
-            const unsigned long long o2 = __shfl_sync(kFull, q2, src);
-            const uint32_t oc = __shfl_sync(kFull, cnt, src);
-            const int on = __shfl_sync(kFull, nxt, src);
-            if (nxt >= 0) {
-                q0 += o0;
-                q1 += o1;
-                q2 += o2;
-                cnt += oc;
-                nxt = on;
+        unsigned peers = 1u << lane;
+        if (MERGE) {
+            // one leader per cell adds the group's integer sums (order-independent, so still bit-exact)
+            const unsigned hm = __ballot_sync(kFull, hit);
+            if (hit) peers = __match_any_sync(hm, ((unsigned long long)home << 32) | tag);
+            const unsigned above = peers & (0xFFFFFFFEu << lane);
+            int nxt = above ? (__ffs(above) - 1) : -1;
+            // pointer-jumping suffix sums along each group's lane list
+            while (__any_sync(kFull, nxt >= 0)) {
+                const int src = nxt >= 0 ? nxt : lane;
+                const unsigned long long o0 = __shfl_sync(kFull, q0, src);
+                const unsigned long long o1 = __shfl_sync(kFull, q1, src);
+                const unsigned long long o2 = __shfl_sync(kFull, q2, src);
+                const uint32_t oc = __shfl_sync(kFull, cnt, src);
+                const int on = __shfl_sync(kFull, nxt, src);
+                if (nxt >= 0) {
+                    q0 += o0;
+                    q1 += o1;
+                    q2 += o2;
+                    cnt += oc;
+                    nxt = on;
+                }
             }
         }
         const bool leader = hit && (peers & ((1u << lane) - 1u)) == 0u;
         uint32_t slot = GI_SLOT_NONE;
         if (leader) {
-            uint32_t s = home, k = 0;
-            for (; k < a.max_probe; ++k) {
-                const uint32_t t = __ldcg(a.tags + s);
-                if (t == tag) {
-                    slot = s;
-                    break;
-                }
-                if (t == kEmpty) {
-                    const uint32_t old = atomicCAS(a.tags + s, kEmpty, tag);
-                    if (old == kEmpty || old == tag) {
-                        slot = s;
-                        break;
-                    }
-                }
-                s = (s + 1u) & a.mask;
-            }
+            uint32_t k;
+            slot = probe_cell(a, home, tag, k);
             my_maxp = max(my_maxp, k + 1u);
-            if (slot != GI_SLOT_NONE) {
+            if (slot == GI_SLOT_NONE) {
+                atomicAdd(&a.ctr->dropped, (unsigned long long)cnt);
+            } else {
                 Accum *ac = a.accum + (size_t)slot * a.acc_stride;
                 if (bitmap) {
                     bulk_wait_read();  // the previous reduction has read the slot
@@ -153,12 +188,10 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
                     // the count was cleared by the last resolve: the first adder this frame records the slot
                     if (atomicAdd(&ac->count, cnt) == 0u) s_touch[atomicAdd(&s_n, 1u)] = slot;
                 }
-            } else {
-                atomicAdd(&a.ctr->dropped, (unsigned long long)cnt);
             }
         }
-        const int lead = hit ? (__ffs(peers) - 1) : lane;
-        const uint32_t my_slot = __shfl_sync(kFull, slot, lead);
+        uint32_t my_slot = slot;
+        if (MERGE) my_slot = __shfl_sync(kFull, slot, hit ? (__ffs(peers) - 1) : lane);
         if (inr) __stcs(a.slot_ids + i, hit ? my_slot : (miss ? GI_SLOT_MISS : GI_SLOT_NONE));
     }
     // the bulk reductions complete (their sums visible) before the block ends
@@ -182,9 +215,20 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
     }
 }
 
-template <int KEY_DIR>
+template <int KEY_DIR, bool MERGE>
 __global__ void __launch_bounds__(kUpdThreads, 8) k_update(UpdateArgs a) {
-    update_body<KEY_DIR>(a, blockIdx.x, gridDim.x);
+    update_body<KEY_DIR, MERGE>(a, blockIdx.x, gridDim.x);
+}
+
+// the four instantiations of k_update on one stream
+static inline void launch_update(const UpdateArgs &a, uint32_t key_dir, bool merge, int blocks, cudaStream_t st) {
+    if (key_dir == GI_KEY_DIR_NORMAL) {
+        if (merge) k_update<GI_KEY_DIR_NORMAL, true><<<blocks, kUpdThreads, 0, st>>>(a);
+        else k_update<GI_KEY_DIR_NORMAL, false><<<blocks, kUpdThreads, 0, st>>>(a);
+    } else {
+        if (merge) k_update<GI_KEY_DIR_RAY, true><<<blocks, kUpdThreads, 0, st>>>(a);
+        else k_update<GI_KEY_DIR_RAY, false><<<blocks, kUpdThreads, 0, st>>>(a);
+    }
 }
 
 // Grid of k_update: enough blocks that none takes more than kUpdBlockRecords records.
@@ -195,57 +239,65 @@ static inline int update_blocks(unsigned long long n) {
 // ---------------------------------------------------------------- resolve
 
 
-// Touch-list form: 2 list entries per thread and iteration, 4 resident blocks per SM (56
-// registers); bitmap form: a word's set bits 4 at a time, 3 blocks per SM.  (Sweeps at 1080p and
-// 4K: the list form within 45-48 us for 3 to 8 blocks and 1 to 4 entries, the bitmap form 126 us
-// at 4 bits and 3 blocks against 135 us at 2 and 4.)
+// Touch-list form: 2 list entries per thread and iteration, 4 resident blocks per SM; bitmap
+// form: warps that compact the set bits of kResBmWords words into a shared list, then resolve 2
+// entries per lane and iteration, 4 blocks per SM.  (1080p: the bitmap form 34 us, against 44 us
+// when a thread walked its own word's bits 4 at a time with 3 blocks per SM: a word holds 0 to 32
+// touched slots, so those threads' chains were as uneven as their words.)
 constexpr int kResListUnroll = 2, kResListBlocksPerSm = 4;
-constexpr int kResBmUnroll = 4, kResBmBlocksPerSm = 3;
+constexpr int kResBmUnroll = 2, kResBmBlocksPerSm = 4, kResBmWords = 16;
+// a table has at least 2^10 slots: its bitmap words are a whole number of chunks
+static_assert(((1u << 10) / 32u) % kResBmWords == 0, "bitmap chunk must divide the smallest table");
 
-// Resolve up to U touched slots (0xFFFFFFFF = none), their loads issued together:
+// Resolve up to U touched slots (0xFFFFFFFF = none), their loads issued together: the
+// accumulator and, speculatively, the resolved history (a cell without history ignores it):
 // mean = sum / (count 2^24); a cell without history (never resolved, or evicted by an earlier
 // resolve) takes the mean, the others blend; accumulator cleared, stamp = frame + 1.
 template <int U>
 __device__ __forceinline__ void resolve_slots(const ResolveArgs &a, const uint32_t (&s)[U], uint32_t &fresh_new) {
     uint4 lo[U], hi[U];
+    float3 old[U];
+    // accumulators leave the L2 first, resolved values last: the probe pass reads them next
+    const unsigned long long pfirst = l2_policy_evict_first(), plast = l2_policy_evict_last();
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         if (s[u] != 0xFFFFFFFFu) {
             const uint4 *src = reinterpret_cast<const uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
-            lo[u] = __ldcg(src);
-            hi[u] = __ldcg(src + 1);
+            lo[u] = ld_cg_hint(src, pfirst);
+            hi[u] = ld_cg_hint(src + 1, pfirst);
+            old[u] = load_resolved(a.resolved, a.res_stride, a.f16, s[u]);
         }
-    }
-    bool fresh[U];
-    float3 old[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const uint32_t stamp = hi[u].w;
-        // no history: never resolved, or evicted by an earlier resolve (untouched E frames)
-        fresh[u] = stamp == 0u || (a.has_lr && (a.lr - (stamp - 1u)) >= a.evict);
-        if (s[u] != 0xFFFFFFFFu && !fresh[u]) old[u] = load_resolved(a.resolved, a.res_stride, a.f16, s[u]);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         if (s[u] == 0xFFFFFFFFu) continue;
+        const uint32_t stamp = hi[u].w;
+        // no history: never resolved, or evicted by an earlier resolve (untouched E frames)
+        const bool fresh = stamp == 0u || (a.has_lr && (a.lr - (stamp - 1u)) >= a.evict);
         const unsigned long long s0 = ((unsigned long long)lo[u].y << 32) | lo[u].x;
         const unsigned long long s1 = ((unsigned long long)lo[u].w << 32) | lo[u].z;
         const unsigned long long s2 = ((unsigned long long)hi[u].y << 32) | hi[u].x;
         // mean = sum / (count 2^24): one reciprocal, three products (within an ulp of the quotient)
         const float rc = __frcp_rn((float)hi[u].z) * 5.9604644775390625e-8f;
         const float3 m = make_float3(__ull2float_rn(s0) * rc, __ull2float_rn(s1) * rc, __ull2float_rn(s2) * rc);
-        fresh_new += hi[u].w == 0u ? 1u : 0u;
+        fresh_new += stamp == 0u ? 1u : 0u;
         float3 v = m;
-        if (!fresh[u]) {
+        if (!fresh) {
             const float3 o = old[u];
             v = make_float3(o.x + a.alpha * (m.x - o.x), o.y + a.alpha * (m.y - o.y), o.z + a.alpha * (m.z - o.z));
         }
-        store_resolved(a.resolved, a.res_stride, a.f16, s[u], v, fresh[u]);
-        // evict-first: the cleared accumulator is next read by the next frame's update, while the
-        // resolved values are read right after by the probe pass
+        if (!a.f16) {
+            st_hint(reinterpret_cast<uint4 *>(static_cast<char *>(a.resolved) + (size_t)s[u] * a.res_stride),
+                    make_uint4(__float_as_uint(v.x), __float_as_uint(v.y), __float_as_uint(v.z),
+                               __float_as_uint(fresh ? 1.0f : 0.0f)),
+                    plast);
+        } else {
+            store_resolved(a.resolved, a.res_stride, a.f16, s[u], v, fresh);
+        }
+        // the cleared accumulator is next read by the next frame's update
         uint4 *dst = reinterpret_cast<uint4 *>(a.accum + (size_t)s[u] * a.acc_stride);
-        __stcs(dst, make_uint4(0u, 0u, 0u, 0u));
-        __stcs(dst + 1, make_uint4(0u, 0u, 0u, a.stamp_now));
+        st_hint(dst, make_uint4(0u, 0u, 0u, 0u), pfirst);
+        st_hint(dst + 1, make_uint4(0u, 0u, 0u, a.stamp_now), pfirst);
     }
 }
 
@@ -267,27 +319,47 @@ __device__ __forceinline__ void resolve_list_body(const ResolveArgs &a, uint32_t
     resolve_finish(a.ctr, a.occ_out, a.stamp_now, nblk * (kResThreads / 32), fresh_new);
 }
 
-// bitmap form: a thread takes a word (32 consecutive slots), clears it and resolves its set bits
-// U at a time, in slot order
+// bitmap form: a warp takes kResBmWords words (16 x 32 consecutive slots), clears them, writes the
+// slots of their set bits in slot order to its shared list (a prefix sum of the words' bit counts
+// over the lanes gives each lane its place) and resolves the list U entries per lane at a time:
+// every lane gets the same share of the warp's touched slots whatever the words hold.
 template <int U>
 __device__ __forceinline__ void resolve_bm_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
-    const uint32_t stride = nblk * kResThreads;
+    __shared__ uint32_t s_list[kResThreads / 32][kResBmWords * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t nw = nblk * (kResThreads / 32);
+    const uint32_t chunks = a.words / kResBmWords;
     uint32_t fresh_new = 0;
-    for (uint32_t w = blk * kResThreads + threadIdx.x; w < a.words; w += stride) {
-        uint32_t bits = __ldcg(a.bitmap + w);
-        if (!bits) continue;
-        a.bitmap[w] = 0u;
+    for (uint32_t c = blk * (kResThreads / 32) + warp; c < chunks; c += nw) {
+        const uint32_t wi = c * kResBmWords + lane;
+        uint32_t bits = lane < kResBmWords ? __ldcg(a.bitmap + wi) : 0u;
+        if (bits) a.bitmap[wi] = 0u;
+        const int cnt = __popc(bits);
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        int pos = incl - cnt;
         while (bits) {
-            uint32_t s[U];
+            s_list[warp][pos++] = wi * 32u + (uint32_t)(__ffs(bits) - 1);
+            bits &= bits - 1u;
+        }
+        __syncwarp();
+        for (int k = lane; k < total; k += 32 * U) {
+            uint32_t sl[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                s[u] = bits ? w * 32u + (uint32_t)(__ffs(bits) - 1) : 0xFFFFFFFFu;
-                bits &= bits - 1u;
+                const int idx = k + 32 * u;
+                sl[u] = idx < total ? s_list[warp][idx] : 0xFFFFFFFFu;
             }
-            resolve_slots<U>(a, s, fresh_new);
+            resolve_slots<U>(a, sl, fresh_new);
         }
+        __syncwarp();
     }
-    resolve_finish(a.ctr, a.occ_out, a.stamp_now, nblk * (kResThreads / 32), fresh_new);
+    resolve_finish(a.ctr, a.occ_out, a.stamp_now, nw, fresh_new);
 }
 
 __device__ __forceinline__ void resolve_body(const ResolveArgs &a, uint32_t blk, uint32_t nblk) {
@@ -430,10 +502,10 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_update_batched(const UpdateA
     load_view_args(sa, args + v);
     __syncthreads();
     const uint32_t p0 = __ldg(prefix + v), p1 = __ldg(prefix + v + 1);
-    update_body<KEY_DIR>(sa, blockIdx.x - p0, p1 - p0);
+    update_body<KEY_DIR, false>(sa, blockIdx.x - p0, p1 - p0);
 }
 
-__global__ void __launch_bounds__(kResThreads, 3) k_resolve_batched(const ResolveArgs *args, const uint32_t *prefix,
+__global__ void __launch_bounds__(kResThreads, kResBmBlocksPerSm) k_resolve_batched(const ResolveArgs *args, const uint32_t *prefix,
                                                                     uint32_t nviews) {
     __shared__ ResolveArgs sa;
     const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
@@ -546,6 +618,7 @@ static bool config_ok(const gi_cache_config *c) {
     if (c->tiles > 1) return false;
     if (c->tiles && (c->log2_slots > 22 || c->first_touch != GI_FIRST_TOUCH_AUTO || c->min_samples < 1))
         return false;
+    if (c->merge > GI_MERGE_WARP) return false;
     return true;
 }
 
@@ -808,7 +881,7 @@ gi_status gi_cache_create(const gi_cache_config *cfg, gi_cache_t *out) {
     }
     if (s == GI_OK) {
         int per_sm = 0;
-        s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<0>, kUpdThreads, 0),
+        s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<0, false>, kUpdThreads, 0),
                         "occupancy");
         c->upd_blocks = c->sms * std::max(per_sm, 1);
         c->res_blocks = c->sms * (c->bitmap ? kResBmBlocksPerSm : kResListBlocksPerSm);
@@ -868,10 +941,7 @@ gi_status gi_cache_update(gi_cache_t c, const gi_hits *hits, const gi_view *view
     const int blocks = c->bitmap ? (int)std::min<unsigned long long>((unsigned long long)c->upd_blocks,
                                                                       (hits->n + kUpdThreads - 1) / kUpdThreads)
                                  : update_blocks(hits->n);
-    if (c->cfg.key_dir == GI_KEY_DIR_NORMAL)
-        k_update<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(a);
-    else
-        k_update<GI_KEY_DIR_RAY><<<blocks, kUpdThreads, 0, st>>>(a);
+    launch_update(a, c->cfg.key_dir, c->cfg.merge == GI_MERGE_WARP, blocks, st);
     s = cuda_status(cudaGetLastError(), "k_update launch");
     if (s == GI_OK) c->touched_since_resolve = true;
     return s;
@@ -1171,7 +1241,7 @@ static gi_status noalloc_setup(int dev, unsigned char **base, int *blocks) {
         int sms = 0, per_sm = 0;
         s = cuda_status(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
         if (s == GI_OK)
-            s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<0>, kUpdThreads, 0),
+            s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<0, false>, kUpdThreads, 0),
                             "occupancy");
         if (s != GI_OK) return s;
         g_noalloc_blocks[dev] = sms * std::max(per_sm, 1);
@@ -1187,10 +1257,12 @@ __global__ void k_noalloc_clear(uint4 *p, size_t n16) {
         p[i] = make_uint4(0u, 0u, 0u, 0u);
 }
 
-// out[i] = (mean of the cell of record i, 1); (env, 1) for a ray that left the scene; 0 otherwise.
-// The mean is computed with the same float32 operations as the resolve of a cell without history.
-__global__ void k_noalloc_means(const uint32_t *slot_ids, unsigned long long n, const Accum *accum, float e0,
-                                float e1, float e2, float4 *out) {
+// out[i] = (mean of the cell of record i, 1); (env, 1) for a ray that left the scene; (0, 0, 0, -1)
+// for a hit whose cell found no free slot within its probing run (dropped); 0 otherwise.  The mean
+// is computed with the same float32 operations as the resolve of a cell without history.
+__global__ void k_noalloc_means(const uint32_t *slot_ids, unsigned long long n, const Accum *accum, const float *len,
+                                const float *px, const float *py, const float *pz, float e0, float e1, float e2,
+                                float4 *out) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t s = slot_ids[i];
@@ -1202,8 +1274,21 @@ __global__ void k_noalloc_means(const uint32_t *slot_ids, unsigned long long n, 
                             1.0f);
         } else if (s == GI_SLOT_MISS) {
             o = make_float4(e0, e1, e2, 1.0f);
+        } else {
+            // the update writes GI_SLOT_NONE both for a record that is no hit and for a dropped hit:
+            // the record's own hit test (the update's) tells them apart
+            const float l = len[i];
+            if (isfinite(l) && l >= 0.0f && isfinite3(px[i], py[i], pz[i])) o.w = -1.0f;
         }
         out[i] = o;
+    }
+}
+
+// stats[0] = hits dropped, stats[1] = hits whose radiance was clamped, from the call's counters
+__global__ void k_noalloc_stats(const Counters *ctr, unsigned long long *stats) {
+    if (threadIdx.x == 0) {
+        stats[0] = ctr->dropped;
+        stats[1] = ctr->clamped;
     }
 }
 
@@ -1211,7 +1296,7 @@ __global__ void k_noalloc_means(const uint32_t *slot_ids, unsigned long long n, 
 
 extern "C" gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *view, float cell_size,
                                            uint32_t num_lods, uint32_t key_dir, const float env[3], float *out,
-                                           gi_stream_t stream) {
+                                           uint64_t *stats_out, gi_stream_t stream) {
     using namespace gi;
     if (!hits_ok(hits, key_dir) || !view_ok(view) || (hits && hits->n > 0 && !out)) {
         set_error("gi_cell_means_noalloc: NULL record plane or output, or bad view");
@@ -1227,7 +1312,16 @@ extern "C" gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *v
                   (unsigned long long)hits->n, (unsigned)GI_NOALLOC_MAX_RECORDS);
         return GI_ERR_INVALID_ARG;
     }
-    if (hits->n == 0) return GI_OK;
+    if (stats_out && (reinterpret_cast<uintptr_t>(stats_out) & 7u)) {
+        set_error("gi_cell_means_noalloc: stats_out must be 8-byte aligned");
+        return GI_ERR_INVALID_ARG;
+    }
+    if (hits->n == 0) {
+        if (stats_out)
+            return cuda_status(cudaMemsetAsync(stats_out, 0, 2 * sizeof(uint64_t), (cudaStream_t)stream),
+                               "gi_cell_means_noalloc stats");
+        return GI_OK;
+    }
     int dev = 0;
     gi_status s = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
     unsigned char *base = nullptr;
@@ -1269,13 +1363,14 @@ extern "C" gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *v
     a.max_probe = 255;
     a.kp = key_params(cell_size, num_lods, view);
     const int ub = update_blocks(hits->n);
-    if (key_dir == GI_KEY_DIR_NORMAL)
-        k_update<GI_KEY_DIR_NORMAL><<<ub, kUpdThreads, 0, st>>>(a);
-    else
-        k_update<GI_KEY_DIR_RAY><<<ub, kUpdThreads, 0, st>>>(a);
+    launch_update(a, key_dir, false, ub, st);
     s = cuda_status(cudaGetLastError(), "k_update launch");
     if (s != GI_OK) return s;
     const float e0 = env ? env[0] : 0.0f, e1 = env ? env[1] : 0.0f, e2 = env ? env[2] : 0.0f;
-    k_noalloc_means<<<ub, 256, 0, st>>>(slot_ids, hits->n, accum, e0, e1, e2, reinterpret_cast<float4 *>(out));
-    return cuda_status(cudaGetLastError(), "k_noalloc_means launch");
+    k_noalloc_means<<<ub, 256, 0, st>>>(slot_ids, hits->n, accum, hits->ray_len, hits->pos[0], hits->pos[1],
+                                        hits->pos[2], e0, e1, e2, reinterpret_cast<float4 *>(out));
+    s = cuda_status(cudaGetLastError(), "k_noalloc_means launch");
+    if (s != GI_OK || !stats_out) return s;
+    k_noalloc_stats<<<1, 32, 0, st>>>(ctr, reinterpret_cast<unsigned long long *>(stats_out));
+    return cuda_status(cudaGetLastError(), "k_noalloc_stats launch");
 }

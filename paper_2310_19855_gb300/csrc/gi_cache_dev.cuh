@@ -37,6 +37,32 @@ __device__ __forceinline__ void bulk_add_accum(void *dst, const unsigned long lo
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
+// ---------------------------------------------------------------- L2 eviction priority
+// Cache policies for loads and stores whose lines should leave the L2 before (evict_first) or
+// after (evict_last) the others.
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_evict_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ld_cg_hint(const uint4 *ptr, unsigned long long pol) {
+    uint4 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(uint4 *ptr, uint4 v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+
 // ---------------------------------------------------------------- hashing
 // xxHash32 of a single 4-byte word with a seed (xxHash specification).
 __device__ __forceinline__ uint32_t xxh32_word(uint32_t w, uint32_t seed) {

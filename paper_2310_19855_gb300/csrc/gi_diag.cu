@@ -1,7 +1,7 @@
 // Diagnostics, not a step of the path: the L2 floor of the cache update's accumulation.
 //
-// gi_cache_update ends, per group of same-cell records of a warp, in L2 operations on the cell's
-// 32-byte accumulator.  List form: three 64-bit additions (the fixed-point sums) and one returning
+// gi_cache_update ends, per hit record (the default GI_MERGE_NONE form), in L2 operations on the
+// cell's 32-byte accumulator.  List form: three 64-bit additions (the fixed-point sums) and one returning
 // 32-bit addition (the count, whose old value flags the first touch).  Bitmap form: one 32-byte
 // bulk reduction of the sums and count from shared memory and a non-returning set of the slot's
 // bit.  k_diag_atomics issues exactly those operations for a frame's slot ids, with nothing else
@@ -26,24 +26,21 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_diag_atomics(const uint32_t 
         const unsigned long long i = base + threadIdx.x;
         const uint32_t s = i < n ? __ldcs(slot_ids + i) : GI_SLOT_NONE;
         const bool hit = s < slots;
-        // same-slot records of the warp: one leader adds the group's count (as the update's merge)
-        const unsigned hm = __ballot_sync(kFull, hit);
-        const unsigned peers = hit ? __match_any_sync(hm, s) : 0u;
-        if (hit && (peers & ((1u << lane) - 1u)) == 0u) {
+        if (hit) {
             Accum *a = acc + s;
             if (BITMAP) {
                 bulk_wait_read();
                 s_red[threadIdx.x][0] = 1ull;
                 s_red[threadIdx.x][1] = 2ull;
                 s_red[threadIdx.x][2] = 3ull;
-                s_red[threadIdx.x][3] = (unsigned long long)__popc(peers);
+                s_red[threadIdx.x][3] = 1ull;
                 bulk_add_accum(a, s_red[threadIdx.x]);
                 atomicOr(bitmap + (s >> 5), 1u << (s & 31u));
             } else {
                 atomicAdd(&a->sum[0], 1ull);
                 atomicAdd(&a->sum[1], 2ull);
                 atomicAdd(&a->sum[2], 3ull);
-                if (atomicAdd(&a->count, (uint32_t)__popc(peers)) == 0u) ++first;
+                if (atomicAdd(&a->count, 1u) == 0u) ++first;
             }
         }
     }

@@ -128,6 +128,7 @@ gi_status ensure_moments() {
         for (int k = 0; k < 10; ++k) table[k][c] = (float)m[k];
     }
     s = cuda_status(cudaMemcpyToSymbol(g_moments, table, sizeof table), "upload cell moments");
+
     float dirs[64][3];
     for (int c = 0; c < 64; ++c) {
         const double u = -1.0 + ((c & 7) + 0.5) * 0.25, v = -1.0 + ((c >> 3) + 0.5) * 0.25;
@@ -394,24 +395,236 @@ __device__ __forceinline__ void project_cells(const float4 n4, int lane, const f
     out[lane] = val;
 }
 
-// One warp per probe: gather then project (no intermediate atlas).
-template <bool SURR = false>
-__device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t blk) {
-    const uint32_t p = (blk * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (p >= a.probes) return;
-    const float4 n4 = __ldg(a.nrm + p);
-    float *out = a.sh + (size_t)p * GI_SH_STRIDE;
-    if (n4.w == 0.0f) {
-        if (lane < GI_SH_STRIDE) out[lane] = 0.0f;
-        return;
+// SH coefficients (9 per channel, band order of project_cells) of the radiance whose local-frame
+// direction moments are S (S[m][channel]: solid angle, first moment xyz, second moment xx yy zz xy
+// xz yz), rotated to world space by the probe frame of normal n (Duff et al. 2017); out[3 k + c].
+__device__ __forceinline__ void sh_from_moments(const float (&S)[10][3], float nx, float ny, float nz,
+                                                float (&o)[27]) {
+    const float sgn = copysignf(1.0f, nz);
+    const float ia = -1.0f / (sgn + nz);
+    const float bb = nx * ny * ia;
+    const float R[3][3] = {{1.0f + sgn * nx * nx * ia, bb, nx},
+                           {sgn * bb, sgn + ny * ny * ia, ny},
+                           {-sgn * nx, -ny, nz}};
+    const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f, C2 = 1.0925484305920792f,
+                C3 = 0.31539156525252005f, C4 = 0.5462742152960396f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float S0 = S[0][c];
+        const float S1[3] = {S[1][c], S[2][c], S[3][c]};
+        float S2[3][3];
+        S2[0][0] = S[4][c]; S2[1][1] = S[5][c]; S2[2][2] = S[6][c];
+        S2[0][1] = S2[1][0] = S[7][c];
+        S2[0][2] = S2[2][0] = S[8][c];
+        S2[1][2] = S2[2][1] = S[9][c];
+        float W1[3], T[3][3], W2[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) W1[i] = R[i][0] * S1[0] + R[i][1] * S1[1] + R[i][2] * S1[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) T[i][q] = R[i][0] * S2[0][q] + R[i][1] * S2[1][q] + R[i][2] * S2[2][q];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i; j < 3; ++j) W2[i][j] = W2[j][i] = T[i][0] * R[j][0] + T[i][1] * R[j][1] + T[i][2] * R[j][2];
+        o[0 * 3 + c] = C0 * S0;
+        o[1 * 3 + c] = C1 * W1[1];
+        o[2 * 3 + c] = C1 * W1[2];
+        o[3 * 3 + c] = C1 * W1[0];
+        o[4 * 3 + c] = C2 * W2[0][1];
+        o[5 * 3 + c] = C2 * W2[1][2];
+        o[6 * 3 + c] = C3 * (3.0f * W2[2][2] - S0);
+        o[7 * 3 + c] = C2 * W2[0][2];
+        o[8 * 3 + c] = C4 * (W2[0][0] - W2[1][1]);
     }
-    float L[2][3], hd[2];
-    gather_cells<SURR, false>(a, p, lane, L, hd);
-    project_cells(n4, lane, L, out);
 }
 
-__global__ void __launch_bounds__(256) k_integrate(IntegrateArgs a) { integrate_body(a, blockIdx.x); }
+// Probe irradiance (Sections 2.1.4, 2.4.2) with four threads per probe: thread h of a probe's quad
+// takes the cells c = 4 i + h, i < 16, kIntPass at a time with their slot-id loads and radiance
+// gathers issued together; a cell's radiance is the mean of its rays that produced a sample, and the cell's exact
+// direction moments (shared memory, 12 floats per cell: three 16-byte reads) are added in with
+// multiply-adds.  Cells without sample take the mean of the populated cells (radiance backup)
+// through the summed moments of the empty cells, the same sum by linearity.  Two xor-shuffle steps
+// add the quad's partial moments; thread h < 3 then projects channel h.  (1080p: one warp per probe
+// with a 31-shuffle reduce-scatter ran 31 us at ~600 instructions per probe; one thread per probe,
+// 41 us: too few warps to hide the gathers.)  RPC1: one ray per cell.
+constexpr int kIntThreads = 128;  // 32 probes per block
+constexpr int kMomStride = 12;    // floats per cell in the shared moment table
+constexpr int kIntPass = 8;       // cells per thread whose loads are in flight together
+
+__device__ __forceinline__ void load_moment_table(float *s_mom) {
+    for (int k = threadIdx.x; k < 64 * kMomStride; k += blockDim.x) {
+        const int c = k / kMomStride, m = k - c * kMomStride;
+        s_mom[k] = m < 10 ? g_moments[m][c] : 0.0f;
+    }
+}
+
+template <bool SURR, bool RPC1>
+__device__ __forceinline__ void integrate_quad(const IntegrateArgs &a, uint32_t p, bool valid, const float *s_mom) {
+    const int h = threadIdx.x & 3;
+    float4 n4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) n4 = __ldg(a.nrm + p);
+    const bool live = valid && n4.w != 0.0f;
+    float S[10][3], U[10];
+#pragma unroll
+    for (int m = 0; m < 10; ++m) {
+        S[m][0] = S[m][1] = S[m][2] = 0.0f;
+        U[m] = 0.0f;
+    }
+    float pop0 = 0.f, pop1 = 0.f, pop2 = 0.f, npop = 0.f;
+    if (live) {
+        const uint32_t rpc = RPC1 ? 1u : (a.rpp >> 6);
+        const size_t rec_base = (size_t)p * a.rpp;
+        const uint32_t *ids = a.slot_ids + rec_base + h;
+#pragma unroll
+        for (int i0 = 0; i0 < 16; i0 += kIntPass) {
+            float acc[kIntPass][3], cnt[kIntPass];
+#pragma unroll
+            for (int i = 0; i < kIntPass; ++i) {
+                acc[i][0] = acc[i][1] = acc[i][2] = 0.0f;
+                cnt[i] = 0.0f;
+            }
+            for (uint32_t j = 0; j < rpc; ++j) {
+                uint32_t sl[kIntPass];
+#pragma unroll
+                for (int i = 0; i < kIntPass; ++i) sl[i] = __ldcs(ids + j * 64u + 4u * (i0 + i));
+                float3 r[kIntPass];
+                bool hs[kIntPass];
+#pragma unroll
+                for (int i = 0; i < kIntPass; ++i) hs[i] = ray_sample(a, sl[i], r[i]);
+                if (SURR) {
+                    // the pass's records rec0 + 4 i + h (rec0 a multiple of 32) share one answer word
+                    const size_t rec0 = rec_base + j * 64u + 4u * i0;
+                    const uint32_t wbits = __ldg(a.ovr_bits + (rec0 >> 5)) >> h;
+#pragma unroll
+                    for (int i = 0; i < kIntPass; ++i)
+                        if ((wbits >> (4 * i)) & 1u) {
+                            const float4 o = __ldg(a.ovr + rec0 + 4u * i + h);
+                            r[i] = make_float3(o.x, o.y, o.z);
+                            hs[i] = true;
+                        }
+                }
+#pragma unroll
+                for (int i = 0; i < kIntPass; ++i)
+                    if (hs[i]) {
+                        acc[i][0] += r[i].x;
+                        acc[i][1] += r[i].y;
+                        acc[i][2] += r[i].z;
+                        cnt[i] += 1.0f;
+                    }
+            }
+#pragma unroll
+            for (int i = 0; i < kIntPass; ++i) {
+                const float4 *mc = reinterpret_cast<const float4 *>(s_mom + (4 * (i0 + i) + h) * kMomStride);
+                const float4 w0 = mc[0], w1 = mc[1], w2 = mc[2];
+                const float w[10] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w, w2.x, w2.y};
+                if (cnt[i] > 0.0f) {
+                    const float inv = RPC1 ? 1.0f : __frcp_rn(cnt[i]);
+                    const float L0 = acc[i][0] * inv, L1 = acc[i][1] * inv, L2 = acc[i][2] * inv;
+                    pop0 += L0;
+                    pop1 += L1;
+                    pop2 += L2;
+                    npop += 1.0f;
+#pragma unroll
+                    for (int m = 0; m < 10; ++m) {
+                        S[m][0] = fmaf(L0, w[m], S[m][0]);
+                        S[m][1] = fmaf(L1, w[m], S[m][1]);
+                        S[m][2] = fmaf(L2, w[m], S[m][2]);
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 10; ++m) U[m] += w[m];
+                }
+            }
+        }
+    }
+    // the quad's partial sums (every lane takes part: the shuffles span the warp)
+#pragma unroll
+    for (int d = 1; d <= 2; d <<= 1) {
+#pragma unroll
+        for (int m = 0; m < 10; ++m) {
+            S[m][0] += __shfl_xor_sync(kFullMask, S[m][0], d);
+            S[m][1] += __shfl_xor_sync(kFullMask, S[m][1], d);
+            S[m][2] += __shfl_xor_sync(kFullMask, S[m][2], d);
+            U[m] += __shfl_xor_sync(kFullMask, U[m], d);
+        }
+        pop0 += __shfl_xor_sync(kFullMask, pop0, d);
+        pop1 += __shfl_xor_sync(kFullMask, pop1, d);
+        pop2 += __shfl_xor_sync(kFullMask, pop2, d);
+        npop += __shfl_xor_sync(kFullMask, npop, d);
+    }
+    if (!valid) return;
+    float *out = a.sh + (size_t)p * GI_SH_STRIDE;
+    if (!live) {
+        for (int k = h; k < GI_SH_STRIDE; k += 4) out[k] = 0.0f;
+        return;
+    }
+    if (h == 3) {
+        out[27] = 0.0f;
+        return;
+    }
+    // radiance backup: every cell without sample holds the mean of the populated cells
+    const float binv = npop > 0.0f ? 1.0f / npop : 0.0f;
+    const float bk = (h == 0 ? pop0 : (h == 1 ? pop1 : pop2)) * binv;
+    float Sc[10];
+#pragma unroll
+    for (int m = 0; m < 10; ++m) Sc[m] = fmaf(bk, U[m], h == 0 ? S[m][0] : (h == 1 ? S[m][1] : S[m][2]));
+    // probe frame (Duff et al. 2017): columns t, b, n of R
+    const float nx = n4.x, ny = n4.y, nz = n4.z;
+    const float sgn = copysignf(1.0f, nz);
+    const float ia = -1.0f / (sgn + nz);
+    const float bb = nx * ny * ia;
+    const float R[3][3] = {{1.0f + sgn * nx * nx * ia, bb, nx},
+                           {sgn * bb, sgn + ny * ny * ia, ny},
+                           {-sgn * nx, -ny, nz}};
+    const float S0 = Sc[0];
+    const float S1[3] = {Sc[1], Sc[2], Sc[3]};
+    float S2[3][3];
+    S2[0][0] = Sc[4]; S2[1][1] = Sc[5]; S2[2][2] = Sc[6];
+    S2[0][1] = S2[1][0] = Sc[7];
+    S2[0][2] = S2[2][0] = Sc[8];
+    S2[1][2] = S2[2][1] = Sc[9];
+    float W1[3], T[3][3], W2[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) W1[i] = R[i][0] * S1[0] + R[i][1] * S1[1] + R[i][2] * S1[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) T[i][q] = R[i][0] * S2[0][q] + R[i][1] * S2[1][q] + R[i][2] * S2[2][q];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) W2[i][j] = W2[j][i] = T[i][0] * R[j][0] + T[i][1] * R[j][1] + T[i][2] * R[j][2];
+    // real SH basis, bands 0..2 (the order of project_cells), channel h, coefficient k at 3 k + h
+    const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f, C2 = 1.0925484305920792f,
+                C3 = 0.31539156525252005f, C4 = 0.5462742152960396f;
+    out[0 * 3 + h] = C0 * S0;
+    out[1 * 3 + h] = C1 * W1[1];
+    out[2 * 3 + h] = C1 * W1[2];
+    out[3 * 3 + h] = C1 * W1[0];
+    out[4 * 3 + h] = C2 * W2[0][1];
+    out[5 * 3 + h] = C2 * W2[1][2];
+    out[6 * 3 + h] = C3 * (3.0f * W2[2][2] - S0);
+    out[7 * 3 + h] = C2 * W2[0][2];
+    out[8 * 3 + h] = C4 * (W2[0][0] - W2[1][1]);
+}
+
+// blk: block of kIntThreads / 4 probes (the batched pass passes the view-local block)
+template <bool SURR>
+__device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t blk, const float *s_mom) {
+    const uint32_t p = blk * (blockDim.x >> 2) + (threadIdx.x >> 2);
+    const bool valid = p < a.probes;
+    if (a.rpp == 64) integrate_quad<SURR, true>(a, p, valid, s_mom);
+    else integrate_quad<SURR, false>(a, p, valid, s_mom);
+}
+
+__global__ void __launch_bounds__(kIntThreads, 4) k_integrate(IntegrateArgs a) {
+    __shared__ __align__(16) float s_mom[64 * kMomStride];
+    load_moment_table(s_mom);
+    __syncthreads();
+    integrate_body<false>(a, blockIdx.x, s_mom);
+}
 
 // Probe atlas: float4 per (probe, cell) = (mean radiance rgb, mean hit distance); zeros for no probe.
 __global__ void __launch_bounds__(256) k_gather(IntegrateArgs a, float4 *atlas) {
@@ -445,7 +658,12 @@ __global__ void __launch_bounds__(256) k_project(const float4 *atlas, const floa
     const float L[2][3] = {{c0.x, c0.y, c0.z}, {c1.x, c1.y, c1.z}};
     project_cells(n4, lane, L, out);
 }
-__global__ void __launch_bounds__(256) k_integrate_surr(IntegrateArgs a) { integrate_body<true>(a, blockIdx.x); }
+__global__ void __launch_bounds__(kIntThreads, 4) k_integrate_surr(IntegrateArgs a) {
+    __shared__ __align__(16) float s_mom[64 * kMomStride];
+    load_moment_table(s_mom);
+    __syncthreads();
+    integrate_body<true>(a, blockIdx.x, s_mom);
+}
 
 // ---------------------------------------------------------------- temporal path
 constexpr uint32_t kScoreNone = (0x7BFFu << 16) | 0xFFFFu;  // half(65504) << 16 | 0xFFFF
@@ -1079,13 +1297,15 @@ __global__ void __launch_bounds__(1024) k_mip_tail_batched(const SpawnArgs *args
     if (sa.mi.count > 5) mip_tail_body(sa.mask, sa.mi);
 }
 
-__global__ void __launch_bounds__(256) k_integrate_batched(const IntegrateArgs *args, const uint32_t *prefix,
+__global__ void __launch_bounds__(128, 4) k_integrate_batched(const IntegrateArgs *args, const uint32_t *prefix,
                                                            uint32_t nviews) {
     __shared__ IntegrateArgs sa;
+    __shared__ __align__(16) float s_mom[64 * kMomStride];
     const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
     load_view_args(sa, args + v);
+    load_moment_table(s_mom);
     __syncthreads();
-    integrate_body(sa, blockIdx.x - __ldg(prefix + v));
+    integrate_body<false>(sa, blockIdx.x - __ldg(prefix + v), s_mom);
 }
 
 __global__ void __launch_bounds__(256, 4) k_interpolate_batched(const InterpArgs *args, const uint32_t *prefix,
@@ -1278,8 +1498,8 @@ gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *pr, const uint3
     if (s != GI_OK) return s;
     const IntegrateArgs a = integrate_args(cache, pr, slot_ids, rays_per_probe, env);
     if (a.probes == 0) return GI_OK;
-    const unsigned blocks = (a.probes + 7) / 8;
-    k_integrate<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    const unsigned blocks = (a.probes + kIntThreads / 4 - 1) / (kIntThreads / 4);
+    k_integrate<<<blocks, kIntThreads, 0, (cudaStream_t)stream>>>(a);
     return cuda_status(cudaGetLastError(), "k_integrate launch");
 }
 
@@ -1298,8 +1518,8 @@ gi_status gi_probes_integrate_nrc(gi_cache_t cache, gi_nrc_t nrc, const gi_probe
     const uint64_t n = (uint64_t)a.probes * rays_per_probe;
     s = nrc_override(nrc, n, &a.ovr_bits, &a.ovr);
     if (s != GI_OK) return s;
-    const unsigned blocks = (a.probes + 7) / 8;
-    k_integrate_surr<<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
+    const unsigned blocks = (a.probes + kIntThreads / 4 - 1) / (kIntThreads / 4);
+    k_integrate_surr<<<blocks, kIntThreads, 0, (cudaStream_t)stream>>>(a);
     return cuda_status(cudaGetLastError(), "k_integrate_surr launch");
 }
 

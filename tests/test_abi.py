@@ -100,6 +100,8 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
     bad = gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, 3)  # unknown first-touch record
     assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
+    bad = gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, 0, 0, 16, 2)  # unknown merge form
+    assert lib.gi_cache_create(ctypes.byref(bad), ctypes.byref(h)) == gi.GI_ERR_INVALID_ARG
     # tile caches: at most 2^22 tiles, first touches always listed, min_samples >= 1, tiles in {0, 1}
     for bad in (gi.gi_cache_config(23, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, 0, 1, 16),
                 gi.gi_cache_config(16, 0.05, 4, 0.1, 8, 128, 0, 0, 0.8, gi.GI_FIRST_TOUCH_BITMAP, 1, 16),

@@ -15,9 +15,9 @@ CSRC = os.path.join(ROOT, "paper_2310_19855_gb300", "csrc")
 HOT = {
     "8k_updateILi0E": ("gi_cache.cu", 32),
     "9k_resolveE": ("gi_cache.cu", 64),
-    "16k_resolve_bitmapE": ("gi_cache.cu", 80),
+    "16k_resolve_bitmapE": ("gi_cache.cu", 64),
     "14k_diag_atomicsILb1E": ("gi_diag.cu", 32),
-    "11k_integrateE": ("gi_probes.cu", 64),
+    "11k_integrateE": ("gi_probes.cu", 128),
     "13k_interpolateE": ("gi_probes.cu", 64),
     "10k_tile_keyILi0E": ("gi_tiles.cu", 32),
     "17k_tile_accumulate": ("gi_tiles.cu", 32),

@@ -89,17 +89,21 @@ def test_gather_matches_oracle(kind):
     _atlas_close(got, want)
 
 
-def test_gather_then_project_equals_integrate_bit_exact():
+def test_gather_then_project_agrees_with_integrate():
+    # the two-pass form (atlas in between, a warp per probe) and the fused pass (a thread per probe)
+    # sum the cells in other orders: float32 agreement relative to the probe's band-0 magnitude
     fr, ls = _frame("boxes")
     pl, view, R = _gpu_frame(fr, ls)
     try:
         pl.integrate()
-        fused = pl.probes.sh.clone()
+        fused = pl.probes.sh.cpu().numpy()[:, :27].reshape(-1, 9, 3).astype(np.float64)
         atlas = torch.empty((pl.probes.layout.num_probes, 64, 4), dtype=torch.float32, device="cuda")
         gi.gi_probes_gather(pl.cache, pl.probes.struct, pl.slot_ids, R[9], fr.rays_per_probe, atlas)
         pl.probes.sh.fill_(-1.0)
         gi.gi_probes_project(pl.probes.struct, atlas)
-        assert torch.equal(fused, pl.probes.sh)
+        two = pl.probes.sh.cpu().numpy()[:, :27].reshape(-1, 9, 3).astype(np.float64)
+        mag = np.abs(two[:, 0:1, :]).max(axis=2, keepdims=True) + 1e-6
+        assert (np.abs(fused - two) / mag).max() < 1e-5
     finally:
         pl.close()
 
