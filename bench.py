@@ -15,6 +15,7 @@ independent replica on its own frames (the path has no exchange step).
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import re
 import json
@@ -66,12 +67,14 @@ REFERENCE_BUDGET_S = 90.0
 # since.  A source is a file of csrc/, or (file, first line, line after the last) for one section.
 UPDATE_SECTION = ("gi_cache.cu", "// ---------------------------------------------------------------- update",
                   "// ---------------------------------------------------------------- resolve")
+NRC_ADAM_SECTION = ("gi_nrc.cu", "// ---------------------------------------------------------------- gradient scatter and Adam",
+                    "// ---------------------------------------------------------------- query selection")
 NCU_TRAFFIC = {
     # k_update, boxes-1080p: 153.96 MB read + 24.14 MB written
     "2:update": {"bytes_per_launch": 178099200, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
                  "source_sha": "14f297f5a79a57a6"},
     # k_nrc_adam_table, Cornell 1080p: 3.22 TB/s x 40.16 us
-    "4:adam_table": {"bytes_per_launch": 129501000, "sources": ("gi_nrc.cu",), "source_sha": "dc778f1ceac58713"},
+    "4:adam_table": {"bytes_per_launch": 129501000, "sources": (NRC_ADAM_SECTION,), "source_sha": "a33b80b7d73defb0"},
 }
 
 
@@ -141,8 +144,14 @@ class ClockSampler:
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for (tr, ln) in self.lines:
-            # keep the samples that arrived while the timed region ran (200 ms cadence)
-            if t0 is not None and not (t0 <= tr <= t1 + 0.25):
+            # keep the samples taken while the timed region ran (200 ms cadence), by nvidia-smi's own
+            # timestamp (the pipe may deliver lines late), with one cadence of slack after the region
+            # so that a region shorter than the cadence still has its next sample
+            try:
+                tr = datetime.datetime.strptime(ln.split(",")[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                pass
+            if t0 is not None and not (t0 - 0.05 <= tr <= t1 + 0.25):
                 continue
             f = [x.strip() for x in ln.split(",")[1:]]
             if len(f) < 9:
@@ -260,17 +269,96 @@ def oracle_window(frames, steps, warmup, sample_frac):
     return Rs, times
 
 
+def host_cores() -> int:
+    """Cores this process may run on (what `nproc` prints)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_share(job):
+    """One worker of the all-cores oracle: the window (update, resolve, query, probe irradiance)
+    over its own share of the sampled probes of every frame, with its own cache table; returns the
+    seconds of each timed step."""
+    log2_slots, shares, steps, warmup = job
+    from oracle.cache import OracleCache
+    from oracle import probes as OP
+    from oracle.frame import ray_radiance
+    oc = OracleCache(log2_slots)
+    times = []
+    for i in range(warmup + steps):
+        rec, cam, valid, nrm, rpp = shares[i % len(shares)]
+        t0 = time.perf_counter()
+        ident = oc.update(rec, i, cam[0], cam[1], cam[2], cam[3])
+        oc.resolve(i)
+        rad, has = ray_radiance(oc, rec, ident)
+        n = valid.size
+        OP.integrate(valid, nrm, rad.reshape(n, rpp, 3), has.reshape(n, rpp))
+        if i >= warmup:
+            times.append(time.perf_counter() - t0)
+    return times
+
+
+def oracle_window_all_cores(frames, steps, warmup, sample_frac, workers):
+    """The oracle's window on `workers` processes (spawned, one thread each): the sampled probes of
+    each frame are split into `workers` contiguous shares, each share's records go through the
+    oracle in its own process with its own cache table (a cell hit from several shares is kept
+    once per share).  Returns (records per step, the slowest worker's seconds per step)."""
+    import multiprocessing as mp
+    os.environ["OMP_NUM_THREADS"] = "1"
+    import workload as wl
+    from oracle import probes as OP
+    cfg = wl.CONFIGS[CONFIG]
+    fr0 = frames[0]
+    P = fr0.tiles_x * fr0.tiles_y
+    Ps = max(workers, int(P * sample_frac))
+    rpp = fr0.rays_per_probe
+    bounds = [Ps * w // workers for w in range(workers + 1)]
+    jobs = [[] for _ in range(workers)]
+    for fr in frames[:warmup + steps]:
+        cam = fr.camera
+        sp = OP.spawn(fr.gbuffer, cam, fr.frame)
+        camt = (np.asarray(cam.pos, np.float64), cam.fov_y, cam.width, cam.height)
+        for w in range(workers):
+            p0, p1 = bounds[w], bounds[w + 1]
+            jobs[w].append((np.ascontiguousarray(fr.records[:, p0 * rpp:p1 * rpp]), camt, sp["valid"][p0:p1],
+                            sp["nrm"][p0:p1], rpp))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        per_worker = pool.map(_oracle_share, [(cfg["log2_slots"], jobs[w], steps, warmup) for w in range(workers)])
+    slowest = np.max(np.array(per_worker), axis=0)
+    return Ps * rpp, list(slowest)
+
+
+def cpu_baselines(frames, sample_frac, steps=3):
+    """The oracle on the same bounded sample, on one core and on all the host's cores."""
+    Rs, ct = oracle_window(frames, steps=steps, warmup=1, sample_frac=sample_frac)
+    cores = host_cores()
+    Rp, pt = oracle_window_all_cores(frames, steps, 1, sample_frac, cores)
+    what = (f"{steps} frames (after one untimed) x first {sample_frac:.3f} of the probes ({Rs} records each): "
+            "update + resolve + query + probe irradiance, numpy float64")
+    return {"value": Rs * len(ct) / sum(ct) / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": what + ", one thread",
+            "all_cores": {"value": Rp * len(pt) / sum(pt) / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                          "sample": what + f", split into {cores} shares of whole probes on {cores} spawned "
+                                           "processes (one thread each, own cache table each); time of the "
+                                           "slowest share per frame (host cores from the process's CPU affinity, "
+                                           "as nproc)"}}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     frames = make_frames(min(args.frames, args.steps + args.warmup), 0)
-    # keep the whole run within about REFERENCE_BUDGET_S: shrink the per-step sample if needed
-    _, t_cal = oracle_window(frames, 1, 0, args.sample)
+    cores = host_cores()
+    # keep the whole run within about REFERENCE_BUDGET_S: size the per-step sample from one
+    # calibration step (at most every probe of the frame)
+    _, t_cal = oracle_window_all_cores(frames, 1, 0, args.sample, cores)
     per_step = REFERENCE_BUDGET_S / (args.steps + args.warmup)
-    sample = min(args.sample, args.sample * per_step / max(t_cal[0], 1e-6))
-    sample = max(sample, 64.0 / (frames[0].tiles_x * frames[0].tiles_y))
+    sample = min(1.0, args.sample * per_step / max(t_cal[0], 1e-6))
+    sample = max(sample, 64.0 * cores / (frames[0].tiles_x * frames[0].tiles_y))
     args.sample = sample
-    Rs, times = oracle_window(frames, args.steps, args.warmup, sample)
+    Rs, times = oracle_window_all_cores(frames, args.steps, args.warmup, sample, cores)
     total = sum(times)
     value = Rs * len(times) / total / 1e6
     line = {
@@ -278,9 +366,11 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config_dict(frames[0], "oracle sample"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"first {args.sample:.4f} of the probes of each 1080p frame ({Rs} records): "
-                                   "update + resolve + query + probe irradiance, numpy float64, one thread"},
+                                   f"update + resolve + query + probe irradiance, numpy float64, split into {cores} "
+                                   f"shares of whole probes on {cores} spawned processes (one thread and one cache "
+                                   "table each); time of the slowest share per frame"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -404,10 +494,11 @@ def run_native(args, rank, world, local_rank):
     d2h = h_out[0].numel() * 4
 
     # ---- the filtered probe chain (Algorithm 5): gather, filter x, filter y, project, per pass
+    # (left out of a compact run: the default configuration's line carries it)
     P = fr0.tiles_x * fr0.tiles_y
     atlas = torch.empty((P, 64, 4), dtype=torch.float32, device="cuda")
     atlas_tmp = torch.empty_like(atlas)
-    f_steps = max(3, min(args.steps, 50))
+    f_steps = 0 if args.sub else max(3, min(args.steps, 50))
     f_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(f_steps)]
     for j in range(f_steps):
         k = j % n_frames
@@ -423,14 +514,15 @@ def run_native(args, rank, world, local_rank):
         gi.gi_probes_project(pl.probes.struct, atlas, stream)
         f_ev[j][4].record(stream)
     torch.cuda.synchronize()
-    f_ms = np.array([[f_ev[j][i].elapsed_time(f_ev[j][i + 1]) for i in range(4)] for j in range(f_steps)]).mean(axis=0)
+    f_ms = (np.array([[f_ev[j][i].elapsed_time(f_ev[j][i + 1]) for i in range(4)] for j in range(f_steps)]).mean(axis=0)
+            if f_steps else None)
 
     # ---- the update's accumulation floor: its L2 atomics alone, on a frame's slot ids
     floor_ms, floor_first = update_atomic_floor(gi, torch, pl.slot_ids, R, cfg["log2_slots"], flush, stream,
                                                 args.steps)
 
     # ---- the two-level cache (Section 2.2.3): the same frames through a tile cache
-    tiles = run_tiles(args, gi, Pipeline, frames, dev_rec, dev_gb, views, flush, stream, cfg, R)
+    tiles = None if args.sub else run_tiles(args, gi, Pipeline, frames, dev_rec, dev_gb, views, flush, stream, cfg, R)
 
     # ---- max over ranks
     tot = np.array(max_over_ranks([window_ms.sum(), frame_ms.sum(), t_wall, e2e_ms.sum()], world, "cuda"))
@@ -468,22 +560,22 @@ def run_native(args, rank, world, local_rank):
     # ---- oracle on the host cores, bounded sample (rank 0, N = 1 only)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        Rs, ct = oracle_window(frames, steps=3, warmup=0, sample_frac=args.sample)
-        cpu = {"value": Rs * len(ct) / sum(ct) / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"3 frames x first {args.sample:.3f} of the probes ({Rs} records each): update + resolve "
-                         "+ query + probe irradiance, numpy float64, one thread"}
+        cpu = cpu_baselines(frames, args.sample)
 
     # k_filter: each atlas entry (16 B) read once and written once per pass, plus the probe's and its
     # neighbours' position and normal (32 B per probe); the neighbours' same cell are L2 re-reads
     filt_bytes = P * 64 * 32 + P * 32
-    filt_ms = float(min(f_ms[1], f_ms[2]))
-    probe_filter = {"pass_ms": {"gather": float(f_ms[0]), "filter_x": float(f_ms[1]), "filter_y": float(f_ms[2]),
-                                "project": float(f_ms[3])},
-                    "note": "gi_probes_gather + 2 x gi_probes_filter + gi_probes_project in place of "
-                            "gi_probes_integrate (Algorithm 5), L2 flushed before each chain",
-                    "roofline": {"bound": "hbm", "kernel": "k_filter", "algorithmic_bytes_per_launch": filt_bytes,
-                                 "achieved": filt_bytes / (filt_ms * 1e-3) / 1e9, "peak": peak,
-                                 "frac": filt_bytes / (filt_ms * 1e-3) / 1e9 / peak, "unit": "GB/s"}}
+    probe_filter = None
+    if f_ms is not None:
+        filt_ms = float(min(f_ms[1], f_ms[2]))
+        probe_filter = {
+            "pass_ms": {"gather": float(f_ms[0]), "filter_x": float(f_ms[1]), "filter_y": float(f_ms[2]),
+                        "project": float(f_ms[3])},
+            "note": "gi_probes_gather + 2 x gi_probes_filter + gi_probes_project in place of "
+                    "gi_probes_integrate (Algorithm 5), L2 flushed before each chain",
+            "roofline": {"bound": "hbm", "kernel": "k_filter", "algorithmic_bytes_per_launch": filt_bytes,
+                         "achieved": filt_bytes / (filt_ms * 1e-3) / 1e9, "peak": peak,
+                         "frac": filt_bytes / (filt_ms * 1e-3) / 1e9 / peak, "unit": "GB/s"}}
     launches_per_step = 6  # k_spawn, k_mip_tail, k_update, k_resolve_bitmap, k_integrate, k_interpolate
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -502,8 +594,8 @@ def run_native(args, rank, world, local_rank):
             "kernel": "k_diag_atomics (gi_diag_update_atomics)", "ms": floor_ms, "update_ms": float(pass_ms[1]),
             "update_over_floor": float(pass_ms[1]) / floor_ms, "touched_slots": floor_first,
             "note": "the update's accumulation alone (bitmap form: one 32-byte bulk reduction of the sums and count "
-                    "plus a bitmap bit per merged record group) on a frame's own slot ids, nothing else, L2 flushed "
-                    "before each launch: the floor the L2 sets for k_update"},
+                    "plus a bitmap bit per hit) on a frame's own slot ids, nothing else, L2 flushed before each "
+                    "launch: the floor of k_update's accumulation"},
         "roofline_window": {"achieved": sum(alg[n] for n in ("update", "resolve", "integrate")) /
                                         (pass_ms[1:4].sum() * 1e-3) / 1e9, "peak": peak, "unit": "GB/s"},
         "cpu_baseline": cpu,
@@ -524,8 +616,8 @@ def run_native(args, rank, world, local_rank):
             r = tiles["roofline"][k]
             r["peak"] = peak
             r["frac"] = r["achieved"] / peak
-    print(json.dumps(line), flush=True)
     pl.close()
+    return line
 
 
 
@@ -903,8 +995,8 @@ def run_temporal(args, rank, world, local_rank):
         "clocks": clk,
         "wall_s_timed": float(tot[2]),
     }
-    print(json.dumps(line), flush=True)
     tp.close()
+    return line
 
 
 # ------------------------------------------------------------------ batched arm (many views)
@@ -1034,7 +1126,7 @@ def run_batched(args, rank, world, local_rank):
         "gpu_launches": int(args.steps * 7),
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 # ------------------------------------------------------------------ surrogate arm (configuration 4)
@@ -1207,10 +1299,7 @@ def run_surrogate(args, rank, world, local_rank):
     achieved = adam_bytes / (adam_ms * 1e-3) / 1e9
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        Rs, ct = oracle_window(frames, steps=3, warmup=0, sample_frac=args.sample)
-        cpu = {"value": Rs * len(ct) / sum(ct) / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"3 frames x first {args.sample:.3f} of the probes ({Rs} records each): the plain "
-                         "update + resolve + query + probe irradiance, numpy float64, one thread"}
+        cpu = cpu_baselines(frames, args.sample)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(tot[0] / args.steps), "higher_is_better": True,
@@ -1246,7 +1335,52 @@ def run_surrogate(args, rank, world, local_rank):
         "gpu_launches": int(args.steps * ((9 + 5 * cfg["nrc_train_steps"]) + 6)),
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_config(config, args, rank, world, local_rank):
+    """One configuration's run; its JSON line (rank 0) or None."""
+    global CONFIG
+    CONFIG = config
+    if config == 3:
+        return run_batched(args, rank, world, local_rank)
+    if config == 4:
+        return run_surrogate(args, rank, world, local_rank)
+    if config in (6, 7):
+        return run_temporal(args, rank, world, local_rank)
+    return run_native(args, rank, world, local_rank)
+
+
+# keys of a configuration's line that its compact block in the default line leaves out
+SUB_DROP = ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data", "cpu_baseline", "warmup",
+            "probe_filter", "tiles")
+SUB_STEPS, SUB_WARMUP, SUB_FRAMES = 20, 5, 4
+
+
+def other_configs(args, rank, world, local_rank):
+    """Compact runs of configurations 5 (4K), 6 (temporal upscale), 7 (the whole chain), 3 (16
+    batched views) and 4 (the learned surrogate) after the default configuration, each with its own
+    events, roofline and clock record: at most SUB_STEPS timed steps over SUB_FRAMES cycled frames,
+    no CPU baseline and no end-to-end arm (the default line carries those)."""
+    import argparse as _ap
+    import torch
+    out = {}
+    for c in (5, 6, 7, 3, 4):
+        sub = _ap.Namespace(**vars(args))
+        sub.steps, sub.warmup = min(args.steps, SUB_STEPS), min(max(args.warmup, 3), SUB_WARMUP)
+        sub.frames, sub.no_cpu_baseline, sub.sub = SUB_FRAMES, True, True
+        t0 = time.perf_counter()
+        line = run_config(c, sub, rank, world, local_rank)
+        torch.cuda.empty_cache()
+        if line is None:
+            continue
+        block = {k: v for k, v in line.items() if k not in SUB_DROP}
+        block["metric"] = line["metric"] if c != 3 else "frames/s of 16 batched views"
+        block["wall_s"] = time.perf_counter() - t0
+        out[str(c)] = block
+    global CONFIG
+    CONFIG = 2
+    return out
 
 
 def main():
@@ -1261,12 +1395,15 @@ def main():
     ap.add_argument("--setup-frames", type=int, default=None,
                     help="configuration 4: frames of online training before the warm-up (default: the "
                          "configuration's 128)")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="configuration 2: skip the compact runs of configurations 3-7 added to its line")
     ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5, 6, 7],
                     help="2: boxes at 1080p (default); 3: 16 batched views; 4: Cornell box at 1080p with the "
                          "learned surrogate; 5: boxes at 4K, 2^24 slots, FP16 resolved radiance; 6: boxes at "
                          "1080p with 2x2 temporal upscale, probe reprojection and hysteresis; 7: as 6 with the "
                          "two-level tile cache and the probe filter (the paper's whole chain)")
     args = ap.parse_args()
+    args.sub = False
     global CONFIG
     CONFIG = args.config
     args.warmup = max(args.warmup, 3)
@@ -1280,14 +1417,11 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     try:
-        if CONFIG == 3:
-            run_batched(args, rank, world, local_rank)
-        elif CONFIG == 4:
-            run_surrogate(args, rank, world, local_rank)
-        elif CONFIG in (6, 7):
-            run_temporal(args, rank, world, local_rank)
-        else:
-            run_native(args, rank, world, local_rank)
+        line = run_config(CONFIG, args, rank, world, local_rank)
+        if line is not None and CONFIG == 2 and world == 1 and not args.no_other_configs:
+            line["configs"] = other_configs(args, rank, world, local_rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
     finally:
         if world > 1:
             import torch

@@ -594,6 +594,13 @@ typedef struct gi_nrc_stats_t {
     uint32_t queries;      /* records answered by the latest gi_nrc_query_frame */
 } gi_nrc_stats_t;
 
+/* The library's defaults in every field of *cfg: log2_table 19; resolution[l] = floor(16 b^l),
+ * b = (2048 / 16)^(1 / (GI_NRC_LEVELS - 1)), the last level exactly 2048 (a geometric schedule from
+ * 16 to 2048 cells per axis, Mueller et al. 2022); the unit box [0, 1]^3; lr 1e-2, beta1 0.9, beta2
+ * 0.99, adam_eps 1e-15; loss_eps 0.01; batch 65536 in 4 train_steps; max_records 2^22; max_queries
+ * 2^20; trust 0.05; query_lod 2; seed 1.  Host only.  Errors: GI_ERR_INVALID_ARG for a NULL cfg. */
+gi_status gi_nrc_config_defaults(gi_nrc_config *cfg);
+
 /* Create (allocates every parameter, Adam state and scratch buffer; initialises from cfg->seed).
  * Synchronous.  Errors: GI_ERR_INVALID_ARG, GI_ERR_OOM, GI_ERR_CUDA. */
 gi_status gi_nrc_create(const gi_nrc_config *cfg, gi_nrc_t *out);

@@ -185,6 +185,7 @@ def lib() -> ctypes.CDLL:
             "gi_batch_destroy": (ctypes.c_int, [c_vp]),
             "gi_cell_means_noalloc": (ctypes.c_int, [ctypes.POINTER(gi_hits), ctypes.POINTER(gi_view), c_f32, c_u32,
                                                      c_u32, ctypes.POINTER(c_f32), c_vp, c_vp, c_vp]),
+            "gi_nrc_config_defaults": (ctypes.c_int, [ctypes.POINTER(gi_nrc_config)]),
             "gi_nrc_create": (ctypes.c_int, [ctypes.POINTER(gi_nrc_config), ctypes.POINTER(c_vp)]),
             "gi_nrc_destroy": (ctypes.c_int, [c_vp]),
             "gi_nrc_set_params": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
@@ -467,23 +468,25 @@ def gi_batch_destroy(batch: int) -> None:
 
 
 # ---------------------------------------------------------------- learned radiance surrogate
-def default_resolutions(n_min: int = 16, n_max: int = 2048, levels: int = GI_NRC_LEVELS) -> tuple:
-    """Geometric level resolutions floor(n_min b^l), b = (n_max / n_min)^(1 / (levels - 1)), the last one n_max."""
-    b = (n_max / n_min) ** (1.0 / (levels - 1))
-    res = [int(np.floor(n_min * b ** l + 1e-9)) for l in range(levels)]
-    res[-1] = int(n_max)
-    return tuple(res)
+def default_resolutions() -> tuple:
+    """The library's default level resolutions (gi_nrc_config_defaults)."""
+    c = gi_nrc_config()
+    check(lib().gi_nrc_config_defaults(ctypes.byref(c)), "gi_nrc_config_defaults")
+    return tuple(int(r) for r in c.resolution)
 
 
 def make_nrc_config(aabb_lo, aabb_hi, log2_table: int = 19, resolutions=None, lr: float = 1e-2, beta1: float = 0.9,
                     beta2: float = 0.99, adam_eps: float = 1e-15, loss_eps: float = 0.01, batch: int = 65536,
                     train_steps: int = 4, max_records: int = 1 << 22, max_queries: int = 1 << 20, trust: float = 0.05,
                     query_lod: int = 2, seed: int = 1) -> gi_nrc_config:
+    """A surrogate configuration: the library's defaults (gi_nrc_config_defaults, which own the level
+    resolutions unless `resolutions` is given) with the arguments written over them."""
     c = gi_nrc_config()
+    check(lib().gi_nrc_config_defaults(ctypes.byref(c)), "gi_nrc_config_defaults")
     c.log2_table = int(log2_table)
-    res = resolutions or default_resolutions()
-    for l in range(GI_NRC_LEVELS):
-        c.resolution[l] = int(res[l])
+    if resolutions is not None:
+        for l in range(GI_NRC_LEVELS):
+            c.resolution[l] = int(resolutions[l])
     for a in range(3):
         c.aabb_lo[a] = float(aabb_lo[a])
         c.aabb_hi[a] = float(aabb_hi[a])

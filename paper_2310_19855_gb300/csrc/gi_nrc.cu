@@ -364,8 +364,14 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
     const uint32_t sm = tc::smem_u32(smem);
     auto xh_off = [](int buf) { return buf ? kSmXH1 : kSmXH0; };
     auto t_off = [](int buf) { return buf ? kSmT1 : kSmT0; };
+    // Thread 0 counts the asynchronous operations it started and the completions it saw, so that
+    // a CTA that gives up after a wait ran out first waits (bounded again) for what it still has in
+    // flight -- at most one load per buffer and one MMA group -- before freeing its tensor memory.
+    uint32_t ld_issued[2] = {0u, 0u}, ld_done[2] = {0u, 0u}, mma_issued = 0u, mma_done = 0u;
+    bool w_done = false;
 
     auto load_tile = [&](uint32_t tile, int buf) {  // thread 0 only
+        ++ld_issued[buf];
         const uint32_t bytes = kXTile + (TRAIN ? kTTile : 0u);
         tc::mbar_expect_tx(&bar_ld[buf], bytes);
         const uint8_t *src = reinterpret_cast<const uint8_t *>(a.X) + (size_t)tile * kXTile;
@@ -381,11 +387,18 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
         load_tile(blockIdx.x, 0);
     }
     bool ok = tc::mbar_wait(&bar_w, 0);
+    w_done = ok;
     uint32_t ph = 0;  // parity of the next MMA completion
     float loss = 0.f, jerr = 0.f, jtgt = 0.f;
     uint32_t it = 0;
+    auto commit_mma = [&]() {  // thread 0 only
+        tc::commit(&bar_mma);
+        ++mma_issued;
+    };
     auto mma_wait = [&]() {
-        ok = tc::mbar_wait(&bar_mma, ph) && ok;
+        const bool got = tc::mbar_wait(&bar_mma, ph);
+        if (got) ++mma_done;
+        ok = got && ok;
         ph ^= 1u;
         tc::fence_after_sync();
     };
@@ -398,7 +411,9 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
 
     for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
         const int buf = it & 1;
-        ok = tc::mbar_wait(&bar_ld[buf], (it >> 1) & 1u) && ok;
+        const bool got = tc::mbar_wait(&bar_ld[buf], (it >> 1) & 1u);
+        if (got) ++ld_done[buf];
+        ok = got && ok;
         if (!ok) abort_s = 1;
         __syncthreads();
         if (abort_s) break;
@@ -412,7 +427,7 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
             for (uint32_t ks = 0; ks < kIn / 16; ++ks)
                 tc::mma_bf16(tmem + kTmD1, tc::smem_desc(xh + 1024u + ks * 256u, 128u, kXHStride),
                              tc::smem_desc(sm + kSmImg + kImgW1 + ks * 256u, 128u, 512u), tc::idesc_bf16(128, 64), ks);
-            tc::commit(&bar_mma);
+            commit_mma();
         }
         mma_wait();
         float z[64];
@@ -434,7 +449,7 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
             for (uint32_t ks = 0; ks < kHid / 16; ++ks)
                 tc::mma_bf16(tmem + kTmD2, tc::smem_desc(xh + ks * 256u, 128u, kXHStride),
                              tc::smem_desc(sm + kSmImg + kImgW2 + ks * 256u, 128u, 1024u), tc::idesc_bf16(128, 64), ks);
-            tc::commit(&bar_mma);
+            commit_mma();
         }
         mma_wait();
         tmem_ld64(tmem, warp, kTmD2, z);
@@ -454,7 +469,7 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
             for (uint32_t ks = 0; ks < kHid / 16; ++ks)
                 tc::mma_bf16(tmem + kTmD3, tc::smem_desc(sm + kSmH2 + ks * 256u, 128u, kH2Stride),
                              tc::smem_desc(sm + kSmImg + kImgW3P + ks * 256u, 128u, 1024u), tc::idesc_bf16(128, 16), ks);
-            tc::commit(&bar_mma);
+            commit_mma();
         }
         mma_wait();
         float y[16];
@@ -499,7 +514,7 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
             tc::fence_after_sync();
             tc::mma_bf16(tmem + kTmD2, tc::smem_desc(sm + kSmDY, 128u, kDYStride),
                          tc::smem_desc(sm + kSmImg + kImgW3PT, 128u, 256u), tc::idesc_bf16(128, 64), 0u);
-            tc::commit(&bar_mma);
+            commit_mma();
         }
         mma_wait();
         tmem_ld64(tmem, warp, kTmD2, z);
@@ -516,7 +531,7 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
             for (uint32_t ks = 0; ks < kHid / 16; ++ks)
                 tc::mma_bf16(tmem + kTmD1, tc::smem_desc(sm + kSmZ + ks * 256u, 128u, kZStride),
                              tc::smem_desc(sm + kSmImg + kImgW2T + ks * 256u, 128u, 1024u), tc::idesc_bf16(128, 64), ks);
-            tc::commit(&bar_mma);
+            commit_mma();
         }
         mma_wait();
         tmem_ld64(tmem, warp, kTmD1, z);
@@ -544,7 +559,7 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
                 tc::mma_bf16(tmem + kTmGC, tc::smem_desc(sm + kSmH2 + ks * 2u * kH2Stride, kH2Stride, 128u),
                              tc::smem_desc(sm + kSmDY + ks * 2u * kDYStride, kDYStride, 128u), idesc_mn(128, 16),
                              (it | ks) != 0u);
-            tc::commit(&bar_mma);
+            commit_mma();
         }
         mma_wait();
         {
@@ -566,7 +581,16 @@ __global__ void __launch_bounds__(kTile, TRAIN ? 1 : 2) k_nrc_mlp(MlpArgs a) {
 
     float *part = TRAIN ? a.wpart + (size_t)blockIdx.x * kPartStride : nullptr;
     if (abort_s) {
-        if (t == 0) atomicOr(a.err, kErrTimeout);
+        if (t == 0) {
+            atomicOr(a.err, kErrTimeout);
+            // what thread 0 started and has not seen complete: the weight image, one load per
+            // buffer, one MMA group (a buffer is reloaded, and an MMA group committed, only after
+            // the previous one was waited for, so each barrier has at most one phase pending)
+            if (!w_done) tc::mbar_wait(&bar_w, 0);
+            for (int b = 0; b < 2; ++b)
+                if (ld_issued[b] > ld_done[b]) tc::mbar_wait(&bar_ld[b], (ld_issued[b] - 1u) & 1u);
+            if (mma_issued > mma_done) tc::mbar_wait(&bar_mma, (mma_issued - 1u) & 1u);
+        }
         if (TRAIN)
             for (int i = t; i < kPartStride; i += kTile) part[i] = 0.0f;
     } else if (TRAIN && it > 0) {
@@ -1033,6 +1057,37 @@ gi_status nrc_override(gi_nrc_t nrc, uint64_t n, const uint32_t **bits, const fl
 }  // namespace gi
 
 extern "C" {
+
+gi_status gi_nrc_config_defaults(gi_nrc_config *cfg) {
+    if (!cfg) {
+        set_error("gi_nrc_config_defaults: NULL config");
+        return GI_ERR_INVALID_ARG;
+    }
+    memset(cfg, 0, sizeof *cfg);
+    cfg->log2_table = 19;
+    // geometric level schedule from 16 to 2048 cells per axis (Mueller et al. 2022, Section 3)
+    const double n_min = 16.0, n_max = 2048.0;
+    const double b = pow(n_max / n_min, 1.0 / (GI_NRC_LEVELS - 1));
+    for (int l = 0; l < GI_NRC_LEVELS; ++l) cfg->resolution[l] = (uint32_t)floor(n_min * pow(b, (double)l) + 1e-9);
+    cfg->resolution[GI_NRC_LEVELS - 1] = (uint32_t)n_max;
+    for (int a = 0; a < 3; ++a) {
+        cfg->aabb_lo[a] = 0.0f;
+        cfg->aabb_hi[a] = 1.0f;
+    }
+    cfg->lr = 1e-2f;
+    cfg->beta1 = 0.9f;
+    cfg->beta2 = 0.99f;
+    cfg->adam_eps = 1e-15f;
+    cfg->loss_eps = 0.01f;
+    cfg->batch = 65536;
+    cfg->train_steps = 4;
+    cfg->max_records = 1u << 22;
+    cfg->max_queries = 1u << 20;
+    cfg->trust = 0.05f;
+    cfg->query_lod = 2;
+    cfg->seed = 1;
+    return GI_OK;
+}
 
 gi_status gi_nrc_create(const gi_nrc_config *cfg, gi_nrc_t *out) {
     if (!cfg || !out) {
