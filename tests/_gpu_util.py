@@ -76,7 +76,19 @@ def sh_gpu(pl):
     return pl.probes.sh.cpu().numpy()[:, :27].reshape(-1, 9, 3).astype(np.float64)
 
 
-def compare_frame(pl, fr, out, allow_sensitive_frac, rel=1e-4):
+# Interpolated irradiance: a pixel's flag (weighted, relaxed, none, sky) is a decision the float32
+# kernel and the float64 oracle could take differently where every neighbour weight sits at zero;
+# such flips may touch at most 1e-5 of the pixels (none observed on any workload).  Every pixel
+# whose flag agrees -- including the decision-sensitive ones, with a neighbour's plane test within
+# 1e-3 of its cut or a weight sum below 1e-2, whose weights are continuous there -- is compared at
+# |dE| <= rel |E| + 1e-5 emag + 1e-7, emag the magnitude of the summed SH terms (float32
+# cancellation in dark pixels).
+MAX_FLIP_FRAC = 1e-5
+
+
+def compare_frame(pl, fr, out, rel=1e-4):
+    """Spawn, probe SH and interpolation of one frame against the oracle; returns (decision-sensitive
+    pixels, flag flips)."""
     P = pl.probes.layout.num_probes
     # spawn: mask levels bit-exact, probe positions to float32 rounding
     mips_o = OP.build_mips(out["spawn"]["mask"])
@@ -100,28 +112,23 @@ def compare_frame(pl, fr, out, allow_sensitive_frac, rel=1e-4):
     Eg = OSH.irradiance(sg[v], out["spawn"]["nrm"][v])
     Eo = OSH.irradiance(so[v], out["spawn"]["nrm"][v])
     assert close(Eg, Eo, rel=rel, atol=1e-6).all()
-    # interpolation
+    # interpolation: flags, then every pixel whose flag agrees
     irr = pl.irr.cpu().numpy()
     flag_g = irr[..., 3].astype(np.int64)
     flag_o = out["flag"]
-    wsum, margin = out["diag"]["wsum"], out["diag"]["margin"]
-    # decision-sensitive pixels: a neighbour's plane test within 1e-3 of its cut, or a weight
-    # sum so small that float32 weight rounding moves the weighted mean by more than 1e-4
-    sensitive = (margin < 1e-3) | ((wsum > 0) & (wsum < 1e-2))
-    agree = ~sensitive
-    assert np.array_equal(flag_g[agree], flag_o[agree]), np.count_nonzero(flag_g[agree] != flag_o[agree])
-    # float32 evaluation of sum_k A_l Y_k(n) c_k cancels in dark pixels: bound the absolute error by the
-    # magnitude of the summed terms (emag) as well as 1e-4 of the value
+    X = flag_o.size
+    flips = flag_g != flag_o
+    assert np.count_nonzero(flips) <= MAX_FLIP_FRAC * X, np.count_nonzero(flips)
     emag = out["diag"]["emag"][..., None]
     ok = (np.abs(irr[..., :3] - out["irr"]) <= rel * np.abs(out["irr"]) + 1e-5 * emag + 1e-7).all(axis=-1)
-    bad = agree & ~ok
+    bad = ~flips & ~ok
     assert np.count_nonzero(bad) == 0, (np.count_nonzero(bad), np.abs(irr[..., :3] - out["irr"])[bad].max())
-    X = flag_o.size
-    assert np.count_nonzero(sensitive) <= allow_sensitive_frac * X, np.count_nonzero(sensitive) / X
-    return np.count_nonzero(sensitive), np.count_nonzero(flag_g != flag_o)
+    wsum, margin = out["diag"]["wsum"], out["diag"]["margin"]
+    sensitive = (margin < 1e-3) | ((wsum > 0) & (wsum < 1e-2))
+    return np.count_nonzero(sensitive), np.count_nonzero(flips)
 
 
-def run_frames(config, frames, allow_sensitive_frac=0.02, rel=1e-4, resolved_format=0):
+def run_frames(config, frames, rel=1e-4, resolved_format=0):
     cfg = wl.CONFIGS[config]
     fr0 = frames[0]
     pl = Pipeline(fr0.camera.width, fr0.camera.height, fr0.rays_per_probe, cfg["log2_slots"],
@@ -136,7 +143,7 @@ def run_frames(config, frames, allow_sensitive_frac=0.02, rel=1e-4, resolved_for
             pl.frame(gb, rec, view)
             torch.cuda.synchronize()
             out = run_frame(oc, fr)
-            stats.append(compare_frame(pl, fr, out, allow_sensitive_frac, rel))
+            stats.append(compare_frame(pl, fr, out, rel))
     finally:
         pl.close()
     return stats
