@@ -1,7 +1,7 @@
 """GPU parity of the learned radiance surrogate against the oracle (oracle/surrogate.py), through
 the C ABI: network output, loss gradients of every parameter, the Adam step, the records a query
-frame picks, probe irradiance with the network's answers, and what training gains over the
-untrained network on the Cornell box's own cache.
+frame picks, probe irradiance with the network's answers, and what the trained network gains
+over the method without it where it answers.
 
 Tolerances: the GPU rounds exactly where the oracle's emulation does (float16 features, bfloat16
 weights / activations / output gradient) and sums in float32, so outputs and gradients differ
@@ -261,20 +261,29 @@ def test_query_selection_matches_the_rules():
         gi.gi_nrc_destroy(nrc)
 
 
-def test_training_on_the_cornell_cache_beats_the_untrained_network():
-    """Online training on the cache's own resolved cells (Cornell box, static camera, 64 frames):
-    the network's relative L1 error against the FP64 oracle cache at every hit of the last frame
-    falls far below the untrained network's (which answers about zero everywhere)."""
+def test_trained_network_gains_over_the_plain_cache_where_it_answers():
+    """What the trained network adds to the method (Cornell box, static camera, 48 frames of
+    online training on a large cache's own resolved cells; trust threshold 0.25).  A second, small cache (2^12 slots for
+    ~10^4 cells a frame) drops inserts, as a full table does: the plain method then has no sample
+    for those rays and the probe pass falls back to the probe's radiance backup; the surrogate form
+    answers them (and the cells seen for the first time) with the network.  Against the float64
+    oracle cache of the large table (no drop), the probe irradiance of the probes with a dropped
+    ray is compared for the two forms: the network must at least halve the plain form's error.
+    The network itself stays within 25 % relative L1 of that oracle at every hit, and its judged
+    error falls by half during training."""
+    from oracle import sh as OSH
+    from oracle.frame import ray_radiance
     W = H = 256
     cfg, scene, seed = _cornell(W, H)
     spec = _spec(resolutions=(16, 22, 30, 42, 58, 80, 111, 153, 212, 294, 406, 561, 776, 1072, 1482, 2048),
                  log2_table=18)
     frames = 48
     n = (W // 8) * (H // 8) * 64
-    kw = dict(batch=65536, train_steps=4, max_records=n, max_queries=n, trust=0.05, query_lod=2, seed=5)
-    trained = _nrc(spec, **kw)
-    untrained = _nrc(spec, **kw)
+    # trust 0.25: above the judged error this short training reaches (~0.15), so that it answers
+    kw = dict(batch=65536, train_steps=4, max_records=n, max_queries=n, trust=0.25, query_lod=2, seed=5)
+    net = _nrc(spec, **kw)
     pl = Pipeline(W, H, 64, 18)
+    small = Pipeline(W, H, 64, 12, max_probe=32)
     oc = OracleCache(18)
     judged = []
     try:
@@ -284,27 +293,58 @@ def test_training_on_the_cornell_cache_beats_the_untrained_network():
             hits, R = _hits(fr)
             pl.update(R, view)
             pl.resolve(f)
-            gi.gi_nrc_train_frame(trained, pl.cache, hits, pl.slot_ids, f)
-            judged.append(gi.gi_nrc_stats(trained)["judged_error"])
+            gi.gi_nrc_train_frame(net, pl.cache, hits, pl.slot_ids, f)
+            judged.append(gi.gi_nrc_stats(net)["judged_error"])
             cam = fr.camera
-            oc.update(fr.records, f, cam.pos, cam.fov_y, cam.width, cam.height)
+            ident = oc.update(fr.records, f, cam.pos, cam.fov_y, cam.width, cam.height)
             oc.resolve(f)
+            if f >= frames - 2:
+                # the small cache sees the last two frames (the last one with history)
+                gb = dev(fr.gbuffer)
+                small.spawn(gb, view)
+                small.update(R, view)
+                small.resolve(f)
+        # --- the network at every hit of the last frame against the FP64 oracle cache
         hit = OK.record_is_hit(fr.records)
         ref, found = oc.query_records(fr.records, cam.pos, cam.fov_y, cam.width, cam.height)
         sel = hit & found
-        pos, nrm = fr.records[0:3, sel], fr.records[3:6, sel]
-        pts, keep = _points(np.ascontiguousarray(pos), np.ascontiguousarray(nrm))
-        errs = {}
-        for name, net in (("trained", trained), ("untrained", untrained)):
-            out = torch.empty((pos.shape[1], 4), dtype=torch.float32, device="cuda")
-            gi.gi_nrc_infer(net, pts, out)
-            y = out.cpu().numpy()[:, :3]
-            errs[name] = np.abs(y - ref[sel]).sum() / np.abs(ref[sel]).sum()
-        print("relative L1 error vs the FP64 oracle cache:", errs, "judged:", judged[0], "->", judged[-1])
-        assert errs["untrained"] > 0.9
-        assert errs["trained"] < 0.25
+        pts, keep = _points(np.ascontiguousarray(fr.records[0:3, sel]), np.ascontiguousarray(fr.records[3:6, sel]))
+        out = torch.empty((int(sel.sum()), 4), dtype=torch.float32, device="cuda")
+        gi.gi_nrc_infer(net, pts, out)
+        net_err = np.abs(out.cpu().numpy()[:, :3] - ref[sel]).sum() / np.abs(ref[sel]).sum()
+        # --- the two forms on the small cache, the reference on the large oracle cache
+        slots = u32(small.slot_ids)
+        dropped = hit & (slots == gi.GI_SLOT_NONE)
+        assert dropped.sum() > 0.2 * hit.sum(), dropped.sum()
+        small.integrate()
+        sh_plain = small.probes.sh.cpu().numpy()[:, :27].reshape(-1, 9, 3).astype(np.float64)
+        gi.gi_nrc_query_frame(net, small.cache, hits, small.slot_ids, view)
+        gi.gi_probes_integrate_nrc(small.cache, net, small.probes.struct, small.slot_ids, 64)
+        sh_surr = small.probes.sh.cpu().numpy()[:, :27].reshape(-1, 9, 3).astype(np.float64)
+        st = gi.gi_nrc_stats(net)
+        print("judged error", st["judged_error"], "trusted", st["trusted"], "dropped", int(dropped.sum()), "of", int(hit.sum()))
+        assert st["trusted"] == 1
+        cnt = gi.gi_nrc_answers(net)
+        recs = torch.empty(cnt, dtype=torch.int32, device="cuda")
+        rads = torch.empty((cnt, 4), dtype=torch.float32, device="cuda")
+        assert gi.gi_nrc_answers(net, recs, rads, cnt) == cnt
+        answered = u32(recs)
+        assert np.isin(np.flatnonzero(dropped), answered).all()
+        sp = OP.spawn(fr.gbuffer, cam, fr.frame)
+        rad, has = ray_radiance(oc, fr.records, ident)
+        P = sp["valid"].size
+        sh_ref = OP.integrate(sp["valid"], sp["nrm"], rad.reshape(P, 64, 3), has.reshape(P, 64))
+        affected = sp["valid"] & dropped.reshape(P, 64).any(axis=1)
+        nrm = sp["nrm"][affected]
+        e_ref = OSH.irradiance(sh_ref[affected], nrm)
+        err = {name: np.abs(OSH.irradiance(sh[affected], nrm) - e_ref).sum() / np.abs(e_ref).sum()
+               for name, sh in (("plain", sh_plain), ("surrogate", sh_surr))}
+        print("probe irradiance error vs the FP64 oracle (probes with a dropped ray):", err,
+              "network error at every hit:", net_err, "judged:", judged[1], "->", judged[-1])
+        assert err["surrogate"] < 0.5 * err["plain"], err
+        assert net_err < 0.25
         assert judged[-1] < 0.5 * judged[1]
     finally:
         pl.close()
-        gi.gi_nrc_destroy(trained)
-        gi.gi_nrc_destroy(untrained)
+        small.close()
+        gi.gi_nrc_destroy(net)
