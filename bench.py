@@ -70,9 +70,9 @@ UPDATE_SECTION = ("gi_cache.cu", "// -------------------------------------------
 NRC_ADAM_SECTION = ("gi_nrc.cu", "// ---------------------------------------------------------------- gradient scatter and Adam",
                     "// ---------------------------------------------------------------- query selection")
 NCU_TRAFFIC = {
-    # k_update, boxes-1080p: 153.96 MB read + 24.14 MB written
-    "2:update": {"bytes_per_launch": 178099200, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
-                 "source_sha": "14f297f5a79a57a6"},
+    # k_update, boxes-1080p (5th launch): 156.80 MB read + 31.07 MB written
+    "2:update": {"bytes_per_launch": 187872000, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
+                 "source_sha": "72d2212f2ef17c93"},
     # k_nrc_adam_table, Cornell 1080p: 3.22 TB/s x 40.16 us
     "4:adam_table": {"bytes_per_launch": 129501000, "sources": (NRC_ADAM_SECTION,), "source_sha": "a33b80b7d73defb0"},
 }
@@ -126,6 +126,10 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi takes a moment to deliver its first sample: the timed region starts after it
+            t_end = time.time() + 3.0
+            while not self.lines and time.time() < t_end:
+                time.sleep(0.02)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -136,6 +140,7 @@ class ClockSampler:
     def stop(self, t0=None, t1=None):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)  # one more sample after the timed region (a region can be shorter than 200 ms)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -1338,6 +1343,155 @@ def run_surrogate(args, rank, world, local_rank):
     return line
 
 
+def run_far_routing(args, rank, world, local_rank):
+    """Far hits to the surrogate on the boxes at 1080p (15 % of the hits have LOD >= 2): a network
+    trained online on a plain cache (the configuration's level schedule over the room), then per
+    frame the plain form (update, resolve, probe irradiance) against the routed form (update with
+    LOD >= 2 hits left out of the table, resolve, query frame answering them, probe irradiance with
+    the answers), each on its own cache over the same frames; the training call timed on its own.
+    The trust threshold is set to 1 so that the routing takes place whatever the network's error;
+    that error, on the routed hits against the plain cache's values of their cells, is reported."""
+    import torch
+    import paper_2310_19855_gb300 as gi
+    from paper_2310_19855_gb300.pipeline import Pipeline, view_of
+    import workload as wl
+
+    global CONFIG
+    CONFIG = 2
+    cfg2, cfg4 = wl.CONFIGS[2], wl.CONFIGS[4]
+    n_frames = min(args.frames, args.steps + args.warmup)
+    frames = make_frames(n_frames, rank)
+    fr0 = frames[0]
+    W, H, R, rpp = fr0.camera.width, fr0.camera.height, fr0.n_records, fr0.rays_per_probe
+    # the box the network normalises positions into: every hit point of the frames, 0.5 m margin
+    allp = np.concatenate([f.records[0:3, np.isfinite(f.records[9])] for f in frames], axis=1)
+    lo, hi = tuple(allp.min(axis=1) - 0.5), tuple(allp.max(axis=1) + 0.5)
+    ncfg = gi.make_nrc_config(lo, hi, log2_table=cfg4["nrc_log2_table"], resolutions=cfg4["nrc_resolutions"],
+                              lr=cfg4["nrc_lr"], batch=cfg4["nrc_batch"], train_steps=cfg4["nrc_train_steps"],
+                              max_records=R, max_queries=min(R, gi.GI_NRC_MAX_BATCH), trust=1.0, query_lod=4,
+                              seed=1)
+    nrc = gi.gi_nrc_create(ncfg)
+    pp = Pipeline(W, H, rpp, cfg2["log2_slots"])   # plain form
+    pr = Pipeline(W, H, rpp, cfg2["log2_slots"])   # routed form
+    dev_rec = [torch.from_numpy(np.ascontiguousarray(f.records[:10])).cuda() for f in frames]
+    dev_gb = [torch.from_numpy(f.gbuffer).cuda() for f in frames]
+    views = [view_of(f.camera, f.frame) for f in frames]
+    flush = L2Flush(torch)
+    stream = torch.cuda.current_stream()
+    try:
+        def plain(i, ev=None):
+            k = i % n_frames
+            mark = (lambda j: ev[j].record(stream)) if ev is not None else (lambda j: None)
+            pp.spawn(dev_gb[k], views[k], stream)
+            mark(0)
+            gi.gi_cache_update(pp.cache, gi.hits_from_planes(dev_rec[k], R), views[k], pp.slot_ids, stream)
+            mark(1)
+            pp.resolve(i, stream)
+            mark(2)
+            pp.integrate((0.0, 0.0, 0.0), stream)
+            mark(3)
+
+        def routed(i, ev=None):
+            k = i % n_frames
+            hits = gi.hits_from_planes(dev_rec[k], R)
+            mark = (lambda j: ev[j].record(stream)) if ev is not None else (lambda j: None)
+            pr.spawn(dev_gb[k], views[k], stream)
+            mark(0)
+            gi.gi_cache_update(pr.cache, hits, views[k], pr.slot_ids, stream)
+            mark(1)
+            pr.resolve(i, stream)
+            mark(2)
+            gi.gi_nrc_query_frame(nrc, pr.cache, hits, pr.slot_ids, views[k], stream)
+            mark(3)
+            gi.gi_probes_integrate_nrc(pr.cache, nrc, pr.probes.struct, pr.slot_ids, rpp, (0.0, 0.0, 0.0), stream)
+            mark(4)
+
+        def train(i, ev=None):
+            k = i % n_frames
+            if ev is not None:
+                ev[0].record(stream)
+            gi.gi_nrc_train_frame(nrc, pp.cache, gi.hits_from_planes(dev_rec[k], R), pp.slot_ids, i, stream)
+            if ev is not None:
+                ev[1].record(stream)
+
+        setup = 4 * cfg4["frames"] // 8
+        for i in range(setup):
+            plain(i)
+            train(i)
+        gi.gi_cache_route_far(pr.cache, nrc, 2)
+        for i in range(setup, setup + args.warmup):
+            plain(i)
+            routed(i)
+            train(i)
+        torch.cuda.synchronize()
+        steps = args.steps
+        ev_p = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        ev_r = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        ev_t = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+        clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+        clocks.start()
+        time.sleep(0.5)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        base = setup + args.warmup
+        for j in range(steps):
+            flush.zero_()
+            plain(base + j, ev_p[j])
+            flush.zero_()
+            routed(base + j, ev_r[j])
+            flush.zero_()
+            train(base + j, ev_t[j])
+        torch.cuda.synchronize()
+        clk = clocks.stop(t0, time.time())
+        pm = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(3)] for e in ev_p]).mean(axis=0)
+        rm = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(4)] for e in ev_r]).mean(axis=0)
+        tm = float(np.mean([e[0].elapsed_time(e[1]) for e in ev_t]))
+        # the routed hits of the last frame: the network's answers against the plain cache's cells
+        ids_r = pr.slot_ids.cpu().numpy().view(np.uint32)
+        far = ids_r == gi.GI_SLOT_FAR
+        cnt = gi.gi_nrc_answers(nrc)
+        recs = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
+        rads = torch.empty((max(cnt, 1), 4), dtype=torch.float32, device="cuda")
+        gi.gi_nrc_answers(nrc, recs, rads, cnt)
+        rec_ids = recs.cpu().numpy().view(np.uint32)[:cnt]
+        ans = rads.cpu().numpy()[:cnt, :3]
+        cache_val = torch.empty((R, 4), dtype=torch.float32, device="cuda")
+        gi.gi_cache_query(pp.cache, cache_val, R, slot_ids=pp.slot_ids)
+        ref_all = cache_val.cpu().numpy()
+        sel = far[rec_ids] & (ref_all[rec_ids, 3] == 1.0)
+        ref = ref_all[rec_ids[sel], :3]
+        net_err = float(np.abs(ans[sel] - ref).sum() / max(np.abs(ref).sum(), 1e-30))
+        st = gi.gi_nrc_stats(nrc, stream)
+    finally:
+        gi.gi_cache_route_far(pr.cache, None, 4)
+        pp.close()
+        pr.close()
+        gi.gi_nrc_destroy(nrc)
+    if rank != 0:
+        return None
+    plain_ms, routed_ms = float(pm.sum()), float(rm.sum())
+    return {
+        "metric": "update + resolve + probe irradiance with far hits routed to the surrogate, against the plain form",
+        "value": R / (routed_ms * 1e-3) / 1e6, "unit": UNIT, "steps": steps, "ms_per_step": routed_ms,
+        "dtype": "f32 cache, bf16 network (f32 accumulate)",
+        "config": {"workload": f"boxes-1080p: {W}x{H}, {R} records/frame, 2^{cfg2['log2_slots']} slots; network "
+                               f"16 levels x 2^{cfg4['nrc_log2_table']} entries over the hits' box, trained online for "
+                               f"{setup} frames on the plain cache; hits with LOD >= 2 routed (trust set to 1)",
+                   "records_per_step": R, "l2": L2_NOTE},
+        "pass_ms": {"plain_form": {"update": float(pm[0]), "resolve": float(pm[1]), "integrate": float(pm[2])},
+                    "routed_form": {"update": float(rm[0]), "resolve": float(rm[1]), "query": float(rm[2]),
+                                    "integrate_with_answers": float(rm[3])},
+                    "training_call": tm},
+        "frames_per_s": {"plain_form": 1e3 / plain_ms, "routed_form_without_training": 1e3 / routed_ms,
+                         "routed_form_with_training": 1e3 / (routed_ms + tm)},
+        "routed_hits_last_frame": int(far.sum()), "answered_last_frame": int(cnt),
+        "network_rel_l1_error_on_routed_hits_vs_plain_cache": net_err,
+        "judged_error": float(st["judged_error"]),
+        "gpu_launches": int(steps * (4 + 7 + 5 * cfg4["nrc_train_steps"])),
+        "clocks": clk,
+    }
+
+
 def run_config(config, args, rank, world, local_rank):
     """One configuration's run; its JSON line (rank 0) or None."""
     global CONFIG
@@ -1365,12 +1519,15 @@ def other_configs(args, rank, world, local_rank):
     import argparse as _ap
     import torch
     out = {}
-    for c in (5, 6, 7, 3, 4):
+    for c in (5, 6, 7, 3, 4, "4-far"):
         sub = _ap.Namespace(**vars(args))
         sub.steps, sub.warmup = min(args.steps, SUB_STEPS), min(max(args.warmup, 3), SUB_WARMUP)
         sub.frames, sub.no_cpu_baseline, sub.sub = SUB_FRAMES, True, True
         t0 = time.perf_counter()
-        line = run_config(c, sub, rank, world, local_rank)
+        if c == "4-far":
+            line = run_far_routing(sub, rank, world, local_rank)
+        else:
+            line = run_config(c, sub, rank, world, local_rank)
         torch.cuda.empty_cache()
         if line is None:
             continue

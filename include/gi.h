@@ -52,6 +52,7 @@ typedef enum gi_status {
 /* Slot-id codes written by gi_cache_update for records that do not name a cell. */
 #define GI_SLOT_MISS 0xFFFFFFFEu  /* the ray left the scene: its radiance is the environment */
 #define GI_SLOT_NONE 0xFFFFFFFFu  /* no sample: invalid record, or a hit dropped for lack of a slot */
+#define GI_SLOT_FAR 0xFFFFFFFDu   /* a far hit left to the surrogate (gi_cache_route_far): no cell */
 
 /* Probe-mask sentinel of a tile without probe (Section 2.1.5). */
 #define GI_PROBE_NONE 0xFFFFFFFFu
@@ -670,6 +671,20 @@ gi_status gi_probes_integrate_nrc(gi_cache_t cache, gi_nrc_t nrc, const gi_probe
 
 /* Counters (synchronises `stream`). */
 gi_status gi_nrc_stats(gi_nrc_t nrc, gi_nrc_stats_t *out, gi_stream_t stream);
+
+/*
+ * Far hits to the surrogate instead of the table (no counterpart in the paper, whose far field is
+ * the tile cache's MIP prefilter, Section 2.2.3).  From the next gi_cache_update of `cache` on,
+ * while `nrc` is trusted (its judged error on its latest training batch within its trust, tested
+ * by the update on the device, so that no call synchronises), hits whose cell LOD is >= far_lod
+ * are neither inserted nor accumulated: their slot id is GI_SLOT_FAR, and gi_nrc_query_frame
+ * answers every GI_SLOT_FAR record with the network (the plain probe pass treats them as rays
+ * without sample).  The network keeps training on the cells the table still holds.  nrc NULL or
+ * far_lod >= 4 ends the routing.  One-level caches only; gi_batch_frame does not route.  nrc must
+ * outlive the routing.  Host only, no synchronisation.  Errors: GI_ERR_INVALID_ARG for a NULL or
+ * tile cache.
+ */
+gi_status gi_cache_route_far(gi_cache_t cache, gi_nrc_t nrc, uint32_t far_lod);
 
 /* ---------------------------------------------------------------- allocation-free variant */
 /*

@@ -22,6 +22,7 @@ GI_OK, GI_ERR_INVALID_ARG, GI_ERR_OOM, GI_ERR_CUDA, GI_ERR_TIMEOUT, GI_ERR_DEVIC
 GI_WARN_DROPPED = 100
 GI_SLOT_MISS = 0xFFFFFFFE
 GI_SLOT_NONE = 0xFFFFFFFF
+GI_SLOT_FAR = 0xFFFFFFFD
 GI_PROBE_NONE = 0xFFFFFFFF
 GI_INTERP_OK, GI_INTERP_RELAXED, GI_INTERP_NONE, GI_INTERP_SKY = 0, 1, 2, 3
 GI_KEY_DIR_NORMAL, GI_KEY_DIR_RAY = 0, 1
@@ -186,6 +187,7 @@ def lib() -> ctypes.CDLL:
             "gi_cell_means_noalloc": (ctypes.c_int, [ctypes.POINTER(gi_hits), ctypes.POINTER(gi_view), c_f32, c_u32,
                                                      c_u32, ctypes.POINTER(c_f32), c_vp, c_vp, c_vp]),
             "gi_nrc_config_defaults": (ctypes.c_int, [ctypes.POINTER(gi_nrc_config)]),
+            "gi_cache_route_far": (ctypes.c_int, [c_vp, c_vp, c_u32]),
             "gi_nrc_create": (ctypes.c_int, [ctypes.POINTER(gi_nrc_config), ctypes.POINTER(c_vp)]),
             "gi_nrc_destroy": (ctypes.c_int, [c_vp]),
             "gi_nrc_set_params": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
@@ -495,6 +497,12 @@ def make_nrc_config(aabb_lo, aabb_hi, log2_table: int = 19, resolutions=None, lr
     c.max_records, c.max_queries = int(max_records), int(max_queries)
     c.trust, c.query_lod, c.seed = float(trust), int(query_lod), int(seed)
     return c
+
+
+def gi_cache_route_far(cache: int, nrc: int | None, far_lod: int) -> None:
+    """While nrc is trusted, hits of LOD >= far_lod skip the table (slot id GI_SLOT_FAR) and are
+    answered by the network (see gi.h); nrc None or far_lod >= 4 ends the routing."""
+    check(lib().gi_cache_route_far(cache, nrc, int(far_lod)), "gi_cache_route_far")
 
 
 def gi_nrc_create(cfg: gi_nrc_config) -> int:

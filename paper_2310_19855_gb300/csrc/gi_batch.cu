@@ -256,7 +256,9 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
             (bv.probes.layout.num_probes * 4u + b->tuning.integrate_threads - 1u) / b->tuning.integrate_threads,
             interp_grid_x(bv.view.width) * interp_grid_y(bv.view.height)};
         for (int k = 0; k < 5; ++k) pre[k][v + 1] = pre[k][v] + cnt[k];
-        reinterpret_cast<UpdateArgs *>(h + L.upd)[v] = cache_update_args(bv.cache, &bv.hits, &bv.view, bv.slot_ids);
+        UpdateArgs ua = cache_update_args(bv.cache, &bv.hits, &bv.view, bv.slot_ids);
+        ua.route_stats = nullptr;  // batched frames never route far hits to a surrogate
+        reinterpret_cast<UpdateArgs *>(h + L.upd)[v] = ua;
         reinterpret_cast<ResolveArgs *>(h + L.res)[v] = cache_resolve_args(bv.cache, bv.resolve_frame);
         reinterpret_cast<SpawnArgs *>(h + L.spawn)[v] = spawn_args(&bv.gbuf, &bv.view, &bv.probes);
         reinterpret_cast<IntegrateArgs *>(h + L.integ)[v] = integrate_args(bv.cache, &bv.probes, bv.slot_ids, b->rpp, bv.env);

@@ -103,6 +103,12 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)nblk * kUpdThreads;
     uint32_t my_clamped = 0, my_maxp = 0;
+    // far hits go to the surrogate while it is trusted (the decision of the whole launch)
+    uint32_t route_lod = 4u;
+    if (a.route_stats) {
+        const float den = __ldg(a.route_stats + 2), err = __ldg(a.route_stats + 1);
+        if (den > 0.0f && err <= a.route_trust * den) route_lod = a.route_lod;
+    }
     for (unsigned long long base = (unsigned long long)blk * kUpdThreads; base < a.n; base += stride) {
         const unsigned long long i = base + threadIdx.x;
         const bool inr = i < a.n;
@@ -113,8 +119,9 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
             py = __ldcs(a.p[1] + i);
             pz = __ldcs(a.p[2] + i);
         }
-        const bool hit = inr && isfinite(len) && len >= 0.0f && isfinite3(px, py, pz);
+        bool hit = inr && isfinite(len) && len >= 0.0f && isfinite3(px, py, pz);
         const bool miss = inr && len == INFINITY;
+        bool far = false;
         unsigned long long q0 = 0, q1 = 0, q2 = 0;
         uint32_t home = 0, tag = 0;
         if (hit) {
@@ -136,6 +143,9 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
             unsigned long long key =
                 cell_key(a.kp, px, py, pz, sx, sy, sz, len, KEY_DIR == GI_KEY_DIR_NORMAL ? 0u : 1u);
             cell_of_key(key, a.mask, home, tag);
+            // the LOD sits in the descriptor's top bits
+            far = (uint32_t)(key >> 61) >= route_lod;
+            hit = !far;
         }
         uint32_t cnt = hit ? 1u : 0u;
         unsigned peers = 1u << lane;
@@ -192,7 +202,7 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
         }
         uint32_t my_slot = slot;
         if (MERGE) my_slot = __shfl_sync(kFull, slot, hit ? (__ffs(peers) - 1) : lane);
-        if (inr) __stcs(a.slot_ids + i, hit ? my_slot : (miss ? GI_SLOT_MISS : GI_SLOT_NONE));
+        if (inr) __stcs(a.slot_ids + i, hit ? my_slot : (far ? GI_SLOT_FAR : (miss ? GI_SLOT_MISS : GI_SLOT_NONE)));
     }
     // the bulk reductions complete (their sums visible) before the block ends
     if (bitmap) bulk_wait_all();
@@ -570,6 +580,8 @@ struct gi_cache_s {
     bool touched_since_resolve;
     bool rebuild_checked;
     uint64_t rebuilds, updates, resolves;
+    gi_nrc_t route_nrc;          // far hits to this surrogate (gi_cache_route_far), or NULL
+    uint32_t route_lod;
 };
 
 namespace gi {
@@ -654,6 +666,15 @@ UpdateArgs cache_update_args(gi_cache_s *c, const gi_hits *h, const gi_view *v, 
     a.mask = c->mask;
     a.max_probe = c->cfg.max_probe;
     a.kp = key_params(c->cfg.cell_size, c->cfg.num_lods, v);
+    a.route_stats = nullptr;
+    a.route_trust = 0.0f;
+    a.route_lod = 4u;
+    if (c->route_nrc && c->route_lod < 4u) {
+        bool trained = false;
+        nrc_route_inputs(c->route_nrc, &a.route_stats, &a.route_trust, &trained);
+        if (!trained) a.route_stats = nullptr;
+        a.route_lod = c->route_lod;
+    }
     return a;
 }
 
@@ -945,6 +966,16 @@ gi_status gi_cache_update(gi_cache_t c, const gi_hits *hits, const gi_view *view
     s = cuda_status(cudaGetLastError(), "k_update launch");
     if (s == GI_OK) c->touched_since_resolve = true;
     return s;
+}
+
+gi_status gi_cache_route_far(gi_cache_t c, gi_nrc_t nrc, uint32_t far_lod) {
+    if (!c || c->tiles) {
+        set_error("gi_cache_route_far: NULL cache or a tile cache");
+        return GI_ERR_INVALID_ARG;
+    }
+    c->route_nrc = far_lod < 4u ? nrc : nullptr;
+    c->route_lod = far_lod;
+    return GI_OK;
 }
 
 gi_status gi_cache_resolve(gi_cache_t c, uint32_t frame, gi_stream_t stream) {
@@ -1362,6 +1393,9 @@ extern "C" gi_status gi_cell_means_noalloc(const gi_hits *hits, const gi_view *v
     a.mask = kNoAllocSlots - 1u;
     a.max_probe = 255;
     a.kp = key_params(cell_size, num_lods, view);
+    a.route_stats = nullptr;
+    a.route_trust = 0.0f;
+    a.route_lod = 4u;
     const int ub = update_blocks(hits->n);
     launch_update(a, key_dir, false, ub, st);
     s = cuda_status(cudaGetLastError(), "k_update launch");

@@ -105,7 +105,13 @@ struct UpdateArgs {
     uint32_t mask;
     uint32_t max_probe;
     KeyParams kp;
-};
+    // far hits to the surrogate (gi_cache_route_far): while the network's judged error stats
+    // (route_stats[1] <= route_trust * route_stats[2], route_stats[2] > 0) allow it, hits with
+    // LOD >= route_lod are left out of the table; route_stats NULL: no routing
+    const float *route_stats;
+    float route_trust;
+    uint32_t route_lod;
+}; // UpdateArgs
 
 struct ResolveArgs {
     const uint32_t *touch;
@@ -361,4 +367,10 @@ __device__ __forceinline__ float3 cam_ray_dir(const CamParams &c, float x, float
     return make_float3(dx * inv, dy * inv, dz * inv);
 }
 
+} // namespace gi
+
+namespace gi {
+// The trust test's inputs of a surrogate (gi_nrc.cu): device stats {loss, sum m|y - t|, sum m|t|},
+// the trust threshold, and whether it has taken an Adam step.
+void nrc_route_inputs(gi_nrc_t nrc, const float **stats, float *trust, bool *trained);
 } // namespace gi

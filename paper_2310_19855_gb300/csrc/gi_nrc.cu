@@ -789,9 +789,13 @@ __global__ void __launch_bounds__(256) k_nrc_select(SelectArgs a) {
     for (uint32_t wd = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; wd < words; wd += warps) {
         const uint32_t r = wd * 32u + lane;
         bool use = false;
-        if (trusted && r < a.n && record_hit(a.pos, a.len, r)) {
+        if (r < a.n && record_hit(a.pos, a.len, r)) {
             const uint32_t slot = __ldg(a.slot_ids + r);
-            if (slot == GI_SLOT_NONE) {
+            if (slot == GI_SLOT_FAR) {
+                // left out of the table by the update (gi_cache_route_far): the network is its only answer
+                use = true;
+            } else if (!trusted) {
+            } else if (slot == GI_SLOT_NONE) {
                 use = true;
             } else if (slot < a.cv.slots) {
                 const bool cold = cache_value(a.cv, slot).w != 0.0f;
@@ -1045,6 +1049,12 @@ gi_status refresh_copies(gi_nrc_s *s) {
 }  // namespace
 
 namespace gi {
+void nrc_route_inputs(gi_nrc_t nrc, const float **stats, float *trust, bool *trained) {
+    *stats = nrc->stats;
+    *trust = nrc->cfg.trust;
+    *trained = nrc->steps > 0;
+}
+
 gi_status nrc_override(gi_nrc_t nrc, uint64_t n, const uint32_t **bits, const float4 **ovr) {
     if (!nrc->queried || nrc->last_query_n != n) {
         set_error("gi_probes_integrate_nrc: no gi_nrc_query_frame for a view of %llu records", (unsigned long long)n);

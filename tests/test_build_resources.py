@@ -13,7 +13,7 @@ CSRC = os.path.join(ROOT, "paper_2310_19855_gb300", "csrc")
 
 # kernel (as its mangled name contains it) -> (source, most registers per thread)
 HOT = {
-    "8k_updateILi0E": ("gi_cache.cu", 32),
+    "8k_updateILi0ELb0E": ("gi_cache.cu", 32),  # the default form (no warp merge)
     "9k_resolveE": ("gi_cache.cu", 64),
     "16k_resolve_bitmapE": ("gi_cache.cu", 64),
     "14k_diag_atomicsILb1E": ("gi_diag.cu", 32),

@@ -261,6 +261,61 @@ def test_query_selection_matches_the_rules():
         gi.gi_nrc_destroy(nrc)
 
 
+@pytest.mark.parametrize("trust", [1e30, 0.0], ids=["trusted", "untrusted"])
+def test_far_hits_routed_to_a_trusted_network(trust):
+    """gi_cache_route_far: while the network is trusted, hits whose cell LOD is >= 2 skip the table
+    (slot id GI_SLOT_FAR) and the query frame answers every one of them; the table then holds
+    exactly the oracle's cells of the nearer hits.  An untrusted network routes nothing."""
+    cfg = dict(wl.CONFIGS[2], width=320, height=180)
+    seed = wl.scene.SEED_BASE + 5000
+    scene = wl.make_scene(cfg, seed)
+    fr = wl.make_frame(cfg, 0, scene, seed_base=seed)
+    cam = fr.camera
+    lo = np.min(fr.records[0:3, np.isfinite(fr.records[9])], axis=1) - 1.0
+    hi = np.max(fr.records[0:3, np.isfinite(fr.records[9])], axis=1) + 1.0
+    spec = _spec(aabb=(tuple(lo), tuple(hi)))
+    nrc = _nrc(spec, batch=1024, max_records=fr.n_records, max_queries=fr.n_records, trust=trust, query_lod=4)
+    pl = Pipeline(320, 180, 64, 16)
+    try:
+        gi.gi_nrc_set_params(nrc, *SI.params(11, LOG2_T))
+        _trust_as_is(nrc, spec)
+        gi.gi_cache_route_far(pl.cache, nrc, 2)
+        view = view_of(cam, 0)
+        hits, R = _hits(fr)
+        pl.update(R, view)
+        pl.resolve(0)
+        slots = u32(pl.slot_ids)
+        hit = OK.record_is_hit(fr.records)
+        lp = OK.lod_params(0.05, 4, cam.fov_y, cam.width, cam.height)
+        _, lod = OK.cell_key(fr.records, cam.pos, lp)
+        far = hit & (np.asarray(lod) >= 2)
+        assert far.sum() > 0.05 * hit.sum()
+        oc = OracleCache(16)
+        near = fr.records.copy()
+        if trust > 0:
+            assert np.array_equal(slots == gi.GI_SLOT_FAR, far)
+            near[9, far] = np.nan  # the oracle's update skips them as no-sample records
+        else:
+            assert not np.any(slots == gi.GI_SLOT_FAR)
+        oc.update(near, 0, cam.pos, cam.fov_y, cam.width, cam.height)
+        oc.resolve(0)
+        assert np.array_equal(gi.gi_cache_export(pl.cache)["identity"], oc.ids)
+        gi.gi_nrc_query_frame(nrc, pl.cache, hits, pl.slot_ids, view)
+        cnt = gi.gi_nrc_answers(nrc)
+        recs = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
+        rads = torch.empty((max(cnt, 1), 4), dtype=torch.float32, device="cuda")
+        gi.gi_nrc_answers(nrc, recs, rads, cnt)
+        answered = u32(recs)[:cnt]
+        if trust > 0:
+            assert np.isin(np.flatnonzero(far), answered).all()
+        else:
+            assert cnt == 0
+    finally:
+        gi.gi_cache_route_far(pl.cache, None, 4)
+        pl.close()
+        gi.gi_nrc_destroy(nrc)
+
+
 def test_trained_network_gains_over_the_plain_cache_where_it_answers():
     """What the trained network adds to the method (Cornell box, static camera, 48 frames of
     online training on a large cache's own resolved cells; trust threshold 0.25).  A second, small cache (2^12 slots for
