@@ -30,9 +30,9 @@ static DescLayout desc_layout(uint32_t n) {
     L.spawn = o; o = align16(o + n * sizeof(SpawnArgs));
     L.integ = o; o = align16(o + n * sizeof(IntegrateArgs));
     L.interp = o; o = align16(o + n * sizeof(InterpArgs));
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 5; ++k) {  // n + 1 prefix entries, then the pass's work-item counter
         L.pre[k] = o;
-        o = align16(o + (n + 1) * sizeof(uint32_t));
+        o = align16(o + (n + 2) * sizeof(uint32_t));
     }
     L.total = o;
     return L;
@@ -265,7 +265,10 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
         reinterpret_cast<InterpArgs *>(h + L.interp)[v] = interp_args(&bv.gbuf, &bv.view, &bv.probes, bv.irradiance);
     }
     std::vector<uint32_t> blocks(5);
-    for (int k = 0; k < 5; ++k) blocks[k] = pre[k][n];
+    for (int k = 0; k < 5; ++k) {
+        blocks[k] = pre[k][n];
+        pre[k][n + 1] = 0;  // the pass's work-item counter starts at zero every frame
+    }
     gi_status s = GI_OK;
     if (use_graph) {
         if (!b->exec[set] || b->sig[set] != blocks) {

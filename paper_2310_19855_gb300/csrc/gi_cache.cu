@@ -508,21 +508,13 @@ template <int KEY_DIR>
 __global__ void __launch_bounds__(kUpdThreads, 8) k_update_batched(const UpdateArgs *args, const uint32_t *prefix,
                                                                    uint32_t nviews) {
     __shared__ UpdateArgs sa;
-    const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
-    load_view_args(sa, args + v);
-    __syncthreads();
-    const uint32_t p0 = __ldg(prefix + v), p1 = __ldg(prefix + v + 1);
-    update_body<KEY_DIR, false>(sa, blockIdx.x - p0, p1 - p0);
+    GI_BATCHED_ITEMS(prefix, nviews, sa, args, (update_body<KEY_DIR, false>(sa, item, items)));
 }
 
 __global__ void __launch_bounds__(kResThreads, kResBmBlocksPerSm) k_resolve_batched(const ResolveArgs *args, const uint32_t *prefix,
                                                                     uint32_t nviews) {
     __shared__ ResolveArgs sa;
-    const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
-    load_view_args(sa, args + v);
-    __syncthreads();
-    const uint32_t p0 = __ldg(prefix + v), p1 = __ldg(prefix + v + 1);
-    resolve_body(sa, blockIdx.x - p0, p1 - p0);
+    GI_BATCHED_ITEMS(prefix, nviews, sa, args, resolve_body(sa, item, items));
 }
 
 uint32_t update_blocks_for(unsigned long long n, uint32_t records_per_block) {
@@ -533,16 +525,21 @@ gi_status launch_update_batched(const UpdateArgs *args, const uint32_t *prefix, 
                                 int key_dir, cudaStream_t st) {
     if (blocks == 0) return GI_OK;
     if (key_dir == GI_KEY_DIR_NORMAL)
-        k_update_batched<GI_KEY_DIR_NORMAL><<<blocks, kUpdThreads, 0, st>>>(args, prefix, nviews);
+        k_update_batched<GI_KEY_DIR_NORMAL>
+            <<<resident_grid(k_update_batched<GI_KEY_DIR_NORMAL>, kUpdThreads, blocks), kUpdThreads, 0, st>>>(
+                args, prefix, nviews);
     else
-        k_update_batched<GI_KEY_DIR_RAY><<<blocks, kUpdThreads, 0, st>>>(args, prefix, nviews);
+        k_update_batched<GI_KEY_DIR_RAY>
+            <<<resident_grid(k_update_batched<GI_KEY_DIR_RAY>, kUpdThreads, blocks), kUpdThreads, 0, st>>>(
+                args, prefix, nviews);
     return cuda_status(cudaGetLastError(), "k_update_batched launch");
 }
 
 gi_status launch_resolve_batched(const ResolveArgs *args, const uint32_t *prefix, uint32_t nviews, uint32_t blocks,
                                  cudaStream_t st) {
     if (blocks == 0) return GI_OK;
-    k_resolve_batched<<<blocks, kResThreads, 0, st>>>(args, prefix, nviews);
+    k_resolve_batched<<<resident_grid(k_resolve_batched, kResThreads, blocks), kResThreads, 0, st>>>(args, prefix,
+                                                                                                    nviews);
     return cuda_status(cudaGetLastError(), "k_resolve_batched launch");
 }
 

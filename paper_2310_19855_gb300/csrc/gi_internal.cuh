@@ -289,6 +289,18 @@ bool cache_tiled(const gi_cache_s *c);
 int cache_device(const gi_cache_s *c);
 int64_t cache_last_resolved(const gi_cache_s *c);
 
+// Blocks of a resident grid of `kernel` (threads per block, dynamic shared memory 0) on the
+// current device, at most `items`.
+template <typename K>
+inline uint32_t resident_grid(K kernel, int threads, uint32_t items) {
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    const uint32_t g = (uint32_t)(sms * (per_sm > 0 ? per_sm : 1));
+    return items < g ? items : g;
+}
+
 // Launchers of the batched passes: one launch per pass over every view; args and prefix tables
 // (nviews + 1 block-count prefixes) live in device memory.
 uint32_t update_blocks_for(unsigned long long n, uint32_t records_per_block);
@@ -329,6 +341,36 @@ __device__ __forceinline__ uint32_t view_of_block(const uint32_t *prefix, uint32
     }
     return lo;
 }
+
+// Persistent batched passes: a resident grid takes the flat work items of every view (the prefix
+// table's blocks) one at a time from a counter that follows the prefix table (prefix[nviews + 1],
+// zero when the pass starts), so that blocks that drew cheap items take more; a view's arguments
+// are reloaded into shared memory only when an item belongs to another view than the last.  The
+// body sees `item` (the view-local block) and `items` (the view's block count).
+#define GI_BATCHED_ITEMS(prefix, nviews, sa, args, body)                                   \
+    do {                                                                                 \
+        __shared__ uint32_t s_w_;                                                        \
+        const uint32_t total_ = __ldg((prefix) + (nviews));                              \
+        uint32_t *ctr_ = const_cast<uint32_t *>(prefix) + (nviews) + 1;                  \
+        uint32_t cur_ = 0xFFFFFFFFu;                                                     \
+        for (;;) {                                                                       \
+            if (threadIdx.x == 0) s_w_ = atomicAdd(ctr_, 1u);                            \
+            __syncthreads();                                                             \
+            const uint32_t w_ = s_w_;                                                    \
+            if (w_ >= total_) break;                                                     \
+            const uint32_t v_ = view_of_block((prefix), (nviews), w_);                   \
+            if (v_ != cur_) {                                                            \
+                load_view_args((sa), (args) + v_);                                       \
+                __syncthreads();                                                         \
+                cur_ = v_;                                                               \
+            }                                                                            \
+            const uint32_t p0_ = __ldg((prefix) + v_), p1_ = __ldg((prefix) + v_ + 1);   \
+            const uint32_t item = w_ - p0_, items = p1_ - p0_;                           \
+            (void)items;                                                                 \
+            body;                                                                        \
+            __syncthreads();                                                             \
+        }                                                                                \
+    } while (0)
 
 // Copy one view's pass arguments from global to shared memory (whole block; sync after).
 template <typename T>

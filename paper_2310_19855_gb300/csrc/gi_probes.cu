@@ -1282,11 +1282,10 @@ __global__ void __launch_bounds__(64 * kFiltProbes) k_filter(FilterArgs a) {
 // ---------------------------------------------------------------- batched passes (many views)
 __global__ void __launch_bounds__(256) k_spawn_batched(const SpawnArgs *args, const uint32_t *prefix, uint32_t nviews) {
     __shared__ SpawnArgs sa;
-    const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
-    load_view_args(sa, args + v);
-    __syncthreads();
-    const uint32_t b = blockIdx.x - __ldg(prefix + v), gx = (sa.tiles_x + 15) / 16;
-    spawn_body(sa, b % gx, b / gx);
+    GI_BATCHED_ITEMS(prefix, nviews, sa, args, {
+        const uint32_t gx = (sa.tiles_x + 15) / 16;
+        spawn_body(sa, item % gx, item / gx);
+    });
 }
 
 // MIP levels 5 and up of every view: one block per view.
@@ -1301,27 +1300,23 @@ __global__ void __launch_bounds__(128, 4) k_integrate_batched(const IntegrateArg
                                                            uint32_t nviews) {
     __shared__ IntegrateArgs sa;
     __shared__ __align__(16) float s_mom[64 * kMomStride];
-    const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
-    load_view_args(sa, args + v);
     load_moment_table(s_mom);
-    __syncthreads();
-    integrate_body<false>(sa, blockIdx.x - __ldg(prefix + v), s_mom);
+    GI_BATCHED_ITEMS(prefix, nviews, sa, args, integrate_body<false>(sa, item, s_mom));
 }
 
 __global__ void __launch_bounds__(256, 4) k_interpolate_batched(const InterpArgs *args, const uint32_t *prefix,
                                                                 uint32_t nviews) {
     __shared__ InterpArgs sa;
-    const uint32_t v = view_of_block(prefix, nviews, blockIdx.x);
-    load_view_args(sa, args + v);
-    __syncthreads();
-    const uint32_t b = blockIdx.x - __ldg(prefix + v), gx = interp_grid_x(sa.width);
-    interpolate_body(sa, b % gx, b / gx);
+    GI_BATCHED_ITEMS(prefix, nviews, sa, args, {
+        const uint32_t gx = interp_grid_x(sa.width);
+        interpolate_body(sa, item % gx, item / gx);
+    });
 }
 
 gi_status launch_spawn_batched(const SpawnArgs *args, const uint32_t *prefix, uint32_t nviews, uint32_t blocks,
                                cudaStream_t st) {
     if (blocks == 0) return GI_OK;
-    k_spawn_batched<<<blocks, 256, 0, st>>>(args, prefix, nviews);
+    k_spawn_batched<<<resident_grid(k_spawn_batched, 256, blocks), 256, 0, st>>>(args, prefix, nviews);
     gi_status s = cuda_status(cudaGetLastError(), "k_spawn_batched launch");
     if (s != GI_OK) return s;
     k_mip_tail_batched<<<nviews, 1024, 0, st>>>(args);
@@ -1331,14 +1326,15 @@ gi_status launch_spawn_batched(const SpawnArgs *args, const uint32_t *prefix, ui
 gi_status launch_integrate_batched(const IntegrateArgs *args, const uint32_t *prefix, uint32_t nviews,
                                    uint32_t blocks, uint32_t threads, cudaStream_t st) {
     if (blocks == 0) return GI_OK;
-    k_integrate_batched<<<blocks, threads, 0, st>>>(args, prefix, nviews);
+    k_integrate_batched<<<resident_grid(k_integrate_batched, (int)threads, blocks), threads, 0, st>>>(args, prefix,
+                                                                                                      nviews);
     return cuda_status(cudaGetLastError(), "k_integrate_batched launch");
 }
 
 gi_status launch_interpolate_batched(const InterpArgs *args, const uint32_t *prefix, uint32_t nviews,
                                      uint32_t blocks, cudaStream_t st) {
     if (blocks == 0) return GI_OK;
-    k_interpolate_batched<<<blocks, 256, 0, st>>>(args, prefix, nviews);
+    k_interpolate_batched<<<resident_grid(k_interpolate_batched, 256, blocks), 256, 0, st>>>(args, prefix, nviews);
     return cuda_status(cudaGetLastError(), "k_interpolate_batched launch");
 }
 
