@@ -72,7 +72,7 @@ NRC_ADAM_SECTION = ("gi_nrc.cu", "// -------------------------------------------
 NCU_TRAFFIC = {
     # k_update, boxes-1080p (5th launch): 156.80 MB read + 31.07 MB written
     "2:update": {"bytes_per_launch": 187872000, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
-                 "source_sha": "72d2212f2ef17c93"},
+                 "source_sha": "3ef82e75fff595ec"},
     # k_nrc_adam_table, Cornell 1080p: 3.22 TB/s x 40.16 us
     "4:adam_table": {"bytes_per_launch": 129501000, "sources": (NRC_ADAM_SECTION,), "source_sha": "a33b80b7d73defb0"},
 }
