@@ -384,8 +384,6 @@ __global__ void __launch_bounds__(kTileResThreads) k_tile_resolve(TileResolveArg
                     samples = sat_add(__float_as_uint(sv[h].w), samples);
                 }
                 cv[h] = make_float4(val.x, val.y, val.z, __uint_as_float(samples));
-                a.t.state[e] = cv[h];
-                a.t.stamp[e] = a.stamp_now;
                 uint4 *dst = reinterpret_cast<uint4 *>(acc + c);
                 dst[0] = make_uint4(0u, 0u, 0u, 0u);
                 dst[1] = make_uint4(0u, 0u, 0u, 0u);
@@ -397,6 +395,19 @@ __global__ void __launch_bounds__(kTileResThreads) k_tile_resolve(TileResolveArg
             // a live cell's sample count is >= 1, so count 0 marks "no value" in the levels
             if (!live[h]) cv[h] = make_float4(0.f, 0.f, 0.f, 0.f);
             lv[c] = cv[h];
+        }
+        // State and stamps go back in whole 32-byte sectors wherever a sector holds a touched cell
+        // (a partly written sector costs the DRAM a read of it): the touched cells' new values, the
+        // untouched cells' unchanged ones -- or zeros for a cell that holds no value (a dead cell's
+        // state is never read: it restarts without history when touched again).
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t c = (uint32_t)lane + 32u * h;
+            const size_t e = base + c;
+            const bool touched = (m >> c) & 1ull;
+            const unsigned tm = __ballot_sync(kFull, touched);
+            if ((tm >> (lane & ~1)) & 3u) a.t.state[e] = touched ? cv[h] : sv[h];
+            if ((tm >> (lane & ~7)) & 0xFFu) a.t.stamp[e] = touched ? a.stamp_now : st[h];
         }
         __syncwarp();
         if (lane < 16) {  // 4x4 value (I, J) = (lane & 3, lane >> 2): cells 2I + 16J + {0, 1, 8, 9}
@@ -414,10 +425,19 @@ __global__ void __launch_bounds__(kTileResThreads) k_tile_resolve(TileResolveArg
             lv[kTileCells + 20] = box4(lv[c0], lv[c0 + 1], lv[c0 + 2], lv[c0 + 3]);
         }
         __syncwarp();
+        // answers in whole sectors too: a cell without value shares its sector with a live one
+        // (2 cells per sector in float32, 4 in float16) writes zeros, never read (not live)
+        const uint32_t span = a.f16 ? 4u : 2u;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint32_t c = (uint32_t)lane + 32u * h;
-            if (!live[h]) continue;
+            const unsigned lm = __ballot_sync(kFull, live[h]);
+            if (!live[h]) {
+                if ((lm >> (lane & ~(span - 1u))) & ((1u << span) - 1u))
+                    store_resolved(a.t.resolved, a.res_stride, a.f16, (uint32_t)(base + c),
+                                   make_float3(0.f, 0.f, 0.f), false);
+                continue;
+            }
             // finest level with enough samples; a live cell has a value at every level above it
             const float4 l1 = lv[kTileCells + ((c & 7u) >> 1) + 4u * (c >> 4)];
             const float4 l2 = lv[kTileCells + 16u + ((c >> 2) & 1u) + 2u * (c >> 5)];
