@@ -67,12 +67,15 @@ REFERENCE_BUDGET_S = 90.0
 # since.  A source is a file of csrc/, or (file, first line, line after the last) for one section.
 UPDATE_SECTION = ("gi_cache.cu", "// ---------------------------------------------------------------- update",
                   "// ---------------------------------------------------------------- resolve")
+# the shared header up to the update's argument block: constants, accumulator, counters, key
+# parameters and hashing, UpdateArgs
+UPDATE_HEADER = ("gi_internal.cuh", "namespace gi {", "struct ResolveArgs {")
 NRC_ADAM_SECTION = ("gi_nrc.cu", "// ---------------------------------------------------------------- gradient scatter and Adam",
                     "// ---------------------------------------------------------------- query selection")
 NCU_TRAFFIC = {
-    # k_update, boxes-1080p (5th launch): 156.80 MB read + 31.07 MB written
-    "2:update": {"bytes_per_launch": 187872000, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", "gi_internal.cuh"),
-                 "source_sha": "3ef82e75fff595ec"},
+    # k_update, boxes-1080p (5th launch): 156.84 MB read + 31.24 MB written
+    "2:update": {"bytes_per_launch": 188079872, "sources": (UPDATE_SECTION, "gi_cache_dev.cuh", UPDATE_HEADER),
+                 "source_sha": "1af4e79846bba09c"},
     # k_nrc_adam_table, Cornell 1080p: 3.22 TB/s x 40.16 us
     "4:adam_table": {"bytes_per_launch": 129501000, "sources": (NRC_ADAM_SECTION,), "source_sha": "a33b80b7d73defb0"},
 }
@@ -211,6 +214,31 @@ def e2e_pipelined(torch, n_steps, upload, compute, download):
     t1.record(ds)
     torch.cuda.synchronize()
     return t0.elapsed_time(t1) / n_steps
+
+
+def host_link(torch, pairs_up, pairs_down, reps=5):
+    """The host link alone: the step's copies (pinned host -> device, device -> pinned host), each
+    direction on its own with nothing else running, best of reps; returns the e2e block's `link`."""
+    st = torch.cuda.current_stream()
+    out = {}
+    for name, pairs in (("h2d", pairs_up), ("d2h", pairs_down)):
+        nbytes = sum(src.numel() * src.element_size() for _, src in pairs)
+        best = None
+        for _ in range(reps):
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0.record(st)
+            for dst, src in pairs:
+                dst.copy_(src, non_blocking=True)
+            t1.record(st)
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1)
+            best = ms if best is None else min(best, ms)
+        out[name + "_ms_per_step"] = best
+        out[name + "_gbs"] = nbytes / (best * 1e-3) / 1e9
+    out["note"] = ("the same copies alone (one direction at a time, one stream, best of 5): the link's "
+                   "copy rate for these buffers, against which the pipelined e2e step is bounded")
+    return out
 
 
 # ------------------------------------------------------------------ workload
@@ -497,6 +525,7 @@ def run_native(args, rank, world, local_rank):
     e2e_ms = np.full(e_steps, e2e_pipelined(torch, e_steps, e_up, e_frame, e_down))
     h2d = h_rec[0].numel() * 4 + h_gb[0].numel() * 4
     d2h = h_out[0].numel() * 4
+    link = host_link(torch, [(d_rec[0], h_rec[0]), (d_gb[0], h_gb[0])], [(h_out[0], d_irr[0])])
 
     # ---- the filtered probe chain (Algorithm 5): gather, filter x, filter y, project, per pass
     # (left out of a compact run: the default configuration's line carries it)
@@ -605,7 +634,7 @@ def run_native(args, rank, world, local_rank):
                                         (pass_ms[1:4].sum() * 1e-3) / 1e9, "peak": peak, "unit": "GB/s"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": float(tot[3] / e_steps), "steps": e_steps, "note": E2E_NOTE},
+                "ms_per_step": float(tot[3] / e_steps), "steps": e_steps, "note": E2E_NOTE, "link": link},
         "gpu_launches": int(args.steps * launches_per_step + rebuilds),
         "dropped_hits": int(st["dropped"]),
         "table": {"slots": int(st["slots"]), "occupied": int(st["occupied"]), "live": int(st["live"]),
@@ -911,6 +940,7 @@ def run_temporal(args, rank, world, local_rank):
     e2e_ms = np.full(e_steps, e2e_pipelined(torch, e_steps, e_up, e_frame, e_down))
     h2d = h_rec[0].numel() * 4 + h_gb[0].numel() * 4 + h_mv[0].numel() * 4
     d2h = h_out[0].numel() * 4
+    link = host_link(torch, [(d_rec[0], h_rec[0]), (d_gb[0], h_gb[0]), (d_mv[0], h_mv[0])], [(h_out[0], d_irr[0])])
 
     tot = np.array(max_over_ranks([window_ms.sum(), frame_ms.sum(), t_wall, e2e_ms.sum()], world, "cuda"))
     if rank != 0:
@@ -991,7 +1021,7 @@ def run_temporal(args, rank, world, local_rank):
                      "peak_source": peak_src},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "ms_per_step": float(tot[3] / e_steps), "steps": e_steps, "note": E2E_NOTE},
+                "ms_per_step": float(tot[3] / e_steps), "steps": e_steps, "note": E2E_NOTE, "link": link},
         # k_reproject, k_spawn, k_mip_tail, the update (1 kernel, or 3 for tiles), the resolve,
         # k_gather_temporal, (2 x k_filter,) k_project, k_interpolate
         "gpu_launches": int(args.steps * (8 + (2 if tiles else 0) + (2 if filtered else 0)) + rebuilds),

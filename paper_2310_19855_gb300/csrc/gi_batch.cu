@@ -136,7 +136,7 @@ static gi_status enqueue_frame(gi_batch_s *b, int set, const std::vector<uint32_
     if (s == GI_OK)
         s = launch_integrate_batched(reinterpret_cast<const IntegrateArgs *>(d + L.integ),
                                      reinterpret_cast<const uint32_t *>(d + L.pre[kPassIntegrate]), n,
-                                     blocks[kPassIntegrate], b->tuning.integrate_threads, st);
+                                     blocks[kPassIntegrate], b->tuning.integrate_threads, b->rpp, st);
     if (s == GI_OK)
         s = launch_interpolate_batched(reinterpret_cast<const InterpArgs *>(d + L.interp),
                                        reinterpret_cast<const uint32_t *>(d + L.pre[kPassInterp]), n,

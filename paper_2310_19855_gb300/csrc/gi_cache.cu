@@ -112,12 +112,21 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
     for (unsigned long long base = (unsigned long long)blk * kUpdThreads; base < a.n; base += stride) {
         const unsigned long long i = base + threadIdx.x;
         const bool inr = i < a.n;
-        float len = inr ? __ldcs(a.len + i) : -1.0f;
-        float px = 0.f, py = 0.f, pz = 0.f;
+        // every plane of an in-range record in one round trip (a miss reads sectors its warp's hits
+        // read anyway)
+        float len = -1.0f, px = 0.f, py = 0.f, pz = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, r0 = 0.f, r1 = 0.f, r2 = 0.f;
         if (inr) {
+            len = __ldcs(a.len + i);
             px = __ldcs(a.p[0] + i);
             py = __ldcs(a.p[1] + i);
             pz = __ldcs(a.p[2] + i);
+            const float *const *sd = KEY_DIR == GI_KEY_DIR_NORMAL ? a.nrm : a.dir;
+            sx = __ldcs(sd[0] + i);
+            sy = __ldcs(sd[1] + i);
+            sz = __ldcs(sd[2] + i);
+            r0 = __ldcs(a.rad[0] + i);
+            r1 = __ldcs(a.rad[1] + i);
+            r2 = __ldcs(a.rad[2] + i);
         }
         bool hit = inr && isfinite(len) && len >= 0.0f && isfinite3(px, py, pz);
         const bool miss = inr && len == INFINITY;
@@ -125,20 +134,10 @@ __device__ __forceinline__ void update_body(const UpdateArgs &a, uint32_t blk, u
         unsigned long long q0 = 0, q1 = 0, q2 = 0;
         uint32_t home = 0, tag = 0;
         if (hit) {
-            float sx, sy, sz;
-            if (KEY_DIR == GI_KEY_DIR_NORMAL) {
-                sx = __ldcs(a.nrm[0] + i);
-                sy = __ldcs(a.nrm[1] + i);
-                sz = __ldcs(a.nrm[2] + i);
-            } else {
-                sx = __ldcs(a.dir[0] + i);
-                sy = __ldcs(a.dir[1] + i);
-                sz = __ldcs(a.dir[2] + i);
-            }
             uint32_t bad = 0;
-            q0 = quantize(__ldcs(a.rad[0] + i), bad);
-            q1 = quantize(__ldcs(a.rad[1] + i), bad);
-            q2 = quantize(__ldcs(a.rad[2] + i), bad);
+            q0 = quantize(r0, bad);
+            q1 = quantize(r1, bad);
+            q2 = quantize(r2, bad);
             my_clamped += bad;
             unsigned long long key =
                 cell_key(a.kp, px, py, pz, sx, sy, sz, len, KEY_DIR == GI_KEY_DIR_NORMAL ? 0u : 1u);

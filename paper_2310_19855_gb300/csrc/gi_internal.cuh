@@ -311,7 +311,7 @@ gi_status launch_resolve_batched(const ResolveArgs *args, const uint32_t *prefix
 gi_status launch_spawn_batched(const SpawnArgs *args, const uint32_t *prefix, uint32_t nviews, uint32_t blocks,
                                cudaStream_t st);
 gi_status launch_integrate_batched(const IntegrateArgs *args, const uint32_t *prefix, uint32_t nviews,
-                                   uint32_t blocks, uint32_t threads, cudaStream_t st);
+                                   uint32_t blocks, uint32_t threads, uint32_t rays_per_probe, cudaStream_t st);
 gi_status launch_interpolate_batched(const InterpArgs *args, const uint32_t *prefix, uint32_t nviews,
                                      uint32_t blocks, cudaStream_t st);
 

@@ -395,54 +395,9 @@ __device__ __forceinline__ void project_cells(const float4 n4, int lane, const f
     out[lane] = val;
 }
 
-// SH coefficients (9 per channel, band order of project_cells) of the radiance whose local-frame
-// direction moments are S (S[m][channel]: solid angle, first moment xyz, second moment xx yy zz xy
-// xz yz), rotated to world space by the probe frame of normal n (Duff et al. 2017); out[3 k + c].
-__device__ __forceinline__ void sh_from_moments(const float (&S)[10][3], float nx, float ny, float nz,
-                                                float (&o)[27]) {
-    const float sgn = copysignf(1.0f, nz);
-    const float ia = -1.0f / (sgn + nz);
-    const float bb = nx * ny * ia;
-    const float R[3][3] = {{1.0f + sgn * nx * nx * ia, bb, nx},
-                           {sgn * bb, sgn + ny * ny * ia, ny},
-                           {-sgn * nx, -ny, nz}};
-    const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f, C2 = 1.0925484305920792f,
-                C3 = 0.31539156525252005f, C4 = 0.5462742152960396f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float S0 = S[0][c];
-        const float S1[3] = {S[1][c], S[2][c], S[3][c]};
-        float S2[3][3];
-        S2[0][0] = S[4][c]; S2[1][1] = S[5][c]; S2[2][2] = S[6][c];
-        S2[0][1] = S2[1][0] = S[7][c];
-        S2[0][2] = S2[2][0] = S[8][c];
-        S2[1][2] = S2[2][1] = S[9][c];
-        float W1[3], T[3][3], W2[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) W1[i] = R[i][0] * S1[0] + R[i][1] * S1[1] + R[i][2] * S1[2];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) T[i][q] = R[i][0] * S2[0][q] + R[i][1] * S2[1][q] + R[i][2] * S2[2][q];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = i; j < 3; ++j) W2[i][j] = W2[j][i] = T[i][0] * R[j][0] + T[i][1] * R[j][1] + T[i][2] * R[j][2];
-        o[0 * 3 + c] = C0 * S0;
-        o[1 * 3 + c] = C1 * W1[1];
-        o[2 * 3 + c] = C1 * W1[2];
-        o[3 * 3 + c] = C1 * W1[0];
-        o[4 * 3 + c] = C2 * W2[0][1];
-        o[5 * 3 + c] = C2 * W2[1][2];
-        o[6 * 3 + c] = C3 * (3.0f * W2[2][2] - S0);
-        o[7 * 3 + c] = C2 * W2[0][2];
-        o[8 * 3 + c] = C4 * (W2[0][0] - W2[1][1]);
-    }
-}
-
 // Probe irradiance (Sections 2.1.4, 2.4.2) with four threads per probe: thread h of a probe's quad
-// takes the cells c = 4 i + h, i < 16, kIntPass at a time with their slot-id loads and radiance
-// gathers issued together; a cell's radiance is the mean of its rays that produced a sample, and the cell's exact
+// takes the cells c = 16 h + i, i < 16, their slot ids in four 16-byte loads, and gathers their
+// radiance kIntPass cells at a time; a cell's radiance is the mean of its rays that produced a sample, and the cell's exact
 // direction moments (shared memory, 12 floats per cell: three 16-byte reads) are added in with
 // multiply-adds.  Cells without sample take the mean of the populated cells (radiance backup)
 // through the summed moments of the empty cells, the same sum by linearity.  Two xor-shuffle steps
@@ -453,9 +408,12 @@ constexpr int kIntThreads = 128;  // 32 probes per block
 constexpr int kMomStride = 12;    // floats per cell in the shared moment table
 constexpr int kIntPass = 8;       // cells per thread whose loads are in flight together
 
+// Entry 4 i + h of the table holds cell 16 h + i, the i-th cell of thread h: the four threads of a
+// quad read four entries 48 bytes apart (distinct banks).
 __device__ __forceinline__ void load_moment_table(float *s_mom) {
     for (int k = threadIdx.x; k < 64 * kMomStride; k += blockDim.x) {
-        const int c = k / kMomStride, m = k - c * kMomStride;
+        const int e = k / kMomStride, m = k - e * kMomStride;
+        const int c = 16 * (e & 3) + (e >> 2);
         s_mom[k] = m < 10 ? g_moments[m][c] : 0.0f;
     }
 }
@@ -476,7 +434,13 @@ __device__ __forceinline__ void integrate_quad(const IntegrateArgs &a, uint32_t 
     if (live) {
         const uint32_t rpc = RPC1 ? 1u : (a.rpp >> 6);
         const size_t rec_base = (size_t)p * a.rpp;
-        const uint32_t *ids = a.slot_ids + rec_base + h;
+        // thread h's 16 cells are consecutive: their slot ids come in four 16-byte loads
+        const uint4 *ids = reinterpret_cast<const uint4 *>(a.slot_ids + rec_base + 16u * h);
+        uint4 idq[4];
+        if (RPC1) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) idq[q] = __ldcs(ids + q);
+        }
 #pragma unroll
         for (int i0 = 0; i0 < 16; i0 += kIntPass) {
             float acc[kIntPass][3], cnt[kIntPass];
@@ -487,20 +451,32 @@ __device__ __forceinline__ void integrate_quad(const IntegrateArgs &a, uint32_t 
             }
             for (uint32_t j = 0; j < rpc; ++j) {
                 uint32_t sl[kIntPass];
+                if (RPC1) {
 #pragma unroll
-                for (int i = 0; i < kIntPass; ++i) sl[i] = __ldcs(ids + j * 64u + 4u * (i0 + i));
+                    for (int q = 0; q < kIntPass / 4; ++q) {
+                        sl[4 * q + 0] = idq[i0 / 4 + q].x;
+                        sl[4 * q + 1] = idq[i0 / 4 + q].y;
+                        sl[4 * q + 2] = idq[i0 / 4 + q].z;
+                        sl[4 * q + 3] = idq[i0 / 4 + q].w;
+                    }
+                } else {
+                    const uint32_t *row = a.slot_ids + rec_base + j * 64u + 16u * h + i0;
+#pragma unroll
+                    for (int i = 0; i < kIntPass; ++i) sl[i] = __ldcs(row + i);
+                }
                 float3 r[kIntPass];
                 bool hs[kIntPass];
 #pragma unroll
                 for (int i = 0; i < kIntPass; ++i) hs[i] = ray_sample(a, sl[i], r[i]);
                 if (SURR) {
-                    // the pass's records rec0 + 4 i + h (rec0 a multiple of 32) share one answer word
-                    const size_t rec0 = rec_base + j * 64u + 4u * i0;
-                    const uint32_t wbits = __ldg(a.ovr_bits + (rec0 >> 5)) >> h;
+                    // records rec0 + i, rec0 = (p rpp + 64 j + 16 h + i0): bits 16 (h & 1) + i0 + i of
+                    // the answer word of the 32 records starting at the probe's 64 j + 32 (h >> 1)
+                    const size_t rec0 = rec_base + j * 64u + 16u * h + i0;
+                    const uint32_t wbits = __ldg(a.ovr_bits + (rec0 >> 5)) >> ((rec0 & 31u));
 #pragma unroll
                     for (int i = 0; i < kIntPass; ++i)
-                        if ((wbits >> (4 * i)) & 1u) {
-                            const float4 o = __ldg(a.ovr + rec0 + 4u * i + h);
+                        if ((wbits >> i) & 1u) {
+                            const float4 o = __ldg(a.ovr + rec0 + i);
                             r[i] = make_float3(o.x, o.y, o.z);
                             hs[i] = true;
                         }
@@ -610,20 +586,21 @@ __device__ __forceinline__ void integrate_quad(const IntegrateArgs &a, uint32_t 
     out[8 * 3 + h] = C4 * (W2[0][0] - W2[1][1]);
 }
 
-// blk: block of kIntThreads / 4 probes (the batched pass passes the view-local block)
-template <bool SURR>
+// blk: block of kIntThreads / 4 probes (the batched pass passes the view-local block).  RPC1: 64
+// rays per probe (one per cell), a kernel of its own so that the general form's registers do not
+// weigh on it.
+template <bool SURR, bool RPC1>
 __device__ __forceinline__ void integrate_body(const IntegrateArgs &a, uint32_t blk, const float *s_mom) {
     const uint32_t p = blk * (blockDim.x >> 2) + (threadIdx.x >> 2);
-    const bool valid = p < a.probes;
-    if (a.rpp == 64) integrate_quad<SURR, true>(a, p, valid, s_mom);
-    else integrate_quad<SURR, false>(a, p, valid, s_mom);
+    integrate_quad<SURR, RPC1>(a, p, p < a.probes, s_mom);
 }
 
+template <bool RPC1>
 __global__ void __launch_bounds__(kIntThreads, 4) k_integrate(IntegrateArgs a) {
     __shared__ __align__(16) float s_mom[64 * kMomStride];
     load_moment_table(s_mom);
     __syncthreads();
-    integrate_body<false>(a, blockIdx.x, s_mom);
+    integrate_body<false, RPC1>(a, blockIdx.x, s_mom);
 }
 
 // Probe atlas: float4 per (probe, cell) = (mean radiance rgb, mean hit distance); zeros for no probe.
@@ -658,11 +635,12 @@ __global__ void __launch_bounds__(256) k_project(const float4 *atlas, const floa
     const float L[2][3] = {{c0.x, c0.y, c0.z}, {c1.x, c1.y, c1.z}};
     project_cells(n4, lane, L, out);
 }
+template <bool RPC1>
 __global__ void __launch_bounds__(kIntThreads, 4) k_integrate_surr(IntegrateArgs a) {
     __shared__ __align__(16) float s_mom[64 * kMomStride];
     load_moment_table(s_mom);
     __syncthreads();
-    integrate_body<true>(a, blockIdx.x, s_mom);
+    integrate_body<true, RPC1>(a, blockIdx.x, s_mom);
 }
 
 // ---------------------------------------------------------------- temporal path
@@ -1296,12 +1274,13 @@ __global__ void __launch_bounds__(1024) k_mip_tail_batched(const SpawnArgs *args
     if (sa.mi.count > 5) mip_tail_body(sa.mask, sa.mi);
 }
 
+template <bool RPC1>
 __global__ void __launch_bounds__(128, 4) k_integrate_batched(const IntegrateArgs *args, const uint32_t *prefix,
                                                            uint32_t nviews) {
     __shared__ IntegrateArgs sa;
     __shared__ __align__(16) float s_mom[64 * kMomStride];
     load_moment_table(s_mom);
-    GI_BATCHED_ITEMS(prefix, nviews, sa, args, integrate_body<false>(sa, item, s_mom));
+    GI_BATCHED_ITEMS(prefix, nviews, sa, args, (integrate_body<false, RPC1>(sa, item, s_mom)));
 }
 
 __global__ void __launch_bounds__(256, 4) k_interpolate_batched(const InterpArgs *args, const uint32_t *prefix,
@@ -1324,10 +1303,14 @@ gi_status launch_spawn_batched(const SpawnArgs *args, const uint32_t *prefix, ui
 }
 
 gi_status launch_integrate_batched(const IntegrateArgs *args, const uint32_t *prefix, uint32_t nviews,
-                                   uint32_t blocks, uint32_t threads, cudaStream_t st) {
+                                   uint32_t blocks, uint32_t threads, uint32_t rays_per_probe, cudaStream_t st) {
     if (blocks == 0) return GI_OK;
-    k_integrate_batched<<<resident_grid(k_integrate_batched, (int)threads, blocks), threads, 0, st>>>(args, prefix,
-                                                                                                      nviews);
+    if (rays_per_probe == 64)
+        k_integrate_batched<true><<<resident_grid(k_integrate_batched<true>, (int)threads, blocks), threads, 0, st>>>(
+            args, prefix, nviews);
+    else
+        k_integrate_batched<false><<<resident_grid(k_integrate_batched<false>, (int)threads, blocks), threads, 0, st>>>(
+            args, prefix, nviews);
     return cuda_status(cudaGetLastError(), "k_integrate_batched launch");
 }
 
@@ -1495,7 +1478,8 @@ gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *pr, const uint3
     const IntegrateArgs a = integrate_args(cache, pr, slot_ids, rays_per_probe, env);
     if (a.probes == 0) return GI_OK;
     const unsigned blocks = (a.probes + kIntThreads / 4 - 1) / (kIntThreads / 4);
-    k_integrate<<<blocks, kIntThreads, 0, (cudaStream_t)stream>>>(a);
+    if (rays_per_probe == 64) k_integrate<true><<<blocks, kIntThreads, 0, (cudaStream_t)stream>>>(a);
+    else k_integrate<false><<<blocks, kIntThreads, 0, (cudaStream_t)stream>>>(a);
     return cuda_status(cudaGetLastError(), "k_integrate launch");
 }
 
@@ -1515,7 +1499,8 @@ gi_status gi_probes_integrate_nrc(gi_cache_t cache, gi_nrc_t nrc, const gi_probe
     s = nrc_override(nrc, n, &a.ovr_bits, &a.ovr);
     if (s != GI_OK) return s;
     const unsigned blocks = (a.probes + kIntThreads / 4 - 1) / (kIntThreads / 4);
-    k_integrate_surr<<<blocks, kIntThreads, 0, (cudaStream_t)stream>>>(a);
+    if (rays_per_probe == 64) k_integrate_surr<true><<<blocks, kIntThreads, 0, (cudaStream_t)stream>>>(a);
+    else k_integrate_surr<false><<<blocks, kIntThreads, 0, (cudaStream_t)stream>>>(a);
     return cuda_status(cudaGetLastError(), "k_integrate_surr launch");
 }
 

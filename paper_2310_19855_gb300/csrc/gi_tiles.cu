@@ -89,32 +89,23 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_key(TileUpdateArgs ta) 
     for (unsigned long long base = (unsigned long long)blockIdx.x * kUpdThreads; base < a.n; base += stride) {
         const unsigned long long i = base + threadIdx.x;
         const bool inr = i < a.n;
-        const float len = inr ? __ldcs(a.len + i) : -1.0f;
-        float px = 0.f, py = 0.f, pz = 0.f;
+        // the key's planes of an in-range record in one round trip; the radiance is read by
+        // k_tile_accumulate, which also counts its clamps (here only those of dropped hits)
+        float len = -1.0f, px = 0.f, py = 0.f, pz = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
         if (inr) {
+            len = __ldcs(a.len + i);
             px = __ldcs(a.p[0] + i);
             py = __ldcs(a.p[1] + i);
             pz = __ldcs(a.p[2] + i);
+            const float *const *sd = KEY_DIR == GI_KEY_DIR_NORMAL ? a.nrm : a.dir;
+            sx = __ldcs(sd[0] + i);
+            sy = __ldcs(sd[1] + i);
+            sz = __ldcs(sd[2] + i);
         }
         const bool hit = inr && isfinite(len) && len >= 0.0f && isfinite3(px, py, pz);
         const bool miss = inr && len == INFINITY;
         uint32_t home = 0, tag = 0, cell = 0;
         if (hit) {
-            float sx, sy, sz;
-            if (KEY_DIR == GI_KEY_DIR_NORMAL) {
-                sx = __ldcs(a.nrm[0] + i);
-                sy = __ldcs(a.nrm[1] + i);
-                sz = __ldcs(a.nrm[2] + i);
-            } else {
-                sx = __ldcs(a.dir[0] + i);
-                sy = __ldcs(a.dir[1] + i);
-                sz = __ldcs(a.dir[2] + i);
-            }
-            uint32_t bad = 0;
-            quantize(__ldg(a.rad[0] + i), bad);
-            quantize(__ldg(a.rad[1] + i), bad);
-            quantize(__ldg(a.rad[2] + i), bad);
-            my_clamped += bad;
             const unsigned long long key =
                 tile_key(a.kp, px, py, pz, sx, sy, sz, len, KEY_DIR == GI_KEY_DIR_NORMAL ? 0u : 1u, cell);
             cell_of_key(key, a.mask, home, tag);
@@ -151,6 +142,13 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_key(TileUpdateArgs ta) 
         const uint32_t my_slot = __shfl_sync(kFull, slot, lead);
         uint32_t id = miss ? GI_SLOT_MISS : GI_SLOT_NONE;
         if (hit && my_slot != GI_SLOT_NONE) id = my_slot * kTileCells + cell;
+        if (hit && my_slot == GI_SLOT_NONE) {
+            uint32_t bad = 0;
+            quantize(__ldcs(a.rad[0] + i), bad);
+            quantize(__ldcs(a.rad[1] + i), bad);
+            quantize(__ldcs(a.rad[2] + i), bad);
+            my_clamped += bad;
+        }
         if (inr) __stcs(a.slot_ids + i, id);
     }
     my_clamped = __reduce_add_sync(kFull, my_clamped);
@@ -206,9 +204,13 @@ __global__ void __launch_bounds__(kCompactThreads) k_tile_compact(const unsigned
 __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_accumulate(const uint32_t *slot_ids, const float *r0,
                                                                     const float *r1, const float *r2,
                                                                     unsigned long long n, const uint32_t *cidx,
-                                                                    uint32_t cells, Accum *accum) {
+                                                                    uint32_t cells, Accum *accum, Counters *ctr) {
     __shared__ __align__(32) unsigned long long s_red[kUpdThreads][4];
+    __shared__ uint32_t s_clamped;
+    if (threadIdx.x == 0) s_clamped = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
+    uint32_t my_clamped = 0;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n; base += stride) {
         const unsigned long long i = base + threadIdx.x;
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_accumulate(const uint32
             q0 = quantize(__ldcs(r0 + i), bad);
             q1 = quantize(__ldcs(r1 + i), bad);
             q2 = quantize(__ldcs(r2 + i), bad);
+            my_clamped += bad;
             blk = __ldcg(cidx + id / kTileCells);
         }
         // a tile with a slot id always has a block (the compaction ran after the keys); a missing
@@ -260,6 +263,11 @@ __global__ void __launch_bounds__(kUpdThreads, 8) k_tile_accumulate(const uint32
         }
     }
     bulk_wait_all();
+    // hits with a tile whose radiance was clamped (k_tile_key counts those of dropped hits)
+    my_clamped = __reduce_add_sync(kFull, my_clamped);
+    if (lane == 0 && my_clamped) atomicAdd(&s_clamped, my_clamped);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_clamped) atomicAdd(&ctr->clamped, (unsigned long long)s_clamped);
 }
 
 // ---------------------------------------------------------------- resolve
@@ -618,7 +626,7 @@ gi_status tile_update_launch(const TileUpdateArgs &a, int key_dir, int resident_
     s = cuda_status(cudaGetLastError(), "k_tile_compact launch");
     if (s != GI_OK) return s;
     k_tile_accumulate<<<blocks, kUpdThreads, 0, st>>>(a.u.slot_ids, a.u.rad[0], a.u.rad[1], a.u.rad[2], a.u.n, a.cidx,
-                                                      tiles * (uint32_t)kTileCells, a.u.accum);
+                                                      tiles * (uint32_t)kTileCells, a.u.accum, a.u.ctr);
     return cuda_status(cudaGetLastError(), "k_tile_accumulate launch");
 }
 

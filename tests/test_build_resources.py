@@ -17,7 +17,8 @@ HOT = {
     "9k_resolveE": ("gi_cache.cu", 64),
     "16k_resolve_bitmapE": ("gi_cache.cu", 64),
     "14k_diag_atomicsILb1E": ("gi_diag.cu", 32),
-    "11k_integrateE": ("gi_probes.cu", 128),
+    "11k_integrateILb1EE": ("gi_probes.cu", 128),  # 64 rays per probe
+    "11k_integrateILb0EE": ("gi_probes.cu", 128),
     "13k_interpolateE": ("gi_probes.cu", 64),
     "10k_tile_keyILi0E": ("gi_tiles.cu", 32),
     "17k_tile_accumulate": ("gi_tiles.cu", 32),
