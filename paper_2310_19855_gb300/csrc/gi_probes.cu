@@ -247,22 +247,6 @@ __device__ __forceinline__ bool ray_sample(const IntegrateArgs &a, uint32_t s, f
     return s == GI_SLOT_MISS;
 }
 
-// Reduce-scatter across the warp: on return lane l holds the warp-wide sum of v[l]
-// (31 shuffles: each halving step sends the half of the values this lane gives up).
-__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) {
-        const bool upper = (lane & d) != 0;
-#pragma unroll
-        for (int j = 0; j < d; ++j) {
-            const float send = upper ? v[j] : v[j + d];
-            const float keep = upper ? v[j + d] : v[j];
-            v[j] = keep + __shfl_xor_sync(kFullMask, send, d);
-        }
-    }
-    return v[0];
-}
-
 // Cell radiance of probe p's rays (one warp; lane l owns cells l and l + 32, ray k samples cell
 // k mod 64): L = per-cell mean of the rays that produced a sample, with the radiance backup (mean
 // over populated cells) where none did; with HITDIST also hd = the mean ray length of the cell's
@@ -327,29 +311,10 @@ __device__ __forceinline__ void gather_cells(const IntegrateArgs &a, uint32_t p,
     for (int h = 0; h < 2; ++h) hd[h] = hn[h] > 0.f ? hs[h] / hn[h] : INFINITY;
 }
 
-// SH coefficients of the cell radiance L (lane l: cells l and l + 32) through the cells' exact
-// direction moments, rotated to world space by the probe frame of normal n4; lanes 0..27 write.
-__device__ __forceinline__ void project_cells(const float4 n4, int lane, const float (&L)[2][3], float *out) {
-    // direction moments of the probe radiance (local frame): value 3 m + c = moment m, channel c
-    float v[32];
-#pragma unroll
-    for (int m = 0; m < 10; ++m) {
-        const float w0 = g_moments[m][lane], w1 = g_moments[m][lane + 32];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) v[3 * m + c] = w0 * L[0][c] + w1 * L[1][c];
-    }
-    v[30] = 0.f;
-    v[31] = 0.f;
-    const float mine = warp_reduce_scatter32(v, lane);
-    // lane k < 27 writes coefficient k / 3 of channel k % 3: gather that channel's 10 moments
-    const int coef = lane / 3, c = lane - 3 * (lane / 3);
-    float Sc[10];
-#pragma unroll
-    for (int m = 0; m < 10; ++m) Sc[m] = __shfl_sync(kFullMask, mine, min(3 * m + c, 31));
-    if (lane >= 27) {
-        if (lane == 27) out[27] = 0.0f;
-        return;
-    }
+// SH coefficients of channel h (coefficient k at out[3 k + h]) from the channel's ten direction
+// moments Sc (local frame: solid angle, first moment xyz, second moment xx yy zz xy xz yz), rotated
+// to world space by the probe frame of normal n4.
+__device__ __forceinline__ void project_channel(const float4 n4, const float (&Sc)[10], int h, float *out) {
     // probe frame (Duff et al. 2017): columns t, b, n of R
     const float nx = n4.x, ny = n4.y, nz = n4.z;
     const float sgn = copysignf(1.0f, nz);
@@ -359,40 +324,35 @@ __device__ __forceinline__ void project_cells(const float4 n4, int lane, const f
                            {sgn * bb, sgn + ny * ny * ia, ny},
                            {-sgn * nx, -ny, nz}};
     const float S0 = Sc[0];
-    float S1[3], S2[3][3];
-    for (int i = 0; i < 3; ++i) S1[i] = Sc[1 + i];
+    const float S1[3] = {Sc[1], Sc[2], Sc[3]};
+    float S2[3][3];
     S2[0][0] = Sc[4]; S2[1][1] = Sc[5]; S2[2][2] = Sc[6];
     S2[0][1] = S2[1][0] = Sc[7];
     S2[0][2] = S2[2][0] = Sc[8];
     S2[1][2] = S2[2][1] = Sc[9];
-    float W1[3], W2[3][3];
+    float W1[3], T[3][3], W2[3][3];
+#pragma unroll
     for (int i = 0; i < 3; ++i) W1[i] = R[i][0] * S1[0] + R[i][1] * S1[1] + R[i][2] * S1[2];
-    // W2 = R S2 R^T through T = R S2
-    float T[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int q2 = 0; q2 < 3; ++q2) T[i][q2] = R[i][0] * S2[0][q2] + R[i][1] * S2[1][q2] + R[i][2] * S2[2][q2];
+        for (int q = 0; q < 3; ++q) T[i][q] = R[i][0] * S2[0][q] + R[i][1] * S2[1][q] + R[i][2] * S2[2][q];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) W2[i][j] = W2[j][i] = T[i][0] * R[j][0] + T[i][1] * R[j][1] + T[i][2] * R[j][2];
-    // real SH basis, bands 0..2: c0; c1 y, c1 z, c1 x; c2 xy, c2 yz, c3 (3z^2-1), c2 xz, c4 (x^2-y^2)
+    // real SH basis, bands 0..2 (the order of project_cells), channel h, coefficient k at 3 k + h
     const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f, C2 = 1.0925484305920792f,
                 C3 = 0.31539156525252005f, C4 = 0.5462742152960396f;
-    float val;
-    switch (coef) {
-    case 0: val = C0 * S0; break;
-    case 1: val = C1 * W1[1]; break;
-    case 2: val = C1 * W1[2]; break;
-    case 3: val = C1 * W1[0]; break;
-    case 4: val = C2 * W2[0][1]; break;
-    case 5: val = C2 * W2[1][2]; break;
-    case 6: val = C3 * (3.0f * W2[2][2] - S0); break;
-    case 7: val = C2 * W2[0][2]; break;
-    default: val = C4 * (W2[0][0] - W2[1][1]); break;
-    }
-    out[lane] = val;
+    out[0 * 3 + h] = C0 * S0;
+    out[1 * 3 + h] = C1 * W1[1];
+    out[2 * 3 + h] = C1 * W1[2];
+    out[3 * 3 + h] = C1 * W1[0];
+    out[4 * 3 + h] = C2 * W2[0][1];
+    out[5 * 3 + h] = C2 * W2[1][2];
+    out[6 * 3 + h] = C3 * (3.0f * W2[2][2] - S0);
+    out[7 * 3 + h] = C2 * W2[0][2];
+    out[8 * 3 + h] = C4 * (W2[0][0] - W2[1][1]);
 }
 
 // Probe irradiance (Sections 2.1.4, 2.4.2) with four threads per probe: thread h of a probe's quad
@@ -546,44 +506,7 @@ __device__ __forceinline__ void integrate_quad(const IntegrateArgs &a, uint32_t 
     float Sc[10];
 #pragma unroll
     for (int m = 0; m < 10; ++m) Sc[m] = fmaf(bk, U[m], h == 0 ? S[m][0] : (h == 1 ? S[m][1] : S[m][2]));
-    // probe frame (Duff et al. 2017): columns t, b, n of R
-    const float nx = n4.x, ny = n4.y, nz = n4.z;
-    const float sgn = copysignf(1.0f, nz);
-    const float ia = -1.0f / (sgn + nz);
-    const float bb = nx * ny * ia;
-    const float R[3][3] = {{1.0f + sgn * nx * nx * ia, bb, nx},
-                           {sgn * bb, sgn + ny * ny * ia, ny},
-                           {-sgn * nx, -ny, nz}};
-    const float S0 = Sc[0];
-    const float S1[3] = {Sc[1], Sc[2], Sc[3]};
-    float S2[3][3];
-    S2[0][0] = Sc[4]; S2[1][1] = Sc[5]; S2[2][2] = Sc[6];
-    S2[0][1] = S2[1][0] = Sc[7];
-    S2[0][2] = S2[2][0] = Sc[8];
-    S2[1][2] = S2[2][1] = Sc[9];
-    float W1[3], T[3][3], W2[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) W1[i] = R[i][0] * S1[0] + R[i][1] * S1[1] + R[i][2] * S1[2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) T[i][q] = R[i][0] * S2[0][q] + R[i][1] * S2[1][q] + R[i][2] * S2[2][q];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = i; j < 3; ++j) W2[i][j] = W2[j][i] = T[i][0] * R[j][0] + T[i][1] * R[j][1] + T[i][2] * R[j][2];
-    // real SH basis, bands 0..2 (the order of project_cells), channel h, coefficient k at 3 k + h
-    const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f, C2 = 1.0925484305920792f,
-                C3 = 0.31539156525252005f, C4 = 0.5462742152960396f;
-    out[0 * 3 + h] = C0 * S0;
-    out[1 * 3 + h] = C1 * W1[1];
-    out[2 * 3 + h] = C1 * W1[2];
-    out[3 * 3 + h] = C1 * W1[0];
-    out[4 * 3 + h] = C2 * W2[0][1];
-    out[5 * 3 + h] = C2 * W2[1][2];
-    out[6 * 3 + h] = C3 * (3.0f * W2[2][2] - S0);
-    out[7 * 3 + h] = C2 * W2[0][2];
-    out[8 * 3 + h] = C4 * (W2[0][0] - W2[1][1]);
+    project_channel(n4, Sc, h, out);
 }
 
 // blk: block of kIntThreads / 4 probes (the batched pass passes the view-local block).  RPC1: 64
@@ -620,20 +543,70 @@ __global__ void __launch_bounds__(256) k_gather(IntegrateArgs a, float4 *atlas) 
     dst[lane + 32] = make_float4(L[1][0], L[1][1], L[1][2], hd[1]);
 }
 
-// SH coefficients of every probe from its atlas (one warp per probe).
-__global__ void __launch_bounds__(256) k_project(const float4 *atlas, const float4 *nrm, float *sh, uint32_t probes) {
-    const uint32_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (p >= probes) return;
-    const float4 n4 = __ldg(nrm + p);
+// SH coefficients of every probe from its atlas, four threads per probe as in the probe pass:
+// thread h reads the consecutive cells 16 h + i (eight 16-byte loads in flight at a time) and adds
+// each cell's radiance times its direction moments (shared table); two xor-shuffle steps add the
+// quad's moments, then thread h < 3 projects channel h.  (1080p: one warp per probe with a
+// 31-shuffle reduce-scatter took 19.5 us.)
+constexpr int kProjThreads = 128;  // 32 probes per block
+__global__ void __launch_bounds__(kProjThreads) k_project(const float4 *atlas, const float4 *nrm, float *sh,
+                                                          uint32_t probes) {
+    __shared__ __align__(16) float s_mom[64 * kMomStride];
+    load_moment_table(s_mom);
+    __syncthreads();
+    const uint32_t p = blockIdx.x * (kProjThreads / 4) + (threadIdx.x >> 2);
+    const int h = threadIdx.x & 3;
+    const bool valid = p < probes;
+    float4 n4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) n4 = __ldg(nrm + p);
+    const bool live = valid && n4.w != 0.0f;
+    float S[10][3];
+#pragma unroll
+    for (int m = 0; m < 10; ++m) S[m][0] = S[m][1] = S[m][2] = 0.0f;
+    if (live) {
+        const float4 *src = atlas + (size_t)p * 64 + 16 * h;
+#pragma unroll
+        for (int i0 = 0; i0 < 16; i0 += 8) {
+            float4 L[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) L[i] = __ldg(src + i0 + i);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 *mc = reinterpret_cast<const float4 *>(s_mom + (4 * (i0 + i) + h) * kMomStride);
+                const float4 w0 = mc[0], w1 = mc[1], w2 = mc[2];
+                const float w[10] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w, w2.x, w2.y};
+#pragma unroll
+                for (int m = 0; m < 10; ++m) {
+                    S[m][0] = fmaf(L[i].x, w[m], S[m][0]);
+                    S[m][1] = fmaf(L[i].y, w[m], S[m][1]);
+                    S[m][2] = fmaf(L[i].z, w[m], S[m][2]);
+                }
+            }
+        }
+    }
+    // the quad's partial sums (every lane takes part: the shuffles span the warp)
+#pragma unroll
+    for (int d = 1; d <= 2; d <<= 1)
+#pragma unroll
+        for (int m = 0; m < 10; ++m) {
+            S[m][0] += __shfl_xor_sync(kFullMask, S[m][0], d);
+            S[m][1] += __shfl_xor_sync(kFullMask, S[m][1], d);
+            S[m][2] += __shfl_xor_sync(kFullMask, S[m][2], d);
+        }
+    if (!valid) return;
     float *out = sh + (size_t)p * GI_SH_STRIDE;
-    if (n4.w == 0.0f) {
-        if (lane < GI_SH_STRIDE) out[lane] = 0.0f;
+    if (!live) {
+        for (int k = h; k < GI_SH_STRIDE; k += 4) out[k] = 0.0f;
         return;
     }
-    const float4 c0 = __ldg(atlas + (size_t)p * 64 + lane), c1 = __ldg(atlas + (size_t)p * 64 + lane + 32);
-    const float L[2][3] = {{c0.x, c0.y, c0.z}, {c1.x, c1.y, c1.z}};
-    project_cells(n4, lane, L, out);
+    if (h == 3) {
+        out[27] = 0.0f;
+        return;
+    }
+    float Sc[10];
+#pragma unroll
+    for (int m = 0; m < 10; ++m) Sc[m] = h == 0 ? S[m][0] : (h == 1 ? S[m][1] : S[m][2]);
+    project_channel(n4, Sc, h, out);
 }
 template <bool RPC1>
 __global__ void __launch_bounds__(kIntThreads, 4) k_integrate_surr(IntegrateArgs a) {
@@ -1561,7 +1534,7 @@ gi_status gi_probes_project(const gi_probes *pr, const float *atlas, gi_stream_t
     if (s != GI_OK) return s;
     const uint32_t P = pr->layout.num_probes;
     if (P == 0) return GI_OK;
-    k_project<<<(P + 7) / 8, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float4 *>(atlas),
+    k_project<<<(P + kProjThreads / 4 - 1) / (kProjThreads / 4), kProjThreads, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float4 *>(atlas),
                                                               reinterpret_cast<const float4 *>(pr->nrm), pr->sh, P);
     return cuda_status(cudaGetLastError(), "k_project launch");
 }
