@@ -401,8 +401,8 @@ gi_status gi_probes_reproject(const gi_gbuffer *gbuf, const gi_view *view, const
  * temporal hysteresis of Algorithm 4 (l = mean of rgb; alpha = max(l1 - l2 - min(l1, l2), 0) /
  * max(l1, l2, 1e-4), clamped to [0, 0.95] and squared; lerp(current, previous, alpha)), keeping
  * the fresh hit distance.  A tile with a reprojected probe and no fresh one copies the source's
- * 64 cells; a tile with neither gets zeros.  slot_ids / ray_len: the spawn tiles' records.
- * prev_atlas and atlas are distinct, 16-byte aligned.  gi_probes_project then gives the SH.
+ * 64 cells; a tile with neither gets zeros.  slot_ids / ray_len: the spawn tiles' records
+ * (slot_ids 16-byte aligned).  prev_atlas and atlas are distinct, 16-byte aligned.  gi_probes_project then gives the SH.
  */
 gi_status gi_probes_gather_temporal(gi_cache_t cache, const gi_gbuffer *gbuf, const gi_view *view, uint32_t upscale,
                                     const gi_probes *probes, const uint32_t *slot_ids, const float *ray_len,
@@ -419,7 +419,8 @@ gi_status gi_probes_gather_temporal(gi_cache_t cache, const gi_gbuffer *gbuf, co
  * for GI_SLOT_MISS; no sample for GI_SLOT_NONE); per-cell means, with the
  * mean of populated cells copied into cells without sample; projection to 3
  * SH bands through exact per-cell direction moments.  Writes probes->sh.
- * rays_per_probe must be a positive multiple of 64.  Call after gi_cache_resolve.
+ * rays_per_probe must be a positive multiple of 64; slot_ids 16-byte aligned (it is read 16 bytes
+ * at a time; GI_ERR_INVALID_ARG otherwise).  Call after gi_cache_resolve.
  */
 gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *probes, const uint32_t *slot_ids,
                               uint32_t rays_per_probe, const float env[3], gi_stream_t stream);
@@ -431,8 +432,8 @@ gi_status gi_probes_integrate(gi_cache_t cache, const gi_probes *probes, const u
  *
  * gi_probes_gather: per cell the mean radiance of its rays as in gi_probes_integrate (radiance
  * backup included) and the mean ray length of its rays that hit a surface (+inf when none did);
- * ray_len = the records' ray lengths (device, num_probes * rays_per_probe floats).  Zeros for a
- * tile without probe.
+ * ray_len = the records' ray lengths (device, num_probes * rays_per_probe floats).  slot_ids
+ * 16-byte aligned.  Zeros for a tile without probe.
  *
  * gi_probes_filter: one pass of the separable 7x7 sparse blur along axis 0 (x) or 1 (y) of the
  * probe grid: each cell is averaged with the same cell of the probes that Algorithm 3 finds at
@@ -498,7 +499,7 @@ typedef struct gi_batch_view {
     gi_hits hits;
     gi_gbuffer gbuf;
     gi_probes probes;
-    uint32_t *slot_ids;
+    uint32_t *slot_ids;      /* 16-byte aligned */
     float *irradiance; /* float4 per pixel */
     float env[3];
 } gi_batch_view;

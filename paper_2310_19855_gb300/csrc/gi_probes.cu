@@ -1058,8 +1058,9 @@ gi_status integrate_check(gi_cache_t cache, const gi_probes *pr, const uint32_t 
         set_error("gi_probes_integrate: NULL argument");
         return GI_ERR_INVALID_ARG;
     }
-    if (rays_per_probe == 0 || rays_per_probe % 64 != 0 || ((uintptr_t)pr->nrm & 15)) {
-        set_error("gi_probes_integrate: rays_per_probe must be a positive multiple of 64; nrm 16-byte aligned");
+    if (rays_per_probe == 0 || rays_per_probe % 64 != 0 || ((uintptr_t)pr->nrm & 15) || ((uintptr_t)slot_ids & 15)) {
+        set_error("gi_probes_integrate: rays_per_probe must be a positive multiple of 64; nrm and slot_ids 16-byte "
+                  "aligned");
         return GI_ERR_INVALID_ARG;
     }
     return GI_OK;

@@ -93,6 +93,22 @@ def test_uniform_radiance_gives_pi_L_on_gpu():
         pl.close()
 
 
+def test_integrate_rejects_misaligned_slot_ids():
+    # the probe pass reads a probe's slot ids 16 bytes at a time: a buffer that does not start on a
+    # 16-byte boundary is refused on the host, before any launch
+    pl = Pipeline(64, 64, 64, 12)
+    try:
+        ids = torch.zeros(pl.n_records + 4, dtype=torch.int32, device="cuda")
+        pl.probes.nrm.zero_()  # no probe: the accepted call below only writes zeros
+        with pytest.raises(gi.GiError) as e:
+            gi.gi_probes_integrate(pl.cache, pl.probes.struct, ids.data_ptr() + 4, 64)
+        assert e.value.status == gi.GI_ERR_INVALID_ARG
+        gi.gi_probes_integrate(pl.cache, pl.probes.struct, ids.data_ptr(), 64)  # aligned: accepted
+        torch.cuda.synchronize()
+    finally:
+        pl.close()
+
+
 def test_spawn_jitter_sequence_and_sky_tiles():
     fr = wl.make_frame(1, 0)
     gb = fr.gbuffer.copy()
