@@ -1120,9 +1120,11 @@ def run_batched(args, rank, world, local_rank):
     for _ in range(args.warmup):
         sequential_frame()
     ms_seq = timed(sequential_frame, max(3, min(args.steps, 50)))
-    tot = np.array(max_over_ranks([ms_graph.sum(), ms_nograph.mean(), ms_seq.mean()], world, "cuda"))
     for sp in singles:
         sp.close()
+    surr = batched_surrogate(args, gi, torch, BatchPipeline, specs, frames, recs, gbufs, gviews, bp, counter, F, V,
+                             timed, stream)
+    tot = np.array(max_over_ranks([ms_graph.sum(), ms_nograph.mean(), ms_seq.mean()], world, "cuda"))
     bp.close()
     if rank != 0:
         return
@@ -1157,11 +1159,111 @@ def run_batched(args, rank, world, local_rank):
                      "frac": alg / (frame_ms * 1e-3) / 1e9 / peak, "traffic": None,
                      "kernel": "whole batched frame (six launches)", "algorithmic_bytes_per_launch": alg,
                      "peak_source": peak_src},
+        "surrogate_batched": surr,
         "cpu_baseline": None,
         "gpu_launches": int(args.steps * 7),
         "clocks": clk,
     }
     return line
+
+
+def batched_surrogate(args, gi, torch, BatchPipeline, specs, frames, recs, gbufs, gviews, bp, counter, F, V, timed,
+                      stream):
+    """The surrogate-plus-batched form on the same 16 views: one network (configuration 4's size, over
+    the box of every view's hits) trained online on the plain batch's caches, one view per frame;
+    then a second batch whose caches route hits of LOD >= 2 to it (trust set to 1 so that the routing
+    takes place) and whose probe pass takes its answers (gi_batch_set_surrogate: the query frame and
+    the probe pass per view), timed against the plain batch with and without the graph; the training
+    call timed on its own.  The network's error on the routed hits of the last view, against the
+    plain batch's cells of the same records, is reported."""
+    import workload as wl
+    cfg4 = wl.CONFIGS[4]
+    allp = np.concatenate([frames[v][k].records[0:3, np.isfinite(frames[v][k].records[9])]
+                           for v in range(V) for k in range(F)], axis=1)
+    lo, hi = tuple(allp.min(axis=1) - 0.5), tuple(allp.max(axis=1) + 0.5)
+    n_max = max(frames[v][0].n_records for v in range(V))
+    ncfg = gi.make_nrc_config(lo, hi, log2_table=cfg4["nrc_log2_table"], resolutions=cfg4["nrc_resolutions"],
+                              lr=cfg4["nrc_lr"], batch=cfg4["nrc_batch"], train_steps=cfg4["nrc_train_steps"],
+                              max_records=n_max, max_queries=min(n_max, gi.GI_NRC_MAX_BATCH), trust=1.0, query_lod=4,
+                              seed=1)
+    nrc = gi.gi_nrc_create(ncfg)
+    bs = BatchPipeline([(cfg["width"], cfg["height"], cfg["log2_slots"]) for cfg, _ in specs], 64)
+    scount = [0]
+
+    def plain_frame():
+        k = counter[0]
+        bp.frame(gbufs[k % F], recs[k % F], gviews[k % F], use_graph=True, stream=stream, resolve_frame=k)
+        counter[0] += 1
+
+    def train():
+        k = counter[0] - 1
+        v = k % V
+        st = bp.views[v]
+        gi.gi_nrc_train_frame(nrc, st["cache"], gi.hits_from_planes(recs[k % F][v], st["n_records"]), st["slot_ids"],
+                              k, stream)
+
+    def surrogate_frame():
+        k = scount[0]
+        bs.frame(gbufs[k % F], recs[k % F], gviews[k % F], stream=stream, resolve_frame=k)
+        scount[0] += 1
+
+    try:
+        setup = 2 * V
+        for _ in range(setup):
+            plain_frame()
+            train()
+        bs.set_surrogate(nrc, far_lod=2)
+        steps = max(3, min(args.steps, 20))
+        for _ in range(args.warmup):
+            surrogate_frame()
+        ms_surr = timed(surrogate_frame, steps)
+        # the routed hits of every view's last frame; the last view's answers (the network's latest
+        # query frame) against the plain batch's cells of the same records
+        k = scount[0] - 1
+        plain_frame_at = counter[0]
+        bp.frame(gbufs[k % F], recs[k % F], gviews[k % F], use_graph=True, stream=stream, resolve_frame=plain_frame_at)
+        counter[0] += 1
+        torch.cuda.synchronize()
+        routed = sum(int(np.count_nonzero(st["slot_ids"].cpu().numpy().view(np.uint32) == gi.GI_SLOT_FAR))
+                     for st in bs.views)
+        hits = sum(int(np.count_nonzero(np.isfinite(frames[v][k % F].records[9]))) for v in range(V))
+        last = bp.views[V - 1]
+        R = last["n_records"]
+        cnt = gi.gi_nrc_answers(nrc)
+        rec_ids = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
+        rads = torch.empty((max(cnt, 1), 4), dtype=torch.float32, device="cuda")
+        gi.gi_nrc_answers(nrc, rec_ids, rads, cnt)
+        ids = rec_ids.cpu().numpy().view(np.uint32)[:cnt]
+        ans = rads.cpu().numpy()[:cnt, :3]
+        far = bs.views[V - 1]["slot_ids"].cpu().numpy().view(np.uint32) == gi.GI_SLOT_FAR
+        cache_val = torch.empty((R, 4), dtype=torch.float32, device="cuda")
+        gi.gi_cache_query(last["cache"], cache_val, R, slot_ids=last["slot_ids"])
+        ref_all = cache_val.cpu().numpy()
+        sel = far[ids] & (ref_all[ids, 3] == 1.0)
+        ref = ref_all[ids[sel], :3]
+        net_err = float(np.abs(ans[sel] - ref).sum() / np.abs(ref).sum()) if sel.any() else None
+        last_counts = {"routed": int(far.sum()), "answered": int(cnt), "compared": int(sel.sum())}
+        judged = float(gi.gi_nrc_stats(nrc, stream)["judged_error"])
+        ms_train = timed(train, steps)
+    finally:
+        bs.set_surrogate(None)
+        bs.close()
+        gi.gi_nrc_destroy(nrc)
+    s_ms, t_ms = float(ms_surr.mean()), float(ms_train.mean())
+    return {
+        "note": "gi_batch_set_surrogate on the same 16 views: hits of LOD >= 2 routed to one network (trust set "
+                "to 1), the probe pass per view through its answers (query frame + probe pass), the other "
+                "passes one launch over all views, no graph; the network trained online on the plain batch's "
+                f"caches for {setup} frames, one view per frame; one training call per frame timed on its own",
+        "ms_per_frame": {"surrogate_batched": s_ms, "training_call": t_ms},
+        "frames_per_s": {"surrogate_batched_without_training": 1e3 / s_ms,
+                         "surrogate_batched_with_one_training_call": 1e3 / (s_ms + t_ms)},
+        "routed_hits_per_frame": routed, "hits_per_frame": hits,
+        "network_rel_l1_error_on_routed_hits_of_the_last_view_vs_plain_cache": net_err,
+        "last_view_hits": last_counts,
+        "judged_error": judged,
+        "gpu_launches_per_frame": 6 + 4 * V,
+    }
 
 
 # ------------------------------------------------------------------ surrogate arm (configuration 4)

@@ -681,11 +681,24 @@ gi_status gi_nrc_stats(gi_nrc_t nrc, gi_nrc_stats_t *out, gi_stream_t stream);
  * are neither inserted nor accumulated: their slot id is GI_SLOT_FAR, and gi_nrc_query_frame
  * answers every GI_SLOT_FAR record with the network (the plain probe pass treats them as rays
  * without sample).  The network keeps training on the cells the table still holds.  nrc NULL or
- * far_lod >= 4 ends the routing.  One-level caches only; gi_batch_frame does not route.  nrc must
- * outlive the routing.  Host only, no synchronisation.  Errors: GI_ERR_INVALID_ARG for a NULL or
- * tile cache.
+ * far_lod >= 4 ends the routing.  One-level caches only; in a batch, only with the batch's
+ * surrogate (gi_batch_set_surrogate).  nrc must outlive the routing.  Host only, no
+ * synchronisation.  Errors: GI_ERR_INVALID_ARG for a NULL or tile cache.
  */
 gi_status gi_cache_route_far(gi_cache_t cache, gi_nrc_t nrc, uint32_t far_lod);
+
+/*
+ * The surrogate in a batch (no counterpart in the paper): with nrc set, gi_batch_frame keeps the
+ * far-hit routing of the views whose caches route to nrc (gi_cache_route_far), and its probe pass
+ * becomes, view after view, gi_nrc_query_frame and gi_probes_integrate_nrc on the view's records
+ * (the network's answer buffers hold one view at a time), with the same results as those calls;
+ * the other passes stay one launch over all views.  That form runs without the CUDA graph
+ * (use_graph is ignored).  nrc NULL restores the plain form; a view whose cache routes to another
+ * surrogate than the batch's is rejected by gi_batch_frame.  Training stays the caller's
+ * (gi_nrc_train_frame on any view's records).  nrc must outlive its use.  Host only.
+ * Errors: GI_ERR_INVALID_ARG for a NULL batch.
+ */
+gi_status gi_batch_set_surrogate(gi_batch_t b, gi_nrc_t nrc);
 
 /* ---------------------------------------------------------------- allocation-free variant */
 /*

@@ -184,6 +184,7 @@ def lib() -> ctypes.CDLL:
             "gi_batch_set_tuning": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_batch_tuning)]),
             "gi_batch_frame": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_batch_view), c_u32, c_vp]),
             "gi_batch_destroy": (ctypes.c_int, [c_vp]),
+            "gi_batch_set_surrogate": (ctypes.c_int, [c_vp, c_vp]),
             "gi_cell_means_noalloc": (ctypes.c_int, [ctypes.POINTER(gi_hits), ctypes.POINTER(gi_view), c_f32, c_u32,
                                                      c_u32, ctypes.POINTER(c_f32), c_vp, c_vp, c_vp]),
             "gi_nrc_config_defaults": (ctypes.c_int, [ctypes.POINTER(gi_nrc_config)]),
@@ -463,6 +464,10 @@ def gi_batch_set_tuning(batch: int, tuning: gi_batch_tuning) -> None:
 def gi_batch_frame(batch: int, views, use_graph: bool = False, stream=None) -> None:
     """views: a ctypes array of gi_batch_view (one entry per view of the batch)."""
     check(lib().gi_batch_frame(batch, views, 1 if use_graph else 0, _stream(stream)), "gi_batch_frame")
+
+
+def gi_batch_set_surrogate(batch: int, nrc: int | None) -> None:
+    check(lib().gi_batch_set_surrogate(batch, nrc), "gi_batch_set_surrogate")
 
 
 def gi_batch_destroy(batch: int) -> None:

@@ -7,6 +7,11 @@
 // finds its view by binary search in the prefix table).  In graph mode the copy and the launches
 // are captured once per descriptor buffer (two buffers, alternating) and replayed every frame;
 // compactions of a table, decided on the host, run before the replay, outside the graph.
+//
+// With a surrogate (gi_batch_set_surrogate), the update keeps the far-hit routing of the caches
+// that route to it, and the probe-irradiance pass becomes, per view, the surrogate's query frame
+// and the probe pass with its answers (gi_nrc_query_frame, gi_probes_integrate_nrc): the network's
+// answer buffers hold one view's records at a time.  That form runs without the graph.
 #include <string.h>
 
 #include <algorithm>
@@ -56,6 +61,7 @@ struct gi_batch_s {
     std::vector<uint32_t> sig[2];  // block counts the graph of each buffer was captured with
     cudaStream_t capture;          // private stream the graphs are captured on
     uint64_t frames;
+    gi_nrc_t nrc;                  // surrogate of the probe pass, or NULL
 };
 
 namespace gi {
@@ -114,9 +120,10 @@ static gi_status check_view(const gi_batch_view &v, uint32_t rpp, int key_dir) {
     return GI_OK;
 }
 
-// Enqueue the descriptor copy and the six batched launches on st.
+// Enqueue the descriptor copy and the six batched launches on st (with a surrogate, the probe
+// pass per view: views must then be given).
 static gi_status enqueue_frame(gi_batch_s *b, int set, const std::vector<uint32_t> &blocks, int key_dir,
-                               cudaStream_t st) {
+                               cudaStream_t st, const gi_batch_view *views = nullptr) {
     const DescLayout &L = b->L;
     unsigned char *d = b->d_desc;
     gi_status s = cuda_status(cudaMemcpyAsync(d, b->h_desc[set], L.total, cudaMemcpyHostToDevice, st),
@@ -133,10 +140,18 @@ static gi_status enqueue_frame(gi_batch_s *b, int set, const std::vector<uint32_
         s = launch_resolve_batched(reinterpret_cast<const ResolveArgs *>(d + L.res),
                                    reinterpret_cast<const uint32_t *>(d + L.pre[kPassResolve]), n,
                                    blocks[kPassResolve], st);
-    if (s == GI_OK)
+    if (s == GI_OK && b->nrc && views) {
+        for (uint32_t v = 0; v < n && s == GI_OK; ++v) {
+            const gi_batch_view &bv = views[v];
+            s = gi_nrc_query_frame(b->nrc, bv.cache, &bv.hits, bv.slot_ids, &bv.view, st);
+            if (s == GI_OK)
+                s = gi_probes_integrate_nrc(bv.cache, b->nrc, &bv.probes, bv.slot_ids, b->rpp, bv.env, st);
+        }
+    } else if (s == GI_OK) {
         s = launch_integrate_batched(reinterpret_cast<const IntegrateArgs *>(d + L.integ),
                                      reinterpret_cast<const uint32_t *>(d + L.pre[kPassIntegrate]), n,
                                      blocks[kPassIntegrate], b->tuning.integrate_threads, b->rpp, st);
+    }
     if (s == GI_OK)
         s = launch_interpolate_batched(reinterpret_cast<const InterpArgs *>(d + L.interp),
                                        reinterpret_cast<const uint32_t *>(d + L.pre[kPassInterp]), n,
@@ -197,6 +212,15 @@ gi_status gi_batch_set_tuning(gi_batch_t b, const gi_batch_tuning *tuning) {
     return s;
 }
 
+gi_status gi_batch_set_surrogate(gi_batch_t b, gi_nrc_t nrc) {
+    if (!b) {
+        set_error("gi_batch_set_surrogate: NULL batch");
+        return GI_ERR_INVALID_ARG;
+    }
+    b->nrc = nrc;
+    return GI_OK;
+}
+
 gi_status gi_batch_destroy(gi_batch_t b) {
     if (!b) return GI_OK;
     cudaError_t e = cudaDeviceSynchronize();
@@ -218,6 +242,11 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
     for (uint32_t v = 0; v < n; ++v) {
         gi_status s = check_view(views[v], b->rpp, key_dir);
         if (s != GI_OK) return s;
+        const gi_nrc_t routes = cache_route_nrc(views[v].cache);
+        if (routes && routes != b->nrc) {
+            set_error("gi_batch_frame: view %u routes far hits to a surrogate the batch does not use", v);
+            return GI_ERR_INVALID_ARG;
+        }
         if (cache_last_resolved(views[v].cache) > (int64_t)views[v].resolve_frame) {
             set_error("gi_batch_frame: view %u resolve frame %u precedes its cache's last resolved frame", v,
                       views[v].resolve_frame);
@@ -256,9 +285,8 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
             (bv.probes.layout.num_probes * 4u + b->tuning.integrate_threads - 1u) / b->tuning.integrate_threads,
             interp_grid_x(bv.view.width) * interp_grid_y(bv.view.height)};
         for (int k = 0; k < 5; ++k) pre[k][v + 1] = pre[k][v] + cnt[k];
-        UpdateArgs ua = cache_update_args(bv.cache, &bv.hits, &bv.view, bv.slot_ids);
-        ua.route_stats = nullptr;  // batched frames never route far hits to a surrogate
-        reinterpret_cast<UpdateArgs *>(h + L.upd)[v] = ua;
+        // far hits go to the surrogate only where the cache routes them to the batch's surrogate
+        reinterpret_cast<UpdateArgs *>(h + L.upd)[v] = cache_update_args(bv.cache, &bv.hits, &bv.view, bv.slot_ids);
         reinterpret_cast<ResolveArgs *>(h + L.res)[v] = cache_resolve_args(bv.cache, bv.resolve_frame);
         reinterpret_cast<SpawnArgs *>(h + L.spawn)[v] = spawn_args(&bv.gbuf, &bv.view, &bv.probes);
         reinterpret_cast<IntegrateArgs *>(h + L.integ)[v] = integrate_args(bv.cache, &bv.probes, bv.slot_ids, b->rpp, bv.env);
@@ -270,7 +298,7 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
         pre[k][n + 1] = 0;  // the pass's work-item counter starts at zero every frame
     }
     gi_status s = GI_OK;
-    if (use_graph) {
+    if (use_graph && !b->nrc) {
         if (!b->exec[set] || b->sig[set] != blocks) {
             if (b->exec[set]) cudaGraphExecDestroy(b->exec[set]);
             b->exec[set] = nullptr;
@@ -290,7 +318,7 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
         }
         s = cuda_status(cudaGraphLaunch(b->exec[set], st), "cudaGraphLaunch");
     } else {
-        s = enqueue_frame(b, set, blocks, key_dir, st);
+        s = enqueue_frame(b, set, blocks, key_dir, st, views);
     }
     if (s != GI_OK) return s;
     s = cuda_status(cudaEventRecord(b->used[set], st), "batch event");

@@ -741,6 +741,7 @@ int cache_key_dir(const gi_cache_s *c) { return (int)c->cfg.key_dir; }
 bool cache_tiled(const gi_cache_s *c) { return c->tiles; }
 int cache_device(const gi_cache_s *c) { return c->device; }
 int64_t cache_last_resolved(const gi_cache_s *c) { return c->last_resolved; }
+gi_nrc_t cache_route_nrc(const gi_cache_s *c) { return c->route_lod < 4u ? c->route_nrc : nullptr; }
 
 static void free_cache(gi_cache_s *c) {
     for (int k = 0; k < 2; ++k) {

@@ -288,6 +288,7 @@ int cache_key_dir(const gi_cache_s *c);
 bool cache_tiled(const gi_cache_s *c);
 int cache_device(const gi_cache_s *c);
 int64_t cache_last_resolved(const gi_cache_s *c);
+gi_nrc_t cache_route_nrc(const gi_cache_s *c);  // the surrogate the cache routes far hits to, or NULL
 
 // Blocks of a resident grid of `kernel` (threads per block, dynamic shared memory 0) on the
 // current device, at most `items`.

@@ -6,8 +6,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (GI_RESOLVED_F32, GI_SH_STRIDE, gi_batch_create, gi_batch_destroy, gi_batch_frame, gi_batch_view,
-               gi_cache_create, gi_cache_destroy, gi_cache_resolve, gi_cache_update, gi_probes_filter, gi_probes_gather,
+from . import (GI_RESOLVED_F32, GI_SH_STRIDE, gi_batch_create, gi_batch_destroy, gi_batch_frame,
+               gi_batch_set_surrogate, gi_batch_view, gi_cache_create, gi_cache_destroy, gi_cache_route_far, gi_cache_resolve, gi_cache_update, gi_probes_filter, gi_probes_gather,
                gi_probes_gather_temporal, gi_probes_integrate, gi_probes_interpolate, gi_probes_layout,
                gi_probes_project, gi_probes_reproject, gi_probes_spawn, gi_probes_spawn_upscaled, hits_from_planes,
                make_gbuffer, make_probes, make_view)
@@ -143,6 +143,13 @@ class BatchPipeline:
             for k in range(3):
                 d.env[k] = float(env[k])
         gi_batch_frame(self.batch, self._desc, use_graph, stream)
+
+    def set_surrogate(self, nrc, far_lod: int = 4):
+        """The batch's probe pass through the surrogate nrc (None: the plain form); far_lod < 4 also
+        routes every view's hits of that LOD and above to it (gi_cache_route_far)."""
+        for st in self.views:
+            gi_cache_route_far(st["cache"], nrc if far_lod < 4 else None, far_lod)
+        gi_batch_set_surrogate(self.batch, nrc)
 
     def close(self):
         if self.batch:

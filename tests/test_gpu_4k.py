@@ -17,9 +17,10 @@ def _gpu():
     require_gpu()
 
 
-def test_4k_cache_two_frames_fp16():
+def test_4k_cache_four_frames_fp16():
+    # four frames of the moving camera: the EMA blends revisited cells at full size
     scene = wl.make_scene(5)
-    frames = [wl.make_frame(5, f, scene) for f in (0, 1)]
+    frames = [wl.make_frame(5, f, scene) for f in (0, 1, 2, 3)]
     bound = 2.0 ** -11 * sum(0.9 ** j for j in range(len(frames))) + 1e-4
     _frames_parity(5, frames, resolved_format=1, value_rel=bound)
 

@@ -134,3 +134,58 @@ def test_batch_rejects_inconsistent_views():
         assert e.value.status == gi.GI_ERR_INVALID_ARG
     finally:
         bp.close()
+
+
+def test_surrogate_batch_equals_single_view_calls():
+    """gi_batch_set_surrogate: far hits of every view routed to one trusted network, the probe pass
+    per view through the network's answers; bit for bit what the single-view calls give (update
+    with routing, resolve, gi_nrc_query_frame, gi_probes_integrate_nrc, interpolation)."""
+    from test_gpu_surrogate import _nrc, _spec, _trust_as_is
+
+    data = _views_and_frames(2)
+    allrec = np.concatenate([frs[f].records for _, frs in data for f in range(2)], axis=1)
+    hitpos = allrec[0:3, np.isfinite(allrec[9])]
+    spec = _spec(aabb=(tuple(hitpos.min(axis=1) - 1.0), tuple(hitpos.max(axis=1) + 1.0)))
+    n_max = max(frs[0].n_records for _, frs in data)
+    nrc = _nrc(spec, batch=1024, max_records=n_max, max_queries=n_max, trust=1e30, query_lod=2)
+    bp = BatchPipeline([(c["width"], c["height"], 16) for c, _ in data], 64)
+    singles = [Pipeline(c["width"], c["height"], 64, 16) for c, _ in data]
+    try:
+        gi.gi_nrc_set_params(nrc, *wl.surrogate_inputs.params(11, spec.log2_table))
+        _trust_as_is(nrc, spec)
+        bp.set_surrogate(nrc, far_lod=2)
+        for sp in singles:
+            gi.gi_cache_route_far(sp.cache, nrc, 2)
+        routed = 0
+        for f in range(2):
+            gbufs = [dev(frs[f].gbuffer) for _, frs in data]
+            recs = [dev(frs[f].records) for _, frs in data]
+            views = [view_of(frs[f].camera, f) for _, frs in data]
+            bp.frame(gbufs, recs, views, use_graph=True)
+            for v, sp in enumerate(singles):
+                sp.spawn(gbufs[v], views[v])
+                sp.update(recs[v], views[v])
+                sp.resolve(f)
+                gi.gi_nrc_query_frame(nrc, sp.cache, gi.hits_from_planes(recs[v], sp.n_records), sp.slot_ids,
+                                      views[v])
+                gi.gi_probes_integrate_nrc(sp.cache, nrc, sp.probes.struct, sp.slot_ids, 64)
+                sp.interpolate(gbufs[v], views[v])
+            torch.cuda.synchronize()
+            for v, sp in enumerate(singles):
+                st = bp.views[v]
+                a, b = u32(st["slot_ids"]), u32(sp.slot_ids)
+                assert np.array_equal(a == gi.GI_SLOT_FAR, b == gi.GI_SLOT_FAR)
+                assert np.array_equal(a >= (1 << 16), b >= (1 << 16))
+                routed += int(np.count_nonzero(a == gi.GI_SLOT_FAR))
+                assert np.array_equal(_export_by_identity(st["cache"]), _export_by_identity(sp.cache))
+                assert torch.equal(st["probes"].sh, sp.probes.sh)
+                assert torch.equal(st["irr"], sp.irr)
+        assert routed > 0
+    finally:
+        bp.set_surrogate(None)
+        for sp in singles:
+            gi.gi_cache_route_far(sp.cache, None, 4)
+        bp.close()
+        for sp in singles:
+            sp.close()
+        gi.gi_nrc_destroy(nrc)
