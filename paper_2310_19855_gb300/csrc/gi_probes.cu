@@ -341,7 +341,8 @@ __device__ __forceinline__ void project_channel(const float4 n4, const float (&S
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) W2[i][j] = W2[j][i] = T[i][0] * R[j][0] + T[i][1] * R[j][1] + T[i][2] * R[j][2];
-    // real SH basis, bands 0..2 (the order of project_cells), channel h, coefficient k at 3 k + h
+    // real SH basis, bands 0..2: c0; c1 y, c1 z, c1 x; c2 xy, c2 yz, c3 (3z^2 - 1), c2 xz, c4 (x^2 - y^2);
+    // channel h, coefficient k at 3 k + h
     const float C0 = 0.28209479177387814f, C1 = 0.4886025119029199f, C2 = 1.0925484305920792f,
                 C3 = 0.31539156525252005f, C4 = 0.5462742152960396f;
     out[0 * 3 + h] = C0 * S0;
