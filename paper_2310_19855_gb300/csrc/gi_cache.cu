@@ -503,8 +503,10 @@ __global__ void k_scan_stats(const SlotWord *tags, const Accum *acc, const uint3
 
 
 // ---------------------------------------------------------------- batched passes (many views)
+// 6 blocks per SM (40 registers): the work-item loop's registers spilled at 8 (16 views: 701
+// against 694 frames/s)
 template <int KEY_DIR>
-__global__ void __launch_bounds__(kUpdThreads, 8) k_update_batched(const UpdateArgs *args, const uint32_t *prefix,
+__global__ void __launch_bounds__(kUpdThreads, 6) k_update_batched(const UpdateArgs *args, const uint32_t *prefix,
                                                                    uint32_t nviews) {
     __shared__ UpdateArgs sa;
     GI_BATCHED_ITEMS(prefix, nviews, sa, args, (update_body<KEY_DIR, false>(sa, item, items)));
