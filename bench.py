@@ -1169,103 +1169,154 @@ def run_batched(args, rank, world, local_rank):
 
 def batched_surrogate(args, gi, torch, BatchPipeline, specs, frames, recs, gbufs, gviews, bp, counter, F, V, timed,
                       stream):
-    """The surrogate-plus-batched form on the same 16 views: one network (configuration 4's size, over
-    the box of every view's hits) trained online on the plain batch's caches, one view per frame;
-    then a second batch whose caches route hits of LOD >= 2 to it (trust set to 1 so that the routing
-    takes place) and whose probe pass takes its answers (gi_batch_set_surrogate: the query frame and
-    the probe pass per view), timed against the plain batch with and without the graph; the training
-    call timed on its own.  The network's error on the routed hits of the view with the most of them,
-    against the plain batch's cells of the same records, is reported."""
+    """The surrogate-plus-batched form on the same 16 views: each view its own network (configuration
+    4's size, over the box of the view's hits; the views are distinct scenes in the same world box,
+    which one network cannot fit), trained online on the plain batch's cache of its view over
+    `rounds` rounds of one plain batched frame and one training call per view (after 64 rounds,
+    only the views that route hits keep their network); then a second batch
+    whose caches route hits of LOD >= 2 to their view's network (trust set to 1 so that the routing
+    takes place) and whose probe pass takes its answers (gi_batch_set_view_surrogates: the query
+    frame and the probe pass per view), timed against the plain batch with and without the graph;
+    one round of training calls timed on its own.  The networks' error on the routed hits of every
+    view, against the plain batch's cells of the same records, is reported."""
     import workload as wl
     cfg4 = wl.CONFIGS[4]
-    allp = np.concatenate([frames[v][k].records[0:3, np.isfinite(frames[v][k].records[9])]
-                           for v in range(V) for k in range(F)], axis=1)
-    lo, hi = tuple(allp.min(axis=1) - 0.5), tuple(allp.max(axis=1) + 0.5)
-    n_max = max(frames[v][0].n_records for v in range(V))
-    ncfg = gi.make_nrc_config(lo, hi, log2_table=cfg4["nrc_log2_table"], resolutions=cfg4["nrc_resolutions"],
-                              lr=cfg4["nrc_lr"], batch=cfg4["nrc_batch"], train_steps=cfg4["nrc_train_steps"],
-                              max_records=n_max, max_queries=min(n_max, gi.GI_NRC_MAX_BATCH), trust=1.0, query_lod=4,
-                              seed=1)
-    nrc = gi.gi_nrc_create(ncfg)
+    rounds = 2048 if args.setup_frames is None else max(1, args.setup_frames)
+    nets = []
+    try:
+        for v in range(V):
+            pv = np.concatenate([frames[v][k].records[0:3, np.isfinite(frames[v][k].records[9])] for k in range(F)],
+                                axis=1)
+            lo, hi = tuple(pv.min(axis=1) - 0.5), tuple(pv.max(axis=1) + 0.5)
+            n_v = frames[v][0].n_records
+            ncfg = gi.make_nrc_config(lo, hi, log2_table=cfg4["nrc_log2_table"], resolutions=cfg4["nrc_resolutions"],
+                                      lr=cfg4["nrc_lr"], batch=cfg4["nrc_batch"], train_steps=cfg4["nrc_train_steps"],
+                                      max_records=n_v, max_queries=min(n_v, gi.GI_NRC_MAX_BATCH), trust=1.0,
+                                      query_lod=4, seed=1 + v)
+            nets.append(gi.gi_nrc_create(ncfg))
+        return _batched_surrogate_run(args, gi, torch, BatchPipeline, specs, frames, recs, gbufs, gviews, bp,
+                                      counter, F, V, timed, stream, nets, rounds)
+    finally:
+        for nrc in nets:
+            gi.gi_nrc_destroy(nrc)
+
+
+def _batched_surrogate_run(args, gi, torch, BatchPipeline, specs, frames, recs, gbufs, gviews, bp, counter, F, V,
+                           timed, stream, nets, rounds):
     bs = BatchPipeline([(cfg["width"], cfg["height"], cfg["log2_slots"]) for cfg, _ in specs], 64)
     scount = [0]
+    tcount = [0]
 
     def plain_frame():
         k = counter[0]
         bp.frame(gbufs[k % F], recs[k % F], gviews[k % F], use_graph=True, stream=stream, resolve_frame=k)
         counter[0] += 1
 
-    def train():
+    def train_round():
+        # one training call per view that keeps a network, on the plain batch's latest frame (its
+        # records and slot ids)
         k = counter[0] - 1
-        v = k % V
-        st = bp.views[v]
-        gi.gi_nrc_train_frame(nrc, st["cache"], gi.hits_from_planes(recs[k % F][v], st["n_records"]), st["slot_ids"],
-                              k, stream)
+        for v in range(V):
+            if active[v] is None:
+                continue
+            st = bp.views[v]
+            gi.gi_nrc_train_frame(active[v], st["cache"], gi.hits_from_planes(recs[k % F][v], st["n_records"]),
+                                  st["slot_ids"], tcount[0], stream)
+        tcount[0] += 1
 
     def surrogate_frame():
         k = scount[0]
         bs.frame(gbufs[k % F], recs[k % F], gviews[k % F], stream=stream, resolve_frame=k)
         scount[0] += 1
 
+    active = list(nets)
     try:
-        setup = 2 * V
-        for _ in range(setup):
+        # every view's network first; then only those of the views that route hits to them
+        t0 = time.time()
+        first = min(rounds, 64)
+        for _ in range(first):
             plain_frame()
-            train()
-        bs.set_surrogate(nrc, far_lod=2)
+            train_round()
+        bs.set_view_surrogates(nets, far_lod=2)
+        surrogate_frame()
+        torch.cuda.synchronize()
+        active = [nets[v] if np.any(st["slot_ids"].cpu().numpy().view(np.uint32) == gi.GI_SLOT_FAR) else None
+                  for v, st in enumerate(bs.views)]
+        bs.set_view_surrogates(active, far_lod=2)
+        for _ in range(rounds - first):
+            plain_frame()
+            train_round()
+        torch.cuda.synchronize()
+        setup_s = time.time() - t0
         steps = max(3, min(args.steps, 20))
         for _ in range(args.warmup):
             surrogate_frame()
         ms_surr = timed(surrogate_frame, steps)
         # the routed hits of every view's last frame; the plain batch on the same inputs
         k = scount[0] - 1
-        plain_frame_at = counter[0]
-        bp.frame(gbufs[k % F], recs[k % F], gviews[k % F], use_graph=True, stream=stream, resolve_frame=plain_frame_at)
+        bp.frame(gbufs[k % F], recs[k % F], gviews[k % F], use_graph=True, stream=stream, resolve_frame=counter[0])
         counter[0] += 1
         torch.cuda.synchronize()
         far_v = [st["slot_ids"].cpu().numpy().view(np.uint32) == gi.GI_SLOT_FAR for st in bs.views]
         routed = sum(int(f.sum()) for f in far_v)
+        # what a viewer sees: the interpolated irradiance of the two batches on the same frame
+        i_num = i_den = 0.0
+        for v in range(V):
+            a_s = bs.views[v]["irr"][..., :3].double()
+            a_p = bp.views[v]["irr"][..., :3].double()
+            i_num += float((a_s - a_p).abs().sum())
+            i_den += float(a_p.abs().sum())
         hits = sum(int(np.count_nonzero(np.isfinite(frames[v][k % F].records[9]))) for v in range(V))
-        # the view with the most routed hits: its query frame again (untimed), the answers against the
-        # plain batch's cells of the same records
-        vs = int(np.argmax([int(f.sum()) for f in far_v]))
-        sv, pv = bs.views[vs], bp.views[vs]
-        R = pv["n_records"]
-        gi.gi_nrc_query_frame(nrc, sv["cache"], gi.hits_from_planes(recs[k % F][vs], R), sv["slot_ids"],
-                              gviews[k % F][vs], stream)
-        cnt = gi.gi_nrc_answers(nrc, stream=stream)
-        rec_ids = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
-        rads = torch.empty((max(cnt, 1), 4), dtype=torch.float32, device="cuda")
-        gi.gi_nrc_answers(nrc, rec_ids, rads, cnt, stream=stream)
-        ids = rec_ids.cpu().numpy().view(np.uint32)[:cnt]
-        ans = rads.cpu().numpy()[:cnt, :3]
-        far = far_v[vs]
-        cache_val = torch.empty((R, 4), dtype=torch.float32, device="cuda")
-        gi.gi_cache_query(pv["cache"], cache_val, R, slot_ids=pv["slot_ids"])
-        ref_all = cache_val.cpu().numpy()
-        sel = far[ids] & (ref_all[ids, 3] == 1.0)
-        ref = ref_all[ids[sel], :3]
-        net_err = float(np.abs(ans[sel] - ref).sum() / np.abs(ref).sum()) if sel.any() else None
-        last_counts = {"view": vs, "routed": int(far.sum()), "answered": int(cnt), "compared": int(sel.sum())}
-        judged = float(gi.gi_nrc_stats(nrc, stream)["judged_error"])
-        ms_train = timed(train, steps)
+        # every view's query frame again (untimed): its network's answers against the plain batch's
+        # cells of the same records
+        num = den = 0.0
+        per_view = []
+        for v in range(V):
+            sv, pv = bs.views[v], bp.views[v]
+            R = pv["n_records"]
+            if active[v] is None or not far_v[v].any():
+                continue
+            gi.gi_nrc_query_frame(nets[v], sv["cache"], gi.hits_from_planes(recs[k % F][v], R), sv["slot_ids"],
+                                  gviews[k % F][v], stream)
+            cnt = gi.gi_nrc_answers(nets[v], stream=stream)
+            rec_ids = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
+            rads = torch.empty((max(cnt, 1), 4), dtype=torch.float32, device="cuda")
+            gi.gi_nrc_answers(nets[v], rec_ids, rads, cnt, stream=stream)
+            ids = rec_ids.cpu().numpy().view(np.uint32)[:cnt]
+            ans = rads.cpu().numpy()[:cnt, :3]
+            cache_val = torch.empty((R, 4), dtype=torch.float32, device="cuda")
+            gi.gi_cache_query(pv["cache"], cache_val, R, slot_ids=pv["slot_ids"])
+            ref_all = cache_val.cpu().numpy()
+            sel = far_v[v][ids] & (ref_all[ids, 3] == 1.0)
+            ref = ref_all[ids[sel], :3]
+            e_num, e_den = float(np.abs(ans[sel] - ref).sum()), float(np.abs(ref).sum())
+            num, den = num + e_num, den + e_den
+            per_view.append({"view": v, "routed": int(far_v[v].sum()), "compared": int(sel.sum()),
+                             "rel_l1": e_num / e_den if e_den > 0 else None})
+        judged = [float(gi.gi_nrc_stats(nrc, stream)["judged_error"]) for nrc in active if nrc is not None]
+        ms_train = timed(train_round, steps)
     finally:
-        bs.set_surrogate(None)
+        bs.set_view_surrogates(None)
         bs.close()
-        gi.gi_nrc_destroy(nrc)
     s_ms, t_ms = float(ms_surr.mean()), float(ms_train.mean())
     return {
-        "note": "gi_batch_set_surrogate on the same 16 views: hits of LOD >= 2 routed to one network (trust set "
-                "to 1), the probe pass per view through its answers (query frame + probe pass), the other "
-                "passes one launch over all views, no graph; the network trained online on the plain batch's "
-                f"caches for {setup} frames, one view per frame; one training call per frame timed on its own",
-        "ms_per_frame": {"surrogate_batched": s_ms, "training_call": t_ms},
+        "note": f"gi_batch_set_view_surrogates on the same {V} views: one network per view (each view is its own "
+                "scene), hits of LOD >= 2 routed to it (trust set to 1), the probe pass per view through its "
+                "answers (query frame + probe pass), the other passes one launch over all views, no graph; each "
+                f"network trained online on its view of the plain batch, {rounds} rounds of one plain frame and "
+                f"one training call per view (after the first {first} rounds only the views that route hits keep "
+                "their network; the others take the plain probe pass); one round of training calls timed on its "
+                "own",
+        "views_with_a_network": [v for v in range(V) if active[v] is not None],
+        "ms_per_frame": {"surrogate_batched": s_ms, "training_round_views_with_a_network": t_ms},
         "frames_per_s": {"surrogate_batched_without_training": 1e3 / s_ms,
-                         "surrogate_batched_with_one_training_call": 1e3 / (s_ms + t_ms)},
+                         "surrogate_batched_with_one_training_round": 1e3 / (s_ms + t_ms)},
         "routed_hits_per_frame": routed, "hits_per_frame": hits,
-        "network_rel_l1_error_on_routed_hits_vs_plain_cache": net_err,
-        "error_view_hits": last_counts,
-        "judged_error": judged,
+        "network_rel_l1_error_on_routed_hits_vs_plain_cache": num / den if den > 0 else None,
+        "per_view_error": per_view,
+        "irradiance_rel_l1_vs_plain_batch": i_num / i_den if i_den > 0 else None,
+        "judged_error_max_over_views": max(judged),
+        "training_rounds": rounds, "setup_s": setup_s,
         "gpu_launches_per_frame": 6 + 4 * V,
     }
 
@@ -1479,9 +1530,13 @@ def run_surrogate(args, rank, world, local_rank):
     return line
 
 
+FAR_SETUP_FRAMES = 2048  # online training of the far-hit network before the timed frames
+
+
 def run_far_routing(args, rank, world, local_rank):
     """Far hits to the surrogate on the boxes at 1080p (15 % of the hits have LOD >= 2): a network
-    trained online on a plain cache (the configuration's level schedule over the room), then per
+    trained online on a plain cache (the configuration's level schedule over the room) for
+    FAR_SETUP_FRAMES frames (4 cycled frames: ~1.2 s), then per
     frame the plain form (update, resolve, probe irradiance) against the routed form (update with
     LOD >= 2 hits left out of the table, resolve, query frame answering them, probe irradiance with
     the answers), each on its own cache over the same frames; the training call timed on its own.
@@ -1550,7 +1605,7 @@ def run_far_routing(args, rank, world, local_rank):
             if ev is not None:
                 ev[1].record(stream)
 
-        setup = 4 * cfg4["frames"] // 8
+        setup = FAR_SETUP_FRAMES if args.setup_frames is None else max(1, args.setup_frames)
         for i in range(setup):
             plain(i)
             train(i)
@@ -1687,7 +1742,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--setup-frames", type=int, default=None,
                     help="configuration 4: frames of online training before the warm-up (default: the "
-                         "configuration's 128)")
+                         "configuration's 128); configuration 3: training rounds of the per-view networks "
+                         "(default 2048); block 4-far: frames of online training (default 2048)")
     ap.add_argument("--no-other-configs", action="store_true",
                     help="configuration 2: skip the compact runs of configurations 3-7 added to its line")
     ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5, 6, 7],

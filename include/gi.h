@@ -681,8 +681,9 @@ gi_status gi_nrc_stats(gi_nrc_t nrc, gi_nrc_stats_t *out, gi_stream_t stream);
  * are neither inserted nor accumulated: their slot id is GI_SLOT_FAR, and gi_nrc_query_frame
  * answers every GI_SLOT_FAR record with the network (the plain probe pass treats them as rays
  * without sample).  The network keeps training on the cells the table still holds.  nrc NULL or
- * far_lod >= 4 ends the routing.  One-level caches only; in a batch, only with the batch's
- * surrogate (gi_batch_set_surrogate).  nrc must outlive the routing.  Host only, no
+ * far_lod >= 4 ends the routing.  One-level caches only; in a batch, only with the view's
+ * surrogate in the batch (gi_batch_set_surrogate, gi_batch_set_view_surrogates).  nrc must outlive
+ * the routing.  Host only, no
  * synchronisation.  Errors: GI_ERR_INVALID_ARG for a NULL or tile cache.
  */
 gi_status gi_cache_route_far(gi_cache_t cache, gi_nrc_t nrc, uint32_t far_lod);
@@ -699,6 +700,19 @@ gi_status gi_cache_route_far(gi_cache_t cache, gi_nrc_t nrc, uint32_t far_lod);
  * Errors: GI_ERR_INVALID_ARG for a NULL batch.
  */
 gi_status gi_batch_set_surrogate(gi_batch_t b, gi_nrc_t nrc);
+
+/*
+ * One surrogate per view (no counterpart in the paper), for views of different scenes, which one
+ * network cannot share: nrcs is a host array of the batch's n_views handles (an entry may be NULL),
+ * read during the call.  View v's probe pass is then gi_nrc_query_frame and
+ * gi_probes_integrate_nrc with nrcs[v], or the plain gi_probes_integrate where nrcs[v] is NULL,
+ * view after view, with the same results as those calls; the other passes stay one launch over
+ * all views, and the form runs without the CUDA graph while any entry is set.  nrcs NULL restores
+ * the plain form.  gi_batch_frame rejects a view whose cache routes far hits to a network other
+ * than nrcs[v].  gi_batch_set_surrogate(b, nrc) is this call with every entry nrc.  Each network
+ * must outlive its use.  Host only.  Errors: GI_ERR_INVALID_ARG for a NULL batch.
+ */
+gi_status gi_batch_set_view_surrogates(gi_batch_t b, const gi_nrc_t *nrcs);
 
 /* ---------------------------------------------------------------- allocation-free variant */
 /*

@@ -185,6 +185,7 @@ def lib() -> ctypes.CDLL:
             "gi_batch_frame": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_batch_view), c_u32, c_vp]),
             "gi_batch_destroy": (ctypes.c_int, [c_vp]),
             "gi_batch_set_surrogate": (ctypes.c_int, [c_vp, c_vp]),
+            "gi_batch_set_view_surrogates": (ctypes.c_int, [c_vp, ctypes.POINTER(c_vp)]),
             "gi_cell_means_noalloc": (ctypes.c_int, [ctypes.POINTER(gi_hits), ctypes.POINTER(gi_view), c_f32, c_u32,
                                                      c_u32, ctypes.POINTER(c_f32), c_vp, c_vp, c_vp]),
             "gi_nrc_config_defaults": (ctypes.c_int, [ctypes.POINTER(gi_nrc_config)]),
@@ -468,6 +469,12 @@ def gi_batch_frame(batch: int, views, use_graph: bool = False, stream=None) -> N
 
 def gi_batch_set_surrogate(batch: int, nrc: int | None) -> None:
     check(lib().gi_batch_set_surrogate(batch, nrc), "gi_batch_set_surrogate")
+
+
+def gi_batch_set_view_surrogates(batch: int, nrcs) -> None:
+    """nrcs: one handle (or None) per view of the batch, or None for the plain form."""
+    arr = None if nrcs is None else (c_vp * len(nrcs))(*nrcs)
+    check(lib().gi_batch_set_view_surrogates(batch, arr), "gi_batch_set_view_surrogates")
 
 
 def gi_batch_destroy(batch: int) -> None:

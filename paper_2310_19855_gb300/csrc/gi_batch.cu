@@ -8,10 +8,12 @@
 // are captured once per descriptor buffer (two buffers, alternating) and replayed every frame;
 // compactions of a table, decided on the host, run before the replay, outside the graph.
 //
-// With a surrogate (gi_batch_set_surrogate), the update keeps the far-hit routing of the caches
-// that route to it, and the probe-irradiance pass becomes, per view, the surrogate's query frame
-// and the probe pass with its answers (gi_nrc_query_frame, gi_probes_integrate_nrc): the network's
-// answer buffers hold one view's records at a time.  That form runs without the graph.
+// With surrogates (gi_batch_set_surrogate: one for every view; gi_batch_set_view_surrogates: one
+// per view, or none), the update keeps the far-hit routing of the caches that route to their
+// view's surrogate, and the probe-irradiance pass becomes, per view, the surrogate's query frame
+// and the probe pass with its answers (gi_nrc_query_frame, gi_probes_integrate_nrc; a network's
+// answer buffers hold one view's records at a time), or the plain probe pass of a view without
+// one.  That form runs without the graph.
 #include <string.h>
 
 #include <algorithm>
@@ -61,7 +63,8 @@ struct gi_batch_s {
     std::vector<uint32_t> sig[2];  // block counts the graph of each buffer was captured with
     cudaStream_t capture;          // private stream the graphs are captured on
     uint64_t frames;
-    gi_nrc_t nrc;                  // surrogate of the probe pass, or NULL
+    std::vector<gi_nrc_t> nrcs;    // surrogate of each view's probe pass, or NULL
+    bool surr;                     // some view has one: the probe pass runs per view
 };
 
 namespace gi {
@@ -140,12 +143,16 @@ static gi_status enqueue_frame(gi_batch_s *b, int set, const std::vector<uint32_
         s = launch_resolve_batched(reinterpret_cast<const ResolveArgs *>(d + L.res),
                                    reinterpret_cast<const uint32_t *>(d + L.pre[kPassResolve]), n,
                                    blocks[kPassResolve], st);
-    if (s == GI_OK && b->nrc && views) {
+    if (s == GI_OK && b->surr && views) {
         for (uint32_t v = 0; v < n && s == GI_OK; ++v) {
             const gi_batch_view &bv = views[v];
-            s = gi_nrc_query_frame(b->nrc, bv.cache, &bv.hits, bv.slot_ids, &bv.view, st);
-            if (s == GI_OK)
-                s = gi_probes_integrate_nrc(bv.cache, b->nrc, &bv.probes, bv.slot_ids, b->rpp, bv.env, st);
+            const gi_nrc_t nrc = b->nrcs[v];
+            if (!nrc) {
+                s = gi_probes_integrate(bv.cache, &bv.probes, bv.slot_ids, b->rpp, bv.env, st);
+                continue;
+            }
+            s = gi_nrc_query_frame(nrc, bv.cache, &bv.hits, bv.slot_ids, &bv.view, st);
+            if (s == GI_OK) s = gi_probes_integrate_nrc(bv.cache, nrc, &bv.probes, bv.slot_ids, b->rpp, bv.env, st);
         }
     } else if (s == GI_OK) {
         s = launch_integrate_batched(reinterpret_cast<const IntegrateArgs *>(d + L.integ),
@@ -179,6 +186,7 @@ gi_status gi_batch_create(uint32_t n_views, uint32_t rays_per_probe, const gi_ba
     }
     gi_batch_s *b = new gi_batch_s();
     b->n = n_views;
+    b->nrcs.assign(n_views, nullptr);
     b->rpp = rays_per_probe;
     b->tuning = t;
     b->L = desc_layout(n_views);
@@ -217,7 +225,21 @@ gi_status gi_batch_set_surrogate(gi_batch_t b, gi_nrc_t nrc) {
         set_error("gi_batch_set_surrogate: NULL batch");
         return GI_ERR_INVALID_ARG;
     }
-    b->nrc = nrc;
+    b->nrcs.assign(b->n, nrc);
+    b->surr = nrc != nullptr;
+    return GI_OK;
+}
+
+gi_status gi_batch_set_view_surrogates(gi_batch_t b, const gi_nrc_t *nrcs) {
+    if (!b) {
+        set_error("gi_batch_set_view_surrogates: NULL batch");
+        return GI_ERR_INVALID_ARG;
+    }
+    b->surr = false;
+    for (uint32_t v = 0; v < b->n; ++v) {
+        b->nrcs[v] = nrcs ? nrcs[v] : nullptr;
+        b->surr = b->surr || b->nrcs[v] != nullptr;
+    }
     return GI_OK;
 }
 
@@ -243,8 +265,8 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
         gi_status s = check_view(views[v], b->rpp, key_dir);
         if (s != GI_OK) return s;
         const gi_nrc_t routes = cache_route_nrc(views[v].cache);
-        if (routes && routes != b->nrc) {
-            set_error("gi_batch_frame: view %u routes far hits to a surrogate the batch does not use", v);
+        if (routes && routes != b->nrcs[v]) {
+            set_error("gi_batch_frame: view %u routes far hits to a surrogate other than its own in the batch", v);
             return GI_ERR_INVALID_ARG;
         }
         if (cache_last_resolved(views[v].cache) > (int64_t)views[v].resolve_frame) {
@@ -298,7 +320,7 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
         pre[k][n + 1] = 0;  // the pass's work-item counter starts at zero every frame
     }
     gi_status s = GI_OK;
-    if (use_graph && !b->nrc) {
+    if (use_graph && !b->surr) {
         if (!b->exec[set] || b->sig[set] != blocks) {
             if (b->exec[set]) cudaGraphExecDestroy(b->exec[set]);
             b->exec[set] = nullptr;

@@ -7,7 +7,8 @@ from __future__ import annotations
 import torch
 
 from . import (GI_RESOLVED_F32, GI_SH_STRIDE, gi_batch_create, gi_batch_destroy, gi_batch_frame,
-               gi_batch_set_surrogate, gi_batch_view, gi_cache_create, gi_cache_destroy, gi_cache_route_far, gi_cache_resolve, gi_cache_update, gi_probes_filter, gi_probes_gather,
+               gi_batch_set_surrogate, gi_batch_set_view_surrogates, gi_batch_view, gi_cache_create,
+               gi_cache_destroy, gi_cache_route_far, gi_cache_resolve, gi_cache_update, gi_probes_filter, gi_probes_gather,
                gi_probes_gather_temporal, gi_probes_integrate, gi_probes_interpolate, gi_probes_layout,
                gi_probes_project, gi_probes_reproject, gi_probes_spawn, gi_probes_spawn_upscaled, hits_from_planes,
                make_gbuffer, make_probes, make_view)
@@ -150,6 +151,15 @@ class BatchPipeline:
         for st in self.views:
             gi_cache_route_far(st["cache"], nrc if far_lod < 4 else None, far_lod)
         gi_batch_set_surrogate(self.batch, nrc)
+
+    def set_view_surrogates(self, nrcs, far_lod: int = 4):
+        """View v's probe pass through the surrogate nrcs[v] (None: that view's plain probe pass;
+        nrcs None: the plain form); far_lod < 4 also routes view v's hits of that LOD and above to
+        nrcs[v] (gi_cache_route_far)."""
+        for v, st in enumerate(self.views):
+            nrc = None if nrcs is None else nrcs[v]
+            gi_cache_route_far(st["cache"], nrc if far_lod < 4 else None, far_lod)
+        gi_batch_set_view_surrogates(self.batch, nrcs)
 
     def close(self):
         if self.batch:

@@ -140,10 +140,13 @@ def test_batch_rejects_inconsistent_views():
         bp.close()
 
 
-def test_surrogate_batch_equals_single_view_calls():
+@pytest.mark.parametrize("per_view", [False, True])
+def test_surrogate_batch_equals_single_view_calls(per_view):
     """gi_batch_set_surrogate: far hits of every view routed to one trusted network, the probe pass
-    per view through the network's answers; bit for bit what the single-view calls give (update
-    with routing, resolve, gi_nrc_query_frame, gi_probes_integrate_nrc, interpolation)."""
+    per view through the network's answers; gi_batch_set_view_surrogates: two networks and two
+    views without one (their plain probe pass).  Bit for bit what the single-view calls give
+    (update with routing, resolve, gi_nrc_query_frame, gi_probes_integrate_nrc or
+    gi_probes_integrate, interpolation)."""
     from test_gpu_surrogate import _nrc, _spec, _trust_as_is
 
     data = _views_and_frames(2)
@@ -151,15 +154,21 @@ def test_surrogate_batch_equals_single_view_calls():
     hitpos = allrec[0:3, np.isfinite(allrec[9])]
     spec = _spec(aabb=(tuple(hitpos.min(axis=1) - 1.0), tuple(hitpos.max(axis=1) + 1.0)))
     n_max = max(frs[0].n_records for _, frs in data)
-    nrc = _nrc(spec, batch=1024, max_records=n_max, max_queries=n_max, trust=1e30, query_lod=2)
+    nets = [_nrc(spec, batch=1024, max_records=n_max, max_queries=n_max, trust=1e30, query_lod=2)
+            for _ in range(2 if per_view else 1)]
+    nrcs = [nets[0], None, nets[1], None, nets[1]] if per_view else [nets[0]] * len(data)
     bp = BatchPipeline([(c["width"], c["height"], 16) for c, _ in data], 64)
     singles = [Pipeline(c["width"], c["height"], 64, 16) for c, _ in data]
     try:
-        gi.gi_nrc_set_params(nrc, *wl.surrogate_inputs.params(11, spec.log2_table))
-        _trust_as_is(nrc, spec)
-        bp.set_surrogate(nrc, far_lod=2)
-        for sp in singles:
-            gi.gi_cache_route_far(sp.cache, nrc, 2)
+        for j, nrc in enumerate(nets):
+            gi.gi_nrc_set_params(nrc, *wl.surrogate_inputs.params(11 + j, spec.log2_table))
+            _trust_as_is(nrc, spec)
+        if per_view:
+            bp.set_view_surrogates(nrcs, far_lod=2)
+        else:
+            bp.set_surrogate(nets[0], far_lod=2)
+        for sp, nrc in zip(singles, nrcs):
+            gi.gi_cache_route_far(sp.cache, nrc, 2 if nrc else 4)
         routed = 0
         for f in range(2):
             gbufs = [dev(frs[f].gbuffer) for _, frs in data]
@@ -170,9 +179,12 @@ def test_surrogate_batch_equals_single_view_calls():
                 sp.spawn(gbufs[v], views[v])
                 sp.update(recs[v], views[v])
                 sp.resolve(f)
-                gi.gi_nrc_query_frame(nrc, sp.cache, gi.hits_from_planes(recs[v], sp.n_records), sp.slot_ids,
-                                      views[v])
-                gi.gi_probes_integrate_nrc(sp.cache, nrc, sp.probes.struct, sp.slot_ids, 64)
+                if nrcs[v] is None:
+                    sp.integrate()
+                else:
+                    gi.gi_nrc_query_frame(nrcs[v], sp.cache, gi.hits_from_planes(recs[v], sp.n_records), sp.slot_ids,
+                                          views[v])
+                    gi.gi_probes_integrate_nrc(sp.cache, nrcs[v], sp.probes.struct, sp.slot_ids, 64)
                 sp.interpolate(gbufs[v], views[v])
             torch.cuda.synchronize()
             for v, sp in enumerate(singles):
@@ -192,4 +204,5 @@ def test_surrogate_batch_equals_single_view_calls():
         bp.close()
         for sp in singles:
             sp.close()
-        gi.gi_nrc_destroy(nrc)
+        for nrc in nets:
+            gi.gi_nrc_destroy(nrc)
