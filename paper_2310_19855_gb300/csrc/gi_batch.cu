@@ -12,8 +12,8 @@
 // per view, or none), the update keeps the far-hit routing of the caches that route to their
 // view's surrogate, and the probe-irradiance pass becomes, per view, the surrogate's query frame
 // and the probe pass with its answers (gi_nrc_query_frame, gi_probes_integrate_nrc; a network's
-// answer buffers hold one view's records at a time), or the plain probe pass of a view without
-// one.  That form runs without the graph.
+// answer buffers hold one view's records at a time), after one batched probe pass over the views
+// without one.  That form runs without the graph.
 #include <string.h>
 
 #include <algorithm>
@@ -143,21 +143,20 @@ static gi_status enqueue_frame(gi_batch_s *b, int set, const std::vector<uint32_
         s = launch_resolve_batched(reinterpret_cast<const ResolveArgs *>(d + L.res),
                                    reinterpret_cast<const uint32_t *>(d + L.pre[kPassResolve]), n,
                                    blocks[kPassResolve], st);
+    // the views without a surrogate (all of them in the plain form): one launch; a view with one
+    // has no blocks in that pass and takes its own query frame and probe pass after it
+    if (s == GI_OK)
+        s = launch_integrate_batched(reinterpret_cast<const IntegrateArgs *>(d + L.integ),
+                                     reinterpret_cast<const uint32_t *>(d + L.pre[kPassIntegrate]), n,
+                                     blocks[kPassIntegrate], b->tuning.integrate_threads, b->rpp, st);
     if (s == GI_OK && b->surr && views) {
         for (uint32_t v = 0; v < n && s == GI_OK; ++v) {
             const gi_batch_view &bv = views[v];
             const gi_nrc_t nrc = b->nrcs[v];
-            if (!nrc) {
-                s = gi_probes_integrate(bv.cache, &bv.probes, bv.slot_ids, b->rpp, bv.env, st);
-                continue;
-            }
+            if (!nrc) continue;
             s = gi_nrc_query_frame(nrc, bv.cache, &bv.hits, bv.slot_ids, &bv.view, st);
             if (s == GI_OK) s = gi_probes_integrate_nrc(bv.cache, nrc, &bv.probes, bv.slot_ids, b->rpp, bv.env, st);
         }
-    } else if (s == GI_OK) {
-        s = launch_integrate_batched(reinterpret_cast<const IntegrateArgs *>(d + L.integ),
-                                     reinterpret_cast<const uint32_t *>(d + L.pre[kPassIntegrate]), n,
-                                     blocks[kPassIntegrate], b->tuning.integrate_threads, b->rpp, st);
     }
     if (s == GI_OK)
         s = launch_interpolate_batched(reinterpret_cast<const InterpArgs *>(d + L.interp),
@@ -304,7 +303,9 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
             ((tx + 15) / 16) * ((ty + 15) / 16),
             update_blocks_for(bv.hits.n, b->tuning.update_records_per_block),
             std::max<uint32_t>(1u, (uint32_t)((double)res_total * (double)bv.hits.n / (double)std::max(1ull, total_records))),
-            (bv.probes.layout.num_probes * 4u + b->tuning.integrate_threads - 1u) / b->tuning.integrate_threads,
+            b->nrcs[v] ? 0u
+                       : (bv.probes.layout.num_probes * 4u + b->tuning.integrate_threads - 1u) /
+                             b->tuning.integrate_threads,
             interp_grid_x(bv.view.width) * interp_grid_y(bv.view.height)};
         for (int k = 0; k < 5; ++k) pre[k][v + 1] = pre[k][v] + cnt[k];
         // far hits go to the surrogate only where the cache routes them to the batch's surrogate
