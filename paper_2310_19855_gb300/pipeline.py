@@ -156,6 +156,8 @@ class BatchPipeline:
         """View v's probe pass through the surrogate nrcs[v] (None: that view's plain probe pass;
         nrcs None: the plain form); far_lod < 4 also routes view v's hits of that LOD and above to
         nrcs[v] (gi_cache_route_far)."""
+        if nrcs is not None and len(nrcs) != len(self.views):
+            raise ValueError(f"set_view_surrogates: {len(nrcs)} networks for {len(self.views)} views")
         for v, st in enumerate(self.views):
             nrc = None if nrcs is None else nrcs[v]
             gi_cache_route_far(st["cache"], nrc if far_lod < 4 else None, far_lod)
