@@ -308,7 +308,7 @@ gi_status gi_batch_frame(gi_batch_t b, const gi_batch_view *views, uint32_t use_
                              b->tuning.integrate_threads,
             interp_grid_x(bv.view.width) * interp_grid_y(bv.view.height)};
         for (int k = 0; k < 5; ++k) pre[k][v + 1] = pre[k][v] + cnt[k];
-        // far hits go to the surrogate only where the cache routes them to the batch's surrogate
+        // far hits go to a surrogate only where the view's cache routes them to the view's surrogate
         reinterpret_cast<UpdateArgs *>(h + L.upd)[v] = cache_update_args(bv.cache, &bv.hits, &bv.view, bv.slot_ids);
         reinterpret_cast<ResolveArgs *>(h + L.res)[v] = cache_resolve_args(bv.cache, bv.resolve_frame);
         reinterpret_cast<SpawnArgs *>(h + L.spawn)[v] = spawn_args(&bv.gbuf, &bv.view, &bv.probes);
