@@ -705,10 +705,12 @@ gi_status gi_batch_set_surrogate(gi_batch_t b, gi_nrc_t nrc);
  * One surrogate per view (no counterpart in the paper), for views of different scenes, which one
  * network cannot share: nrcs is a host array of the batch's n_views handles (an entry may be NULL),
  * read during the call.  The probe pass of the views whose entry is NULL stays one launch over
- * them; then, view after view, each view v with a network takes gi_nrc_query_frame and
- * gi_probes_integrate_nrc with nrcs[v]; the results are those of the single-view calls.  The
- * other passes stay one launch over all views, and the form runs without the CUDA graph while
- * any entry is set.  nrcs NULL restores
+ * them; each view v with a network takes gi_nrc_query_frame and gi_probes_integrate_nrc with
+ * nrcs[v] on one of the batch's four internal streams, forked from `stream` after the resolve and
+ * joined back before the interpolation: distinct networks run side by side, the views of one
+ * network in view order on one stream (its answer buffers hold one view at a time).  The results
+ * are those of the single-view calls.  The other passes stay one launch over all views, and the
+ * form runs without the CUDA graph while any entry is set.  nrcs NULL restores
  * the plain form.  gi_batch_frame rejects a view whose cache routes far hits to a network other
  * than nrcs[v].  gi_batch_set_surrogate(b, nrc) is this call with every entry nrc.  Each network
  * must outlive its use.  Host only.  Errors: GI_ERR_INVALID_ARG for a NULL batch.

@@ -12,8 +12,8 @@
 // per view, or none), the update keeps the far-hit routing of the caches that route to their
 // view's surrogate, and the probe-irradiance pass becomes, per view, the surrogate's query frame
 // and the probe pass with its answers (gi_nrc_query_frame, gi_probes_integrate_nrc; a network's
-// answer buffers hold one view's records at a time), after one batched probe pass over the views
-// without one.  That form runs without the graph.
+// answer buffers hold one view's records at a time), on side streams beside one batched probe
+// pass over the views without one.  That form runs without the graph.
 #include <string.h>
 
 #include <algorithm>
@@ -65,6 +65,10 @@ struct gi_batch_s {
     uint64_t frames;
     std::vector<gi_nrc_t> nrcs;    // surrogate of each view's probe pass, or NULL
     bool surr;                     // some view has one: the probe pass runs per view
+    // streams of the surrogate views' probe passes: distinct networks run side by side (a
+    // network's answer buffers hold one view at a time, so views that share one share a stream)
+    cudaStream_t side[4];
+    cudaEvent_t fork, join[4];
 };
 
 namespace gi {
@@ -91,6 +95,11 @@ static void free_batch(gi_batch_s *b) {
         if (b->used[k]) cudaEventDestroy(b->used[k]);
     }
     if (b->capture) cudaStreamDestroy(b->capture);
+    for (int k = 0; k < 4; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 
@@ -143,19 +152,44 @@ static gi_status enqueue_frame(gi_batch_s *b, int set, const std::vector<uint32_
         s = launch_resolve_batched(reinterpret_cast<const ResolveArgs *>(d + L.res),
                                    reinterpret_cast<const uint32_t *>(d + L.pre[kPassResolve]), n,
                                    blocks[kPassResolve], st);
-    // the views without a surrogate (all of them in the plain form): one launch; a view with one
-    // has no blocks in that pass and takes its own query frame and probe pass after it
+    // the views with a surrogate: query frame and probe pass with its answers, per view, on the
+    // side streams (from the resolve on), beside one launch over the views without one (all of
+    // them in the plain form; a view with a surrogate has no blocks in it)
+    const bool per_view = s == GI_OK && b->surr && views;
+    gi_nrc_t owner[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (per_view) s = cuda_status(cudaEventRecord(b->fork, st), "fork record");
     if (s == GI_OK)
         s = launch_integrate_batched(reinterpret_cast<const IntegrateArgs *>(d + L.integ),
                                      reinterpret_cast<const uint32_t *>(d + L.pre[kPassIntegrate]), n,
                                      blocks[kPassIntegrate], b->tuning.integrate_threads, b->rpp, st);
-    if (s == GI_OK && b->surr && views) {
+    if (per_view) {
+        int used = 0;
         for (uint32_t v = 0; v < n && s == GI_OK; ++v) {
             const gi_batch_view &bv = views[v];
             const gi_nrc_t nrc = b->nrcs[v];
             if (!nrc) continue;
-            s = gi_nrc_query_frame(nrc, bv.cache, &bv.hits, bv.slot_ids, &bv.view, st);
-            if (s == GI_OK) s = gi_probes_integrate_nrc(bv.cache, nrc, &bv.probes, bv.slot_ids, b->rpp, bv.env, st);
+            // the stream of this network: the one it already has, else the next (round robin)
+            int k = 0;
+            while (k < used && owner[k] != nrc) ++k;
+            if (k == used) {
+                if (used < 4) {
+                    owner[used++] = nrc;
+                    s = cuda_status(cudaStreamWaitEvent(b->side[k], b->fork, 0), "side stream wait");
+                } else {
+                    // more than four networks: the others share the streams, each network always
+                    // on the same one (every side stream has waited for the fork by now)
+                    k = (int)(((uintptr_t)nrc >> 6) % 4u);
+                }
+            }
+            cudaStream_t ss = b->side[k];
+            if (s == GI_OK) s = gi_nrc_query_frame(nrc, bv.cache, &bv.hits, bv.slot_ids, &bv.view, ss);
+            if (s == GI_OK) s = gi_probes_integrate_nrc(bv.cache, nrc, &bv.probes, bv.slot_ids, b->rpp, bv.env, ss);
+        }
+        // the frame's later work waits for every side stream, also after an error above
+        for (int k = 0; k < used; ++k) {
+            gi_status sj = cuda_status(cudaEventRecord(b->join[k], b->side[k]), "join record");
+            if (sj == GI_OK) sj = cuda_status(cudaStreamWaitEvent(st, b->join[k], 0), "join wait");
+            if (s == GI_OK) s = sj;
         }
     }
     if (s == GI_OK)
@@ -199,6 +233,11 @@ gi_status gi_batch_create(uint32_t n_views, uint32_t rays_per_probe, const gi_ba
         if (s == GI_OK) s = cuda_status(cudaEventCreateWithFlags(&b->used[k], cudaEventDisableTiming), "event");
     }
     if (s == GI_OK) s = cuda_status(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
+    for (int k = 0; k < 4 && s == GI_OK; ++k) {
+        s = cuda_status(cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking), "surrogate stream");
+        if (s == GI_OK) s = cuda_status(cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming), "event");
+    }
+    if (s == GI_OK) s = cuda_status(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "event");
     if (s == GI_OK) s = ensure_moments();
     if (s != GI_OK) {
         free_batch(b);
