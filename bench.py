@@ -1167,6 +1167,20 @@ def run_batched(args, rank, world, local_rank):
     return line
 
 
+def lr_step(gi, nrcs, lr0, i, total):
+    """Adam's step size of the online training at step i of `total`: lr0 over the first half, a
+    quarter of it over the third quarter, a sixteenth over the last (gi_nrc_set_learning_rate).
+    Used by the blocks that train for 2048 steps (configuration 3's per-view networks, 4-far: 0.9 %
+    and 4.1 % error on the routed hits against 2.9 % and 6.7 % at a constant step size); the
+    Cornell block's 128 setup frames keep the configuration's step size (6.3 % with this schedule
+    against 4.3 % without)."""
+    if total >= 4 and i in (total // 2, (3 * total) // 4):
+        lr = lr0 / (4.0 if i == total // 2 else 16.0)
+        for nrc in nrcs:
+            if nrc is not None:
+                gi.gi_nrc_set_learning_rate(nrc, lr)
+
+
 def batched_surrogate(args, gi, torch, BatchPipeline, specs, frames, recs, gbufs, gviews, bp, counter, F, V, timed,
                       stream):
     """The surrogate-plus-batched form on the same 16 views: each view its own network (configuration
@@ -1203,6 +1217,7 @@ def batched_surrogate(args, gi, torch, BatchPipeline, specs, frames, recs, gbufs
 
 def _batched_surrogate_run(args, gi, torch, BatchPipeline, specs, frames, recs, gbufs, gviews, bp, counter, F, V,
                            timed, stream, nets, rounds):
+    import workload as wl
     bs = BatchPipeline([(cfg["width"], cfg["height"], cfg["log2_slots"]) for cfg, _ in specs], 64)
     scount = [0]
     tcount = [0]
@@ -1243,7 +1258,8 @@ def _batched_surrogate_run(args, gi, torch, BatchPipeline, specs, frames, recs, 
         active = [nets[v] if np.any(st["slot_ids"].cpu().numpy().view(np.uint32) == gi.GI_SLOT_FAR) else None
                   for v, st in enumerate(bs.views)]
         bs.set_view_surrogates(active, far_lod=2)
-        for _ in range(rounds - first):
+        for r in range(first, rounds):
+            lr_step(gi, active, float(wl.CONFIGS[4]["nrc_lr"]), r, rounds)
             plain_frame()
             train_round()
         torch.cuda.synchronize()
@@ -1607,6 +1623,7 @@ def run_far_routing(args, rank, world, local_rank):
 
         setup = FAR_SETUP_FRAMES if args.setup_frames is None else max(1, args.setup_frames)
         for i in range(setup):
+            lr_step(gi, [nrc], float(cfg4["nrc_lr"]), i, setup)
             plain(i)
             train(i)
         gi.gi_cache_route_far(pr.cache, nrc, 2)

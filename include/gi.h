@@ -635,6 +635,14 @@ gi_status gi_nrc_backward(gi_nrc_t nrc, const gi_points *pts, const float *const
 gi_status gi_nrc_adam(gi_nrc_t nrc, gi_stream_t stream);
 
 /*
+ * Adam's step size (cfg.lr) for the Adam steps enqueued after the call, gi_nrc_adam's and
+ * gi_nrc_train_frame's, so that a caller can lower it as training goes on (no counterpart in the
+ * paper, which has no learned part).  Host only, no synchronisation.  Errors: GI_ERR_INVALID_ARG
+ * for a NULL surrogate or a step size that is not finite and > 0.
+ */
+gi_status gi_nrc_set_learning_rate(gi_nrc_t nrc, float lr);
+
+/*
  * Training on a view's resolved cells (call after gi_cache_resolve of the frame): sample
  * k < cfg.batch is record pcg(k ^ pcg(frame + 1)) mod hits->n (PCG hash: one LCG step with
  * multiplier 747796405 and increment 2891336453, then the RXS-M-XS output permutation); its

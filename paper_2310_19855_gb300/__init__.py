@@ -200,6 +200,7 @@ def lib() -> ctypes.CDLL:
             "gi_nrc_backward": (ctypes.c_int, [c_vp, ctypes.POINTER(gi_points), ctypes.POINTER(c_vp), c_vp, c_u32,
                                                c_vp]),
             "gi_nrc_adam": (ctypes.c_int, [c_vp, c_vp]),
+            "gi_nrc_set_learning_rate": (ctypes.c_int, [c_vp, c_f32]),
             "gi_nrc_train_frame": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(gi_hits), c_vp, c_u32, c_vp]),
             "gi_nrc_query_frame": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(gi_hits), c_vp,
                                                   ctypes.POINTER(gi_view), c_vp]),
@@ -587,6 +588,10 @@ def gi_nrc_backward(nrc: int, pts: gi_points, target_planes, mask=None, batch_no
 
 def gi_nrc_adam(nrc: int, stream=None) -> None:
     check(lib().gi_nrc_adam(nrc, _stream(stream)), "gi_nrc_adam")
+
+
+def gi_nrc_set_learning_rate(nrc: int, lr: float) -> None:
+    check(lib().gi_nrc_set_learning_rate(nrc, float(lr)), "gi_nrc_set_learning_rate")
 
 
 def gi_nrc_train_frame(nrc: int, cache: int, hits: gi_hits, slot_ids, frame: int, stream=None) -> None:

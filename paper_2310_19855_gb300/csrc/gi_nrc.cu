@@ -1299,6 +1299,15 @@ gi_status gi_nrc_backward(gi_nrc_t nrc, const gi_points *pts, const float *const
     return st;
 }
 
+gi_status gi_nrc_set_learning_rate(gi_nrc_t nrc, float lr) {
+    if (!nrc || !(lr > 0.0f) || !std::isfinite(lr)) {
+        set_error("gi_nrc_set_learning_rate: NULL surrogate or step size not finite and > 0");
+        return GI_ERR_INVALID_ARG;
+    }
+    nrc->cfg.lr = lr;
+    return GI_OK;
+}
+
 gi_status gi_nrc_adam(gi_nrc_t nrc, gi_stream_t stream) {
     if (!nrc) {
         set_error("gi_nrc_adam: NULL surrogate");

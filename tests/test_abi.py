@@ -151,4 +151,5 @@ def test_surrogate_arguments_are_rejected_on_the_host(lib):
     assert lib.gi_nrc_stats(None, None, None) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_batch_set_surrogate(None, None) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_batch_set_view_surrogates(None, None) == gi.GI_ERR_INVALID_ARG
+    assert lib.gi_nrc_set_learning_rate(None, 1e-3) == gi.GI_ERR_INVALID_ARG
     assert lib.gi_nrc_destroy(None) == gi.GI_OK
