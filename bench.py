@@ -1333,7 +1333,9 @@ def _batched_surrogate_run(args, gi, torch, BatchPipeline, specs, frames, recs, 
         "irradiance_rel_l1_vs_plain_batch": i_num / i_den if i_den > 0 else None,
         "judged_error_max_over_views": max(judged),
         "training_rounds": rounds, "setup_s": setup_s,
-        "gpu_launches_per_frame": 6 + 4 * V,
+        # six batched passes, and per view with a network its query frame (selection, encoding,
+        # network) and its probe pass with answers
+        "gpu_launches_per_frame": 6 + 4 * sum(nrc is not None for nrc in active),
     }
 
 
